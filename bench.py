@@ -1,0 +1,332 @@
+"""Benchmark of the leapfrog hot path (GLUPS, HBM roofline fraction).
+
+One bench step = one pass of the whole forward hot path over the 8192^2 point-singularity
+workload: mollified face depth (tsu_make_depth), Taylor start (tsu_init), 4999 leapfrog steps
+with the discrete energy of every step fused in (tsu_step_n), and the final energy (tsu_observe):
+5000 steps of (N-2)^2 interior lattice-point updates.  Inputs live in HBM before the timed
+region; the four fields (4 x 256 MiB) exceed the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one problem per rank, weak scaling; the path has no
+exchange step).  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s (GLUPS) and HBM roofline %; adjoint/forward time ratio"
+UNIT = "GLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tsu", choices=["tsu", "reference"])
+    ap.add_argument("--n", type=int, default=8192, help="grid nodes per side (default: the 8192^2 workload)")
+    ap.add_argument("--nsteps", type=int, default=5000, help="leapfrog steps per bench step")
+    ap.add_argument("--form", default="increment", choices=["increment", "standard"])
+    ap.add_argument("--rows", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch (from profiles/)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except Exception:
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        os.unlink(self.path)
+        return out
+
+
+# -----------------------------------------------------------------------------------------------
+# CPU oracle leg (the reference arm of this build and the cpu_baseline object)
+# -----------------------------------------------------------------------------------------------
+def oracle_sample(n: int, steps_sample: int):
+    """Time the FP64 oracle, as it stands, on the workload's full grid for a few steps."""
+    import oracle
+    from paper_2005_11931_gb300 import inputs
+
+    cores = len(os.sched_getaffinity(0))
+    threads = oracle.set_threads(cores)
+    p = inputs.point_fp32(n)
+    g = oracle.grid(n, n)
+    u0 = p.initial()
+    t0 = time.perf_counter()
+    hx, hy, ext = oracle.make_depth(g, p.depth)
+    tau = inputs.CFL * g.dx / max(ext[1], ext[3]) ** 0.5
+    oracle.forward(g, tau, hx, hy, u0, None, steps_sample, want_energy=True)
+    dt = time.perf_counter() - t0
+    lups = (n - 2) ** 2 * steps_sample
+    return dict(value=lups / dt / 1e9, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"FP64 oracle, {n}x{n} point workload, depth + Taylor start + {steps_sample - 1} "
+                       f"leapfrog steps with energy every step ({steps_sample} steps of {(n - 2) ** 2} "
+                       f"interior updates), {threads} OpenMP threads", seconds=dt)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # bounded sample: a few steps of the full grid per bench step
+    steps_sample = 4 if args.n >= 4096 else 16
+    for _ in range(args.warmup):
+        oracle_sample(args.n, 2)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(args.n, steps_sample)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"point_fp32_{args.n} sample", "n": args.n, "leapfrog_steps": steps_sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -----------------------------------------------------------------------------------------------
+# GPU leg
+# -----------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2005_11931_gb300 import inputs, tsu
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    form = tsu.TSU_FORM_INCREMENT if args.form == "increment" else tsu.TSU_FORM_STANDARD
+    p = inputs.point_fp32(args.n, args.nsteps)
+    S = p.steps
+    g = tsu.grid(p.n)
+    code = tsu.TSU_F32
+
+    # device-resident inputs and buffers
+    hx = tsu.empty_field(g, code, dev)
+    hy = tsu.empty_field(g, code, dev)
+    ext_dev = torch.zeros(4, dtype=torch.float64, device=dev)
+    u0 = torch.from_numpy(p.initial(g.ld, np.float32)).to(dev)
+    nb = 3 if form == tsu.TSU_FORM_INCREMENT else 2
+    bufs = [tsu.empty_field(g, code, dev) for _ in range(nb)]
+    st = tsu.State()
+    ws_bytes = tsu.tsu_step_workspace(g, code)
+    ws = torch.zeros(ws_bytes, dtype=torch.uint8, device=dev)
+    energy = torch.zeros(S, dtype=torch.float64, device=dev)
+    ext = tsu.tsu_make_depth(g, p.depth, code, hx, hy, ext_dev, sync=True)
+    tau = inputs.CFL * g.dx / float(np.sqrt(max(ext[1], ext[3])))
+    med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
+    opts = tsu.StepOpts()
+    opts.energy = energy.data_ptr()
+    opts.kernel, opts.rows = args.kernel, args.rows
+    ev_k0 = torch.cuda.Event(enable_timing=True)
+    ev_k1 = torch.cuda.Event(enable_timing=True)
+    kernel_ms = []
+
+    def one_step(u0_dev, timed_kernel=False):
+        for k, b in enumerate(bufs):
+            st.buf[k] = b.data_ptr()
+        st.form = form
+        tsu.tsu_make_depth(g, p.depth, code, hx, hy, ext_dev, sync=False, stream=stream)
+        tsu.tsu_init(g, code, tau, med, u0_dev, None, st, stream)
+        if timed_kernel:
+            ev_k0.record(stream)
+        tsu.tsu_step_n(g, code, tau, med, st, S - 1, opts, ws, ws_bytes, stream)
+        if timed_kernel:
+            ev_k1.record(stream)
+        o_e = energy[S - 1:]
+        tsu.tsu_observe(g, code, tau, med, st, o_e, None, None, ws, ws_bytes, stream)
+
+    launches_per_step = 3 + 1 + (S - 1) + 1  # depth (reset, eval, decode), init, leapfrog, observe
+
+    for _ in range(args.warmup):
+        one_step(u0)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            one_step(u0, timed_kernel=True)
+            ev_k1.synchronize()
+            kernel_ms.append(ev_k0.elapsed_time(ev_k1))
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    lups_step = (p.n - 2) ** 2 * S
+    value = world * lups_step * args.steps / (ms / 1e3) / 1e9
+    # roofline of the dominant kernel (the leapfrog pass)
+    bpl = 24 if form == tsu.TSU_FORM_INCREMENT else 20  # algorithmic bytes per interior update
+    launch_ms = sum(kernel_ms) / (len(kernel_ms) * (S - 1))
+    achieved = bpl * (p.n - 2) ** 2 / (launch_ms / 1e3) / 1e9
+    peak, peak_kind = load_peaks()
+    e_final = energy.cpu().numpy()
+    drift = float(np.max(np.abs(e_final - e_final[0])) / e_final[0])
+
+    # end to end through the C ABI with host buffers: H2D of u0, full run, D2H of u^S and energy
+    e2e = None
+    if not args.no_e2e:
+        u0_host = torch.from_numpy(p.initial(g.ld, np.float32)).pin_memory()
+        u_host = torch.empty_like(u0_host).pin_memory()
+        e_host = torch.empty(S, dtype=torch.float64).pin_memory()
+        u0_stage = torch.empty_like(u0)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 3))
+        a0.record(stream)
+        for _ in range(reps):
+            u0_stage.copy_(u0_host, non_blocking=True)
+            one_step(u0_stage)
+            u_host.copy_(bufs[st.cur], non_blocking=True)
+            e_host.copy_(energy, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * lups_step * reps / (ems / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(u0_host.numel() * 4),
+               "d2h_bytes_per_step": int(u_host.numel() * 4 + e_host.numel() * 8)}
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        r = oracle_sample(p.n, 4 if p.n >= 4096 else 16)
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"point_fp32_{p.n}: {p.n}x{p.n} grid, depth 0.5 + 0.01 phi_eps(|r-(0.5,0.5)|), "
+                               f"eps = 4dx, Gaussian hump width 0.02 at (0.3,0.5), {S} steps, "
+                               f"{'increment' if form else 'standard'} form, energy every step",
+                   "n": p.n, "leapfrog_steps": S, "form": args.form, "tau": tau,
+                   "l2": "inputs larger than L2 (four 256 MiB fields), no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": args.traffic, "peak_kind": peak_kind, "bytes_per_update": bpl,
+                     "kernel": "k_leapfrog", "launch_ms": launch_ms},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": launches_per_step * args.steps,
+        "energy_drift": drift,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * tsu.h -- C ABI of libtsu, a GB300 (sm_103a) explicit leapfrog stepper for the
+ * regularised 2D tsunami wave equation of
+ *   "Tsunami propagation for singular topographies" (arXiv:2005.11931):
+ *
+ *     u_tt = d_x(h_x d_x u) + d_y(h_y d_y u)        Sec. 2, eq. (2.1) (vector depth)
+ *     u(0) = u0, u_t(0) = u1                        Cauchy data, eq. (2.1)
+ *     u = 0 on the edges of the box [0,1]^2          Sec. 3.3 (2D boundary value problem)
+ *     h_eps = h * psi_eps, psi_eps = eps^-d psi(./eps)  Sec. 2.1 (regularisation), Sec. 3.1
+ *
+ * Discretisation (the library's definition of every result):
+ *   grid     x_i = i dx, y_j = j dy, i < nx, j < ny (boundary nodes included), Sec. 3.3 grid omega.
+ *   faces    hx[j][i] = h_eps(x_i + dx/2, y_j), i <= nx-2;  hy[j][i] = h_eps(x_i, y_j + dy/2), j <= ny-2.
+ *   operator B u = cx [hx_ij (u_i+1 - u_i) - hx_i-1,j (u_i - u_i-1)]
+ *                + cy [hy_ij (u_j+1 - u_j) - hy_i,j-1 (u_j - u_j-1)],  cx = tau^2/dx^2, cy = tau^2/dy^2
+ *            (B = tau^2 L_h, the conservative 5-point form of eq. (2.1)'s spatial part).
+ *   start    u^1 = u^0 + tau u1 + B u^0 / 2              (Taylor start; the start counts as step 1)
+ *   leapfrog u^{n+1} = 2 u^n - u^{n-1} + B u^n            (interior nodes; edges stay 0)
+ *   energy   E^{n+1/2} = dxdy/(2 tau^2) sum_nodes [(u^{n+1}-u^n)^2 - (B u^{n+1}) u^n],
+ *            the leapfrog analogue of the conservation law (CL-01) in Theorem 2.1; it equals
+ *            1/2 sum ((u^{n+1}-u^n)/tau)^2 dxdy + 1/2 sum_faces h (D u^{n+1})(D u^n) dxdy.
+ *
+ * Memory layout: every field is row-major, x fastest, a[j*ld + i], ny rows of ld elements,
+ * ld >= nx and ld a multiple of 4; every pointer 16-byte aligned.  Entries with i >= nx
+ * (padding) are read and written as 0; the caller allocates them.
+ *
+ * Ownership: the caller owns every buffer (host or device, as stated per argument).  The
+ * library keeps no pointer after a call returns and allocates no device memory: scratch is
+ * the caller's workspace (sizes from tsu_*_workspace).  Work is enqueued on the caller's
+ * stream (a cudaStream_t passed as void*; NULL is the legacy default stream) and is
+ * asynchronous unless an argument says the call synchronises.
+ *
+ * Errors: every entry point returns a tsu_status.  On failure nothing is enqueued (argument
+ * errors) or the CUDA error is reported (TSU_ECUDA); tsu_last_error() gives a message for the
+ * calling thread.
+ */
+#ifndef TSU_H
+#define TSU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TSU_OK = 0,
+  TSU_EINVAL = 1,   /* null pointer, nx or ny < 3, ld < nx, ld % 4 != 0, misaligned pointer, bad enum */
+  TSU_ECFL = 2,     /* tau^2 (hx_max/dx^2 + hy_max/dy^2) > 1: outside the leapfrog stability bound */
+  TSU_ENONPOS = 3,  /* min face depth <= 0: the positivity 0 < c0 <= h_j of Sec. 2 fails */
+  TSU_ENOMEM = 4,   /* caller workspace smaller than tsu_*_workspace reports */
+  TSU_ECUDA = 5,    /* a CUDA runtime error (message in tsu_last_error) */
+  TSU_ETIMEOUT = 6  /* a bounded device-side wait expired */
+} tsu_status;
+
+enum { TSU_F32 = 0, TSU_F64 = 1 };                      /* element type of u, hx, hy, traces */
+enum { TSU_FORM_STANDARD = 0, TSU_FORM_INCREMENT = 1 }; /* see tsu_state */
+enum { TSU_LINE_X = 0, TSU_LINE_Y = 1, TSU_POINT = 2, TSU_STEP_X = 3, TSU_STEP_Y = 4 };
+enum { TSU_GAUSS = 0, TSU_FRIEDRICHS = 1 };
+
+/* Unit-box grid: nx x ny nodes including the boundary; dx = 1/(nx-1), dy = 1/(ny-1) are
+ * passed explicitly so callers may scale the box. */
+typedef struct {
+  int32_t nx, ny;
+  int64_t ld; /* row pitch in elements */
+  double dx, dy;
+} tsu_grid;
+
+/* One singularity of the depth (Sec. 3.1, Cases 1-3; Sec. 3.3):
+ *   TSU_LINE_X  amp * phi_eps(x - cx)^power      (a line delta across the box, h varies in x)
+ *   TSU_LINE_Y  amp * phi_eps(y - cy)^power
+ *   TSU_POINT   amp * phi2_eps(|(x,y) - (cx,cy)|)^power   (2D mollifier, eps^-2 scaling)
+ *   TSU_STEP_X  amp * Phi_eps(cx - x)             (mollified jump: amp for x < cx, 0 after)
+ *   TSU_STEP_Y  amp * Phi_eps(cy - y)
+ * power 1 is the delta, power 2 the delta^2 of Case 3 (phi_eps^2). */
+typedef struct {
+  int32_t kind, power;
+  double amp, cx, cy;
+} tsu_sing;
+
+/* Depth h_eps = background + sum of singularities, regularised at width eps with
+ *   TSU_GAUSS       phi_eps(s) = exp(-s^2/eps^2)/(eps sqrt(pi)), phi2_eps(r) = exp(-r^2/eps^2)/(pi eps^2)
+ *   TSU_FRIEDRICHS  phi_eps(s) = c1/eps bump(s/eps), phi2_eps(r) = c2/eps^2 bump(r/eps),
+ *                   bump(t) = exp(1/(t^2-1)) on |t| < 1 (Sec. 3.1, c1 ~ 2.2523). */
+typedef struct {
+  double background, eps;
+  int32_t mollifier, nsing;
+  const tsu_sing* sing; /* host array [nsing] */
+} tsu_depth;
+
+/* The medium as the steppers see it: device face arrays (element type = dtype) and the
+ * face maxima returned by tsu_make_depth, used for the CFL check. */
+typedef struct {
+  const void* hx;
+  const void* hy;
+  double hx_max, hy_max;
+} tsu_medium;
+
+/* Time-stepping state (device buffers of ny*ld elements, owned by the caller).
+ *   TSU_FORM_STANDARD : buf[cur] = u^n, buf[cur^1] = u^{n-1}; a step writes u^{n+1} over u^{n-1}.
+ *   TSU_FORM_INCREMENT: buf[cur] = u^n, buf[2] = v^n = u^n - u^{n-1}; a step writes
+ *                       v^{n+1} = v^n + B u^n in place and u^{n+1} = u^n + v^{n+1} into buf[cur^1].
+ *                       Same scheme, rounded differently: it keeps FP32 fields accurate when the
+ *                       per-step change is far below one ulp of u.
+ * step = n.  cur and step are updated on the host when work is enqueued. */
+typedef struct {
+  void* buf[3];
+  int32_t cur;
+  int32_t form;
+  int64_t step;
+} tsu_state;
+
+/* Optional outputs and tuning of tsu_step_n (pass NULL for none / defaults).  For a call that
+ * starts at step s and makes nsteps steps, step k (k = 0..nsteps-1) reads the pair (u^{s+k-1},
+ * u^{s+k}) and produces u^{s+k+1}; on the way it records
+ *   energy[k]          = E^{s+k-1/2}                      (device double [nsteps])
+ *   traces[k*nrec + r] = u^{s+k}[rec_idx[r]]              (device, element type = dtype)
+ * and, when (s+k-1) % ckpt_every == 0, copies the state (both fields of the form) into slot
+ * (s+k-1)/ckpt_every of ckpt (device, [slots][2][ny][ld]); slots beyond ckpt_slots are skipped.
+ * The final pair's energy and traces come from tsu_observe. */
+typedef struct {
+  double* energy;
+  int32_t nrec;
+  const int64_t* rec_idx; /* device [nrec], flat node indices j*ld + i */
+  void* traces;
+  void* ckpt;
+  int64_t ckpt_every, ckpt_slots;
+  int32_t kernel;   /* 0 auto, 1 register-streaming, 2 TMA-pipelined, 3 temporally blocked */
+  int32_t rows;     /* rows per CTA (0 = auto) */
+  int32_t tdepth;   /* steps per HBM pass for kernel 3 (0 = auto) */
+  int32_t reserved;
+} tsu_step_opts;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int tsu_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* tsu_last_error(void);
+
+/* Face coefficients of the regularised depth (Sec. 2.1 h_eps = h * psi_eps; Sec. 3.1 mollifier).
+ *   g        grid; d  depth descriptor (host); dtype TSU_F32/TSU_F64 of hx, hy.
+ *   hx, hy   device [ny][ld], written completely (unused faces and padding = 0).
+ *   ext_dev  device double[4] receiving {min hx, max hx, min hy, max hy} over the defined faces.
+ *   ext_host host double[4] or NULL; when given, the call synchronises the stream, copies ext,
+ *            and returns TSU_ENONPOS if a minimum is <= 0.
+ * The depth is evaluated in FP64 and rounded once to dtype. */
+int tsu_make_depth(const tsu_grid* g, const tsu_depth* d, int dtype, void* hx, void* hy,
+                   double* ext_dev, double* ext_host, void* stream);
+
+/* Largest tau allowed by the leapfrog bound tau^2 (hx_max/dx^2 + hy_max/dy^2) <= 1, times cfl
+ * (0 < cfl <= 1).  Host only.  Returns 0 on bad input. */
+double tsu_tau_for(const tsu_grid* g, double hx_max, double hy_max, double cfl);
+
+/* Cauchy data to the first two time levels (eq. (2.1) initial conditions; Taylor start above).
+ *   u0       device [ny][ld] displacement (boundary values ignored: taken as 0).
+ *   u1       device [ny][ld] velocity, or NULL for u1 = 0.
+ *   st       st->buf[0..1] (and buf[2] for the increment form) device buffers; st->form is read.
+ *            On return st->step = 1, st->cur set.
+ * Errors: TSU_EINVAL, TSU_ECFL. */
+int tsu_init(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, const void* u0,
+             const void* u1, tsu_state* st, void* stream);
+
+/* Bytes of device workspace tsu_step_n and tsu_observe need (energy partial sums). */
+int tsu_step_workspace(const tsu_grid* g, int dtype, size_t* bytes);
+
+/* Advance the state by nsteps leapfrog steps (spec hot path; scheme above).
+ *   opts  NULL or tsu_step_opts (outputs, tuning).  ws/ws_bytes: device workspace, needed
+ *         only when opts->energy is set.
+ * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
+int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, tsu_state* st,
+               int64_t nsteps, const tsu_step_opts* opts, void* ws, size_t ws_bytes, void* stream);
+
+/* Energy E^{n-1/2} of the current pair (u^{n-1}, u^n) into energy_dev[0] (device double, or NULL)
+ * and u^n at the receivers into trace (device [nrec], or NULL).  Does not step. */
+int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, const tsu_state* st,
+                double* energy_dev, int32_t nrec, const int64_t* rec_idx, void* trace, void* ws,
+                size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSU_H */

@@ -1,0 +1,218 @@
+// Face-sampled regularised depth h_eps = background + sum_s amp_s * phi_eps(dist_s)^p_s
+// (arXiv:2005.11931 Sec. 2.1: h_eps = h * psi_eps; Sec. 3.1: the Friedrichs bump, delta and
+// delta^2 singularities, the mollified step h0).  Evaluated in FP64 on the device, rounded once
+// to the field type; the extrema of the stored values are reduced with ordered-integer atomics.
+#include <math.h>
+
+#include "tsu_internal.h"
+
+namespace tsu {
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+__device__ __forceinline__ double bump(double t) {
+  return (fabs(t) < 1.0) ? exp(1.0 / (t * t - 1.0)) : 0.0;
+}
+
+// Mass of the 1D Friedrichs mollifier on (-inf, t]: c1 * int_{-1}^{t} bump, by the
+// tanh-sinh rule on [-1, t] (step 1/16, |k| <= 64), which handles the flat endpoint.
+__device__ double friedrichs_cdf(double c1, double t) {
+  if (t <= -1.0) return 0.0;
+  if (t >= 1.0) return 1.0;
+  const double a = -1.0, b = t, half = 0.5 * (b - a), mid = 0.5 * (a + b);
+  const double h = 1.0 / 16.0;
+  double s = 0.0;
+  for (int k = -64; k <= 64; ++k) {
+    double x = k * h;
+    double sh = sinh(x), ch = cosh(x);
+    double arg = 0.5 * kPi * sh;
+    double th = tanh(arg), cha = cosh(arg);
+    double w = 0.5 * kPi * ch / (cha * cha);
+    double tt = mid + half * th;
+    s += w * bump(tt);
+  }
+  return c1 * s * h * half;
+}
+
+__device__ __forceinline__ double phi1(const DepthParams& p, double s) {
+  const double e = p.eps;
+  if (p.mollifier == TSU_GAUSS) {
+    double q = s / e;
+    return exp(-q * q) / (e * sqrt(kPi));
+  }
+  return p.c1 / e * bump(s / e);
+}
+
+__device__ __forceinline__ double phi2(const DepthParams& p, double r) {
+  const double e = p.eps;
+  if (p.mollifier == TSU_GAUSS) {
+    double q = r / e;
+    return exp(-q * q) / (kPi * e * e);
+  }
+  return p.c2 / (e * e) * bump(r / e);
+}
+
+__device__ __forceinline__ double step1(const DepthParams& p, double s) {
+  if (p.mollifier == TSU_GAUSS) return 0.5 * erfc(-s / p.eps);
+  return friedrichs_cdf(p.c1, s / p.eps);
+}
+
+__device__ double depth_at(const DepthParams& p, double x, double y) {
+  double h = p.background;
+  for (int k = 0; k < p.nsing; ++k) {
+    const tsu_sing& s = p.sing[k];
+    double v;
+    switch (s.kind) {
+      case TSU_LINE_X: v = phi1(p, x - s.cx); break;
+      case TSU_LINE_Y: v = phi1(p, y - s.cy); break;
+      case TSU_POINT: {
+        double dx = x - s.cx, dy = y - s.cy;
+        v = phi2(p, sqrt(dx * dx + dy * dy));
+        break;
+      }
+      case TSU_STEP_X: v = step1(p, s.cx - x); break;
+      default: v = step1(p, s.cy - y); break;
+    }
+    double pw = v;
+    for (int q = 1; q < s.power; ++q) pw *= v;
+    h += s.amp * pw;
+  }
+  return h;
+}
+
+// Order-preserving map of doubles to unsigned 64-bit integers (for atomicMin/Max).
+__device__ __forceinline__ unsigned long long ord_enc(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_dec(unsigned long long e) {
+  unsigned long long b = (e & 0x8000000000000000ull) ? (e & 0x7fffffffffffffffull) : ~e;
+  return __longlong_as_double((long long)b);
+}
+
+__global__ void k_ext_reset(unsigned long long* ext) {
+  ext[0] = ~0ull;  // min hx
+  ext[1] = 0ull;   // max hx
+  ext[2] = ~0ull;  // min hy
+  ext[3] = 0ull;   // max hy
+}
+
+__global__ void k_ext_decode(unsigned long long* ext) {
+  double* d = reinterpret_cast<double*>(ext);
+  for (int k = 0; k < 4; ++k) d[k] = ord_dec(ext[k]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_make_depth(int32_t nx, int32_t ny, int64_t ld, double dx, double dy,
+                                                    const DepthParams p, T* __restrict__ hx,
+                                                    T* __restrict__ hy, unsigned long long* ext) {
+  const int64_t total = (int64_t)ny * ld;
+  double mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = k / ld, i = k - j * ld;
+    T vx = T(0), vy = T(0);
+    if (i <= nx - 2) {
+      vx = T(depth_at(p, (i + 0.5) * dx, j * dy));
+      mnx = fmin(mnx, (double)vx);
+      mxx = fmax(mxx, (double)vx);
+    }
+    if (i < nx && j <= ny - 2) {
+      vy = T(depth_at(p, i * dx, (j + 0.5) * dy));
+      mny = fmin(mny, (double)vy);
+      mxy = fmax(mxy, (double)vy);
+    }
+    hx[k] = vx;
+    hy[k] = vy;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mnx = fmin(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+    mxx = fmax(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+    mny = fmin(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+    mxy = fmax(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+  }
+  __shared__ double red[4][8];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][w] = mnx;
+    red[1][w] = mxx;
+    red[2][w] = mny;
+    red[3][w] = mxy;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int q = 1; q < nw; ++q) {
+      mnx = fmin(mnx, red[0][q]);
+      mxx = fmax(mxx, red[1][q]);
+      mny = fmin(mny, red[2][q]);
+      mxy = fmax(mxy, red[3][q]);
+    }
+    if (mnx <= mxx) {
+      atomicMin(&ext[0], ord_enc(mnx));
+      atomicMax(&ext[1], ord_enc(mxx));
+    }
+    if (mny <= mxy) {
+      atomicMin(&ext[2], ord_enc(mny));
+      atomicMax(&ext[3], ord_enc(mxy));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_make_depth(const tsu_grid& g, const DepthParams& p, int dtype, void* hx, void* hy,
+                              double* ext_dev, cudaStream_t s) {
+  auto* ext = reinterpret_cast<unsigned long long*>(ext_dev);
+  k_ext_reset<<<1, 1, 0, s>>>(ext);
+  const int64_t total = (int64_t)g.ny * g.ld;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (dtype == TSU_F32)
+    k_make_depth<float><<<(unsigned)blocks, 256, 0, s>>>(g.nx, g.ny, g.ld, g.dx, g.dy, p, (float*)hx,
+                                                           (float*)hy, ext);
+  else
+    k_make_depth<double><<<(unsigned)blocks, 256, 0, s>>>(g.nx, g.ny, g.ld, g.dx, g.dy, p, (double*)hx,
+                                                            (double*)hy, ext);
+  k_ext_decode<<<1, 1, 0, s>>>(ext);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host: Friedrichs normalisers by the double-exponential (tanh-sinh) rule.
+// ---------------------------------------------------------------------------------------------
+namespace {
+double host_bump(double t) { return (fabs(t) < 1.0) ? exp(1.0 / (t * t - 1.0)) : 0.0; }
+
+// int_{-1}^{1} f(t) dt with t = tanh(pi/2 sinh x), step h, |x| <= 6.
+template <typename F>
+double tanh_sinh(F f) {
+  const double h = 1.0 / 64.0;
+  double s = 0.0;
+  for (int k = -384; k <= 384; ++k) {
+    double x = k * h;
+    double arg = 0.5 * kPi * sinh(x);
+    double ca = cosh(arg);
+    double w = 0.5 * kPi * cosh(x) / (ca * ca);
+    s += w * f(tanh(arg));
+  }
+  return s * h;
+}
+}  // namespace
+
+double friedrichs_c1() {
+  static const double c = 1.0 / tanh_sinh([](double t) { return host_bump(t); });
+  return c;
+}
+
+double friedrichs_c2() {
+  // int_{R^2} bump(|r|) dA = 2 pi int_0^1 r bump(r) dr, with r = (1+t)/2 mapped onto [-1, 1]
+  static const double c = 1.0 / (2.0 * kPi * 0.5 * tanh_sinh([](double t) {
+                                   const double r = 0.5 * (1.0 + t);
+                                   return r * host_bump(r);
+                                 }));
+  return c;
+}
+
+}  // namespace tsu

@@ -1,0 +1,274 @@
+"""Thin Python binding of libtsu (include/tsu.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of
+``libtsu.so``.  PyTorch supplies device memory and streams.  The functions carry the C names
+(``tsu_make_depth``, ``tsu_init``, ``tsu_step_n`` ...); ``Simulation`` bundles the buffers of
+one forward problem.  If the library has not been built, ``load()`` raises: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtsu.so")
+
+TSU_OK, TSU_EINVAL, TSU_ECFL, TSU_ENONPOS, TSU_ENOMEM, TSU_ECUDA, TSU_ETIMEOUT = range(7)
+TSU_F32, TSU_F64 = 0, 1
+TSU_FORM_STANDARD, TSU_FORM_INCREMENT = 0, 1
+TSU_LINE_X, TSU_LINE_Y, TSU_POINT, TSU_STEP_X, TSU_STEP_Y = range(5)
+TSU_GAUSS, TSU_FRIEDRICHS = 0, 1
+_NAMES = {0: "TSU_OK", 1: "TSU_EINVAL", 2: "TSU_ECFL", 3: "TSU_ENONPOS", 4: "TSU_ENOMEM", 5: "TSU_ECUDA",
+          6: "TSU_ETIMEOUT"}
+
+DTYPES = {TSU_F32: torch.float32, TSU_F64: torch.float64, "f32": torch.float32, "f64": torch.float64}
+
+
+def dtype_code(dt) -> int:
+    if dt in (TSU_F32, "f32", torch.float32, np.float32):
+        return TSU_F32
+    if dt in (TSU_F64, "f64", torch.float64, np.float64):
+        return TSU_F64
+    raise ValueError(f"unsupported dtype {dt!r}")
+
+
+class TsuError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__(f"{func}: {_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ld", C.c_int64), ("dx", C.c_double), ("dy", C.c_double)]
+
+
+class Sing(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("power", C.c_int32), ("amp", C.c_double), ("cx", C.c_double),
+                ("cy", C.c_double)]
+
+
+class Depth(C.Structure):
+    _fields_ = [("background", C.c_double), ("eps", C.c_double), ("mollifier", C.c_int32), ("nsing", C.c_int32),
+                ("sing", C.POINTER(Sing))]
+
+
+class Medium(C.Structure):
+    _fields_ = [("hx", C.c_void_p), ("hy", C.c_void_p), ("hx_max", C.c_double), ("hy_max", C.c_double)]
+
+
+class State(C.Structure):
+    _fields_ = [("buf", C.c_void_p * 3), ("cur", C.c_int32), ("form", C.c_int32), ("step", C.c_int64)]
+
+
+class StepOpts(C.Structure):
+    _fields_ = [("energy", C.c_void_p), ("nrec", C.c_int32), ("rec_idx", C.c_void_p), ("traces", C.c_void_p),
+                ("ckpt", C.c_void_p), ("ckpt_every", C.c_int64), ("ckpt_slots", C.c_int64), ("kernel", C.c_int32),
+                ("rows", C.c_int32), ("tdepth", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libtsu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libtsu.so not built ({LIB_PATH}); run paper_2005_11931_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "tsu_version": ([], C.c_int),
+        "tsu_last_error": ([], C.c_char_p),
+        "tsu_make_depth": ([C.POINTER(Grid), C.POINTER(Depth), C.c_int, vp, vp, vp, C.POINTER(C.c_double), vp], C.c_int),
+        "tsu_tau_for": ([C.POINTER(Grid), dbl, dbl, dbl], dbl),
+        "tsu_init": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), vp, vp, C.POINTER(State), vp], C.c_int),
+        "tsu_step_workspace": ([C.POINTER(Grid), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+        "tsu_step_n": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), i64,
+                        C.POINTER(StepOpts), vp, C.c_size_t, vp], C.c_int),
+        "tsu_observe": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), vp, i32, vp, vp, vp,
+                         C.c_size_t, vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/tsu.h (parsed from the header text)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "tsu.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:int|double|const char\*)\s+(tsu_\w+)\s*\(", text, re.M)))
+
+
+def _check(rc: int, func: str):
+    if rc != TSU_OK:
+        raise TsuError(rc, func, load().tsu_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr()
+    return int(t)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def grid(n: int, ny: int | None = None, ld: int | None = None) -> Grid:
+    """Unit box with n x ny nodes (boundary included), rows padded to a multiple of 32."""
+    ny = ny or n
+    ld = ld or (n + 31) // 32 * 32
+    return Grid(n, ny, ld, 1.0 / (n - 1), 1.0 / (ny - 1))
+
+
+def depth_struct(depth: dict):
+    sings = depth.get("sings", [])
+    arr = (Sing * max(1, len(sings)))(*[Sing(*s) for s in sings])
+    d = Depth(float(depth["background"]), float(depth["eps"]), int(depth.get("mollifier", TSU_GAUSS)), len(sings),
+              C.cast(arr, C.POINTER(Sing)))
+    d._keep = arr
+    return d
+
+
+def empty_field(g: Grid, dtype, device="cuda") -> torch.Tensor:
+    return torch.zeros((g.ny, g.ld), dtype=DTYPES[dtype_code(dtype)], device=device)
+
+
+# ---------------------------------------------------------------------------------------------
+# C entry points
+# ---------------------------------------------------------------------------------------------
+def tsu_make_depth(g: Grid, depth: dict, dtype, hx: torch.Tensor, hy: torch.Tensor, ext_dev: torch.Tensor,
+                   sync: bool = True, stream=None):
+    """Face coefficients of the regularised depth; returns [min hx, max hx, min hy, max hy] when sync."""
+    d = depth_struct(depth)
+    ext = (C.c_double * 4)() if sync else None
+    rc = load().tsu_make_depth(C.byref(g), C.byref(d), dtype_code(dtype), _ptr(hx), _ptr(hy), _ptr(ext_dev),
+                               ext, _stream(stream))
+    _check(rc, "tsu_make_depth")
+    return np.array(list(ext)) if sync else None
+
+
+def tsu_tau_for(g: Grid, hx_max: float, hy_max: float, cfl: float) -> float:
+    return float(load().tsu_tau_for(C.byref(g), hx_max, hy_max, cfl))
+
+
+def tsu_init(g: Grid, dtype, tau: float, medium: Medium, u0, u1, state: State, stream=None):
+    rc = load().tsu_init(C.byref(g), dtype_code(dtype), tau, C.byref(medium), _ptr(u0), _ptr(u1), C.byref(state),
+                         _stream(stream))
+    _check(rc, "tsu_init")
+
+
+def tsu_step_workspace(g: Grid, dtype) -> int:
+    n = C.c_size_t(0)
+    _check(load().tsu_step_workspace(C.byref(g), dtype_code(dtype), C.byref(n)), "tsu_step_workspace")
+    return int(n.value)
+
+
+def tsu_step_n(g: Grid, dtype, tau: float, medium: Medium, state: State, nsteps: int, opts: StepOpts | None = None,
+               ws=None, ws_bytes: int = 0, stream=None):
+    rc = load().tsu_step_n(C.byref(g), dtype_code(dtype), tau, C.byref(medium), C.byref(state), int(nsteps),
+                           C.byref(opts) if opts is not None else None, _ptr(ws), int(ws_bytes), _stream(stream))
+    _check(rc, "tsu_step_n")
+
+
+def tsu_observe(g: Grid, dtype, tau: float, medium: Medium, state: State, energy_dev=None, rec_idx=None,
+                trace=None, ws=None, ws_bytes: int = 0, stream=None):
+    nrec = 0 if rec_idx is None else int(rec_idx.numel())
+    rc = load().tsu_observe(C.byref(g), dtype_code(dtype), tau, C.byref(medium), C.byref(state), _ptr(energy_dev),
+                            nrec, _ptr(rec_idx), _ptr(trace), _ptr(ws), int(ws_bytes), _stream(stream))
+    _check(rc, "tsu_observe")
+
+
+# ---------------------------------------------------------------------------------------------
+# Convenience: one forward problem with torch-owned buffers
+# ---------------------------------------------------------------------------------------------
+@dataclass
+class Simulation:
+    """Buffers and calls of one forward problem (marshalling only)."""
+    g: Grid
+    dtype: int
+    form: int
+    hx: torch.Tensor
+    hy: torch.Tensor
+    ext: np.ndarray
+    tau: float
+    medium: Medium
+    bufs: list
+    state: State
+    ws: torch.Tensor
+
+    @classmethod
+    def create(cls, n: int, depth: dict, dtype="f32", form=TSU_FORM_STANDARD, cfl: float = 0.4, tau=None,
+               ny=None, ld=None, stream=None, device="cuda"):
+        g = grid(n, ny, ld)
+        code = dtype_code(dtype)
+        hx = empty_field(g, code, device)
+        hy = empty_field(g, code, device)
+        ext_dev = torch.zeros(4, dtype=torch.float64, device=device)
+        ext = tsu_make_depth(g, depth, code, hx, hy, ext_dev, sync=True, stream=stream)
+        if tau is None:
+            # the workloads' rule: tau = cfl * dx / sqrt(max h) over both face families
+            tau = cfl * min(g.dx, g.dy) / float(np.sqrt(max(ext[1], ext[3])))
+        med = Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
+        nb = 3 if form == TSU_FORM_INCREMENT else 2
+        bufs = [empty_field(g, code, device) for _ in range(nb)]
+        st = State()
+        for k, b in enumerate(bufs):
+            st.buf[k] = b.data_ptr()
+        st.form = form
+        ws_bytes = tsu_step_workspace(g, code)
+        ws = torch.zeros(ws_bytes, dtype=torch.uint8, device=device)
+        return cls(g, code, form, hx, hy, ext, float(tau), med, bufs, st, ws)
+
+    def init(self, u0: torch.Tensor, u1: torch.Tensor | None = None, stream=None):
+        tsu_init(self.g, self.dtype, self.tau, self.medium, u0, u1, self.state, stream)
+
+    def step(self, nsteps: int, energy: torch.Tensor | None = None, rec_idx: torch.Tensor | None = None,
+             traces: torch.Tensor | None = None, ckpt: torch.Tensor | None = None, ckpt_every: int = 0,
+             kernel: int = 0, rows: int = 0, tdepth: int = 0, stream=None):
+        o = StepOpts()
+        o.energy = _ptr(energy)
+        o.nrec = 0 if rec_idx is None else int(rec_idx.numel())
+        o.rec_idx = _ptr(rec_idx)
+        o.traces = _ptr(traces)
+        o.ckpt = _ptr(ckpt)
+        o.ckpt_every = int(ckpt_every)
+        o.ckpt_slots = 0 if ckpt is None else int(ckpt.shape[0])
+        o.kernel, o.rows, o.tdepth = int(kernel), int(rows), int(tdepth)
+        tsu_step_n(self.g, self.dtype, self.tau, self.medium, self.state, nsteps, o, self.ws, self.ws.numel(), stream)
+
+    def observe(self, energy: torch.Tensor | None = None, rec_idx=None, trace=None, stream=None):
+        tsu_observe(self.g, self.dtype, self.tau, self.medium, self.state, energy, rec_idx, trace, self.ws,
+                    self.ws.numel(), stream)
+
+    @property
+    def u(self) -> torch.Tensor:
+        """u^n (current level)."""
+        return self.bufs[self.state.cur]
+
+    @property
+    def u_prev(self) -> torch.Tensor:
+        """u^{n-1} (standard form; for the increment form the buffer holds u^{n-1} as well)."""
+        return self.bufs[self.state.cur ^ 1]
+
+    @property
+    def v(self) -> torch.Tensor | None:
+        return self.bufs[2] if self.form == TSU_FORM_INCREMENT else None
