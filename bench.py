@@ -148,7 +148,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     # bounded sample: a few steps of the full grid per bench step
-    steps_sample = 4 if args.n >= 4096 else 16
+    steps_sample = 16 if args.n >= 4096 else 64
     for _ in range(args.warmup):
         oracle_sample(args.n, 2)
     vals, secs = [], 0.0
@@ -194,7 +194,7 @@ def run_gpu(args):
     hy = tsu.empty_field(g, code, dev)
     ext_dev = torch.zeros(4, dtype=torch.float64, device=dev)
     u0 = torch.from_numpy(p.initial(g.ld, np.float32)).to(dev)
-    nb = 3 if form == tsu.TSU_FORM_INCREMENT else 2
+    nb = 4
     bufs = [tsu.empty_field(g, code, dev) for _ in range(nb)]
     st = tsu.State()
     ws_bytes = tsu.tsu_step_workspace(g, code)
@@ -213,6 +213,7 @@ def run_gpu(args):
     def one_step(u0_dev, timed_kernel=False):
         for k, b in enumerate(bufs):
             st.buf[k] = b.data_ptr()
+        st.nbuf = nb
         st.form = form
         tsu.tsu_make_depth(g, p.depth, code, hx, hy, ext_dev, sync=False, stream=stream)
         tsu.tsu_init(g, code, tau, med, u0_dev, None, st, stream)
@@ -294,7 +295,7 @@ def run_gpu(args):
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        r = oracle_sample(p.n, 4 if p.n >= 4096 else 16)
+        r = oracle_sample(p.n, 64 if p.n >= 4096 else 256)
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

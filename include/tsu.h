@@ -98,16 +98,20 @@ typedef struct {
 } tsu_medium;
 
 /* Time-stepping state (device buffers of ny*ld elements, owned by the caller).
- *   TSU_FORM_STANDARD : buf[cur] = u^n, buf[cur^1] = u^{n-1}; a step writes u^{n+1} over u^{n-1}.
- *   TSU_FORM_INCREMENT: buf[cur] = u^n, buf[2] = v^n = u^n - u^{n-1}; a step writes
- *                       v^{n+1} = v^n + B u^n in place and u^{n+1} = u^n + v^{n+1} into buf[cur^1].
- *                       Same scheme, rounded differently: it keeps FP32 fields accurate when the
- *                       per-step change is far below one ulp of u.
- * step = n.  cur and step are updated on the host when work is enqueued. */
+ *   buf[cur] = u^n;  buf[aux] = u^{n-1} (TSU_FORM_STANDARD) or v^n = u^n - u^{n-1}
+ *   (TSU_FORM_INCREMENT); the other buffers are scratch the steppers write into.
+ *   TSU_FORM_STANDARD : a plain step writes u^{n+1} over u^{n-1} (needs nbuf >= 2).
+ *   TSU_FORM_INCREMENT: a plain step writes v^{n+1} = v^n + B u^n in place and u^{n+1} = u^n + v^{n+1}
+ *                       into a scratch buffer (nbuf >= 3).  Same scheme, rounded differently: it
+ *                       keeps FP32 fields accurate when the per-step change is far below one ulp of u.
+ *   The temporally blocked kernel writes both output levels into scratch buffers (nbuf = 4).
+ * step = n.  cur, aux and step are updated on the host when work is enqueued.  tsu_init fills
+ * every provided buffer (scratch buffers with zeros). */
 typedef struct {
-  void* buf[3];
-  int32_t cur;
+  void* buf[4];
+  int32_t nbuf;
   int32_t form;
+  int32_t cur, aux;
   int64_t step;
 } tsu_state;
 
@@ -155,8 +159,9 @@ double tsu_tau_for(const tsu_grid* g, double hx_max, double hy_max, double cfl);
 /* Cauchy data to the first two time levels (eq. (2.1) initial conditions; Taylor start above).
  *   u0       device [ny][ld] displacement (boundary values ignored: taken as 0).
  *   u1       device [ny][ld] velocity, or NULL for u1 = 0.
- *   st       st->buf[0..1] (and buf[2] for the increment form) device buffers; st->form is read.
- *            On return st->step = 1, st->cur set.
+ *   st       st->buf[0..nbuf-1] device buffers, st->nbuf and st->form are read.  On return
+ *            st->step = 1 and cur/aux are set (standard: buf[0] = u^0, buf[1] = u^1;
+ *            increment: buf[0] = u^1, buf[1] = v^1 = tau u1 + B u^0 / 2).
  * Errors: TSU_EINVAL, TSU_ECFL. */
 int tsu_init(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, const void* u0,
              const void* u1, tsu_state* st, void* stream);

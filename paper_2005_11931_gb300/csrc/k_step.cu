@@ -273,7 +273,7 @@ __device__ __forceinline__ T u0_at(const T* u0, int32_t nx, int32_t ny, int64_t 
 template <typename T>
 __global__ void k_init(const int32_t nx, const int32_t ny, const int64_t ld, const typename ArithOf<T>::type ar,
                        const T tau, const T* __restrict__ hx, const T* __restrict__ hy, const T* __restrict__ u0,
-                       const T* __restrict__ u1, T* __restrict__ o_prev, T* __restrict__ o_cur, T* __restrict__ o_v) {
+                       const T* __restrict__ u1, T* __restrict__ o_u0, T* __restrict__ o_u1, T* __restrict__ o_v) {
   const int64_t total = (int64_t)ny * ld;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = k / ld, i = k - j * ld;
@@ -292,8 +292,8 @@ __global__ void k_init(const int32_t nx, const int32_t ny, const int64_t ld, con
         v = tau * w + 0.5f * b;
       }
     }
-    o_prev[k] = a;
-    o_cur[k] = cur;
+    if (o_u0) o_u0[k] = a;
+    o_u1[k] = cur;
     if (o_v) o_v[k] = v;
   }
 }
@@ -357,19 +357,23 @@ cudaError_t launch_init(const StencilGeom& g, int dtype, int form, const void* h
   const int64_t total = (int64_t)g.ny * g.ld;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  // standard: buf[0] = u^0, buf[1] = u^1 (cur = 1); increment: buf[0] = u^1, buf[1] = u^0, buf[2] = v^1 (cur = 0)
-  void* o_prev = form == TSU_FORM_STANDARD ? st->buf[0] : st->buf[1];
-  void* o_cur = form == TSU_FORM_STANDARD ? st->buf[1] : st->buf[0];
-  void* o_v = form == TSU_FORM_STANDARD ? nullptr : st->buf[2];
+  // standard: buf[0] = u^0, buf[1] = u^1; increment: buf[0] = u^1, buf[1] = v^1; the rest zeroed
+  void* o_u0 = form == TSU_FORM_STANDARD ? st->buf[0] : nullptr;
+  void* o_u1 = form == TSU_FORM_STANDARD ? st->buf[1] : st->buf[0];
+  void* o_v = form == TSU_FORM_STANDARD ? nullptr : st->buf[1];
+  const size_t esz = dtype == TSU_F32 ? 4 : 8;
+  for (int b = 2; b < st->nbuf; ++b) {
+    cudaError_t e = cudaMemsetAsync(st->buf[b], 0, (size_t)total * esz, s);
+    if (e != cudaSuccess) return e;
+  }
   if (dtype == TSU_F32)
     k_init<float><<<(unsigned)blocks, 256, 0, s>>>(g.nx, g.ny, g.ld, make_arith<float>(g), (float)g.tau,
                                                     (const float*)hx, (const float*)hy, (const float*)u0,
-                                                    (const float*)u1, (float*)o_prev, (float*)o_cur, (float*)o_v);
+                                                    (const float*)u1, (float*)o_u0, (float*)o_u1, (float*)o_v);
   else
     k_init<double><<<(unsigned)blocks, 256, 0, s>>>(g.nx, g.ny, g.ld, make_arith<double>(g), g.tau,
                                                      (const double*)hx, (const double*)hy, (const double*)u0,
-                                                     (const double*)u1, (double*)o_prev, (double*)o_cur,
-                                                     (double*)o_v);
+                                                     (const double*)u1, (double*)o_u0, (double*)o_u1, (double*)o_v);
   return cudaGetLastError();
 }
 

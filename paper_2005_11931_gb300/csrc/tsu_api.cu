@@ -56,6 +56,29 @@ int check_cfl(const tsu_grid* g, double tau, const tsu_medium* m) {
   return TSU_OK;
 }
 
+int check_state(const tsu_state* st, bool need_roles) {
+  if (!st) return fail(TSU_EINVAL, "state is NULL");
+  if (st->form != TSU_FORM_STANDARD && st->form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
+  const int need = st->form == TSU_FORM_STANDARD ? 2 : 3;
+  if (st->nbuf < need || st->nbuf > 4)
+    return fail(TSU_EINVAL, "state needs %d..4 buffers for this form (nbuf = %d)", need, st->nbuf);
+  for (int b = 0; b < st->nbuf; ++b) {
+    if (!st->buf[b] || ((uintptr_t)st->buf[b] & 15u)) return fail(TSU_EINVAL, "state buf[%d] NULL or misaligned", b);
+  }
+  if (need_roles) {
+    if (st->cur < 0 || st->cur >= st->nbuf || st->aux < 0 || st->aux >= st->nbuf || st->cur == st->aux)
+      return fail(TSU_EINVAL, "state cur/aux invalid (%d, %d)", st->cur, st->aux);
+  }
+  return TSU_OK;
+}
+
+// first buffer index that is neither cur nor aux
+int scratch_index(const tsu_state* st, int skip) {
+  for (int b = 0; b < st->nbuf; ++b)
+    if (b != st->cur && b != st->aux && b != skip) return b;
+  return -1;
+}
+
 tsu::StencilGeom geom(const tsu_grid* g, double tau) {
   tsu::StencilGeom s;
   s.nx = g->nx;
@@ -140,14 +163,11 @@ int tsu_init(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, cons
   TRY(check_field(m->hy, "hy"));
   TRY(check_field(u0, "u0"));
   if (u1) TRY(check_field(u1, "u1"));
-  if (!st) return fail(TSU_EINVAL, "state is NULL");
-  if (st->form != TSU_FORM_STANDARD && st->form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
-  TRY(check_field(st->buf[0], "state buf[0]"));
-  TRY(check_field(st->buf[1], "state buf[1]"));
-  if (st->form == TSU_FORM_INCREMENT) TRY(check_field(st->buf[2], "state buf[2]"));
+  TRY(check_state(st, false));
   cudaError_t e = tsu::launch_init(geom(g, tau), dtype, st->form, m->hx, m->hy, u0, u1, st, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_init launch");
   st->cur = st->form == TSU_FORM_STANDARD ? 1 : 0;
+  st->aux = st->form == TSU_FORM_STANDARD ? 0 : 1;
   st->step = 1;
   return TSU_OK;
 }
@@ -169,12 +189,7 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   TRY(check_cfl(g, tau, m));
   TRY(check_field(m->hx, "hx"));
   TRY(check_field(m->hy, "hy"));
-  if (!st) return fail(TSU_EINVAL, "state is NULL");
-  if (st->form != TSU_FORM_STANDARD && st->form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
-  if (st->cur != 0 && st->cur != 1) return fail(TSU_EINVAL, "state cur must be 0 or 1");
-  TRY(check_field(st->buf[0], "state buf[0]"));
-  TRY(check_field(st->buf[1], "state buf[1]"));
-  if (st->form == TSU_FORM_INCREMENT) TRY(check_field(st->buf[2], "state buf[2]"));
+  TRY(check_state(st, true));
   if (nsteps < 0) return fail(TSU_EINVAL, "nsteps must be >= 0");
   tsu_step_opts o;
   memset(&o, 0, sizeof o);
@@ -210,15 +225,23 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
       po.ckpt_a = slot;
       po.ckpt_b = slot + field_bytes;
     }
-    void* cur = st->buf[st->cur];
-    void* other = st->buf[st->cur ^ 1];
     cudaError_t e;
-    if (st->form == TSU_FORM_STANDARD)
-      e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, other, cur, nullptr, other, po, true, o.rows, s);
-    else
-      e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, nullptr, cur, st->buf[2], other, po, true, o.rows, s);
+    if (st->form == TSU_FORM_STANDARD) {
+      e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, st->buf[st->aux], st->buf[st->cur], nullptr,
+                           st->buf[st->aux], po, true, o.rows, s);
+    } else {
+      const int f = scratch_index(st, -1);
+      e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, nullptr, st->buf[st->cur], st->buf[st->aux],
+                           st->buf[f], po, true, o.rows, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n launch");
-    st->cur ^= 1;
+    if (st->form == TSU_FORM_STANDARD) {
+      const int t = st->cur;
+      st->cur = st->aux;
+      st->aux = t;
+    } else {
+      st->cur = scratch_index(st, -1);
+    }
     st->step += 1;
   }
   return TSU_OK;
@@ -233,9 +256,7 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
   TRY(check_cfl(g, tau, m));
   TRY(check_field(m->hx, "hx"));
   TRY(check_field(m->hy, "hy"));
-  if (!st) return fail(TSU_EINVAL, "state is NULL");
-  if (st->form != TSU_FORM_STANDARD && st->form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
-  if (st->cur != 0 && st->cur != 1) return fail(TSU_EINVAL, "state cur must be 0 or 1");
+  TRY(check_state(st, true));
   if (trace && (nrec <= 0 || !rec_idx)) return fail(TSU_EINVAL, "trace needs nrec > 0 and rec_idx");
   tsu::PassOut po{};
   if (energy_dev) {
@@ -250,13 +271,11 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
   po.rec_idx = rec_idx;
   po.trace = trace;
   if (!energy_dev && !trace) return TSU_OK;
-  void* cur = st->buf[st->cur];
-  void* other = st->buf[st->cur ^ 1];
   cudaError_t e = st->form == TSU_FORM_STANDARD
-                      ? tsu::launch_step(geom(g, tau), dtype, st->form, m->hx, m->hy, other, cur, nullptr, nullptr,
-                                         po, false, 0, (cudaStream_t)stream)
-                      : tsu::launch_step(geom(g, tau), dtype, st->form, m->hx, m->hy, nullptr, cur, st->buf[2],
-                                         nullptr, po, false, 0, (cudaStream_t)stream);
+                      ? tsu::launch_step(geom(g, tau), dtype, st->form, m->hx, m->hy, st->buf[st->aux],
+                                         st->buf[st->cur], nullptr, nullptr, po, false, 0, (cudaStream_t)stream)
+                      : tsu::launch_step(geom(g, tau), dtype, st->form, m->hx, m->hy, nullptr, st->buf[st->cur],
+                                         st->buf[st->aux], nullptr, po, false, 0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_observe launch");
   return TSU_OK;
 }

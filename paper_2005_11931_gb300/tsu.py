@@ -62,7 +62,8 @@ class Medium(C.Structure):
 
 
 class State(C.Structure):
-    _fields_ = [("buf", C.c_void_p * 3), ("cur", C.c_int32), ("form", C.c_int32), ("step", C.c_int64)]
+    _fields_ = [("buf", C.c_void_p * 4), ("nbuf", C.c_int32), ("form", C.c_int32), ("cur", C.c_int32),
+                ("aux", C.c_int32), ("step", C.c_int64)]
 
 
 class StepOpts(C.Structure):
@@ -216,10 +217,12 @@ class Simulation:
     ws: torch.Tensor
 
     @classmethod
-    def create(cls, n: int, depth: dict, dtype="f32", form=TSU_FORM_STANDARD, cfl: float = 0.4, tau=None,
-               ny=None, ld=None, stream=None, device="cuda"):
+    def create(cls, n: int, depth: dict, dtype="f32", form=None, cfl: float = 0.4, tau=None,
+               ny=None, ld=None, stream=None, device="cuda", nbuf=None):
         g = grid(n, ny, ld)
         code = dtype_code(dtype)
+        if form is None:  # FP32 fields keep their accuracy over long runs in the increment form
+            form = TSU_FORM_INCREMENT if code == TSU_F32 else TSU_FORM_STANDARD
         hx = empty_field(g, code, device)
         hy = empty_field(g, code, device)
         ext_dev = torch.zeros(4, dtype=torch.float64, device=device)
@@ -228,11 +231,12 @@ class Simulation:
             # the workloads' rule: tau = cfl * dx / sqrt(max h) over both face families
             tau = cfl * min(g.dx, g.dy) / float(np.sqrt(max(ext[1], ext[3])))
         med = Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
-        nb = 3 if form == TSU_FORM_INCREMENT else 2
+        nb = 4 if nbuf is None else nbuf
         bufs = [empty_field(g, code, device) for _ in range(nb)]
         st = State()
         for k, b in enumerate(bufs):
             st.buf[k] = b.data_ptr()
+        st.nbuf = nb
         st.form = form
         ws_bytes = tsu_step_workspace(g, code)
         ws = torch.zeros(ws_bytes, dtype=torch.uint8, device=device)
@@ -260,15 +264,16 @@ class Simulation:
                     self.ws.numel(), stream)
 
     @property
-    def u(self) -> torch.Tensor:
-        """u^n (current level)."""
-        return self.bufs[self.state.cur]
-
-    @property
-    def u_prev(self) -> torch.Tensor:
-        """u^{n-1} (standard form; for the increment form the buffer holds u^{n-1} as well)."""
-        return self.bufs[self.state.cur ^ 1]
+    def u_prev(self) -> torch.Tensor | None:
+        """u^{n-1} (standard form only)."""
+        return self.bufs[self.state.aux] if self.form == TSU_FORM_STANDARD else None
 
     @property
     def v(self) -> torch.Tensor | None:
-        return self.bufs[2] if self.form == TSU_FORM_INCREMENT else None
+        """v^n = u^n - u^{n-1} (increment form only)."""
+        return self.bufs[self.state.aux] if self.form == TSU_FORM_INCREMENT else None
+
+    @property
+    def u(self) -> torch.Tensor:
+        """u^n (current level)."""
+        return self.bufs[self.state.cur]

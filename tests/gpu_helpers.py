@@ -42,7 +42,8 @@ def run_gpu(n, depth, u0_np, steps, dtype="f32", form=tsu.TSU_FORM_STANDARD, ny=
                  traces=tr[: steps - 1] if tr is not None else None, rows=rows, kernel=kernel)
     sim.observe(energy=e[steps - 1:] if energy else None, rec_idx=rec, trace=tr[steps - 1] if tr is not None else None)
     torch.cuda.synchronize()
-    return dict(u=sim.u[:, : g.nx].double().cpu().numpy(), u_prev=sim.u_prev[:, : g.nx].double().cpu().numpy(),
+    up = sim.u_prev if sim.u_prev is not None else sim.u - sim.v
+    return dict(u=sim.u[:, : g.nx].double().cpu().numpy(), u_prev=up[:, : g.nx].double().cpu().numpy(),
                 energy=e.cpu().numpy() if energy else None, traces=tr.double().cpu().numpy() if tr is not None else None,
                 tau=sim.tau, ext=sim.ext, sim=sim)
 

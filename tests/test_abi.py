@@ -31,7 +31,7 @@ def test_binding_structs_match_header_layout():
     hdr = open(tsu.declared_symbols.__code__.co_filename.replace("paper_2005_11931_gb300/tsu.py",
                                                                  "include/tsu.h")).read()
     assert C.sizeof(tsu.Grid) == 32 and C.sizeof(tsu.Sing) == 32
-    assert C.sizeof(tsu.State) == 3 * 8 + 4 + 4 + 8
+    assert C.sizeof(tsu.State) == 4 * 8 + 4 * 4 + 8
     for struct, cname in ((tsu.StepOpts, "tsu_step_opts"), (tsu.State, "tsu_state"), (tsu.Medium, "tsu_medium")):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + ";", hdr).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
