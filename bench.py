@@ -27,6 +27,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "grid-point updates/s (GLUPS) and HBM roofline %; adjoint/forward time ratio"
+# DRAM bytes (read + write) per launch of the dominant kernel from ncu captures (profiles/),
+# keyed by (kernel, form, n, steps per launch); only for kernels unchanged since the capture.
+TRAFFIC = {
+    # profiles/k_leapfrog_increment_4096.md, scaled by 8190^2/4094^2 (writes under-counted: L2 residency)
+    ("k_leapfrog", "increment", 8192, 1): 1.483e9,
+    # profiles/k_leapfrog_standard_4096.md, scaled likewise
+    ("k_leapfrog", "standard", 8192, 1): 1.280e9,
+}
 UNIT = "GLUPS"
 
 
@@ -40,7 +48,8 @@ def parse():
     ap.add_argument("--nsteps", type=int, default=5000, help="leapfrog steps per bench step")
     ap.add_argument("--form", default="increment", choices=["increment", "standard"])
     ap.add_argument("--rows", type=int, default=0)
-    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one step per pass, 3 temporally blocked")
+    ap.add_argument("--tdepth", type=int, default=0, help="steps per blocked pass (4 or 8; 0 = 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch (from profiles/)")
@@ -203,9 +212,18 @@ def run_gpu(args):
     ext = tsu.tsu_make_depth(g, p.depth, code, hx, hy, ext_dev, sync=True)
     tau = inputs.CFL * g.dx / float(np.sqrt(max(ext[1], ext[3])))
     med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
+    # the blocked kernel runs when it is chosen (or by default: FP32, 4 buffers, a large grid);
+    # its steps and the leftover single steps are separate calls so that each is timed on its own
+    K = args.tdepth or 8
+    blocked = args.kernel == 3 or (args.kernel == 0 and p.n * p.n >= (1 << 20))
+    n_main = ((S - 1) // K) * K if blocked else S - 1
+    n_left = (S - 1) - n_main
     opts = tsu.StepOpts()
     opts.energy = energy.data_ptr()
-    opts.kernel, opts.rows = args.kernel, args.rows
+    opts.kernel, opts.rows, opts.tdepth = (3 if blocked else 1), args.rows, K
+    opts_left = tsu.StepOpts()
+    opts_left.energy = energy.data_ptr() + 8 * n_main
+    opts_left.kernel = 1
     ev_k0 = torch.cuda.Event(enable_timing=True)
     ev_k1 = torch.cuda.Event(enable_timing=True)
     kernel_ms = []
@@ -219,13 +237,17 @@ def run_gpu(args):
         tsu.tsu_init(g, code, tau, med, u0_dev, None, st, stream)
         if timed_kernel:
             ev_k0.record(stream)
-        tsu.tsu_step_n(g, code, tau, med, st, S - 1, opts, ws, ws_bytes, stream)
+        tsu.tsu_step_n(g, code, tau, med, st, n_main, opts, ws, ws_bytes, stream)
         if timed_kernel:
             ev_k1.record(stream)
+        if n_left:
+            tsu.tsu_step_n(g, code, tau, med, st, n_left, opts_left, ws, ws_bytes, stream)
         o_e = energy[S - 1:]
         tsu.tsu_observe(g, code, tau, med, st, o_e, None, None, ws, ws_bytes, stream)
 
-    launches_per_step = 3 + 1 + (S - 1) + 1  # depth (reset, eval, decode), init, leapfrog, observe
+    main_launches = n_main // K if blocked else n_main
+    # depth (reset, eval, decode), init, main passes, leftover passes, observe
+    launches_per_step = 3 + 1 + main_launches + n_left + 1
 
     for _ in range(args.warmup):
         one_step(u0)
@@ -250,10 +272,20 @@ def run_gpu(args):
         ms = float(t.item())
     lups_step = (p.n - 2) ** 2 * S
     value = world * lups_step * args.steps / (ms / 1e3) / 1e9
-    # roofline of the dominant kernel (the leapfrog pass)
-    bpl = 24 if form == tsu.TSU_FORM_INCREMENT else 20  # algorithmic bytes per interior update
-    launch_ms = sum(kernel_ms) / (len(kernel_ms) * (S - 1))
-    achieved = bpl * (p.n - 2) ** 2 / (launch_ms / 1e3) / 1e9
+    tsu.tsu_sync_status(ws, ws_bytes, stream)  # raises if a bounded device wait expired
+    # roofline of the dominant kernel.  Algorithmic bytes per launch: one read of the state and
+    # the faces and one write of the state: 24 B per node (increment form) / 20 B (standard,
+    # one step per pass); the blocked pass reads and writes two state fields: 24 B per node for
+    # K steps.
+    if blocked:
+        bpn = 24
+        kname = "k_leapfrog_tb"
+    else:
+        bpn = 24 if form == tsu.TSU_FORM_INCREMENT else 20
+        kname = "k_leapfrog"
+    launch_ms = sum(kernel_ms) / (len(kernel_ms) * main_launches)
+    achieved = bpn * (p.n - 2) ** 2 / (launch_ms / 1e3) / 1e9
+    traffic = args.traffic if args.traffic is not None else TRAFFIC.get((kname, args.form, p.n, K if blocked else 1))
     peak, peak_kind = load_peaks()
     e_final = energy.cpu().numpy()
     drift = float(np.max(np.abs(e_final - e_final[0])) / e_final[0])
@@ -303,13 +335,15 @@ def run_gpu(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"point_fp32_{p.n}: {p.n}x{p.n} grid, depth 0.5 + 0.01 phi_eps(|r-(0.5,0.5)|), "
                                f"eps = 4dx, Gaussian hump width 0.02 at (0.3,0.5), {S} steps, "
-                               f"{'increment' if form else 'standard'} form, energy every step",
+                               f"{'increment' if form else 'standard'} form, energy every step, "
+                               f"{'%d steps per blocked pass' % K if blocked else 'one step per pass'}",
                    "n": p.n, "leapfrog_steps": S, "form": args.form, "tau": tau,
                    "l2": "inputs larger than L2 (four 256 MiB fields), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": args.traffic, "peak_kind": peak_kind, "bytes_per_update": bpl,
-                     "kernel": "k_leapfrog", "launch_ms": launch_ms},
+                     "traffic": traffic, "peak_kind": peak_kind, "bytes_per_launch_per_node": bpn,
+                     "steps_per_launch": K if blocked else 1, "kernel": kname, "launch_ms": launch_ms,
+                     "launches_per_step": main_launches},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),

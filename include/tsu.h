@@ -130,10 +130,14 @@ typedef struct {
   void* traces;
   void* ckpt;
   int64_t ckpt_every, ckpt_slots;
-  int32_t kernel;   /* 0 auto, 1 register-streaming, 2 TMA-pipelined, 3 temporally blocked */
+  int32_t kernel;   /* 0 auto, 1 register-streaming (one step per pass), 3 temporally blocked
+                       (tdepth steps per pass; FP32, nbuf = 4, workspace, no traces/checkpoints);
+                       auto picks 3 when it is possible and the grid has >= 2^20 nodes */
   int32_t rows;     /* rows per CTA (0 = auto) */
-  int32_t tdepth;   /* steps per HBM pass for kernel 3 (0 = auto) */
-  int32_t reserved;
+  int32_t tdepth;   /* steps per pass of kernel 3: 4 or 8 (0 = 8); leftover steps run one per pass */
+  int32_t reserved; /* 0.  Bit 0 is a test hook of the failure detection: kernel 3 then never
+                       issues one row copy, its bounded wait (20 ms) expires and tsu_sync_status
+                       reports TSU_ETIMEOUT; outputs of that call are invalid. */
 } tsu_step_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -170,11 +174,72 @@ int tsu_init(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, cons
 int tsu_step_workspace(const tsu_grid* g, int dtype, size_t* bytes);
 
 /* Advance the state by nsteps leapfrog steps (spec hot path; scheme above).
- *   opts  NULL or tsu_step_opts (outputs, tuning).  ws/ws_bytes: device workspace, needed
- *         only when opts->energy is set.
+ *   opts  NULL or tsu_step_opts (outputs, tuning).  ws/ws_bytes: device workspace of
+ *         tsu_step_workspace bytes (or NULL), zero-filled by the caller before its first use;
+ *         needed for the energy and the temporally blocked kernel.
  * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
 int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, tsu_state* st,
                int64_t nsteps, const tsu_step_opts* opts, void* ws, size_t ws_bytes, void* stream);
+
+/* Number of checkpoint slots a forward run of nsteps steps (Taylor start included) fills when
+ * tsu_step_n is given ckpt_every: states m = 1, 1 + every, ... <= nsteps - 1.  Host only. */
+int64_t tsu_ckpt_slots(int64_t nsteps, int64_t ckpt_every);
+
+/* Bytes of device workspace tsu_adjoint needs: (ckpt_every + 4) fields of dtype, plus two FP32
+ * gradient accumulators for FP32 fields. */
+int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, size_t* bytes);
+
+/* Reverse-time discrete adjoint of the forward run "tsu_init(u0, u1) then tsu_step_n(nsteps-1)"
+ * for a receiver functional J(traces) (the paper has no adjoint; it is the exact reverse of the
+ * scheme above, with multipliers lam^n = g^n + (2I + B) lam^{n+1} - lam^{n+2}).
+ *   form      the form of that forward run (its checkpoints hold that form's two fields)
+ *   nsteps    S (final state u^S); ckpt_every, ckpt: the checkpoint store the forward filled
+ *             (tsu_ckpt_slots(S, every) slots); segments are recomputed from it
+ *   u0        device [ny][ld], the forward's initial displacement (boundary read as 0)
+ *   dtraces   device [S][nrec] of dtype: dJ/d(u^n at receiver r), n = 1..S
+ *   g_hx, g_hy  device double [ny][ld], overwritten with dJ/dhx, dJ/dhy (FP64 accumulation;
+ *             for FP32 fields FP32 partial sums over one segment are added into them)
+ *   g_u0, g_u1  device [ny][ld] of dtype, overwritten with dJ/du0, dJ/du1
+ * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
+int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_medium* m, int64_t nsteps,
+                int64_t ckpt_every, const void* ckpt, const void* u0, int32_t nrec, const int64_t* rec_idx,
+                const void* dtraces, double* g_hx, double* g_hy, void* g_u0, void* g_u1, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* One problem of a batched family (all FP32, same form): grid, time step, medium, state (nbuf = 4,
+ * initialised by tsu_init) and the number of steps to advance it. */
+typedef struct {
+  tsu_grid grid;
+  double tau;
+  tsu_medium medium;
+  tsu_state* state;
+  int64_t nsteps;
+} tsu_problem;
+
+/* Options of tsu_batch_run (NULL = defaults). */
+typedef struct {
+  int32_t tdepth; /* steps per batched pass: 4 or 8 (0 = 8) */
+  int32_t rows;   /* rows per chunk (0 = 256) */
+  int32_t reserved[2];
+} tsu_batch_opts;
+
+/* Bytes of device workspace tsu_batch_run needs for these problems (descriptors and tile table). */
+int tsu_batch_workspace(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, size_t* bytes);
+
+/* Advance a whole family of regularised problems (the eps-family (u_eps)_eps of Sec. 3.2, with
+ * different singularities, widths, grid sizes and time steps) together: every launch of the
+ * temporally blocked pass covers the tiles of all problems that still have tdepth steps to go;
+ * leftover steps (nsteps % tdepth) run one per pass.  Each problem ends in the same state as
+ * tsu_step_n(kernel 3) would leave it.  The call uploads descriptors (it synchronises with the
+ * host once) and updates every state's cur/aux/step; tsu_sync_status(ws) reports expired waits.
+ * Errors: TSU_EINVAL (mixed forms, non-FP32 fields, nbuf != 4), TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
+int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, void* ws, size_t ws_bytes,
+                  void* stream);
+
+/* Synchronise the stream, then read and clear the device status word in the workspace of
+ * tsu_step_n: TSU_OK, or TSU_ETIMEOUT if a bounded device-side wait of a kernel expired (that
+ * kernel stopped early; its outputs are invalid). */
+int tsu_sync_status(void* ws, size_t ws_bytes, void* stream);
 
 /* Energy E^{n-1/2} of the current pair (u^{n-1}, u^n) into energy_dev[0] (device double, or NULL)
  * and u^n at the receivers into trace (device [nrec], or NULL).  Does not step. */

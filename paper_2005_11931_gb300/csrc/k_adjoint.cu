@@ -1,0 +1,219 @@
+// Discrete adjoint of the leapfrog scheme (the paper has no adjoint; this is the exact reverse of
+// the scheme of k_step.cu, whose PDE is arXiv:2005.11931 Sec. 2 eq. (2.1) on the Sec. 3.3 box).
+//
+// For a receiver functional J(traces), g^n = S^T dJ/dtrace^n, the multipliers obey
+//   lam^n = g^n + (2I + B) lam^{n+1} - lam^{n+2},  n = S..1,   lam^{S+1} = lam^{S+2} = 0,
+//   dJ/du0 = (I + B/2) lam^1 - lam^2,  dJ/du1 = tau lam^1,
+//   dJ/dhx_ij += -cx (lam^{n+1}_{i+1,j} - lam^{n+1}_ij)(u^n_{i+1,j} - u^n_ij)   (n = 1..S-1, and
+//                with -cx/2, lam^1 and u^0 for the start), dJ/dhy likewise in j.
+// k_adjoint_pass computes lam^n from lam^{n+1} (5-point) and lam^{n+2} (centre), written over
+// lam^{n+2}, with the same register-streaming layout as the forward pass, and accumulates both
+// face gradients from lam^{n+1} and the recomputed forward state u^n.  In FP32 the face
+// gradients are summed in FP32 over one checkpoint segment and flushed into FP64 per segment.
+#include "stencil_common.cuh"
+
+namespace tsu {
+namespace {
+using namespace dev;
+
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<float> { using type = float; };
+template <>
+struct AccOf<double> { using type = double; };
+
+// MODE 0: lam_out = (2 lam_c - lam_pp) + B lam_c          (the recursion)
+// MODE 1: lam_out = (lam_c - lam_pp) + B lam_c / 2 = dJ/du0; g_u1 = tau lam_c   (the start)
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const int32_t ny, const int64_t ld,
+                                                      const typename ArithOf<T>::type ar, const T gwx, const T gwy,
+                                                      const T tau, const T* __restrict__ hx, const T* __restrict__ hy,
+                                                      const T* __restrict__ lam, const T* lam_pp, T* lam_out,
+                                                      const T* __restrict__ u, typename AccOf<T>::type* gx,
+                                                      typename AccOf<T>::type* gy, T* g_u1, const int rows) {
+  using A = typename AccOf<T>::type;
+  constexpr int V = Vec<T>::V;
+  const int lane = threadIdx.x & 31;
+  int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+  const bool active = i0 < ld;
+  if (!active) i0 = 0;
+  const int j0 = 1 + blockIdx.y * rows;
+  const int j1 = min(j0 + rows, ny - 1);
+  if (j0 >= j1) return;  // uniform per CTA
+
+  // u^n with its boundary nodes read as zero (the start pass reads the caller's u0)
+  auto umask = [&](Pack<T> v, int j) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int64_t i = i0 + e;
+      if (!(i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2)) v.a[e] = T(0);
+    }
+    return v;
+  };
+  auto u_at = [&](int64_t i, int j) -> T {
+    return (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2) ? u[(int64_t)j * ld + i] : T(0);
+  };
+
+  Pack<T> lm = ld_vec(lam + (int64_t)(j0 - 1) * ld + i0);
+  Pack<T> lc = ld_vec(lam + (int64_t)j0 * ld + i0);
+  Pack<T> hym = ld_vec(hy + (int64_t)(j0 - 1) * ld + i0);
+  Pack<T> uc = umask(ld_vec(u + (int64_t)j0 * ld + i0), j0);
+  for (int j = j0; j < j1; ++j) {
+    const int64_t row = (int64_t)j * ld + i0;
+    const Pack<T> ln = ld_vec(lam + row + ld);
+    const Pack<T> lp = ld_vec_cg(lam_pp + row);
+    const Pack<T> hxv = ld_vec(hx + row);
+    const Pack<T> hyv = ld_vec(hy + row);
+    const Pack<T> un = umask(ld_vec(u + row + ld), j + 1);
+    T ll = __shfl_up_sync(0xffffffffu, lc.a[V - 1], 1);
+    T hl = __shfl_up_sync(0xffffffffu, hxv.a[V - 1], 1);
+    T lr = __shfl_down_sync(0xffffffffu, lc.a[0], 1);
+    T ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
+    if (lane == 0) {
+      ll = (i0 > 0) ? lam[row - 1] : T(0);
+      hl = (i0 > 0) ? hx[row - 1] : T(0);
+    }
+    if (lane == 31) {
+      lr = (i0 + V < ld) ? lam[row + V] : T(0);
+      ur = u_at(i0 + V, j);
+    }
+    Pack<T> out, gu1;
+    A gxv[V], gyv[V], gy0[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int64_t i = i0 + e;
+      const T xl = (e == 0) ? ll : lc.a[e - 1];
+      const T xr = (e == V - 1) ? lr : lc.a[e + 1];
+      const T hxl = (e == 0) ? hl : hxv.a[e - 1];
+      const T b = ar.b(hxv.a[e], hxl, hyv.a[e], hym.a[e], lc.a[e], xl, xr, ln.a[e], lm.a[e]);
+      const bool interior = (i >= 1) && (i <= nx - 2);
+      T val;
+      if constexpr (MODE == 0) {
+        val = ar.lf(lc.a[e], lp.a[e], b);
+      } else {
+        if constexpr (sizeof(T) == 8)
+          val = __dadd_rn(__dsub_rn(lc.a[e], lp.a[e]), __dmul_rn(0.5, b));
+        else
+          val = (lc.a[e] - lp.a[e]) + 0.5f * b;
+        gu1.a[e] = interior ? tau * lc.a[e] : T(0);
+      }
+      out.a[e] = interior ? val : T(0);
+      // face gradients: x-face (i, i+1) on this row, y-face (j, j+1) on this column
+      const T uxr = (e == V - 1) ? ur : uc.a[e + 1];
+      const T dlx = xr - lc.a[e], dux = uxr - uc.a[e];
+      const T dly = ln.a[e] - lc.a[e], duy = un.a[e] - uc.a[e];
+      gxv[e] = (i <= nx - 2) ? (A)(gwx * (dlx * dux)) : A(0);
+      gyv[e] = interior ? (A)(gwy * (dly * duy)) : A(0);
+      gy0[e] = interior ? (A)(gwy * (lc.a[e] * uc.a[e])) : A(0);  // y-face (0, 1), used on row 1
+    }
+    if (active) {
+      if constexpr (MODE == 0)
+        st_vec(lam_out + row, out);
+      else {
+        st_vec(lam_out + row, out);
+        st_vec(g_u1 + row, gu1);
+      }
+      // the accumulators have the field's vector width (float4 / double2): 16-byte read-modify-write
+      Pack<A> ax = ld_vec_cg(gx + row), ay = ld_vec_cg(gy + row);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        ax.a[e] += gxv[e];
+        ay.a[e] += gyv[e];
+      }
+      st_vec(gx + row, ax);
+      st_vec(gy + row, ay);
+      if (j == 1) {
+        Pack<A> a0 = ld_vec_cg(gy + i0);
+#pragma unroll
+        for (int e = 0; e < V; ++e) a0.a[e] += gy0[e];
+        st_vec(gy + i0, a0);
+      }
+    }
+    lm = lc;
+    lc = ln;
+    hym = hyv;
+    uc = un;
+  }
+}
+
+// lam[rec_idx[r]] += g[r] for interior receiver nodes (boundary receivers record a constant 0)
+template <typename T>
+__global__ void k_inject(const int32_t nx, const int32_t ny, const int64_t ld, T* lam, const T* g, const int64_t* idx,
+                         const int32_t nrec) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrec) return;
+  const int64_t q = idx[r];
+  if (q < 0 || q >= (int64_t)ny * ld) return;
+  const int64_t j = q / ld, i = q - j * ld;
+  if (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2) atomicAdd(&lam[q], g[r]);
+}
+
+__global__ void k_flush(const int64_t total, float* g32x, float* g32y, double* gx, double* gy) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    gx[k] += (double)g32x[k];
+    gy[k] += (double)g32y[k];
+    g32x[k] = 0.0f;
+    g32y[k] = 0.0f;
+  }
+}
+
+template <typename T>
+typename ArithOf<T>::type arith(const StencilGeom& g) {
+  typename ArithOf<T>::type a;
+  a.cx = (T)g.cx;
+  a.cy = (T)g.cy;
+  return a;
+}
+
+template <typename T>
+cudaError_t pass_t(const StencilGeom& g, bool start, const void* hx, const void* hy, const void* lam,
+                   const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy, void* g_u1, cudaStream_t s) {
+  using A = typename AccOf<T>::type;
+  constexpr int V = Vec<T>::V;
+  const int rows = 32, threads = 128;
+  const int64_t cpc = (int64_t)threads * V;
+  dim3 grid((unsigned)((g.ld + cpc - 1) / cpc), (unsigned)((g.ny - 2 + rows - 1) / rows));
+  const T w = start ? T(0.5) : T(1);
+  const T gwx = -(T)g.cx * w, gwy = -(T)g.cy * w;
+  if (!start)
+    k_adjoint_pass<T, 0><<<grid, threads, 0, s>>>(g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx,
+                                                   (const T*)hy, (const T*)lam, (const T*)lam_pp, (T*)lam_out,
+                                                   (const T*)u, (A*)gx, (A*)gy, nullptr, rows);
+  else
+    k_adjoint_pass<T, 1><<<grid, threads, 0, s>>>(g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx,
+                                                   (const T*)hy, (const T*)lam, (const T*)lam_pp, (T*)lam_out,
+                                                   (const T*)u, (A*)gx, (A*)gy, (T*)g_u1, rows);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
+                                const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
+                                void* g_u1, cudaStream_t s) {
+  return dtype == TSU_F32 ? pass_t<float>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, s)
+                          : pass_t<double>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, s);
+}
+
+cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,
+                          int32_t nrec, cudaStream_t s) {
+  if (nrec <= 0) return cudaSuccess;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((nrec + threads - 1) / threads);
+  if (dtype == TSU_F32)
+    k_inject<float><<<blocks, threads, 0, s>>>(g.nx, g.ny, g.ld, (float*)lam, (const float*)gvals, idx, nrec);
+  else
+    k_inject<double><<<blocks, threads, 0, s>>>(g.nx, g.ny, g.ld, (double*)lam, (const double*)gvals, idx, nrec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flush(const StencilGeom& g, void* g32x, void* g32y, double* gx, double* gy, cudaStream_t s) {
+  const int64_t total = (int64_t)g.ny * g.ld;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_flush<<<(unsigned)blocks, 256, 0, s>>>(total, (float*)g32x, (float*)g32y, gx, gy);
+  return cudaGetLastError();
+}
+
+}  // namespace tsu

@@ -6,6 +6,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "tsu_internal.h"
 
 namespace {
@@ -198,21 +201,46 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   if (o.traces && (o.nrec == 0 || !o.rec_idx)) return fail(TSU_EINVAL, "traces need nrec > 0 and rec_idx");
   if (o.ckpt && (o.ckpt_every < 1 || o.ckpt_slots < 1 || !aligned16(o.ckpt)))
     return fail(TSU_EINVAL, "checkpoints need ckpt_every >= 1, ckpt_slots >= 1 and an aligned store");
-  if (o.kernel < 0 || o.kernel > 3) return fail(TSU_EINVAL, "kernel must be 0..3");
+  if (o.kernel < 0 || o.kernel > 3 || o.kernel == 2) return fail(TSU_EINVAL, "kernel must be 0, 1 or 3");
   if (o.rows < 0) return fail(TSU_EINVAL, "rows must be >= 0");
+  if (o.tdepth != 0 && !tsu::tb_supported_depth(o.tdepth)) return fail(TSU_EINVAL, "tdepth must be 0, 4 or 8");
+  const bool have_ws = ws && ws_bytes >= tsu::energy_ws_bytes(g->ny, g->ld);
   tsu::EnergyWs ews{};
-  if (o.energy) {
-    if (!ws) return fail(TSU_ENOMEM, "energy needs a workspace (tsu_step_workspace)");
-    if (ws_bytes < tsu::energy_ws_bytes(g->ny, g->ld))
-      return fail(TSU_ENOMEM, "workspace %zu B < %zu B", ws_bytes, tsu::energy_ws_bytes(g->ny, g->ld));
+  if (o.energy && !ws) return fail(TSU_ENOMEM, "energy needs a workspace (tsu_step_workspace)");
+  if (ws && !have_ws)
+    return fail(TSU_ENOMEM, "workspace %zu B < %zu B", ws_bytes, tsu::energy_ws_bytes(g->ny, g->ld));
+  if (have_ws) {
     ews = tsu::energy_ws_carve(ws, ws_bytes, g->ny, g->ld);
     cudaError_t e = cudaMemsetAsync(ews.counter, 0, sizeof(unsigned int), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n workspace reset");
   }
+  // kernel choice: the temporally blocked pass needs FP32 fields, four state buffers, a workspace
+  // (status word), and no per-step side outputs other than the energy
+  const bool tb_possible = dtype == TSU_F32 && st->nbuf == 4 && have_ws && !o.traces && !o.ckpt;
+  if (o.kernel == 3 && !tb_possible)
+    return fail(TSU_EINVAL, "kernel 3 needs FP32, nbuf = 4, a workspace and no traces/checkpoints");
+  const int tdepth = o.tdepth ? o.tdepth : 8;
+  const bool use_tb = tb_possible && nsteps >= tdepth &&
+                      (o.kernel == 3 || (o.kernel == 0 && (int64_t)g->nx * g->ny >= (int64_t)1 << 20));
+  int tb_rows = o.rows ? o.rows : 512;
+  if (tb_rows < 16) tb_rows = 16;
   const tsu::StencilGeom sg = geom(g, tau);
   const size_t field_bytes = (size_t)g->ny * g->ld * elem_size(dtype);
   cudaStream_t s = (cudaStream_t)stream;
-  for (int64_t k = 0; k < nsteps; ++k) {
+  int64_t k = 0;
+  if (use_tb) {
+    for (; k + tdepth <= nsteps; k += tdepth) {
+      const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
+      cudaError_t e = tsu::launch_step_tb(sg, st->form, tdepth, m->hx, m->hy, st->buf[st->cur], st->buf[st->aux],
+                                          st->buf[f1], st->buf[f2], o.energy ? o.energy + k : nullptr, ews,
+                                          ews.status, tb_rows, o.reserved, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n temporally blocked launch");
+      st->cur = f1;
+      st->aux = f2;
+      st->step += tdepth;
+    }
+  }
+  for (; k < nsteps; ++k) {
     tsu::PassOut po{};
     po.energy = o.energy ? o.energy + k : nullptr;
     po.ews = ews;
@@ -228,11 +256,11 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
     cudaError_t e;
     if (st->form == TSU_FORM_STANDARD) {
       e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, st->buf[st->aux], st->buf[st->cur], nullptr,
-                           st->buf[st->aux], po, true, o.rows, s);
+                           st->buf[st->aux], po, true, use_tb ? 0 : o.rows, s);
     } else {
       const int f = scratch_index(st, -1);
       e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, nullptr, st->buf[st->cur], st->buf[st->aux],
-                           st->buf[f], po, true, o.rows, s);
+                           st->buf[f], po, true, use_tb ? 0 : o.rows, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n launch");
     if (st->form == TSU_FORM_STANDARD) {
@@ -244,6 +272,287 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
     }
     st->step += 1;
   }
+  return TSU_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint: workspace = 2 multiplier fields + (E+1) recomputed states + 1 restore field
+// (u^{m-1} or v^m) [+ 2 FP32 gradient accumulators for FP32 fields]
+// ---------------------------------------------------------------------------------------------
+static size_t adjoint_ws_bytes(const tsu_grid* g, int dtype, int64_t every) {
+  const size_t fb = (size_t)g->ny * g->ld * elem_size(dtype);
+  size_t b = (size_t)(every + 4) * fb;
+  if (dtype == TSU_F32) b += 2 * (size_t)g->ny * g->ld * sizeof(float);
+  return b + 256;
+}
+
+int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, size_t* bytes) {
+  g_err[0] = 0;
+  TRY(check_grid(g));
+  TRY(check_dtype(dtype));
+  if (!bytes) return fail(TSU_EINVAL, "bytes is NULL");
+  if (nsteps < 1 || ckpt_every < 1) return fail(TSU_EINVAL, "nsteps and ckpt_every must be >= 1");
+  *bytes = adjoint_ws_bytes(g, dtype, ckpt_every);
+  return TSU_OK;
+}
+
+int64_t tsu_ckpt_slots(int64_t nsteps, int64_t ckpt_every) {
+  if (nsteps < 2 || ckpt_every < 1) return 0;
+  return (nsteps - 2) / ckpt_every + 1;
+}
+
+int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_medium* m, int64_t nsteps,
+                int64_t ckpt_every, const void* ckpt, const void* u0, int32_t nrec, const int64_t* rec_idx,
+                const void* dtraces, double* g_hx, double* g_hy, void* g_u0, void* g_u1, void* ws, size_t ws_bytes,
+                void* stream) {
+  g_err[0] = 0;
+  TRY(check_grid(g));
+  TRY(check_dtype(dtype));
+  TRY(check_cfl(g, tau, m));
+  TRY(check_field(m->hx, "hx"));
+  TRY(check_field(m->hy, "hy"));
+  TRY(check_field(u0, "u0"));
+  TRY(check_field(g_hx, "g_hx"));
+  TRY(check_field(g_hy, "g_hy"));
+  TRY(check_field(g_u0, "g_u0"));
+  TRY(check_field(g_u1, "g_u1"));
+  if (form != TSU_FORM_STANDARD && form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
+  if (nsteps < 1 || ckpt_every < 1) return fail(TSU_EINVAL, "nsteps and ckpt_every must be >= 1");
+  const int64_t C = tsu_ckpt_slots(nsteps, ckpt_every);
+  if (C > 0) TRY(check_field(ckpt, "ckpt"));
+  if (nrec < 0 || (nrec > 0 && (!rec_idx || !dtraces))) return fail(TSU_EINVAL, "receivers need rec_idx and dtraces");
+  if (!ws || ws_bytes < adjoint_ws_bytes(g, dtype, ckpt_every))
+    return fail(TSU_ENOMEM, "adjoint workspace %zu B < %zu B", ws_bytes, adjoint_ws_bytes(g, dtype, ckpt_every));
+  TRY(check_field(ws, "workspace"));
+  cudaStream_t s = (cudaStream_t)stream;
+  const tsu::StencilGeom sg = geom(g, tau);
+  const size_t es = elem_size(dtype);
+  const size_t fb = (size_t)g->ny * g->ld * es;
+  char* w = (char*)ws;
+  char* lam[2] = {w, w + fb};                    // lam^{n+1}, lam^{n+2}
+  char* seg = w + 2 * fb;                        // seg[k] = u^{m_c + k}, k = 0..E
+  char* extra = seg + (size_t)(ckpt_every + 1) * fb;  // u^{m_c - 1} (standard) or v (increment)
+  char* g32 = extra + fb;                        // FP32 accumulators [2][ny][ld]
+  const size_t f32b = (size_t)g->ny * g->ld * sizeof(float);
+  void* accx = dtype == TSU_F32 ? (void*)g32 : (void*)g_hx;
+  void* accy = dtype == TSU_F32 ? (void*)(g32 + f32b) : (void*)g_hy;
+  auto segp = [&](int64_t k) { return (void*)(seg + (size_t)k * fb); };
+  cudaError_t e = cudaMemsetAsync(ws, 0, adjoint_ws_bytes(g, dtype, ckpt_every) - 256, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g_hx, 0, (size_t)g->ny * g->ld * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g_hy, 0, (size_t)g->ny * g->ld * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint reset");
+  int a = 0;  // lam[a] = lam^{n+1}, lam[a^1] = lam^{n+2}
+  auto step_back = [&](int64_t n, const void* un) -> cudaError_t {
+    cudaError_t r = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam[a], lam[a ^ 1], lam[a ^ 1], un, accx,
+                                             accy, nullptr, s);
+    if (r == cudaSuccess && nrec > 0)
+      r = tsu::launch_inject(sg, dtype, lam[a ^ 1], (const char*)dtraces + (size_t)(n - 1) * nrec * es, rec_idx, nrec,
+                             s);
+    a ^= 1;  // lam[a] = lam^n now
+    return r;
+  };
+  if (C == 0) {  // nsteps == 1: lam^1 = g^1 (the gradient term of n = 1 vanishes with lam^2 = 0)
+    e = step_back(1, segp(0));
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
+  }
+  for (int64_t c = C - 1; c >= 0; --c) {
+    const int64_t mc = 1 + c * ckpt_every;
+    const int64_t mend = (mc + ckpt_every < nsteps) ? mc + ckpt_every : nsteps;
+    // restore the checkpointed state, then recompute u^{mc+1}..u^{mend} into seg[1..]
+    const char* slot = (const char*)ckpt + (size_t)c * 2 * fb;
+    if (form == TSU_FORM_STANDARD) {
+      e = cudaMemcpyAsync(extra, slot, fb, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(segp(0), slot + fb, fb, cudaMemcpyDeviceToDevice, s);
+    } else {
+      e = cudaMemcpyAsync(segp(0), slot, fb, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(extra, slot + fb, fb, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint restore");
+    tsu::PassOut none{};
+    for (int64_t k = 0; k < mend - mc; ++k) {
+      if (form == TSU_FORM_STANDARD)
+        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, k == 0 ? (void*)extra : segp(k - 1), segp(k), nullptr,
+                             segp(k + 1), none, true, 0, s);
+      else
+        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, nullptr, segp(k), extra, segp(k + 1), none, true, 0, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint recompute");
+    }
+    const int64_t nlo = (c == 0) ? 1 : mc + 1;
+    for (int64_t n = mend; n >= nlo; --n) {
+      e = step_back(n, segp(n - mc));
+      if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
+    }
+    if (dtype == TSU_F32) {
+      e = tsu::launch_flush(sg, accx, accy, g_hx, g_hy, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint flush");
+    }
+  }
+  // the start: dJ/du0 = (I + B/2) lam^1 - lam^2, dJ/du1 = tau lam^1, face terms with u^0 and weight 1/2
+  e = tsu::launch_adjoint_pass(sg, dtype, true, m->hx, m->hy, lam[a], lam[a ^ 1], g_u0, u0, accx, accy, g_u1, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g_u0, 0, (size_t)g->ld * es, s);  // boundary rows of the outputs
+  if (e == cudaSuccess) e = cudaMemsetAsync((char*)g_u0 + (size_t)(g->ny - 1) * g->ld * es, 0, (size_t)g->ld * es, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g_u1, 0, (size_t)g->ld * es, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync((char*)g_u1 + (size_t)(g->ny - 1) * g->ld * es, 0, (size_t)g->ld * es, s);
+  if (e == cudaSuccess && dtype == TSU_F32) e = tsu::launch_flush(sg, accx, accy, g_hx, g_hy, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint start");
+  return TSU_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched family
+// ---------------------------------------------------------------------------------------------
+static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, int* k_out,
+                        int* rows_out, int64_t* ntiles_out, size_t* bytes_out) {
+  if (nprob < 1 || !probs) return fail(TSU_EINVAL, "need at least one problem");
+  const int k = (opts && opts->tdepth) ? opts->tdepth : 8;
+  const int rows = (opts && opts->rows) ? opts->rows : 256;
+  if (!tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "tdepth must be 4 or 8");
+  if (rows < 16) return fail(TSU_EINVAL, "rows must be >= 16");
+  const int W = tsu::tb_strip_width(k);
+  int64_t ntiles = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const tsu_grid& g = probs[i].grid;
+    TRY(check_grid(&g));
+    ntiles += ((g.ld + W - 1) / W) * ((g.ny - 2 + rows - 1) / rows);
+  }
+  *k_out = k;
+  *rows_out = rows;
+  *ntiles_out = ntiles;
+  *bytes_out = 256 + 3 * (size_t)nprob * ((tsu::tb_args_bytes() + 15) / 16 * 16) + (size_t)ntiles * 16;
+  return TSU_OK;
+}
+
+int tsu_batch_workspace(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, size_t* bytes) {
+  g_err[0] = 0;
+  if (!bytes) return fail(TSU_EINVAL, "bytes is NULL");
+  int k, rows;
+  int64_t nt;
+  return batch_layout(nprob, probs, opts, &k, &rows, &nt, bytes);
+}
+
+int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, void* ws, size_t ws_bytes,
+                  void* stream) {
+  g_err[0] = 0;
+  int k, rows;
+  int64_t ntiles;
+  size_t need;
+  TRY(batch_layout(nprob, probs, opts, &k, &rows, &ntiles, &need));
+  if (!ws || ws_bytes < need) return fail(TSU_ENOMEM, "batch workspace %zu B < %zu B", ws_bytes, need);
+  TRY(check_field(ws, "workspace"));
+  const int form = probs[0].state ? probs[0].state->form : -1;
+  for (int i = 0; i < nprob; ++i) {
+    const tsu_problem& p = probs[i];
+    TRY(check_cfl(&p.grid, p.tau, &p.medium));
+    TRY(check_field(p.medium.hx, "hx"));
+    TRY(check_field(p.medium.hy, "hy"));
+    TRY(check_state(p.state, true));
+    if (p.state->form != form) return fail(TSU_EINVAL, "problem %d: all problems need the same form", i);
+    if (p.state->nbuf != 4) return fail(TSU_EINVAL, "problem %d: nbuf must be 4", i);
+    if (p.nsteps < 0) return fail(TSU_EINVAL, "problem %d: nsteps < 0", i);
+  }
+  const int W = tsu::tb_strip_width(k);
+  const size_t ab = (tsu::tb_args_bytes() + 15) / 16 * 16;
+  // problems in decreasing order of blocked rounds: round r launches a prefix of the tile table
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return probs[a].nsteps / k > probs[b].nsteps / k; });
+  std::vector<int32_t> tiles;  // int4 per tile
+  std::vector<int64_t> prefix;  // tiles of problems order[0..i]
+  tiles.reserve((size_t)ntiles * 4);
+  for (int oi = 0; oi < nprob; ++oi) {
+    const int i = order[oi];
+    const tsu_grid& g = probs[i].grid;
+    const int strips = (int)((g.ld + W - 1) / W), chunks = (int)((g.ny - 2 + rows - 1) / rows);
+    for (int c = 0; c < chunks; ++c)
+      for (int st = 0; st < strips; ++st) {
+        tiles.push_back(i);
+        tiles.push_back(st);
+        tiles.push_back(c);
+        tiles.push_back(0);
+      }
+    prefix.push_back((int64_t)tiles.size() / 4);
+  }
+  // descriptor sets: launch 0, then the two role assignments that alternate from launch 1 on
+  std::vector<unsigned char> host(3 * (size_t)nprob * ab, 0);
+  std::vector<tsu_state> sim(nprob);
+  char* base = (char*)ws;
+  int* status = (int*)(base + 4);
+  for (int i = 0; i < nprob; ++i) sim[i] = *probs[i].state;
+  for (int set = 0; set < 3; ++set) {
+    for (int i = 0; i < nprob; ++i) {
+      tsu_state& st = sim[i];
+      const int f1 = scratch_index(&st, -1), f2 = scratch_index(&st, f1);
+      tsu::tb_fill_args(&host[((size_t)set * nprob + i) * ab], geom(&probs[i].grid, probs[i].tau), probs[i].medium.hx,
+                        probs[i].medium.hy, st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], status, rows);
+      st.cur = f1;
+      st.aux = f2;
+    }
+  }
+  for (int i = 0; i < nprob; ++i) {  // the inputs of launch 3 must be those of launch 1
+    tsu_state t = *probs[i].state;
+    int cur1 = -1, aux1 = -1;
+    for (int q = 1; q <= 3; ++q) {
+      const int f1 = scratch_index(&t, -1), f2 = scratch_index(&t, f1);
+      t.cur = f1;
+      t.aux = f2;
+      if (q == 1) {
+        cur1 = t.cur;
+        aux1 = t.aux;
+      }
+    }
+    if (t.cur != cur1 || t.aux != aux1) return fail(TSU_EINVAL, "problem %d: unexpected buffer roles", i);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  char* desc = base + 256;
+  char* tdev = desc + 3 * (size_t)nprob * ab;
+  cudaError_t e = cudaMemcpyAsync(desc, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tdev, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffers go out of scope
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run upload");
+  const int64_t rounds_max = probs[order[0]].nsteps / k;
+  for (int64_t r = 0; r < rounds_max; ++r) {
+    // tiles of the problems that still have a full round
+    int64_t nt = 0;
+    for (int oi = 0; oi < nprob; ++oi)
+      if (probs[order[oi]].nsteps / k > r) nt = prefix[oi];
+    const int set = r == 0 ? 0 : ((r & 1) ? 1 : 2);
+    e = tsu::launch_step_tb_batched(form, k, desc + (size_t)set * nprob * ab, tdev, nt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run launch");
+  }
+  // host-side roles after the blocked rounds, then the leftover single steps per problem
+  for (int i = 0; i < nprob; ++i) {
+    tsu_state* st = probs[i].state;
+    const int64_t rounds = probs[i].nsteps / k;
+    for (int64_t r = 0; r < rounds; ++r) {
+      const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
+      st->cur = f1;
+      st->aux = f2;
+    }
+    st->step += rounds * k;
+    const int64_t left = probs[i].nsteps - rounds * k;
+    if (left > 0) {
+      tsu_step_opts o;
+      memset(&o, 0, sizeof o);
+      o.kernel = 1;
+      const int rc = tsu_step_n(&probs[i].grid, TSU_F32, probs[i].tau, &probs[i].medium, st, left, &o, nullptr, 0,
+                                stream);
+      if (rc != TSU_OK) return rc;
+    }
+  }
+  return TSU_OK;
+}
+
+int tsu_sync_status(void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  if (!ws || ws_bytes < 256) return fail(TSU_EINVAL, "workspace missing");
+  int h = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&h, (char*)ws + 4, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync((char*)ws + 4, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_sync_status");
+  if (h != TSU_OK) return fail(h, "device reported status %d (a bounded wait expired)", h);
   return TSU_OK;
 }
 

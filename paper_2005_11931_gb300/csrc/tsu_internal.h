@@ -24,9 +24,11 @@ struct StencilGeom {
   double dxdy;
 };
 
-// Workspace for the energy reduction: a ticket counter then per-CTA FP64 partials.
+// Workspace of the steppers: a ticket counter and a device status word in the first 256 bytes,
+// then per-CTA FP64 energy partials.
 struct EnergyWs {
   unsigned int* counter;
+  int* status;
   double* partials;
   int64_t capacity;  // number of partial slots
 };
@@ -60,5 +62,29 @@ cudaError_t launch_init(const StencilGeom& g, int dtype, int form, const void* h
 cudaError_t launch_step(const StencilGeom& g, int dtype, int form, const void* hx, const void* hy,
                         const void* u_prev, const void* u_cur, void* v, void* u_next, const PassOut& o,
                         bool store, int rows, cudaStream_t s);
+
+// Temporally blocked FP32 pass (k_step_tb.cu): k in {4, 8} steps per launch.
+bool tb_supported_depth(int k);
+int64_t tb_energy_slots(int64_t ny, int64_t ld, int k, int rows);
+cudaError_t launch_step_tb(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
+                           const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int* status,
+                           int rows, int debug_flags, cudaStream_t s);
+
+// Batched family (k_step_tb.cu): per-problem descriptors (tb_args_bytes() each, filled on the
+// host by tb_fill_args) and an int4 tile table (problem, strip, chunk, 0).
+size_t tb_args_bytes();
+int tb_strip_width(int k);
+void tb_fill_args(void* dst, const StencilGeom& g, const void* hx, const void* hy, const void* u, const void* p,
+                  void* out_a, void* out_b, int* status, int rows);
+cudaError_t launch_step_tb_batched(int form, int k, const void* probs_dev, const void* tiles_dev, int64_t ntiles,
+                                   cudaStream_t s);
+
+// Adjoint (k_adjoint.cu).
+cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
+                                const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
+                                void* g_u1, cudaStream_t s);
+cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,
+                          int32_t nrec, cudaStream_t s);
+cudaError_t launch_flush(const StencilGeom& g, void* g32x, void* g32y, double* gx, double* gy, cudaStream_t s);
 
 }  // namespace tsu

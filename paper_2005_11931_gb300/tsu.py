@@ -72,6 +72,15 @@ class StepOpts(C.Structure):
                 ("rows", C.c_int32), ("tdepth", C.c_int32), ("reserved", C.c_int32)]
 
 
+class Problem(C.Structure):
+    _fields_ = [("grid", Grid), ("tau", C.c_double), ("medium", Medium), ("state", C.POINTER(State)),
+                ("nsteps", C.c_int64)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("tdepth", C.c_int32), ("rows", C.c_int32), ("reserved", C.c_int32 * 2)]
+
+
 _lib = None
 
 
@@ -93,6 +102,13 @@ def load():
         "tsu_step_workspace": ([C.POINTER(Grid), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
         "tsu_step_n": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), i64,
                         C.POINTER(StepOpts), vp, C.c_size_t, vp], C.c_int),
+        "tsu_sync_status": ([vp, C.c_size_t, vp], C.c_int),
+        "tsu_ckpt_slots": ([i64, i64], i64),
+        "tsu_batch_workspace": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), C.POINTER(C.c_size_t)], C.c_int),
+        "tsu_batch_run": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), vp, C.c_size_t, vp], C.c_int),
+        "tsu_adjoint_workspace": ([C.POINTER(Grid), C.c_int, i64, i64, C.POINTER(C.c_size_t)], C.c_int),
+        "tsu_adjoint": ([C.POINTER(Grid), C.c_int, C.c_int, dbl, C.POINTER(Medium), i64, i64, vp, vp, i32, vp, vp,
+                         vp, vp, vp, vp, vp, C.c_size_t, vp], C.c_int),
         "tsu_observe": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), vp, i32, vp, vp, vp,
                          C.c_size_t, vp], C.c_int),
     }
@@ -109,7 +125,7 @@ def declared_symbols() -> list[str]:
     import re
     hdr = os.path.join(os.path.dirname(_HERE), "include", "tsu.h")
     text = open(hdr).read()
-    return sorted(set(re.findall(r"^\s*(?:int|double|const char\*)\s+(tsu_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|double|const char\*)\s+(tsu_\w+)\s*\(", text, re.M)))
 
 
 def _check(rc: int, func: str):
@@ -190,6 +206,58 @@ def tsu_step_n(g: Grid, dtype, tau: float, medium: Medium, state: State, nsteps:
     _check(rc, "tsu_step_n")
 
 
+def tsu_sync_status(ws, ws_bytes: int, stream=None):
+    """Synchronise and raise TsuError if a kernel recorded an expired bounded wait."""
+    _check(load().tsu_sync_status(_ptr(ws), int(ws_bytes), _stream(stream)), "tsu_sync_status")
+
+
+def _problems(sims, nsteps):
+    arr = (Problem * len(sims))()
+    for k, (sim, n) in enumerate(zip(sims, nsteps)):
+        arr[k].grid = sim.g
+        arr[k].tau = sim.tau
+        arr[k].medium = sim.medium
+        arr[k].state = C.pointer(sim.state)
+        arr[k].nsteps = int(n)
+    return arr
+
+
+def tsu_batch_workspace(sims, nsteps, tdepth: int = 0, rows: int = 0) -> int:
+    arr = _problems(sims, nsteps)
+    o = BatchOpts(int(tdepth), int(rows))
+    n = C.c_size_t(0)
+    _check(load().tsu_batch_workspace(len(sims), arr, C.byref(o), C.byref(n)), "tsu_batch_workspace")
+    return int(n.value)
+
+
+def tsu_batch_run(sims, nsteps, ws, ws_bytes: int, tdepth: int = 0, rows: int = 0, stream=None):
+    """Advance every Simulation in ``sims`` by its entry of ``nsteps`` in batched launches."""
+    arr = _problems(sims, nsteps)
+    o = BatchOpts(int(tdepth), int(rows))
+    rc = load().tsu_batch_run(len(sims), arr, C.byref(o), _ptr(ws), int(ws_bytes), _stream(stream))
+    _check(rc, "tsu_batch_run")
+
+
+def tsu_ckpt_slots(nsteps: int, ckpt_every: int) -> int:
+    return int(load().tsu_ckpt_slots(int(nsteps), int(ckpt_every)))
+
+
+def tsu_adjoint_workspace(g: Grid, dtype, nsteps: int, ckpt_every: int) -> int:
+    n = C.c_size_t(0)
+    _check(load().tsu_adjoint_workspace(C.byref(g), dtype_code(dtype), int(nsteps), int(ckpt_every), C.byref(n)),
+           "tsu_adjoint_workspace")
+    return int(n.value)
+
+
+def tsu_adjoint(g: Grid, dtype, form: int, tau: float, medium: Medium, nsteps: int, ckpt_every: int, ckpt, u0,
+                rec_idx, dtraces, g_hx, g_hy, g_u0, g_u1, ws, ws_bytes: int, stream=None):
+    nrec = 0 if rec_idx is None else int(rec_idx.numel())
+    rc = load().tsu_adjoint(C.byref(g), dtype_code(dtype), int(form), tau, C.byref(medium), int(nsteps),
+                            int(ckpt_every), _ptr(ckpt), _ptr(u0), nrec, _ptr(rec_idx), _ptr(dtraces), _ptr(g_hx),
+                            _ptr(g_hy), _ptr(g_u0), _ptr(g_u1), _ptr(ws), int(ws_bytes), _stream(stream))
+    _check(rc, "tsu_adjoint")
+
+
 def tsu_observe(g: Grid, dtype, tau: float, medium: Medium, state: State, energy_dev=None, rec_idx=None,
                 trace=None, ws=None, ws_bytes: int = 0, stream=None):
     nrec = 0 if rec_idx is None else int(rec_idx.numel())
@@ -247,7 +315,7 @@ class Simulation:
 
     def step(self, nsteps: int, energy: torch.Tensor | None = None, rec_idx: torch.Tensor | None = None,
              traces: torch.Tensor | None = None, ckpt: torch.Tensor | None = None, ckpt_every: int = 0,
-             kernel: int = 0, rows: int = 0, tdepth: int = 0, stream=None):
+             kernel: int = 0, rows: int = 0, tdepth: int = 0, debug: int = 0, stream=None):
         o = StepOpts()
         o.energy = _ptr(energy)
         o.nrec = 0 if rec_idx is None else int(rec_idx.numel())
@@ -256,7 +324,7 @@ class Simulation:
         o.ckpt = _ptr(ckpt)
         o.ckpt_every = int(ckpt_every)
         o.ckpt_slots = 0 if ckpt is None else int(ckpt.shape[0])
-        o.kernel, o.rows, o.tdepth = int(kernel), int(rows), int(tdepth)
+        o.kernel, o.rows, o.tdepth, o.reserved = int(kernel), int(rows), int(tdepth), int(debug)
         tsu_step_n(self.g, self.dtype, self.tau, self.medium, self.state, nsteps, o, self.ws, self.ws.numel(), stream)
 
     def observe(self, energy: torch.Tensor | None = None, rec_idx=None, trace=None, stream=None):

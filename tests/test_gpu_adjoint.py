@@ -1,0 +1,148 @@
+"""GPU tests of the discrete adjoint (tsu_adjoint) and the autograd wrapper.
+
+The adjoint must equal the oracle's FP64 discrete adjoint (same recursion, same order) and the
+derivative of the forward map (central differences of the oracle's forward), for both forward
+forms, any checkpoint period, duplicate and boundary receivers.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2005_11931_gb300 import inputs, tsu
+from paper_2005_11931_gb300.autograd import TsunamiConfig, tsunami_traces
+from tests.gpu_helpers import relerr
+
+pytestmark = pytest.mark.gpu
+
+DEPTH = dict(background=1.0, eps=0.06, mollifier=0, sings=[(0, 1, 0.5, 0.5, 0.5), (2, 1, 0.002, 0.4, 0.6)])
+
+
+def gpu_forward_adjoint(nx, ny, depth, u0n, u1n, S, rec_ij, dtr, dtype, form, every):
+    """Forward with checkpoints through tsu_step_n, then tsu_adjoint.  Returns numpy gradients."""
+    sim = tsu.Simulation.create(nx, depth, dtype=dtype, form=form, ny=ny, nbuf=3)
+    g = sim.g
+    tdt = tsu.DTYPES[sim.dtype]
+    pad = lambda a: torch.from_numpy(np.pad(a[:, :nx], ((0, 0), (0, g.ld - nx)))).to(tdt).cuda()
+    u0, u1 = pad(u0n), pad(u1n)
+    sim.init(u0, u1)
+    slots = max(tsu.tsu_ckpt_slots(S, every), 1)
+    ck = torch.zeros((slots, 2, g.ny, g.ld), dtype=tdt, device="cuda")
+    if S > 1:
+        sim.step(S - 1, ckpt=ck, ckpt_every=every)
+    rec = torch.from_numpy(inputs.flat_index(rec_ij, g.ld)).cuda()
+    dt = torch.from_numpy(dtr).to(tdt).cuda()
+    out = {k: torch.zeros((g.ny, g.ld), dtype=torch.float64 if k in ("g_hx", "g_hy") else tdt, device="cuda")
+           for k in ("g_hx", "g_hy", "g_u0", "g_u1")}
+    wsb = tsu.tsu_adjoint_workspace(g, sim.dtype, S, every)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    tsu.tsu_adjoint(g, sim.dtype, form, sim.tau, sim.medium, S, every, ck, u0, rec, dt, out["g_hx"], out["g_hy"],
+                    out["g_u0"], out["g_u1"], ws, wsb)
+    torch.cuda.synchronize()
+    return {k: v[:, :nx].double().cpu().numpy() for k, v in out.items()}, sim.tau
+
+
+def receivers(nx, ny):
+    rng = np.random.default_rng(inputs.SEED)
+    rec = inputs.receivers_on_row(nx, 0.7, 6, rng)
+    # a duplicate and a boundary receiver
+    return np.concatenate([rec, rec[2:3], np.array([[0, ny // 2]])])
+
+
+@pytest.mark.parametrize("form", [tsu.TSU_FORM_STANDARD, tsu.TSU_FORM_INCREMENT])
+@pytest.mark.parametrize("every,S", [(1, 30), (7, 61), (64, 61), (10, 2), (5, 1)])
+def test_fp64_adjoint_matches_oracle(form, every, S):
+    nx, ny = 61, 47
+    rng = np.random.default_rng(11)
+    u0 = inputs.random_field(nx, ny, None, rng)
+    u1 = inputs.random_field(nx, ny, None, rng)
+    rec = receivers(nx, ny)
+    dtr = rng.standard_normal((S, len(rec)))
+    gg, tau = gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f64", form, every)
+    og = oracle.grid(nx, ny)
+    hx, hy, ext = oracle.make_depth(og, DEPTH)
+    ref = oracle.adjoint(og, tau, hx, hy, u0, u1, S, inputs.flat_index(rec, nx), dtr)
+    tol = 1e-12 if form == tsu.TSU_FORM_STANDARD else 1e-10  # the increment form rounds its states differently
+    for k in ("g_hx", "g_hy", "g_u0", "g_u1"):
+        assert relerr(gg[k], ref[k]) <= tol, (k, relerr(gg[k], ref[k]))
+
+
+def test_fp64_adjoint_independent_of_checkpoint_period():
+    nx, ny, S = 90, 70, 150
+    rng = np.random.default_rng(2)
+    u0 = inputs.gaussian_hump(nx, ny, None, 0.4, 0.5, 0.1)
+    u1 = np.zeros_like(u0)
+    rec = receivers(nx, ny)
+    dtr = rng.standard_normal((S, len(rec)))
+    a, _ = gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f64", tsu.TSU_FORM_STANDARD, 1)
+    b, _ = gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f64", tsu.TSU_FORM_STANDARD, 37)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_fp32_adjoint_directional_derivatives_match_central_differences():
+    """FP32 fields, FP64-accumulated face gradients: <dJ/dh, d> against central differences of the
+    oracle's FP64 forward map along seeded random directions, relative error <= 1e-4."""
+    n, S, every = 97, 240, 64
+    depth = dict(background=1.0, eps=0.04, mollifier=0, sings=[(0, 1, 0.5, 0.5, 0.5)])
+    rng = np.random.default_rng(inputs.SEED)
+    u0 = inputs.gaussian_hump(n, n, None, 0.42, 0.70, 0.06)
+    u1 = np.zeros_like(u0)
+    rec = inputs.receivers_on_row(n, 0.8, 16, rng)
+    og = oracle.grid(n, n)
+    hx, hy, ext = oracle.make_depth(og, depth)
+    tau = 0.4 * og.dx / math.sqrt(max(ext[1], ext[3]))
+    ridx = inputs.flat_index(rec, n)
+    obs = oracle.forward(og, tau, hx * 1.05, hy * 1.05, u0, None, S, want_energy=False, rec_idx=ridx)["traces"]
+
+    def J(hx_, hy_):
+        tr = oracle.forward(og, tau, hx_, hy_, u0, None, S, want_energy=False, rec_idx=ridx)["traces"]
+        return 0.5 * float(np.sum((tr - obs) ** 2)), tr
+
+    J0, tr0 = J(hx, hy)
+    gg, gtau = gpu_forward_adjoint(n, n, depth, u0, u1, S, rec, tr0 - obs, "f32", tsu.TSU_FORM_INCREMENT, every)
+    assert abs(gtau / tau - 1) < 1e-6
+    mx = np.zeros_like(hx)
+    mx[:, : n - 1] = 1
+    my = np.zeros_like(hy)
+    my[: n - 1, :] = 1
+    for trial in range(8):
+        dx_ = rng.standard_normal(hx.shape) * mx
+        dy_ = rng.standard_normal(hy.shape) * my
+        st = 1e-4
+        fd = (J(hx + st * dx_, hy + st * dy_)[0] - J(hx - st * dx_, hy - st * dy_)[0]) / (2 * st)
+        ad = float(np.sum(gg["g_hx"] * dx_) + np.sum(gg["g_hy"] * dy_))
+        assert abs(fd - ad) <= 1e-4 * abs(fd), (trial, fd, ad)
+
+
+def test_tsunami_fn_autograd_matches_oracle_adjoint():
+    n, S = 80, 120
+    depth = dict(background=1.0, eps=0.05, mollifier=0, sings=[(0, 1, 0.5, 0.5, 0.5)])
+    sim = tsu.Simulation.create(n, depth, dtype="f64", form=tsu.TSU_FORM_STANDARD)
+    g = sim.g
+    rng = np.random.default_rng(4)
+    rec = inputs.receivers_on_row(n, 0.8, 10, rng)
+    u0n = inputs.gaussian_hump(n, n, g.ld, 0.45, 0.6, 0.08)
+    obs = torch.from_numpy(rng.standard_normal((S, len(rec))) * 1e-3).cuda()
+    hx = sim.hx.clone().requires_grad_(True)
+    hy = sim.hy.clone().requires_grad_(True)
+    u0 = torch.from_numpy(u0n).cuda().requires_grad_(True)
+    u1 = torch.zeros_like(u0).requires_grad_(True)
+    cfg = TsunamiConfig(g, sim.tau, S, torch.from_numpy(inputs.flat_index(rec, g.ld)).cuda(), sim.ext[1], sim.ext[3],
+                        form=tsu.TSU_FORM_STANDARD, ckpt_every=16)
+    tr = tsunami_traces(hx, hy, u0, u1, cfg)
+    loss = 0.5 * ((tr - obs) ** 2).sum()
+    loss.backward()
+    og = oracle.grid(n, n)
+    ohx, ohy, _ = oracle.make_depth(og, depth)
+    fwd = oracle.forward(og, sim.tau, ohx, ohy, u0n[:, :n], None, S, want_energy=False,
+                         rec_idx=inputs.flat_index(rec, n))
+    assert relerr(tr.detach().cpu().numpy(), fwd["traces"]) <= 1e-12
+    ref = oracle.adjoint(og, sim.tau, ohx, ohy, u0n[:, :n], None, S, inputs.flat_index(rec, n),
+                         fwd["traces"] - obs.cpu().numpy())
+    assert relerr(hx.grad[:, :n].cpu().numpy(), ref["g_hx"]) <= 1e-11
+    assert relerr(hy.grad[:, :n].cpu().numpy(), ref["g_hy"]) <= 1e-11
+    assert relerr(u0.grad[:, :n].cpu().numpy(), ref["g_u0"]) <= 1e-11
+    assert relerr(u1.grad[:, :n].cpu().numpy(), ref["g_u1"]) <= 1e-11

@@ -1,0 +1,69 @@
+"""GPU tests of the batched eps-family launch (tsu_batch_run)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2005_11931_gb300 import inputs, tsu
+from tests.gpu_helpers import relerr, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def family(steps, sizes=(129, 200, 257, 300), count_eps=3):
+    return inputs.batched_family(steps=steps, count_eps=count_eps, sizes=sizes)
+
+
+def make_sims(probs, form):
+    sims = []
+    for p in probs:
+        sim = tsu.Simulation.create(p.n, p.depth, dtype="f32", form=form)
+        sim.init(torch.from_numpy(p.initial(sim.g.ld, np.float32)).cuda())
+        sims.append(sim)
+    return sims
+
+
+@pytest.mark.parametrize("form", [tsu.TSU_FORM_INCREMENT, tsu.TSU_FORM_STANDARD])
+@pytest.mark.parametrize("K", [4, 8])
+def test_batched_equals_sequential_bitwise(form, K):
+    probs = family(steps=1 + 5 * K + 3)
+    steps = [p.steps - 1 for p in probs]
+    seq = make_sims(probs, form)
+    for sim, n in zip(seq, steps):
+        sim.step(n, kernel=3, tdepth=K, rows=64)
+    bat = make_sims(probs, form)
+    wsb = tsu.tsu_batch_workspace(bat, steps, tdepth=K, rows=64)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    tsu.tsu_batch_run(bat, steps, ws, wsb, tdepth=K, rows=64)
+    tsu.tsu_sync_status(ws, wsb)
+    for a, b in zip(seq, bat):
+        assert a.state.step == b.state.step
+        assert torch.equal(a.u, b.u)
+        assert torch.equal(a.bufs[a.state.aux], b.bufs[b.state.aux])
+
+
+def test_batched_uneven_step_counts():
+    probs = family(steps=40)
+    rng = np.random.default_rng(3)
+    steps = [int(s) for s in rng.integers(0, 60, size=len(probs))]
+    seq = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    for sim, n in zip(seq, steps):
+        sim.step(n, kernel=3, tdepth=8, rows=64) if n >= 8 else sim.step(n, kernel=1)
+    bat = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    wsb = tsu.tsu_batch_workspace(bat, steps, tdepth=8, rows=64)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    tsu.tsu_batch_run(bat, steps, ws, wsb, tdepth=8, rows=64)
+    for a, b, n in zip(seq, bat, steps):
+        assert b.state.step == 1 + n
+        assert torch.equal(a.u, b.u), n
+
+
+def test_batched_problem_matches_oracle():
+    probs = family(steps=1 + 8 * 6 + 2, sizes=(200, 257), count_eps=2)
+    steps = [p.steps - 1 for p in probs]
+    bat = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    wsb = tsu.tsu_batch_workspace(bat, steps)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    tsu.tsu_batch_run(bat, steps, ws, wsb)
+    for p, sim in zip(probs, bat):
+        orc = run_oracle(p.n, p.depth, p.initial(), p.steps, energy=False)
+        assert relerr(sim.u[:, : p.n].double().cpu().numpy(), orc["u"]) <= 1e-5, p.name

@@ -1,0 +1,123 @@
+"""GPU tests of the temporally blocked pass (several leapfrog steps per HBM pass).
+
+It must give the scheme's result: bit for bit on integer data at Courant 1 (where FP32 is
+exact), within the FP32 bars against the FP64 oracle otherwise, across strip and chunk borders,
+ragged tails, tiny grids and leftover steps; and its bounded waits must report, not hang.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2005_11931_gb300 import inputs, tsu
+from tests.gpu_helpers import relerr, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def odd_ext_shift(f, s):
+    F = np.concatenate([f, -f[-2:0:-1]])
+    idx = np.arange(len(f))
+    return 0.5 * (F[(idx - s) % len(F)] + F[(idx + s) % len(F)])
+
+
+def courant_one(axis, n_along, n_across, S, K, form, rows=64):
+    """hx = 1, hy = 0 (axis 'x') or hx = 0, hy = 1 (axis 'y'), tau = spacing: d'Alembert exactly."""
+    nx, ny = (n_along, n_across) if axis == "x" else (n_across, n_along)
+    g = tsu.grid(nx, ny)
+    hx = tsu.empty_field(g, "f32")
+    hy = tsu.empty_field(g, "f32")
+    if axis == "x":
+        hx[:, : nx - 1] = 1.0
+        tau, med = g.dx, None
+    else:
+        hy[: ny - 1, :nx] = 1.0
+        tau = g.dy
+    med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), 1.0 if axis == "x" else 0.0, 1.0 if axis == "y" else 0.0)
+    rng = np.random.default_rng(17)
+    u0n = np.zeros((ny, nx))
+    u0n[1:-1, 1:-1] = 2.0 * rng.integers(-300, 300, size=(ny - 2, nx - 2))
+    u0 = tsu.empty_field(g, "f32")
+    u0[:, :nx] = torch.from_numpy(u0n).float()
+    bufs = [tsu.empty_field(g, "f32") for _ in range(4)]
+    st = tsu.State()
+    for k in range(4):
+        st.buf[k] = bufs[k].data_ptr()
+    st.nbuf, st.form = 4, form
+    ws_b = tsu.tsu_step_workspace(g, "f32")
+    ws = torch.zeros(ws_b, dtype=torch.uint8, device="cuda")
+    tsu.tsu_init(g, "f32", tau, med, u0, None, st)
+    o = tsu.StepOpts()
+    o.kernel, o.tdepth, o.rows = 3, K, rows
+    tsu.tsu_step_n(g, "f32", tau, med, st, S - 1, o, ws, ws_b)
+    tsu.tsu_sync_status(ws, ws_b)
+    u = bufs[st.cur][:, :nx].double().cpu().numpy()
+    if axis == "x":
+        exact = np.stack([odd_ext_shift(u0n[j], S) for j in range(ny)])
+    else:
+        exact = np.stack([odd_ext_shift(u0n[:, i], S) for i in range(nx)], axis=1)
+    return u, exact
+
+
+@pytest.mark.parametrize("K", [4, 8])
+@pytest.mark.parametrize("form", [tsu.TSU_FORM_STANDARD, tsu.TSU_FORM_INCREMENT])
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_tb_courant_one_bit_exact(K, form, axis):
+    S = 1 + 5 * K + 3  # several blocked passes plus leftover single steps
+    u, exact = courant_one(axis, 769, 37, S, K, form)
+    assert np.array_equal(u, exact)
+
+
+@pytest.mark.parametrize("K", [4, 8])
+@pytest.mark.parametrize("form,tol", [(tsu.TSU_FORM_INCREMENT, 1e-5), (tsu.TSU_FORM_STANDARD, 1e-4)])
+def test_tb_ragged_parity_with_energy(K, form, tol):
+    nx, ny = 700, 613  # 3 strips (last one partial), 5 chunks of 128 rows (last one partial)
+    depth = dict(background=1.0, eps=0.015, mollifier=0, sings=[(0, 1, 1.0, 0.5, 0.5), (2, 1, 0.01, 0.52, 0.47)])
+    u0 = inputs.gaussian_hump(nx, ny, None, 0.45, 0.55, 0.03)
+    S = 1 + 12 * K + 5
+    gpu = run_gpu(nx, depth, u0, S, dtype="f32", form=form, ny=ny, kernel=3, rows=128)
+    orc = run_oracle(nx, depth, u0, S, ny=ny)
+    tsu.tsu_sync_status(gpu["sim"].ws, gpu["sim"].ws.numel())
+    assert relerr(gpu["u"], orc["u"]) <= tol
+    assert np.max(np.abs(gpu["energy"] - orc["energy"]) / orc["energy"]) <= tol
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (5, 4), (9, 300), (300, 6), (37, 41), (250, 251)])
+def test_tb_tiny_and_thin_grids(nx, ny):
+    depth = dict(background=1.0, eps=0.2, sings=[(2, 1, 0.05, 0.4, 0.6)])
+    rng = np.random.default_rng(nx * 7 + ny)
+    u0 = inputs.random_field(nx, ny, None, rng)
+    S = 1 + 3 * 8 + 2
+    gpu = run_gpu(nx, depth, u0, S, dtype="f32", ny=ny, kernel=3, rows=16)
+    orc = run_oracle(nx, depth, u0, S, ny=ny)
+    assert relerr(gpu["u"], orc["u"]) <= 1e-5
+
+
+def test_tb_matches_register_streaming_pass():
+    n = 1500
+    depth = dict(background=0.5, eps=0.004, mollifier=0, sings=[(2, 1, 0.01, 0.5, 0.5)])
+    u0 = inputs.gaussian_hump(n, n, None, 0.3, 0.5, 0.02)
+    a = run_gpu(n, depth, u0, 201, dtype="f32", kernel=3)
+    b = run_gpu(n, depth, u0, 201, dtype="f32", kernel=1)
+    assert relerr(a["u"], b["u"]) <= 1e-6
+    assert np.max(np.abs(a["energy"] - b["energy"]) / b["energy"]) <= 1e-6
+
+
+def test_tb_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: the test hook withholds one row copy, the consumers'
+    bounded wait expires, the status word says TSU_ETIMEOUT, and the next call works."""
+    n = 600
+    depth = dict(background=1.0, eps=0.02, mollifier=0, sings=[(0, 1, 1.0, 0.5, 0.5)])
+    sim = tsu.Simulation.create(n, depth, dtype="f32")
+    u0 = torch.from_numpy(inputs.gaussian_hump(n, n, sim.g.ld, 0.3, 0.5, 0.05)).float().cuda()
+    sim.init(u0)
+    sim.step(8, kernel=3, tdepth=8, debug=1)
+    with pytest.raises(tsu.TsuError) as ei:
+        tsu.tsu_sync_status(sim.ws, sim.ws.numel())
+    assert ei.value.code == tsu.TSU_ETIMEOUT
+    # the status was cleared and the context is usable
+    sim2 = tsu.Simulation.create(n, depth, dtype="f32")
+    sim2.init(u0)
+    sim2.step(16, kernel=3, tdepth=8)
+    tsu.tsu_sync_status(sim2.ws, sim2.ws.numel())
+    ref = run_gpu(n, depth, u0.cpu().numpy(), 17, dtype="f32", kernel=1)
+    assert relerr(sim2.u[:, :n].double().cpu().numpy(), ref["u"]) <= 1e-6
