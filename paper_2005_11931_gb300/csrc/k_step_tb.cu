@@ -87,7 +87,9 @@ constexpr size_t tb_smem_bytes() {
          sizeof(uint64_t) * TbShape<K>::S + 64;
 }
 
-struct TbArgs {
+// 16-byte aligned so that an array of descriptors has the same stride on the host (which packs
+// them) and on the device (which indexes them).
+struct alignas(16) TbArgs {
   int32_t nx, ny;
   int64_t ld;
   float cx, cy;
@@ -383,7 +385,10 @@ cudaError_t tb_launch_batched(const TbArgs* probs, const int4* tiles, int64_t nt
 
 bool tb_supported_depth(int k) { return k == 4 || k == 8; }
 
-size_t tb_args_bytes() { return sizeof(TbArgs); }
+size_t tb_args_bytes() {
+  static_assert(sizeof(TbArgs) % 16 == 0, "descriptor stride must be a multiple of 16 bytes");
+  return sizeof(TbArgs);
+}
 
 int tb_strip_width(int k) { return kTbThreads - 2 * k; }
 

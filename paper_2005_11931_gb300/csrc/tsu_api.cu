@@ -418,7 +418,7 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
   *k_out = k;
   *rows_out = rows;
   *ntiles_out = ntiles;
-  *bytes_out = 256 + 3 * (size_t)nprob * ((tsu::tb_args_bytes() + 15) / 16 * 16) + (size_t)ntiles * 16;
+  *bytes_out = 256 + 3 * (size_t)nprob * (tsu::tb_args_bytes()) + (size_t)ntiles * 16;
   return TSU_OK;
 }
 
@@ -451,7 +451,7 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
     if (p.nsteps < 0) return fail(TSU_EINVAL, "problem %d: nsteps < 0", i);
   }
   const int W = tsu::tb_strip_width(k);
-  const size_t ab = (tsu::tb_args_bytes() + 15) / 16 * 16;
+  const size_t ab = tsu::tb_args_bytes();
   // problems in decreasing order of blocked rounds: round r launches a prefix of the tile table
   std::vector<int> order(nprob);
   for (int i = 0; i < nprob; ++i) order[i] = i;

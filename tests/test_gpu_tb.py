@@ -120,4 +120,4 @@ def test_tb_bounded_wait_reports_timeout_and_context_survives():
     sim2.step(16, kernel=3, tdepth=8)
     tsu.tsu_sync_status(sim2.ws, sim2.ws.numel())
     ref = run_gpu(n, depth, u0.cpu().numpy(), 17, dtype="f32", kernel=1)
-    assert relerr(sim2.u[:, :n].double().cpu().numpy(), ref["u"]) <= 1e-6
+    assert relerr(sim2.u[:, :n].double().cpu().numpy(), ref["u"]) <= 1e-5
