@@ -236,6 +236,25 @@ int tsu_batch_workspace(int32_t nprob, const tsu_problem* probs, const tsu_batch
 int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, void* ws, size_t ws_bytes,
                   void* stream);
 
+/* tsu_step_n without a workspace, for callers that cannot allocate device memory (a host
+ * application that owns the allocator and hands over only its buffers, a real-time loop that
+ * must not stall on an allocation, a plugin whose host forbids it).  The paper has no
+ * counterpart: this is an interface variant only.  It makes nsteps one-step passes exactly as
+ * tsu_step_n does with kernel = 1 and opts->energy = energy (NULL: no energy), and takes the
+ * energy-reduction scratch from a fixed array inside the library (256 B + 65536 FP64 partial
+ * sums, kept on every device that uses the library until it is unloaded) instead of a workspace.
+ *   - Grids needing more than 65536 partial sums (ceil(ld/512) * ceil((ny-2)/32) in FP32,
+ *     ceil(ld/256) * ceil((ny-2)/32) in FP64) are refused with TSU_ENOMEM when energy is set.
+ *   - The first call on a device looks up the array's device address with that device current;
+ *     make that first call before any stream capture.
+ *   - All calls on a device share the array and leave their last contents in it; each call zeroes
+ *     what must start at zero.  Calls that overlap on the GPU race: order them.
+ * It allocates nothing (no cudaMalloc, no library allocator).  Errors as tsu_step_n; the message
+ * is in tsu_noalloc_last_error(). */
+int tsu_step_n_noalloc(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, tsu_state* st,
+                       int64_t nsteps, double* energy, void* stream);
+const char* tsu_noalloc_last_error(void);
+
 /* Synchronise the stream, then read and clear the device status word in the workspace of
  * tsu_step_n: TSU_OK, or TSU_ETIMEOUT if a bounded device-side wait of a kernel expired (that
  * kernel stopped early; its outputs are invalid). */

@@ -104,6 +104,9 @@ def load():
                         C.POINTER(StepOpts), vp, C.c_size_t, vp], C.c_int),
         "tsu_sync_status": ([vp, C.c_size_t, vp], C.c_int),
         "tsu_ckpt_slots": ([i64, i64], i64),
+        "tsu_step_n_noalloc": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), i64, vp, vp],
+                               C.c_int),
+        "tsu_noalloc_last_error": ([], C.c_char_p),
         "tsu_batch_workspace": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), C.POINTER(C.c_size_t)], C.c_int),
         "tsu_batch_run": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), vp, C.c_size_t, vp], C.c_int),
         "tsu_adjoint_workspace": ([C.POINTER(Grid), C.c_int, i64, i64, C.POINTER(C.c_size_t)], C.c_int),
@@ -236,6 +239,16 @@ def tsu_batch_run(sims, nsteps, ws, ws_bytes: int, tdepth: int = 0, rows: int = 
     o = BatchOpts(int(tdepth), int(rows))
     rc = load().tsu_batch_run(len(sims), arr, C.byref(o), _ptr(ws), int(ws_bytes), _stream(stream))
     _check(rc, "tsu_batch_run")
+
+
+def tsu_step_n_noalloc(g: Grid, dtype, tau: float, medium: Medium, state: State, nsteps: int, energy=None,
+                       stream=None):
+    """tsu_step_n (one step per pass, optional energy) without a caller workspace."""
+    lib = load()
+    rc = lib.tsu_step_n_noalloc(C.byref(g), dtype_code(dtype), tau, C.byref(medium), C.byref(state), int(nsteps),
+                                _ptr(energy), _stream(stream))
+    if rc != TSU_OK:
+        raise TsuError(rc, "tsu_step_n_noalloc", lib.tsu_noalloc_last_error().decode())
 
 
 def tsu_ckpt_slots(nsteps: int, ckpt_every: int) -> int:
