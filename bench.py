@@ -36,6 +36,7 @@ TRAFFIC = {
     ("k_leapfrog", "standard", 8192, 1): 1.280e9,
 }
 UNIT = "GLUPS"
+DEFAULT_KERNEL = 2  # warp-blocked pass, 4 steps per HBM pass
 
 
 def parse():
@@ -52,6 +53,7 @@ def parse():
     ap.add_argument("--tdepth", type=int, default=0, help="steps per blocked pass (4 or 8; 0 = 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched and 16384^2 measurements")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch (from profiles/)")
     return ap.parse_args()
 
@@ -212,15 +214,16 @@ def run_gpu(args):
     ext = tsu.tsu_make_depth(g, p.depth, code, hx, hy, ext_dev, sync=True)
     tau = inputs.CFL * g.dx / float(np.sqrt(max(ext[1], ext[3])))
     med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
-    # the blocked kernel runs when it is chosen (or by default: FP32, 4 buffers, a large grid);
-    # its steps and the leftover single steps are separate calls so that each is timed on its own
-    K = args.tdepth or 8
-    blocked = args.kernel == 3 or (args.kernel == 0 and p.n * p.n >= (1 << 20))
+    # kernel: --kernel, else the default below; the blocked kernels' steps and the leftover single
+    # steps are separate calls so that each is timed on its own
+    kernel = args.kernel or DEFAULT_KERNEL
+    blocked = kernel in (2, 3)
+    K = (args.tdepth or (4 if kernel == 2 else 8)) if blocked else 1
     n_main = ((S - 1) // K) * K if blocked else S - 1
     n_left = (S - 1) - n_main
     opts = tsu.StepOpts()
     opts.energy = energy.data_ptr()
-    opts.kernel, opts.rows, opts.tdepth = (3 if blocked else 1), args.rows, K
+    opts.kernel, opts.rows, opts.tdepth = kernel, args.rows, (K if blocked else 0)
     opts_left = tsu.StepOpts()
     opts_left.energy = energy.data_ptr() + 8 * n_main
     opts_left.kernel = 1
@@ -279,7 +282,7 @@ def run_gpu(args):
     # K steps.
     if blocked:
         bpn = 24
-        kname = "k_leapfrog_tb"
+        kname = "k_leapfrog_wtb" if kernel == 2 else "k_leapfrog_tb"
     else:
         bpn = 24 if form == tsu.TSU_FORM_INCREMENT else 20
         kname = "k_leapfrog"
@@ -325,6 +328,11 @@ def run_gpu(args):
     if rank != 0:
         dist.destroy_process_group()
         return 0
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras["adjoint"] = measure_adjoint()
+        extras["batched"] = measure_batched()
+        extras["large"] = measure_large()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         r = oracle_sample(p.n, 64 if p.n >= 4096 else 256)
@@ -349,11 +357,159 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "gpu_launches": launches_per_step * args.steps,
         "energy_drift": drift,
+        **extras,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# -----------------------------------------------------------------------------------------------
+# The other workloads of the metric, measured in the same run (device-resident inputs, CUDA events)
+# -----------------------------------------------------------------------------------------------
+def _events_ms(fn, reps=1):
+    import torch
+    s = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
+    """Adjoint/forward time ratio on the receiver-misfit workload: forward with traces and
+    checkpoints every 64 steps vs tsu_adjoint (segment recompute + reverse sweep)."""
+    import numpy as np
+    import torch
+
+    from paper_2005_11931_gb300 import inputs, tsu
+
+    case = inputs.adjoint_case(n, steps)
+    p, every = case["problem"], case["ckpt_every"]
+    S = p.steps
+    sim = tsu.Simulation.create(p.n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT, nbuf=3)
+    g = sim.g
+    u0 = torch.from_numpy(p.initial(g.ld, np.float32)).cuda()
+    rec = torch.from_numpy(inputs.flat_index(case["receivers"], g.ld)).cuda()
+    nrec = rec.numel()
+    traces = torch.zeros((S, nrec), dtype=torch.float32, device="cuda")
+    slots = tsu.tsu_ckpt_slots(S, every)
+    ck = torch.empty((slots, 2, g.ny, g.ld), dtype=torch.float32, device="cuda")
+    obs = torch.zeros_like(traces)
+
+    def forward(tr):
+        sim.init(u0)
+        sim.step(S - 1, rec_idx=rec, traces=tr[: S - 1], ckpt=ck, ckpt_every=every)
+        sim.observe(rec_idx=rec, trace=tr[S - 1])
+
+    # observations: the same run with eps = 0.012 (a different medium)
+    osim = tsu.Simulation.create(p.n, case["depth_obs"], dtype="f32", form=tsu.TSU_FORM_INCREMENT, nbuf=3,
+                                 tau=sim.tau)
+    osim.init(u0)
+    osim.step(S - 1, rec_idx=rec, traces=obs[: S - 1])
+    osim.observe(rec_idx=rec, trace=obs[S - 1])
+    gx = torch.zeros((g.ny, g.ld), dtype=torch.float64, device="cuda")
+    gy = torch.zeros_like(gx)
+    gu0 = torch.zeros_like(u0)
+    gu1 = torch.zeros_like(u0)
+    wsb = tsu.tsu_adjoint_workspace(g, tsu.TSU_F32, S, every, nrec)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+
+    def adjoint():
+        tsu.tsu_adjoint(g, tsu.TSU_F32, tsu.TSU_FORM_INCREMENT, sim.tau, sim.medium, S, every, ck, u0, rec,
+                        traces - obs, gx, gy, gu0, gu1, ws, wsb)
+
+    for _ in range(warm):
+        forward(traces)
+        adjoint()
+    t_f = _events_ms(lambda: forward(traces), reps)
+    t_a = _events_ms(adjoint, reps)
+    lups = (n - 2) ** 2 * S
+    J = 0.5 * float(((traces - obs).double() ** 2).sum())
+    return {"workload": f"adjoint_{n}: {n}^2 FP32 (increment form), depth 1 + 0.5 phi_eps(x-0.5), eps 0.01, "
+                        f"{S} steps, {nrec} receivers on y = 0.8, checkpoints every {every}",
+            "forward_ms": t_f, "adjoint_ms": t_a, "ratio": t_a / t_f, "forward_glups": lups / t_f / 1e6,
+            "adjoint_glups": lups / t_a / 1e6, "J": J, "grad_norm_hx": float(gx.norm())}
+
+
+def measure_batched(steps=2000, warm=1):
+    """The 64-problem eps-family: one batched launch per K steps vs the same problems run one
+    after the other (one step per pass, and the automatic kernel choice)."""
+    import numpy as np
+    import torch
+
+    from paper_2005_11931_gb300 import inputs, tsu
+
+    probs = inputs.batched_family(steps=steps)
+    sims = []
+    for pr in probs:
+        sim = tsu.Simulation.create(pr.n, pr.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+        sims.append((pr, sim, torch.from_numpy(pr.initial(sim.g.ld, np.float32)).cuda()))
+    nsteps = [pr.steps - 1 for pr in probs]
+    wsb = tsu.tsu_batch_workspace([s for _, s, _ in sims], nsteps)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+
+    def init_all():
+        for _, sim, u0 in sims:
+            sim.init(u0)
+
+    def batched():
+        init_all()
+        tsu.tsu_batch_run([s for _, s, _ in sims], nsteps, ws, wsb)
+
+    def sequential(kernel):
+        init_all()
+        for (pr, sim, _), n in zip(sims, nsteps):
+            sim.step(n, kernel=kernel)
+
+    for _ in range(warm):
+        batched()
+        sequential(1)
+    t_init = _events_ms(init_all)
+    t_b = _events_ms(batched)
+    snap = [sim.u.clone() for _, sim, _ in sims]
+    t_s1 = _events_ms(lambda: sequential(1))
+    diff = max(float((sim.u - a).abs().max() / a.abs().max().clamp_min(1e-30)) for (_, sim, _), a in zip(sims, snap))
+    t_s0 = _events_ms(lambda: sequential(0))
+    tsu.tsu_sync_status(ws, wsb)
+    lups = sum((pr.n - 2) ** 2 * pr.steps for pr in probs)
+    return {"workload": f"eps-family: {len(probs)} problems (16 eps x line-x, line-y, point, line+point), "
+                        f"N in {{512..2048}}, {steps} steps each, FP32 increment form",
+            "lups": lups, "batched_ms": t_b, "sequential_one_step_ms": t_s1, "sequential_auto_ms": t_s0,
+            "init_ms": t_init, "batched_glups": lups / t_b / 1e6, "speedup_vs_sequential_one_step": t_s1 / t_b,
+            "speedup_vs_sequential_auto": t_s0 / t_b, "max_rel_diff_batched_vs_sequential": diff}
+
+
+def measure_large(n=16384, steps=2000, warm=1):
+    """16384^2 crossing lines, FP32: throughput of the blocked pass over a bounded number of steps
+    (the 20000-step run advances at the same rate)."""
+    import numpy as np
+    import torch
+
+    from paper_2005_11931_gb300 import inputs, tsu
+
+    p = inputs.crossing_lines_fp32(n, steps)
+    sim = tsu.Simulation.create(n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+    u0 = torch.from_numpy(p.initial(sim.g.ld, np.float32)).cuda()
+    e = torch.zeros(steps, dtype=torch.float64, device="cuda")
+
+    def run():
+        sim.init(u0)
+        sim.step(steps - 1, energy=e[: steps - 1])
+
+    for _ in range(warm):
+        run()
+    t = _events_ms(run)
+    tsu.tsu_sync_status(sim.ws, sim.ws.numel())
+    en = e[: steps - 1].cpu().numpy()
+    return {"workload": f"crossing_lines_fp32_{n}: {n}^2, 1 + phi(x-0.5) + phi(y-0.5), eps 8dx, {steps} of 20000 "
+                        f"steps timed, energy every step", "ms": t, "glups": (n - 2) ** 2 * steps / t / 1e6,
+            "energy_drift": float(np.max(np.abs(en - en[0])) / en[0])}
 
 
 def main():

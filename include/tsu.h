@@ -130,11 +130,12 @@ typedef struct {
   void* traces;
   void* ckpt;
   int64_t ckpt_every, ckpt_slots;
-  int32_t kernel;   /* 0 auto, 1 register-streaming (one step per pass), 3 temporally blocked
-                       (tdepth steps per pass; FP32, nbuf = 4, workspace, no traces/checkpoints);
-                       auto picks 3 when it is possible and the grid has >= 2^20 nodes */
+  int32_t kernel;   /* 0 auto, 1 register-streaming (one step per pass), 2 warp-blocked (tdepth =
+                       2 or 4 steps per pass, default 4), 3 CTA-blocked (tdepth = 4 or 8, default 8);
+                       2 and 3 need FP32, nbuf = 4, a workspace and no traces/checkpoints; auto picks
+                       a blocked kernel when possible and its tiles fill the GPU */
   int32_t rows;     /* rows per CTA (0 = auto) */
-  int32_t tdepth;   /* steps per pass of kernel 3: 4 or 8 (0 = 8); leftover steps run one per pass */
+  int32_t tdepth;   /* steps per pass of kernels 2 and 3 (0 = default); leftover steps run one per pass */
   int32_t reserved; /* 0.  Bit 0 is a test hook of the failure detection: kernel 3 then never
                        issues one row copy, its bounded wait (20 ms) expires and tsu_sync_status
                        reports TSU_ETIMEOUT; outputs of that call are invalid. */
@@ -185,9 +186,11 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
  * tsu_step_n is given ckpt_every: states m = 1, 1 + every, ... <= nsteps - 1.  Host only. */
 int64_t tsu_ckpt_slots(int64_t nsteps, int64_t ckpt_every);
 
-/* Bytes of device workspace tsu_adjoint needs: (ckpt_every + 4) fields of dtype, plus two FP32
- * gradient accumulators for FP32 fields. */
-int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, size_t* bytes);
+/* Bytes of device workspace tsu_adjoint needs for nrec receivers: 2 (ckpt_every + 3) fields of
+ * dtype (multipliers and two segment buffers), two FP32 gradient accumulators for FP32 fields,
+ * and a receiver table. */
+int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, int32_t nrec,
+                          size_t* bytes);
 
 /* Reverse-time discrete adjoint of the forward run "tsu_init(u0, u1) then tsu_step_n(nsteps-1)"
  * for a receiver functional J(traces) (the paper has no adjoint; it is the exact reverse of the
@@ -200,6 +203,9 @@ int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t 
  *   g_hx, g_hy  device double [ny][ld], overwritten with dJ/dhx, dJ/dhy (FP64 accumulation;
  *             for FP32 fields FP32 partial sums over one segment are added into them)
  *   g_u0, g_u1  device [ny][ld] of dtype, overwritten with dJ/du0, dJ/du1
+ * The recompute of one segment runs on a library-owned stream (one per device, created by the
+ * first call) concurrently with the reverse sweep of the previous one; all of it is ordered before
+ * the call's last work on the caller's stream.
  * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
 int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_medium* m, int64_t nsteps,
                 int64_t ckpt_every, const void* ckpt, const void* u0, int32_t nrec, const int64_t* rec_idx,
@@ -218,9 +224,10 @@ typedef struct {
 
 /* Options of tsu_batch_run (NULL = defaults). */
 typedef struct {
-  int32_t tdepth; /* steps per batched pass: 4 or 8 (0 = 8) */
+  int32_t tdepth; /* steps per batched pass (0 = the kernel's default: 4 for kernel 2, 8 for kernel 3) */
   int32_t rows;   /* rows per chunk (0 = 256) */
-  int32_t reserved[2];
+  int32_t kernel; /* 0 or 2: warp-blocked (tdepth 2 or 4); 3: CTA-blocked (tdepth 4 or 8) */
+  int32_t reserved;
 } tsu_batch_opts;
 
 /* Bytes of device workspace tsu_batch_run needs for these problems (descriptors and tile table). */

@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
                                                       const T tau, const T* __restrict__ hx, const T* __restrict__ hy,
                                                       const T* __restrict__ lam, const T* lam_pp, T* lam_out,
                                                       const T* __restrict__ u, typename AccOf<T>::type* gx,
-                                                      typename AccOf<T>::type* gy, T* g_u1, const int rows) {
+                                                      typename AccOf<T>::type* gy, T* g_u1, const int rows,
+                                                      const RecBuckets rb) {
   using A = typename AccOf<T>::type;
   constexpr int V = Vec<T>::V;
   const int lane = threadIdx.x & 31;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
   for (int j = j0; j < j1; ++j) {
     const int64_t row = (int64_t)j * ld + i0;
     const Pack<T> ln = ld_vec(lam + row + ld);
-    const Pack<T> lp = ld_vec_cg(lam_pp + row);
+    const Pack<T> lp = ld_vec_l2(lam_pp + row);
     const Pack<T> hxv = ld_vec(hx + row);
     const Pack<T> hyv = ld_vec(hy + row);
     const Pack<T> un = umask(ld_vec(u + row + ld), j + 1);
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
         st_vec(g_u1 + row, gu1);
       }
       // the accumulators have the field's vector width (float4 / double2): 16-byte read-modify-write
-      Pack<A> ax = ld_vec_cg(gx + row), ay = ld_vec_cg(gy + row);
+      Pack<A> ax = ld_vec_l2(gx + row), ay = ld_vec_l2(gy + row);
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         ax.a[e] += gxv[e];
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       st_vec(gx + row, ax);
       st_vec(gy + row, ay);
       if (j == 1) {
-        Pack<A> a0 = ld_vec_cg(gy + i0);
+        Pack<A> a0 = ld_vec_l2(gy + i0);
 #pragma unroll
         for (int e = 0; e < V; ++e) a0.a[e] += gy0[e];
         st_vec(gy + i0, a0);
@@ -135,6 +136,43 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
     hym = hyv;
     uc = un;
   }
+  // receiver injection lam^n += g^n at this CTA's receivers, in receiver order, after the CTA's
+  // own stores of lam^n (visible to the CTA after the barrier)
+  if (rb.off) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int64_t cta = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+      for (int q = rb.off[cta]; q < rb.off[cta + 1]; ++q) {
+        const int r = rb.ord[q];
+        lam_out[rb.idx[r]] += ((const T*)rb.g)[r];
+      }
+    }
+  }
+}
+
+// Receivers grouped by the CTA of the adjoint pass that owns their node (interior nodes only),
+// in receiver order: off[ncta + 1], ord[nrec].  One thread; nrec and ncta are small.
+__global__ void k_rec_bucket(const int32_t nx, const int32_t ny, const int64_t ld, const int64_t* idx,
+                             const int32_t nrec, const int64_t cols_per_cta, const int rows, const int64_t gridx,
+                             const int64_t ncta, int* off, int* ord, int* cta_of) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int64_t c = 0; c <= ncta; ++c) off[c] = 0;
+  for (int r = 0; r < nrec; ++r) {
+    const int64_t q = idx[r];
+    int c = -1;
+    if (q >= 0 && q < (int64_t)ny * ld) {
+      const int64_t j = q / ld, i = q - j * ld;
+      if (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2) c = (int)(((j - 1) / rows) * gridx + i / cols_per_cta);
+    }
+    cta_of[r] = c;
+    if (c >= 0) off[c + 1] += 1;
+  }
+  for (int64_t c = 0; c < ncta; ++c) off[c + 1] += off[c];
+  // stable fill with off[c] as the cursor of bucket c, then shift the cursors back to the starts
+  for (int r = 0; r < nrec; ++r)
+    if (cta_of[r] >= 0) ord[off[cta_of[r]]++] = r;
+  for (int64_t c = ncta; c >= 1; --c) off[c] = off[c - 1];
+  off[0] = 0;
 }
 
 // lam[rec_idx[r]] += g[r] for interior receiver nodes (boundary receivers record a constant 0)
@@ -166,34 +204,57 @@ typename ArithOf<T>::type arith(const StencilGeom& g) {
   return a;
 }
 
+}  // namespace
+
+void adjoint_pass_shape(const StencilGeom& g, int dtype, int64_t* gridx, int64_t* gridy, int* rows,
+                        int64_t* cols_per_cta) {
+  const int64_t cpc = (int64_t)128 * (dtype == TSU_F32 ? 4 : 2);
+  const int r = auto_rows(g.ld, g.ny, cpc);
+  *cols_per_cta = cpc;
+  *rows = r;
+  *gridx = (g.ld + cpc - 1) / cpc;
+  *gridy = (g.ny - 2 + r - 1) / r;
+}
+
+namespace {
 template <typename T>
 cudaError_t pass_t(const StencilGeom& g, bool start, const void* hx, const void* hy, const void* lam,
-                   const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy, void* g_u1, cudaStream_t s) {
+                   const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy, void* g_u1,
+                   const RecBuckets& rb, cudaStream_t s) {
   using A = typename AccOf<T>::type;
-  constexpr int V = Vec<T>::V;
-  const int rows = 32, threads = 128;
-  const int64_t cpc = (int64_t)threads * V;
-  dim3 grid((unsigned)((g.ld + cpc - 1) / cpc), (unsigned)((g.ny - 2 + rows - 1) / rows));
+  int64_t gx_, gy_, cpc;
+  int rows;
+  adjoint_pass_shape(g, sizeof(T) == 4 ? TSU_F32 : TSU_F64, &gx_, &gy_, &rows, &cpc);
+  const int threads = 128;
+  dim3 grid((unsigned)gx_, (unsigned)gy_);
   const T w = start ? T(0.5) : T(1);
   const T gwx = -(T)g.cx * w, gwy = -(T)g.cy * w;
   if (!start)
     k_adjoint_pass<T, 0><<<grid, threads, 0, s>>>(g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx,
                                                    (const T*)hy, (const T*)lam, (const T*)lam_pp, (T*)lam_out,
-                                                   (const T*)u, (A*)gx, (A*)gy, nullptr, rows);
+                                                   (const T*)u, (A*)gx, (A*)gy, nullptr, rows, rb);
   else
     k_adjoint_pass<T, 1><<<grid, threads, 0, s>>>(g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx,
                                                    (const T*)hy, (const T*)lam, (const T*)lam_pp, (T*)lam_out,
-                                                   (const T*)u, (A*)gx, (A*)gy, (T*)g_u1, rows);
+                                                   (const T*)u, (A*)gx, (A*)gy, (T*)g_u1, rows, rb);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_rec_bucket(const StencilGeom& g, int dtype, const int64_t* idx, int32_t nrec, int* off, int* ord,
+                              int* cta_of, cudaStream_t s) {
+  int64_t gx_, gy_, cpc;
+  int rows;
+  adjoint_pass_shape(g, dtype, &gx_, &gy_, &rows, &cpc);
+  k_rec_bucket<<<1, 32, 0, s>>>(g.nx, g.ny, g.ld, idx, nrec, cpc, rows, gx_, gx_ * gy_, off, ord, cta_of);
   return cudaGetLastError();
 }
 
-}  // namespace
-
 cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
                                 const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
-                                void* g_u1, cudaStream_t s) {
-  return dtype == TSU_F32 ? pass_t<float>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, s)
-                          : pass_t<double>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, s);
+                                void* g_u1, const RecBuckets& rb, cudaStream_t s) {
+  return dtype == TSU_F32 ? pass_t<float>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, s)
+                          : pass_t<double>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, s);
 }
 
 cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,

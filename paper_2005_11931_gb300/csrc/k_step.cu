@@ -222,8 +222,8 @@ cudaError_t step_t(const StencilGeom& g, const void* hx, const void* hy, const v
                    void* v, void* u_next, const PassOut& o, bool store, int rows, cudaStream_t s) {
   constexpr int V = Vec<T>::V;
   const int threads = 128;
-  if (rows <= 0) rows = 32;
   const int64_t cols_per_cta = (int64_t)threads * V;
+  if (rows <= 0) rows = auto_rows(g.ld, g.ny, cols_per_cta);
   dim3 grid((unsigned)((g.ld + cols_per_cta - 1) / cols_per_cta), (unsigned)((g.ny - 2 + rows - 1) / rows));
   const auto ar = make_arith<T>(g);
   const T* p_in = (const T*)(FORM == 0 ? u_prev : v);

@@ -1,0 +1,395 @@
+// Warp-blocked leapfrog pass: K = 2 or 4 steps of the scheme of k_step.cu per read of the fields
+// from HBM (arXiv:2005.11931, Sec. 2 eq. (2.1) on the Sec. 3.3 box), without any CTA barrier.
+//
+// Every warp works alone on a tile: a strip of 128 columns (one float4 per lane) of which the
+// middle 120 are output (a 4-column halo on each side covers the K-step dependency cone), and a
+// chunk of L output rows it streams down.  Each thread stages its own float4 of every input row
+// (u^n, u^{n-1} or v^n, hx, hy) through a private ring in shared memory with 16-byte cp.async
+// copies, P rows ahead, and reads back only what it copied itself (cp.async.wait_group), so no
+// thread waits for another.  Time level t lags the input by t rows; for each level the thread
+// keeps the last three rows of its four columns in registers (y-neighbours), and takes the
+// x-neighbours of its two edge columns from the adjacent lanes with shuffles.  Level K is written
+// with level K-1 (standard form) or v (increment form) of the same row.
+//
+// HBM traffic per K steps: 16 B read + 8 B written per node, x 128/120 for the halo columns and
+// x (L + 2K)/L for the halo rows: 6.4 B per lattice update at K = 4.
+#include <string.h>
+
+#include "stencil_common.cuh"
+
+namespace tsu {
+namespace {
+using namespace dev;
+
+constexpr int kWtbWarps = 4;       // warps (independent tiles) per CTA
+constexpr int kWtbOut = 120;       // output columns per strip
+constexpr int kWtbPre = 2;         // rows in flight ahead of the one being consumed
+
+template <int K>
+struct WtbShape {
+  static constexpr int SA = kWtbPre + 2;      // ring of (u, p) rows: in flight + current + previous
+  static constexpr int SB = K + 2 + kWtbPre;  // ring of (hx, hy) rows: levels' rows + in flight
+  // bytes per thread
+  static constexpr int bytes = (SA * 2 + SB * 2) * 16;
+};
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;  // 0: fill with zeros, read nothing
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// 16-byte aligned: arrays of descriptors have the same stride on the host and the device.
+struct alignas(16) WtbArgs {
+  int32_t nx, ny;
+  int64_t ld;
+  float cx, cy;
+  const float* hx;
+  const float* hy;
+  const float* u;   // u^n
+  const float* p;   // u^{n-1} (standard) or v^n (increment)
+  float* out_a;     // u^{n+K}
+  float* out_b;     // u^{n+K-1} (standard) or v^{n+K} (increment)
+  int rows;         // output rows per chunk
+  int64_t nstrips, ntiles;
+  double* energy;   // K doubles or nullptr
+  EnergyWs ews;
+  double escale;
+};
+
+struct F4 {
+  float a[4];
+};
+__device__ __forceinline__ F4 lds4(const float* s) {
+  const float4 v = *reinterpret_cast<const float4*>(s);
+  return F4{{v.x, v.y, v.z, v.w}};
+}
+__device__ __forceinline__ void stg4(float* g, const F4& v) {
+  *reinterpret_cast<float4*>(g) = make_float4(v.a[0], v.a[1], v.a[2], v.a[3]);
+}
+
+template <int K>
+__device__ void wtb_energy(float (&es)[K], float (&ec)[K], const WtbArgs& a) {
+  __shared__ double red[K][kWtbWarps];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    double v = (double)es[t] - (double)ec[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[t][w] = v;
+  }
+  __syncthreads();
+  const int64_t ncta = gridDim.x;
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int q = 0; q < kWtbWarps; ++q) s += red[threadIdx.x][q];
+    a.ews.partials[(int64_t)threadIdx.x * ncta + blockIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int tk = atomicAdd(a.ews.counter, 1u);
+    last = (tk == (unsigned int)(ncta - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int t = 0; t < K; ++t) {
+    double s = 0.0;
+    for (int64_t q = threadIdx.x; q < ncta; q += blockDim.x) s += __ldcg(&a.ews.partials[(int64_t)t * ncta + q]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) red[0][w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int q = 0; q < kWtbWarps; ++q) tot += red[0][q];
+      a.energy[t] = tot * a.escale;
+    }
+  }
+  if (threadIdx.x == 0) *a.ews.counter = 0u;
+}
+
+template <int K, int FORM, bool ENERGY>
+__device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, const int64_t strip,
+                                         const int64_t chunk) {
+  using Sh = WtbShape<K>;
+  extern __shared__ __align__(16) unsigned char wtb_smem[];
+  const int lane = threadIdx.x & 31;
+  // this thread's private ring: A[SA][2] float4 (u, p), B[SB][2] float4 (hx, hy)
+  float* ringA = reinterpret_cast<float*>(wtb_smem) + (size_t)threadIdx.x * 4;
+  const int stride = kWtbWarps * 32 * 4;  // floats between consecutive float4 slots of one thread
+  auto slotA = [&](int s, int f) { return ringA + (size_t)(s * 2 + f) * stride; };
+  auto slotB = [&](int s, int f) { return ringA + (size_t)(Sh::SA * 2 + s * 2 + f) * stride; };
+
+  const int64_t xs = strip * kWtbOut - 4;
+  const int64_t c0 = xs + 4 * lane;  // first of this lane's four columns
+  const int y0 = 1 + (int)chunk * a.rows;
+  const int y1 = tile_ok ? min(y0 + a.rows, a.ny - 1) : y0;
+  const int r_first = y0 - K, nit = tile_ok ? (y1 - y0) + 2 * K : 0;
+  const bool col_in = c0 >= 0 && c0 < a.ld;  // the whole float4 lies in the row (ld % 4 == 0)
+  const bool col_out = lane >= 1 && lane <= 30 && col_in;
+  bool node_col[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) node_col[e] = (c0 + e >= 1) && (c0 + e <= a.nx - 2);
+
+  auto issue = [&](int r) {  // copies of input row r into the rings (zeros outside the grid)
+    const bool ok = col_in && r >= 0 && r < a.ny;
+    const int64_t go = ok ? (int64_t)r * a.ld + c0 : 0;
+    const int sa = ((r - r_first) % Sh::SA + Sh::SA) % Sh::SA, sb = ((r - r_first) % Sh::SB + Sh::SB) % Sh::SB;
+    cp16(slotA(sa, 0), a.u + go, ok);
+    cp16(slotA(sa, 1), a.p + go, ok);
+    cp16(slotB(sb, 0), a.hx + go, ok);
+    cp16(slotB(sb, 1), a.hy + go, ok);
+  };
+  auto ringB = [&](int r, int f) -> F4 {  // hx (f = 0) or hy (f = 1) of row r, zeros outside
+    if (r < r_first) return F4{{0.f, 0.f, 0.f, 0.f}};
+    return lds4(slotB((r - r_first) % Sh::SB, f));
+  };
+
+  // registers: w[t][0..2] = level t at its latest three rows, v[t][0..1] likewise (increment form)
+  F4 w[K + 1][3];
+  F4 vv[K][2];
+#pragma unroll
+  for (int t = 0; t <= K; ++t)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) w[t][q] = F4{{0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+  for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = F4{{0.f, 0.f, 0.f, 0.f}};
+  float es[K], ec[K];  // compensated per-level energy sums of this thread
+#pragma unroll
+  for (int t = 0; t < K; ++t) es[t] = ec[t] = 0.f;
+
+  for (int q = 0; q < kWtbPre; ++q) {
+    if (q < nit) issue(r_first + q);
+    cp_commit();
+  }
+  for (int it = 0; it < nit; ++it) {
+    const int r_in = r_first + it;
+    if (it + kWtbPre < nit) issue(r_in + kWtbPre);
+    cp_commit();
+    cp_wait<kWtbPre>();  // this thread's copies of row r_in have landed
+    const int sa = it % Sh::SA;
+    // ---- level 0: the input row
+#pragma unroll
+    for (int t = 0; t <= K; ++t) {
+      w[t][2] = w[t][1];
+      w[t][1] = w[t][0];
+    }
+    w[0][0] = lds4(slotA(sa, 0));
+    if constexpr (FORM == 1) {
+      vv[0][1] = vv[0][0];
+      vv[0][0] = lds4(slotA(sa, 1));
+    }
+    // ---- levels 1..K
+#pragma unroll
+    for (int t = 1; t <= K; ++t) {
+      const int rt = r_in - t;
+      const F4 hxv = ringB(rt, 0), hyv = ringB(rt, 1), hyd = ringB(rt - 1, 1);
+      const F4 uc = w[t - 1][1], uu = w[t - 1][0], ud = w[t - 1][2];
+      F4 pc;  // u^{n-1} (standard) or v at row rt of the level below
+      if (t == 1) {
+        pc = (it >= 1) ? lds4(slotA((it - 1) % Sh::SA, 1)) : F4{{0.f, 0.f, 0.f, 0.f}};
+        if constexpr (FORM == 1) pc = vv[0][1];
+      } else {
+        if constexpr (FORM == 0)
+          pc = w[t - 2][2];
+        else
+          pc = vv[t - 1][1];
+      }
+      float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1);
+      float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
+      float hl = __shfl_up_sync(0xffffffffu, hxv.a[3], 1);
+      const bool row_in = rt >= 1 && rt <= a.ny - 2;
+      const bool row_out = rt >= y0 && rt < y1;
+      F4 un, vn;
+      float erow = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float xl = (e == 0) ? ul : uc.a[e - 1];
+        const float xr = (e == 3) ? ur : uc.a[e + 1];
+        const float hxl = (e == 0) ? hl : hxv.a[e - 1];
+        const float fx = hxv.a[e] * (xr - uc.a[e]) - hxl * (uc.a[e] - xl);
+        const float fy = hyv.a[e] * (uu.a[e] - uc.a[e]) - hyd.a[e] * (uc.a[e] - ud.a[e]);
+        const float b = fmaf(a.cx, fx, a.cy * fy);
+        const bool node = row_in && node_col[e];
+        float unew, vnew = 0.f, up;
+        if constexpr (FORM == 0) {
+          up = pc.a[e];
+          unew = (2.0f * uc.a[e] - up) + b;
+        } else {
+          up = uc.a[e] - pc.a[e];
+          vnew = pc.a[e] + b;
+          unew = uc.a[e] + vnew;
+        }
+        un.a[e] = node ? unew : 0.f;
+        vn.a[e] = node ? vnew : 0.f;
+        if constexpr (ENERGY) {
+          if (node && row_out && col_out) {
+            const float d = uc.a[e] - up;
+            erow += d * d - b * up;
+          }
+        }
+      }
+      if constexpr (ENERGY) {
+        const float y = erow - ec[t - 1];
+        const float sum = es[t - 1] + y;
+        ec[t - 1] = (sum - es[t - 1]) - y;
+        es[t - 1] = sum;
+      }
+      w[t][0] = un;
+      if constexpr (FORM == 1) {
+        if (t < K) {
+          vv[t][1] = vv[t][0];
+          vv[t][0] = vn;
+        }
+      }
+      if (t == K && row_out && col_out) {
+        const int64_t o = (int64_t)rt * a.ld + c0;
+        stg4(a.out_a + o, un);
+        if constexpr (FORM == 1)
+          stg4(a.out_b + o, vn);
+        else
+          stg4(a.out_b + o, w[K - 1][1]);  // level K-1 at the same row
+      }
+    }
+  }
+  cp_wait<0>();
+  if constexpr (ENERGY) wtb_energy<K>(es, ec, a);
+}
+
+template <int K, int FORM, bool ENERGY>
+__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb(const WtbArgs a) {
+  const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
+  const bool ok = tile < a.ntiles;
+  wtb_body<K, FORM, ENERGY>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
+}
+
+// Batched family: warp w of CTA b works on tile tiles[4 b + w] = (problem, strip, chunk) of
+// descriptor probs[problem]; one launch advances every problem by K steps.
+template <int K, int FORM>
+__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_batched(const WtbArgs* __restrict__ probs,
+                                                                        const int4* __restrict__ tiles,
+                                                                        const int64_t ntiles) {
+  const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
+  const bool ok = tile < ntiles;
+  const int4 t = ok ? tiles[tile] : make_int4(0, 0, 0, 0);
+  const WtbArgs a = probs[t.x];
+  wtb_body<K, FORM, false>(a, ok, t.y, t.z);
+}
+
+template <int K, int FORM>
+cudaError_t wtb_launch(const WtbArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)WtbShape<K>::bytes * kWtbWarps * 32;
+  const unsigned grid = (unsigned)((a.ntiles + kWtbWarps - 1) / kWtbWarps);
+  if (a.energy) {
+    if ((int64_t)grid * K > a.ews.capacity) return cudaErrorInvalidValue;
+    auto kern = k_leapfrog_wtb<K, FORM, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kWtbWarps * 32, smem, s>>>(a);
+  } else {
+    auto kern = k_leapfrog_wtb<K, FORM, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kWtbWarps * 32, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int K, int FORM>
+cudaError_t wtb_launch_batched(const WtbArgs* probs, const int4* tiles, int64_t ntiles, cudaStream_t s) {
+  const size_t smem = (size_t)WtbShape<K>::bytes * kWtbWarps * 32;
+  auto kern = k_leapfrog_wtb_batched<K, FORM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)((ntiles + kWtbWarps - 1) / kWtbWarps), kWtbWarps * 32, smem, s>>>(probs, tiles, ntiles);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool wtb_supported_depth(int k) { return k == 2 || k == 4; }
+
+int wtb_strip_width() { return kWtbOut; }
+
+size_t wtb_args_bytes() {
+  static_assert(sizeof(WtbArgs) % 16 == 0, "descriptor stride must be a multiple of 16 bytes");
+  return sizeof(WtbArgs);
+}
+
+void wtb_fill_args(void* dst, const StencilGeom& g, const void* hx, const void* hy, const void* u, const void* p,
+                   void* out_a, void* out_b, int rows) {
+  WtbArgs a{};
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.ld = g.ld;
+  a.cx = (float)g.cx;
+  a.cy = (float)g.cy;
+  a.hx = (const float*)hx;
+  a.hy = (const float*)hy;
+  a.u = (const float*)u;
+  a.p = (const float*)p;
+  a.out_a = (float*)out_a;
+  a.out_b = (float*)out_b;
+  a.rows = rows;
+  a.nstrips = (g.ld + kWtbOut - 1) / kWtbOut;
+  a.ntiles = a.nstrips * ((g.ny - 2 + rows - 1) / rows);
+  a.energy = nullptr;
+  memcpy(dst, &a, sizeof a);
+}
+
+cudaError_t launch_step_wtb_batched(int form, int k, const void* probs_dev, size_t stride, const void* tiles_dev,
+                                    int64_t ntiles, cudaStream_t s) {
+  if (stride != sizeof(WtbArgs)) return cudaErrorInvalidValue;
+  const WtbArgs* p = (const WtbArgs*)probs_dev;
+  const int4* t = (const int4*)tiles_dev;
+  if (k == 2) return form == TSU_FORM_STANDARD ? wtb_launch_batched<2, 0>(p, t, ntiles, s)
+                                               : wtb_launch_batched<2, 1>(p, t, ntiles, s);
+  if (k == 4) return form == TSU_FORM_STANDARD ? wtb_launch_batched<4, 0>(p, t, ntiles, s)
+                                               : wtb_launch_batched<4, 1>(p, t, ntiles, s);
+  return cudaErrorInvalidValue;
+}
+
+int64_t wtb_tiles(int64_t ny, int64_t ld, int rows) {
+  return ((ld + 4 + kWtbOut - 1) / kWtbOut) * ((ny - 2 + rows - 1) / rows);
+}
+
+int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows) {
+  return ((wtb_tiles(ny, ld, rows) + kWtbWarps - 1) / kWtbWarps) * k;
+}
+
+cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
+                            const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int rows,
+                            cudaStream_t s) {
+  WtbArgs a;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.ld = g.ld;
+  a.cx = (float)g.cx;
+  a.cy = (float)g.cy;
+  a.hx = (const float*)hx;
+  a.hy = (const float*)hy;
+  a.u = (const float*)u;
+  a.p = (const float*)p;
+  a.out_a = (float*)out_a;
+  a.out_b = (float*)out_b;
+  a.rows = rows;
+  // strips cover columns [0, ld): the last output column of strip s is 120 s + 119
+  a.nstrips = (g.ld + kWtbOut - 1) / kWtbOut;
+  a.ntiles = a.nstrips * ((g.ny - 2 + rows - 1) / rows);
+  a.energy = energy;
+  a.ews = ews;
+  a.escale = g.dxdy / (2.0 * g.tau * g.tau);
+  if (k == 2) return form == TSU_FORM_STANDARD ? wtb_launch<2, 0>(a, s) : wtb_launch<2, 1>(a, s);
+  if (k == 4) return form == TSU_FORM_STANDARD ? wtb_launch<4, 0>(a, s) : wtb_launch<4, 1>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace tsu

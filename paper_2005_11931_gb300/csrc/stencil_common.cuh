@@ -39,7 +39,20 @@ __device__ __forceinline__ Pack<T> ld_vec(const T* p) {
 }
 
 template <typename T>
-__device__ __forceinline__ Pack<T> ld_vec_cg(const T* p) {  // data this kernel also writes
+__device__ __forceinline__ Pack<T> ld_vec_l2(const T* p) {  // data this kernel rewrites and reuses: keep in L2
+  Pack<T> r;
+  using VT = typename Vec<T>::type;
+  VT v = __ldcg(reinterpret_cast<const VT*>(p));
+  if constexpr (Vec<T>::V == 4) {
+    r.a[0] = v.x; r.a[1] = v.y; r.a[2] = v.z; r.a[3] = v.w;
+  } else {
+    r.a[0] = v.x; r.a[1] = v.y;
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ Pack<T> ld_vec_cg(const T* p) {  // data this kernel also writes (streamed)
   Pack<T> r;
   using VT = typename Vec<T>::type;
   VT v = __ldcs(reinterpret_cast<const VT*>(p));

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "tsu_internal.h"
@@ -201,9 +202,12 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   if (o.traces && (o.nrec == 0 || !o.rec_idx)) return fail(TSU_EINVAL, "traces need nrec > 0 and rec_idx");
   if (o.ckpt && (o.ckpt_every < 1 || o.ckpt_slots < 1 || !aligned16(o.ckpt)))
     return fail(TSU_EINVAL, "checkpoints need ckpt_every >= 1, ckpt_slots >= 1 and an aligned store");
-  if (o.kernel < 0 || o.kernel > 3 || o.kernel == 2) return fail(TSU_EINVAL, "kernel must be 0, 1 or 3");
+  if (o.kernel < 0 || o.kernel > 3) return fail(TSU_EINVAL, "kernel must be 0..3");
   if (o.rows < 0) return fail(TSU_EINVAL, "rows must be >= 0");
-  if (o.tdepth != 0 && !tsu::tb_supported_depth(o.tdepth)) return fail(TSU_EINVAL, "tdepth must be 0, 4 or 8");
+  if (o.tdepth != 0 && o.kernel == 3 && !tsu::tb_supported_depth(o.tdepth))
+    return fail(TSU_EINVAL, "kernel 3: tdepth must be 0, 4 or 8");
+  if (o.tdepth != 0 && o.kernel == 2 && !tsu::wtb_supported_depth(o.tdepth))
+    return fail(TSU_EINVAL, "kernel 2: tdepth must be 0, 2 or 4");
   const bool have_ws = ws && ws_bytes >= tsu::energy_ws_bytes(g->ny, g->ld);
   tsu::EnergyWs ews{};
   if (o.energy && !ws) return fail(TSU_ENOMEM, "energy needs a workspace (tsu_step_workspace)");
@@ -217,17 +221,41 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   // kernel choice: the temporally blocked pass needs FP32 fields, four state buffers, a workspace
   // (status word), and no per-step side outputs other than the energy
   const bool tb_possible = dtype == TSU_F32 && st->nbuf == 4 && have_ws && !o.traces && !o.ckpt;
-  if (o.kernel == 3 && !tb_possible)
-    return fail(TSU_EINVAL, "kernel 3 needs FP32, nbuf = 4, a workspace and no traces/checkpoints");
+  if ((o.kernel == 3 || o.kernel == 2) && !tb_possible)
+    return fail(TSU_EINVAL, "kernels 2 and 3 need FP32, nbuf = 4, a workspace and no traces/checkpoints");
+  // kernel 2: warp-blocked pass, tdepth steps per launch (default 4).  Auto (kernel 0) takes it
+  // when its tiles give at least ~500 CTAs (rows per chunk 256, halved down to 64 to get there);
+  // smaller grids run one step per pass (their fields largely stay in L2)
+  const int wdepth = o.tdepth ? o.tdepth : 4;
+  int wrows = o.rows ? (o.rows < 16 ? 16 : o.rows) : 256;
+  if (!o.rows)
+    while (wrows > 64 && (tsu::wtb_tiles(g->ny, g->ld, wrows) + 3) / 4 < 500) wrows /= 2;
+  const bool wtb_fills = (tsu::wtb_tiles(g->ny, g->ld, wrows) + 3) / 4 >= 300;
+  const bool use_wtb = tb_possible && nsteps >= wdepth && tsu::wtb_supported_depth(wdepth) &&
+                       (o.kernel == 2 || (o.kernel == 0 && wtb_fills));
   const int tdepth = o.tdepth ? o.tdepth : 8;
-  const bool use_tb = tb_possible && nsteps >= tdepth &&
-                      (o.kernel == 3 || (o.kernel == 0 && (int64_t)g->nx * g->ny >= (int64_t)1 << 20));
-  int tb_rows = o.rows ? o.rows : 512;
+  int tb_rows = o.rows ? o.rows : 128;
   if (tb_rows < 16) tb_rows = 16;
+  // auto: the blocked pass only when its tiles fill the GPU at least twice over (152 SMs x 2 CTAs);
+  // smaller grids run one step per pass (their fields largely stay in L2)
+  const int64_t tb_ctas = ((g->ld + tsu::tb_strip_width(tdepth) - 1) / tsu::tb_strip_width(tdepth)) *
+                          ((g->ny - 2 + tb_rows - 1) / tb_rows);
+  const bool use_tb = !use_wtb && tb_possible && nsteps >= tdepth && o.kernel == 3;
   const tsu::StencilGeom sg = geom(g, tau);
   const size_t field_bytes = (size_t)g->ny * g->ld * elem_size(dtype);
   cudaStream_t s = (cudaStream_t)stream;
   int64_t k = 0;
+  if (use_wtb) {
+    for (; k + wdepth <= nsteps; k += wdepth) {
+      const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
+      cudaError_t e = tsu::launch_step_wtb(sg, st->form, wdepth, m->hx, m->hy, st->buf[st->cur], st->buf[st->aux],
+                                           st->buf[f1], st->buf[f2], o.energy ? o.energy + k : nullptr, ews, wrows, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n warp-blocked launch");
+      st->cur = f1;
+      st->aux = f2;
+      st->step += wdepth;
+    }
+  }
   if (use_tb) {
     for (; k + tdepth <= nsteps; k += tdepth) {
       const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
@@ -256,11 +284,11 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
     cudaError_t e;
     if (st->form == TSU_FORM_STANDARD) {
       e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, st->buf[st->aux], st->buf[st->cur], nullptr,
-                           st->buf[st->aux], po, true, use_tb ? 0 : o.rows, s);
+                           st->buf[st->aux], po, true, (use_tb || use_wtb) ? 0 : o.rows, s);
     } else {
       const int f = scratch_index(st, -1);
       e = tsu::launch_step(sg, dtype, st->form, m->hx, m->hy, nullptr, st->buf[st->cur], st->buf[st->aux],
-                           st->buf[f], po, true, use_tb ? 0 : o.rows, s);
+                           st->buf[f], po, true, (use_tb || use_wtb) ? 0 : o.rows, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n launch");
     if (st->form == TSU_FORM_STANDARD) {
@@ -277,24 +305,69 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
 
 // ---------------------------------------------------------------------------------------------
 // Adjoint: workspace = 2 multiplier fields + (E+1) recomputed states + 1 restore field
-// (u^{m-1} or v^m) [+ 2 FP32 gradient accumulators for FP32 fields]
+// (u^{m-1} or v^m) [+ 2 FP32 gradient accumulators for FP32 fields] + receiver buckets
 // ---------------------------------------------------------------------------------------------
-static size_t adjoint_ws_bytes(const tsu_grid* g, int dtype, int64_t every) {
-  const size_t fb = (size_t)g->ny * g->ld * elem_size(dtype);
-  size_t b = (size_t)(every + 4) * fb;
-  if (dtype == TSU_F32) b += 2 * (size_t)g->ny * g->ld * sizeof(float);
-  return b + 256;
+static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
+  int64_t gx, gy, cpc;
+  int rows;
+  tsu::adjoint_pass_shape(geom(g, 1.0), dtype, &gx, &gy, &rows, &cpc);
+  return gx * gy;
 }
 
-int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, size_t* bytes) {
+static size_t adjoint_ws_bytes(const tsu_grid* g, int dtype, int64_t every, int32_t nrec) {
+  const size_t fb = (size_t)g->ny * g->ld * elem_size(dtype);
+  size_t b = (size_t)(2 * (every + 2) + 2) * fb;  // 2 multipliers + two segment buffers of E + 2 fields
+  if (dtype == TSU_F32) b += 2 * (size_t)g->ny * g->ld * sizeof(float);
+  const size_t buckets = ((size_t)(adjoint_ctas(g, dtype) + 1) + 2 * (size_t)(nrec > 0 ? nrec : 0)) * sizeof(int);
+  return b + (buckets + 255) / 256 * 256 + 256;
+}
+
+int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, int32_t nrec,
+                          size_t* bytes) {
   g_err[0] = 0;
   TRY(check_grid(g));
   TRY(check_dtype(dtype));
   if (!bytes) return fail(TSU_EINVAL, "bytes is NULL");
-  if (nsteps < 1 || ckpt_every < 1) return fail(TSU_EINVAL, "nsteps and ckpt_every must be >= 1");
-  *bytes = adjoint_ws_bytes(g, dtype, ckpt_every);
+  if (nsteps < 1 || ckpt_every < 1 || nrec < 0) return fail(TSU_EINVAL, "nsteps, ckpt_every >= 1 and nrec >= 0");
+  *bytes = adjoint_ws_bytes(g, dtype, ckpt_every, nrec);
   return TSU_OK;
 }
+
+}  // extern "C"
+
+// One auxiliary (non-blocking) stream per device with its events, created on first use, for
+// overlapping the adjoint's segment recompute with its reverse sweep.
+namespace {
+struct AuxStream {
+  cudaStream_t s;
+  cudaEvent_t start, computed[2], swept[2];
+};
+std::mutex g_aux_mu;
+AuxStream* g_aux[64] = {};
+
+AuxStream* aux_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_aux_mu);
+  if (!g_aux[dev]) {
+    AuxStream* a = new AuxStream();
+    bool ok = cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&a->start, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b) {
+      ok = cudaEventCreateWithFlags(&a->computed[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&a->swept[b], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      delete a;
+      return nullptr;
+    }
+    g_aux[dev] = a;
+  }
+  return g_aux[dev];
+}
+}  // namespace
+
+extern "C" {
 
 int64_t tsu_ckpt_slots(int64_t nsteps, int64_t ckpt_every) {
   if (nsteps < 2 || ckpt_every < 1) return 0;
@@ -321,8 +394,8 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   const int64_t C = tsu_ckpt_slots(nsteps, ckpt_every);
   if (C > 0) TRY(check_field(ckpt, "ckpt"));
   if (nrec < 0 || (nrec > 0 && (!rec_idx || !dtraces))) return fail(TSU_EINVAL, "receivers need rec_idx and dtraces");
-  if (!ws || ws_bytes < adjoint_ws_bytes(g, dtype, ckpt_every))
-    return fail(TSU_ENOMEM, "adjoint workspace %zu B < %zu B", ws_bytes, adjoint_ws_bytes(g, dtype, ckpt_every));
+  const size_t need = adjoint_ws_bytes(g, dtype, ckpt_every, nrec);
+  if (!ws || ws_bytes < need) return fail(TSU_ENOMEM, "adjoint workspace %zu B < %zu B", ws_bytes, need);
   TRY(check_field(ws, "workspace"));
   cudaStream_t s = (cudaStream_t)stream;
   const tsu::StencilGeom sg = geom(g, tau);
@@ -330,65 +403,90 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   const size_t fb = (size_t)g->ny * g->ld * es;
   char* w = (char*)ws;
   char* lam[2] = {w, w + fb};                    // lam^{n+1}, lam^{n+2}
-  char* seg = w + 2 * fb;                        // seg[k] = u^{m_c + k}, k = 0..E
-  char* extra = seg + (size_t)(ckpt_every + 1) * fb;  // u^{m_c - 1} (standard) or v (increment)
-  char* g32 = extra + fb;                        // FP32 accumulators [2][ny][ld]
+  // two segment buffers, each seg[k] = u^{m_c + k} (k = 0..E) followed by one restore field
+  // (u^{m_c - 1} or v); the recompute of one segment overlaps the reverse sweep of the other
+  char* segbuf[2] = {w + 2 * fb, w + 2 * fb + (size_t)(ckpt_every + 2) * fb};
+  char* g32 = w + (size_t)(2 * (ckpt_every + 2) + 2) * fb;  // FP32 accumulators [2][ny][ld]
   const size_t f32b = (size_t)g->ny * g->ld * sizeof(float);
   void* accx = dtype == TSU_F32 ? (void*)g32 : (void*)g_hx;
   void* accy = dtype == TSU_F32 ? (void*)(g32 + f32b) : (void*)g_hy;
-  auto segp = [&](int64_t k) { return (void*)(seg + (size_t)k * fb); };
-  cudaError_t e = cudaMemsetAsync(ws, 0, adjoint_ws_bytes(g, dtype, ckpt_every) - 256, s);
+  char* bk = (dtype == TSU_F32 ? g32 + 2 * f32b : g32);  // receiver buckets (ints)
+  int* b_off = (int*)bk;
+  int* b_ord = b_off + (adjoint_ctas(g, dtype) + 1);
+  int* b_cta = b_ord + (nrec > 0 ? nrec : 0);
+  auto segp = [&](int b, int64_t k) { return (void*)(segbuf[b] + (size_t)k * fb); };
+  auto extra = [&](int b) { return (void*)(segbuf[b] + (size_t)(ckpt_every + 1) * fb); };
+  AuxStream* aux = aux_stream();
+  if (!aux) return fail(TSU_ECUDA, "tsu_adjoint: could not create the recompute stream");
+  cudaError_t e = cudaMemsetAsync(ws, 0, need - 256, s);
+  if (e == cudaSuccess && nrec > 0) e = tsu::launch_rec_bucket(sg, dtype, rec_idx, nrec, b_off, b_ord, b_cta, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hx, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hy, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint reset");
   int a = 0;  // lam[a] = lam^{n+1}, lam[a^1] = lam^{n+2}
   auto step_back = [&](int64_t n, const void* un) -> cudaError_t {
+    tsu::RecBuckets rb{};
+    if (nrec > 0) rb = {b_off, b_ord, rec_idx, (const char*)dtraces + (size_t)(n - 1) * nrec * es};
     cudaError_t r = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam[a], lam[a ^ 1], lam[a ^ 1], un, accx,
-                                             accy, nullptr, s);
-    if (r == cudaSuccess && nrec > 0)
-      r = tsu::launch_inject(sg, dtype, lam[a ^ 1], (const char*)dtraces + (size_t)(n - 1) * nrec * es, rec_idx, nrec,
-                             s);
+                                             accy, nullptr, rb, s);
     a ^= 1;  // lam[a] = lam^n now
     return r;
   };
   if (C == 0) {  // nsteps == 1: lam^1 = g^1 (the gradient term of n = 1 vanishes with lam^2 = 0)
-    e = step_back(1, segp(0));
+    e = step_back(1, segp(0, 0));
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
   }
-  for (int64_t c = C - 1; c >= 0; --c) {
+  // the recompute stream starts after the resets above
+  e = cudaEventRecord(aux->start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(aux->s, aux->start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint stream setup");
+  for (int64_t c = C - 1, idx = 0; c >= 0; --c, ++idx) {
+    const int b = (int)(idx & 1);
     const int64_t mc = 1 + c * ckpt_every;
     const int64_t mend = (mc + ckpt_every < nsteps) ? mc + ckpt_every : nsteps;
-    // restore the checkpointed state, then recompute u^{mc+1}..u^{mend} into seg[1..]
+    // recompute stream: wait until the sweep that last read buffer b is done, restore the
+    // checkpointed state, recompute u^{mc+1}..u^{mend} into seg[b][1..]
+    if (idx >= 2) e = cudaStreamWaitEvent(aux->s, aux->swept[b], 0);
     const char* slot = (const char*)ckpt + (size_t)c * 2 * fb;
-    if (form == TSU_FORM_STANDARD) {
-      e = cudaMemcpyAsync(extra, slot, fb, cudaMemcpyDeviceToDevice, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(segp(0), slot + fb, fb, cudaMemcpyDeviceToDevice, s);
-    } else {
-      e = cudaMemcpyAsync(segp(0), slot, fb, cudaMemcpyDeviceToDevice, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(extra, slot + fb, fb, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+      if (form == TSU_FORM_STANDARD) {
+        e = cudaMemcpyAsync(extra(b), slot, fb, cudaMemcpyDeviceToDevice, aux->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(segp(b, 0), slot + fb, fb, cudaMemcpyDeviceToDevice, aux->s);
+      } else {
+        e = cudaMemcpyAsync(segp(b, 0), slot, fb, cudaMemcpyDeviceToDevice, aux->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(extra(b), slot + fb, fb, cudaMemcpyDeviceToDevice, aux->s);
+      }
     }
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint restore");
     tsu::PassOut none{};
     for (int64_t k = 0; k < mend - mc; ++k) {
       if (form == TSU_FORM_STANDARD)
-        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, k == 0 ? (void*)extra : segp(k - 1), segp(k), nullptr,
-                             segp(k + 1), none, true, 0, s);
+        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, k == 0 ? extra(b) : segp(b, k - 1), segp(b, k), nullptr,
+                             segp(b, k + 1), none, true, 0, aux->s);
       else
-        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, nullptr, segp(k), extra, segp(k + 1), none, true, 0, s);
+        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, nullptr, segp(b, k), extra(b), segp(b, k + 1), none, true,
+                             0, aux->s);
       if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint recompute");
     }
+    e = cudaEventRecord(aux->computed[b], aux->s);
+    // caller's stream: the reverse sweep over this segment once its states are there
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->computed[b], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint stream order");
     const int64_t nlo = (c == 0) ? 1 : mc + 1;
     for (int64_t n = mend; n >= nlo; --n) {
-      e = step_back(n, segp(n - mc));
+      e = step_back(n, segp(b, n - mc));
       if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
     }
     if (dtype == TSU_F32) {
       e = tsu::launch_flush(sg, accx, accy, g_hx, g_hy, s);
       if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint flush");
     }
+    e = cudaEventRecord(aux->swept[b], s);
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint stream order");
   }
   // the start: dJ/du0 = (I + B/2) lam^1 - lam^2, dJ/du1 = tau lam^1, face terms with u^0 and weight 1/2
-  e = tsu::launch_adjoint_pass(sg, dtype, true, m->hx, m->hy, lam[a], lam[a ^ 1], g_u0, u0, accx, accy, g_u1, s);
+  e = tsu::launch_adjoint_pass(sg, dtype, true, m->hx, m->hy, lam[a], lam[a ^ 1], g_u0, u0, accx, accy, g_u1,
+                               tsu::RecBuckets{}, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_u0, 0, (size_t)g->ld * es, s);  // boundary rows of the outputs
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)g_u0 + (size_t)(g->ny - 1) * g->ld * es, 0, (size_t)g->ld * es, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_u1, 0, (size_t)g->ld * es, s);
@@ -401,14 +499,22 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
 // ---------------------------------------------------------------------------------------------
 // Batched family
 // ---------------------------------------------------------------------------------------------
+// kernel 2 (warp-blocked, default, tdepth 2 or 4, default 4) or 3 (CTA-blocked, tdepth 4 or 8,
+// default 8); descriptor size and strip width follow the kernel
+static int batch_kernel(const tsu_batch_opts* opts) { return (opts && opts->kernel) ? opts->kernel : 2; }
+
 static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, int* k_out,
                         int* rows_out, int64_t* ntiles_out, size_t* bytes_out) {
   if (nprob < 1 || !probs) return fail(TSU_EINVAL, "need at least one problem");
-  const int k = (opts && opts->tdepth) ? opts->tdepth : 8;
+  const int kern = batch_kernel(opts);
+  if (kern != 2 && kern != 3) return fail(TSU_EINVAL, "batch kernel must be 2 or 3");
+  const int k = (opts && opts->tdepth) ? opts->tdepth : (kern == 2 ? 4 : 8);
   const int rows = (opts && opts->rows) ? opts->rows : 256;
-  if (!tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "tdepth must be 4 or 8");
+  if (kern == 3 && !tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 3: tdepth must be 4 or 8");
+  if (kern == 2 && !tsu::wtb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 2: tdepth must be 2 or 4");
   if (rows < 16) return fail(TSU_EINVAL, "rows must be >= 16");
-  const int W = tsu::tb_strip_width(k);
+  const int W = kern == 2 ? tsu::wtb_strip_width() : tsu::tb_strip_width(k);
+  const size_t ab = kern == 2 ? tsu::wtb_args_bytes() : tsu::tb_args_bytes();
   int64_t ntiles = 0;
   for (int i = 0; i < nprob; ++i) {
     const tsu_grid& g = probs[i].grid;
@@ -418,7 +524,7 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
   *k_out = k;
   *rows_out = rows;
   *ntiles_out = ntiles;
-  *bytes_out = 256 + 3 * (size_t)nprob * (tsu::tb_args_bytes()) + (size_t)ntiles * 16;
+  *bytes_out = 256 + 3 * (size_t)nprob * ab + (size_t)ntiles * 16;
   return TSU_OK;
 }
 
@@ -450,8 +556,9 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
     if (p.state->nbuf != 4) return fail(TSU_EINVAL, "problem %d: nbuf must be 4", i);
     if (p.nsteps < 0) return fail(TSU_EINVAL, "problem %d: nsteps < 0", i);
   }
-  const int W = tsu::tb_strip_width(k);
-  const size_t ab = tsu::tb_args_bytes();
+  const int kern = batch_kernel(opts);
+  const int W = kern == 2 ? tsu::wtb_strip_width() : tsu::tb_strip_width(k);
+  const size_t ab = kern == 2 ? tsu::wtb_args_bytes() : tsu::tb_args_bytes();
   // problems in decreasing order of blocked rounds: round r launches a prefix of the tile table
   std::vector<int> order(nprob);
   for (int i = 0; i < nprob; ++i) order[i] = i;
@@ -483,8 +590,13 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
     for (int i = 0; i < nprob; ++i) {
       tsu_state& st = sim[i];
       const int f1 = scratch_index(&st, -1), f2 = scratch_index(&st, f1);
-      tsu::tb_fill_args(&host[((size_t)set * nprob + i) * ab], geom(&probs[i].grid, probs[i].tau), probs[i].medium.hx,
-                        probs[i].medium.hy, st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], status, rows);
+      void* dst = &host[((size_t)set * nprob + i) * ab];
+      if (kern == 2)
+        tsu::wtb_fill_args(dst, geom(&probs[i].grid, probs[i].tau), probs[i].medium.hx, probs[i].medium.hy,
+                           st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], rows);
+      else
+        tsu::tb_fill_args(dst, geom(&probs[i].grid, probs[i].tau), probs[i].medium.hx, probs[i].medium.hy,
+                          st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], status, rows);
       st.cur = f1;
       st.aux = f2;
     }
@@ -517,7 +629,8 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
     for (int oi = 0; oi < nprob; ++oi)
       if (probs[order[oi]].nsteps / k > r) nt = prefix[oi];
     const int set = r == 0 ? 0 : ((r & 1) ? 1 : 2);
-    e = tsu::launch_step_tb_batched(form, k, desc + (size_t)set * nprob * ab, tdev, nt, s);
+    e = kern == 2 ? tsu::launch_step_wtb_batched(form, k, desc + (size_t)set * nprob * ab, ab, tdev, nt, s)
+                  : tsu::launch_step_tb_batched(form, k, desc + (size_t)set * nprob * ab, tdev, nt, s);
     if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run launch");
   }
   // host-side roles after the blocked rounds, then the leftover single steps per problem

@@ -33,6 +33,15 @@ struct EnergyWs {
   int64_t capacity;  // number of partial slots
 };
 
+// Rows per CTA of the one-step passes when the caller does not choose: 32, halved (down to 4)
+// until the grid has at least 4 CTAs per SM (152 SMs), so that small grids still fill the GPU.
+inline int auto_rows(int64_t ld, int64_t ny, int64_t cols_per_cta) {
+  const int64_t cx = (ld + cols_per_cta - 1) / cols_per_cta;
+  int rows = 32;
+  while (rows > 4 && cx * ((ny - 2 + rows - 1) / rows) < 4 * 152) rows /= 2;
+  return rows;
+}
+
 size_t energy_ws_bytes(int64_t ny, int64_t ld);
 EnergyWs energy_ws_carve(void* ws, size_t bytes, int64_t ny, int64_t ld);
 
@@ -70,6 +79,21 @@ cudaError_t launch_step_tb(const StencilGeom& g, int form, int k, const void* hx
                            const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int* status,
                            int rows, int debug_flags, cudaStream_t s);
 
+// Warp-blocked FP32 pass (k_step_wtb.cu): k in {2, 4} steps per launch, no CTA barriers.
+bool wtb_supported_depth(int k);
+int64_t wtb_tiles(int64_t ny, int64_t ld, int rows);
+int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows);
+cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
+                            const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int rows,
+                            cudaStream_t s);
+// batched warp-blocked pass: descriptors of wtb_args_bytes() each, int4 tiles (problem, strip, chunk)
+int wtb_strip_width();
+size_t wtb_args_bytes();
+void wtb_fill_args(void* dst, const StencilGeom& g, const void* hx, const void* hy, const void* u, const void* p,
+                   void* out_a, void* out_b, int rows);
+cudaError_t launch_step_wtb_batched(int form, int k, const void* probs_dev, size_t stride, const void* tiles_dev,
+                                    int64_t ntiles, cudaStream_t s);
+
 // Batched family (k_step_tb.cu): per-problem descriptors (tb_args_bytes() each, filled on the
 // host by tb_fill_args) and an int4 tile table (problem, strip, chunk, 0).
 size_t tb_args_bytes();
@@ -80,9 +104,21 @@ cudaError_t launch_step_tb_batched(int form, int k, const void* probs_dev, const
                                    cudaStream_t s);
 
 // Adjoint (k_adjoint.cu).
+// Receivers bucketed by the adjoint-pass CTA owning their node (off[ncta+1], ord[nrec]) and the
+// values g[r] injected into lam^n by that CTA after its stores; off == nullptr: no injection.
+struct RecBuckets {
+  const int* off;
+  const int* ord;
+  const int64_t* idx;
+  const void* g;
+};
+void adjoint_pass_shape(const StencilGeom& g, int dtype, int64_t* gridx, int64_t* gridy, int* rows,
+                        int64_t* cols_per_cta);
+cudaError_t launch_rec_bucket(const StencilGeom& g, int dtype, const int64_t* idx, int32_t nrec, int* off, int* ord,
+                              int* cta_of, cudaStream_t s);
 cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
                                 const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
-                                void* g_u1, cudaStream_t s);
+                                void* g_u1, const RecBuckets& rb, cudaStream_t s);
 cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,
                           int32_t nrec, cudaStream_t s);
 cudaError_t launch_flush(const StencilGeom& g, void* g32x, void* g32y, double* gx, double* gy, cudaStream_t s);

@@ -78,7 +78,7 @@ class Problem(C.Structure):
 
 
 class BatchOpts(C.Structure):
-    _fields_ = [("tdepth", C.c_int32), ("rows", C.c_int32), ("reserved", C.c_int32 * 2)]
+    _fields_ = [("tdepth", C.c_int32), ("rows", C.c_int32), ("kernel", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -109,7 +109,7 @@ def load():
         "tsu_noalloc_last_error": ([], C.c_char_p),
         "tsu_batch_workspace": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), C.POINTER(C.c_size_t)], C.c_int),
         "tsu_batch_run": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), vp, C.c_size_t, vp], C.c_int),
-        "tsu_adjoint_workspace": ([C.POINTER(Grid), C.c_int, i64, i64, C.POINTER(C.c_size_t)], C.c_int),
+        "tsu_adjoint_workspace": ([C.POINTER(Grid), C.c_int, i64, i64, i32, C.POINTER(C.c_size_t)], C.c_int),
         "tsu_adjoint": ([C.POINTER(Grid), C.c_int, C.c_int, dbl, C.POINTER(Medium), i64, i64, vp, vp, i32, vp, vp,
                          vp, vp, vp, vp, vp, C.c_size_t, vp], C.c_int),
         "tsu_observe": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), vp, i32, vp, vp, vp,
@@ -225,18 +225,18 @@ def _problems(sims, nsteps):
     return arr
 
 
-def tsu_batch_workspace(sims, nsteps, tdepth: int = 0, rows: int = 0) -> int:
+def tsu_batch_workspace(sims, nsteps, tdepth: int = 0, rows: int = 0, kernel: int = 0) -> int:
     arr = _problems(sims, nsteps)
-    o = BatchOpts(int(tdepth), int(rows))
+    o = BatchOpts(int(tdepth), int(rows), int(kernel))
     n = C.c_size_t(0)
     _check(load().tsu_batch_workspace(len(sims), arr, C.byref(o), C.byref(n)), "tsu_batch_workspace")
     return int(n.value)
 
 
-def tsu_batch_run(sims, nsteps, ws, ws_bytes: int, tdepth: int = 0, rows: int = 0, stream=None):
+def tsu_batch_run(sims, nsteps, ws, ws_bytes: int, tdepth: int = 0, rows: int = 0, kernel: int = 0, stream=None):
     """Advance every Simulation in ``sims`` by its entry of ``nsteps`` in batched launches."""
     arr = _problems(sims, nsteps)
-    o = BatchOpts(int(tdepth), int(rows))
+    o = BatchOpts(int(tdepth), int(rows), int(kernel))
     rc = load().tsu_batch_run(len(sims), arr, C.byref(o), _ptr(ws), int(ws_bytes), _stream(stream))
     _check(rc, "tsu_batch_run")
 
@@ -255,10 +255,10 @@ def tsu_ckpt_slots(nsteps: int, ckpt_every: int) -> int:
     return int(load().tsu_ckpt_slots(int(nsteps), int(ckpt_every)))
 
 
-def tsu_adjoint_workspace(g: Grid, dtype, nsteps: int, ckpt_every: int) -> int:
+def tsu_adjoint_workspace(g: Grid, dtype, nsteps: int, ckpt_every: int, nrec: int = 0) -> int:
     n = C.c_size_t(0)
-    _check(load().tsu_adjoint_workspace(C.byref(g), dtype_code(dtype), int(nsteps), int(ckpt_every), C.byref(n)),
-           "tsu_adjoint_workspace")
+    _check(load().tsu_adjoint_workspace(C.byref(g), dtype_code(dtype), int(nsteps), int(ckpt_every), int(nrec),
+                                        C.byref(n)), "tsu_adjoint_workspace")
     return int(n.value)
 
 

@@ -23,7 +23,7 @@ def oracle_tau(ext, g) -> float:
 
 
 def run_gpu(n, depth, u0_np, steps, dtype="f32", form=tsu.TSU_FORM_STANDARD, ny=None, rec_ij=None, tau=None,
-            energy=True, rows=0, kernel=0):
+            energy=True, rows=0, kernel=0, tdepth=0):
     """Taylor start + (steps-1) steps + observe.  Returns dict(u, u_prev, energy[steps], traces[steps][nrec],
     tau, ext, sim)."""
     sim = tsu.Simulation.create(n, depth, dtype=dtype, form=form, ny=ny, tau=tau)
@@ -39,7 +39,7 @@ def run_gpu(n, depth, u0_np, steps, dtype="f32", form=tsu.TSU_FORM_STANDARD, ny=
         tr = torch.zeros((steps, len(rec_ij)), dtype=tdt, device="cuda")
     if steps > 1:
         sim.step(steps - 1, energy=e[: steps - 1] if energy else None, rec_idx=rec,
-                 traces=tr[: steps - 1] if tr is not None else None, rows=rows, kernel=kernel)
+                 traces=tr[: steps - 1] if tr is not None else None, rows=rows, kernel=kernel, tdepth=tdepth)
     sim.observe(energy=e[steps - 1:] if energy else None, rec_idx=rec, trace=tr[steps - 1] if tr is not None else None)
     torch.cuda.synchronize()
     up = sim.u_prev if sim.u_prev is not None else sim.u - sim.v

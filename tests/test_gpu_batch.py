@@ -23,17 +23,17 @@ def make_sims(probs, form):
 
 
 @pytest.mark.parametrize("form", [tsu.TSU_FORM_INCREMENT, tsu.TSU_FORM_STANDARD])
-@pytest.mark.parametrize("K", [4, 8])
-def test_batched_equals_sequential_bitwise(form, K):
+@pytest.mark.parametrize("kernel,K", [(3, 4), (3, 8), (2, 2), (2, 4)])
+def test_batched_equals_sequential_bitwise(form, kernel, K):
     probs = family(steps=1 + 5 * K + 3)
     steps = [p.steps - 1 for p in probs]
     seq = make_sims(probs, form)
     for sim, n in zip(seq, steps):
-        sim.step(n, kernel=3, tdepth=K, rows=64)
+        sim.step(n, kernel=kernel, tdepth=K, rows=64)
     bat = make_sims(probs, form)
-    wsb = tsu.tsu_batch_workspace(bat, steps, tdepth=K, rows=64)
+    wsb = tsu.tsu_batch_workspace(bat, steps, tdepth=K, rows=64, kernel=kernel)
     ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
-    tsu.tsu_batch_run(bat, steps, ws, wsb, tdepth=K, rows=64)
+    tsu.tsu_batch_run(bat, steps, ws, wsb, tdepth=K, rows=64, kernel=kernel)
     tsu.tsu_sync_status(ws, wsb)
     for a, b in zip(seq, bat):
         assert a.state.step == b.state.step
@@ -47,11 +47,11 @@ def test_batched_uneven_step_counts():
     steps = [int(s) for s in rng.integers(0, 60, size=len(probs))]
     seq = make_sims(probs, tsu.TSU_FORM_INCREMENT)
     for sim, n in zip(seq, steps):
-        sim.step(n, kernel=3, tdepth=8, rows=64) if n >= 8 else sim.step(n, kernel=1)
+        sim.step(n, kernel=2, tdepth=4, rows=64) if n >= 4 else sim.step(n, kernel=1)
     bat = make_sims(probs, tsu.TSU_FORM_INCREMENT)
-    wsb = tsu.tsu_batch_workspace(bat, steps, tdepth=8, rows=64)
+    wsb = tsu.tsu_batch_workspace(bat, steps, tdepth=4, rows=64)
     ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
-    tsu.tsu_batch_run(bat, steps, ws, wsb, tdepth=8, rows=64)
+    tsu.tsu_batch_run(bat, steps, ws, wsb, tdepth=4, rows=64)
     for a, b, n in zip(seq, bat, steps):
         assert b.state.step == 1 + n
         assert torch.equal(a.u, b.u), n

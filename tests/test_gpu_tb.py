@@ -20,7 +20,11 @@ def odd_ext_shift(f, s):
     return 0.5 * (F[(idx - s) % len(F)] + F[(idx + s) % len(F)])
 
 
-def courant_one(axis, n_along, n_across, S, K, form, rows=64):
+# (kernel, steps per pass): CTA-blocked (3) and warp-blocked (2)
+BLOCKED = [(3, 4), (3, 8), (2, 2), (2, 4)]
+
+
+def courant_one(axis, n_along, n_across, S, K, form, rows=64, kernel=3):
     """hx = 1, hy = 0 (axis 'x') or hx = 0, hy = 1 (axis 'y'), tau = spacing: d'Alembert exactly."""
     nx, ny = (n_along, n_across) if axis == "x" else (n_across, n_along)
     g = tsu.grid(nx, ny)
@@ -47,7 +51,7 @@ def courant_one(axis, n_along, n_across, S, K, form, rows=64):
     ws = torch.zeros(ws_b, dtype=torch.uint8, device="cuda")
     tsu.tsu_init(g, "f32", tau, med, u0, None, st)
     o = tsu.StepOpts()
-    o.kernel, o.tdepth, o.rows = 3, K, rows
+    o.kernel, o.tdepth, o.rows = kernel, K, rows
     tsu.tsu_step_n(g, "f32", tau, med, st, S - 1, o, ws, ws_b)
     tsu.tsu_sync_status(ws, ws_b)
     u = bufs[st.cur][:, :nx].double().cpu().numpy()
@@ -58,45 +62,47 @@ def courant_one(axis, n_along, n_across, S, K, form, rows=64):
     return u, exact
 
 
-@pytest.mark.parametrize("K", [4, 8])
+@pytest.mark.parametrize("kernel,K", BLOCKED)
 @pytest.mark.parametrize("form", [tsu.TSU_FORM_STANDARD, tsu.TSU_FORM_INCREMENT])
 @pytest.mark.parametrize("axis", ["x", "y"])
-def test_tb_courant_one_bit_exact(K, form, axis):
+def test_tb_courant_one_bit_exact(kernel, K, form, axis):
     S = 1 + 5 * K + 3  # several blocked passes plus leftover single steps
-    u, exact = courant_one(axis, 769, 37, S, K, form)
+    u, exact = courant_one(axis, 769, 37, S, K, form, rows=64 if kernel == 3 else 16, kernel=kernel)
     assert np.array_equal(u, exact)
 
 
-@pytest.mark.parametrize("K", [4, 8])
+@pytest.mark.parametrize("kernel,K", BLOCKED)
 @pytest.mark.parametrize("form,tol", [(tsu.TSU_FORM_INCREMENT, 1e-5), (tsu.TSU_FORM_STANDARD, 1e-4)])
-def test_tb_ragged_parity_with_energy(K, form, tol):
+def test_tb_ragged_parity_with_energy(kernel, K, form, tol):
     nx, ny = 700, 613  # 3 strips (last one partial), 5 chunks of 128 rows (last one partial)
     depth = dict(background=1.0, eps=0.015, mollifier=0, sings=[(0, 1, 1.0, 0.5, 0.5), (2, 1, 0.01, 0.52, 0.47)])
     u0 = inputs.gaussian_hump(nx, ny, None, 0.45, 0.55, 0.03)
     S = 1 + 12 * K + 5
-    gpu = run_gpu(nx, depth, u0, S, dtype="f32", form=form, ny=ny, kernel=3, rows=128)
+    gpu = run_gpu(nx, depth, u0, S, dtype="f32", form=form, ny=ny, kernel=kernel, rows=128, tdepth=K)
     orc = run_oracle(nx, depth, u0, S, ny=ny)
     tsu.tsu_sync_status(gpu["sim"].ws, gpu["sim"].ws.numel())
     assert relerr(gpu["u"], orc["u"]) <= tol
     assert np.max(np.abs(gpu["energy"] - orc["energy"]) / orc["energy"]) <= tol
 
 
+@pytest.mark.parametrize("kernel,K", [(3, 8), (2, 4), (2, 2)])
 @pytest.mark.parametrize("nx,ny", [(3, 3), (5, 4), (9, 300), (300, 6), (37, 41), (250, 251)])
-def test_tb_tiny_and_thin_grids(nx, ny):
+def test_tb_tiny_and_thin_grids(nx, ny, kernel, K):
     depth = dict(background=1.0, eps=0.2, sings=[(2, 1, 0.05, 0.4, 0.6)])
     rng = np.random.default_rng(nx * 7 + ny)
     u0 = inputs.random_field(nx, ny, None, rng)
-    S = 1 + 3 * 8 + 2
-    gpu = run_gpu(nx, depth, u0, S, dtype="f32", ny=ny, kernel=3, rows=16)
+    S = 1 + 3 * K + 2
+    gpu = run_gpu(nx, depth, u0, S, dtype="f32", ny=ny, kernel=kernel, rows=16, tdepth=K)
     orc = run_oracle(nx, depth, u0, S, ny=ny)
     assert relerr(gpu["u"], orc["u"]) <= 1e-5
 
 
-def test_tb_matches_register_streaming_pass():
+@pytest.mark.parametrize("kernel,K", BLOCKED)
+def test_tb_matches_register_streaming_pass(kernel, K):
     n = 1500
     depth = dict(background=0.5, eps=0.004, mollifier=0, sings=[(2, 1, 0.01, 0.5, 0.5)])
     u0 = inputs.gaussian_hump(n, n, None, 0.3, 0.5, 0.02)
-    a = run_gpu(n, depth, u0, 201, dtype="f32", kernel=3)
+    a = run_gpu(n, depth, u0, 201, dtype="f32", kernel=kernel, tdepth=K)
     b = run_gpu(n, depth, u0, 201, dtype="f32", kernel=1)
     assert relerr(a["u"], b["u"]) <= 1e-6
     assert np.max(np.abs(a["energy"] - b["energy"]) / b["energy"]) <= 1e-6

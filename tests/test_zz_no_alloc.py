@@ -25,7 +25,8 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(dtype, form):
     e_ref = torch.zeros(90, dtype=torch.float64, device="cuda")
     e_na = torch.full((90,), -1.0, dtype=torch.float64, device="cuda")
     for a, b in ((0, 50), (50, 90)):  # two calls in a row
-        ref.step(b - a, energy=e_ref[a:b], kernel=1)
+        # the same pass with the same CTA partition (32 rows per CTA, which the fixed scratch is sized for)
+        ref.step(b - a, energy=e_ref[a:b], kernel=1, rows=32)
         tsu.tsu_step_n_noalloc(na.g, na.dtype, na.tau, na.medium, na.state, b - a, energy=e_na[a:b])
         torch.cuda.synchronize()
         assert na.state.step == ref.state.step
