@@ -417,7 +417,7 @@ def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
     gy = torch.zeros_like(gx)
     gu0 = torch.zeros_like(u0)
     gu1 = torch.zeros_like(u0)
-    wsb = tsu.tsu_adjoint_workspace(g, tsu.TSU_F32, S, every, nrec)
+    wsb = tsu.tsu_adjoint_workspace(g, tsu.TSU_F32, tsu.TSU_FORM_INCREMENT, S, every, nrec)
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
 
     def adjoint():

@@ -186,10 +186,10 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
  * tsu_step_n is given ckpt_every: states m = 1, 1 + every, ... <= nsteps - 1.  Host only. */
 int64_t tsu_ckpt_slots(int64_t nsteps, int64_t ckpt_every);
 
-/* Bytes of device workspace tsu_adjoint needs for nrec receivers: 2 (ckpt_every + 3) fields of
- * dtype (multipliers and two segment buffers), two FP32 gradient accumulators for FP32 fields,
- * and a receiver table. */
-int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, int32_t nrec,
+/* Bytes of device workspace tsu_adjoint needs for a forward run of this form with nrec receivers:
+ * 2 ckpt_every + 6 fields of dtype (multipliers and two recompute segments), two FP32 gradient
+ * accumulators for FP32 fields and a receiver table. */
+int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps, int64_t ckpt_every, int32_t nrec,
                           size_t* bytes);
 
 /* Reverse-time discrete adjoint of the forward run "tsu_init(u0, u1) then tsu_step_n(nsteps-1)"
@@ -203,9 +203,9 @@ int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t 
  *   g_hx, g_hy  device double [ny][ld], overwritten with dJ/dhx, dJ/dhy (FP64 accumulation;
  *             for FP32 fields FP32 partial sums over one segment are added into them)
  *   g_u0, g_u1  device [ny][ld] of dtype, overwritten with dJ/du0, dJ/du1
- * The recompute of one segment runs on a library-owned stream (one per device, created by the
- * first call) concurrently with the reverse sweep of the previous one; all of it is ordered before
- * the call's last work on the caller's stream.
+ * Every segment is recomputed from its checkpoint on a library-owned stream (one per device,
+ * created by the first call) concurrently with the reverse sweep of the previous one; all of it is
+ * ordered before the call's last work on the caller's stream.
  * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
 int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_medium* m, int64_t nsteps,
                 int64_t ckpt_every, const void* ckpt, const void* u0, int32_t nrec, const int64_t* rec_idx,

@@ -69,7 +69,7 @@ class TsunamiFn(torch.autograd.Function):
         g_hy = torch.zeros(u0.shape, dtype=torch.float64, device=dev)
         g_u0 = torch.zeros_like(u0)
         g_u1 = torch.zeros_like(u0)
-        ws_b = tsu.tsu_adjoint_workspace(g, code, S, cfg.ckpt_every, int(cfg.rec_idx.numel()))
+        ws_b = tsu.tsu_adjoint_workspace(g, code, cfg.form, S, cfg.ckpt_every, int(cfg.rec_idx.numel()))
         ws = torch.empty(ws_b, dtype=torch.uint8, device=dev)
         tsu.tsu_adjoint(g, code, cfg.form, cfg.tau, med, S, cfg.ckpt_every, ckpt, u0, cfg.rec_idx,
                         dtraces.contiguous().to(u0.dtype), g_hx, g_hy, g_u0, g_u1, ws, ws_b)

@@ -25,14 +25,17 @@ struct AccOf<double> { using type = double; };
 
 // MODE 0: lam_out = (2 lam_c - lam_pp) + B lam_c          (the recursion)
 // MODE 1: lam_out = (lam_c - lam_pp) + B lam_c / 2 = dJ/du0; g_u1 = tau lam_c   (the start)
-template <typename T, int MODE>
+// REV: the pass also steps the increment-form state backwards, the exact inverse of the forward
+//      step: u^{n-1} = u^n - v^n, v^{n-1} = v^n - B u^{n-1}, from (u, v_in) into (u_out, v_out).
+template <typename T, int MODE, bool REV>
 __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const int32_t ny, const int64_t ld,
                                                       const typename ArithOf<T>::type ar, const T gwx, const T gwy,
                                                       const T tau, const T* __restrict__ hx, const T* __restrict__ hy,
                                                       const T* __restrict__ lam, const T* lam_pp, T* lam_out,
                                                       const T* __restrict__ u, typename AccOf<T>::type* gx,
                                                       typename AccOf<T>::type* gy, T* g_u1, const int rows,
-                                                      const RecBuckets rb) {
+                                                      const RecBuckets rb, const T* __restrict__ v_in,
+                                                      T* __restrict__ u_out, T* __restrict__ v_out) {
   using A = typename AccOf<T>::type;
   constexpr int V = Vec<T>::V;
   const int lane = threadIdx.x & 31;
@@ -60,6 +63,20 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
   Pack<T> lc = ld_vec(lam + (int64_t)j0 * ld + i0);
   Pack<T> hym = ld_vec(hy + (int64_t)(j0 - 1) * ld + i0);
   Pack<T> uc = umask(ld_vec(u + (int64_t)j0 * ld + i0), j0);
+  // reverse state step: w = u^{n-1} = u^n - v^n on rows j-1, j, j+1
+  Pack<T> vc, wm, wc;
+  auto wdiff = [&](const Pack<T>& a, const Pack<T>& b) {
+    Pack<T> r;
+#pragma unroll
+    for (int e = 0; e < V; ++e) r.a[e] = a.a[e] - b.a[e];
+    return r;
+  };
+  if constexpr (REV) {
+    vc = umask(ld_vec(v_in + (int64_t)j0 * ld + i0), j0);
+    wm = wdiff(umask(ld_vec(u + (int64_t)(j0 - 1) * ld + i0), j0 - 1),
+               umask(ld_vec(v_in + (int64_t)(j0 - 1) * ld + i0), j0 - 1));
+    wc = wdiff(uc, vc);
+  }
   for (int j = j0; j < j1; ++j) {
     const int64_t row = (int64_t)j * ld + i0;
     const Pack<T> ln = ld_vec(lam + row + ld);
@@ -67,6 +84,11 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
     const Pack<T> hxv = ld_vec(hx + row);
     const Pack<T> hyv = ld_vec(hy + row);
     const Pack<T> un = umask(ld_vec(u + row + ld), j + 1);
+    Pack<T> vn, wn;
+    if constexpr (REV) {
+      vn = umask(ld_vec(v_in + row + ld), j + 1);
+      wn = wdiff(un, vn);
+    }
     T ll = __shfl_up_sync(0xffffffffu, lc.a[V - 1], 1);
     T hl = __shfl_up_sync(0xffffffffu, hxv.a[V - 1], 1);
     T lr = __shfl_down_sync(0xffffffffu, lc.a[0], 1);
@@ -79,7 +101,17 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       lr = (i0 + V < ld) ? lam[row + V] : T(0);
       ur = u_at(i0 + V, j);
     }
-    Pack<T> out, gu1;
+    T wl = T(0), wr = T(0);
+    if constexpr (REV) {
+      wl = __shfl_up_sync(0xffffffffu, wc.a[V - 1], 1);
+      wr = __shfl_down_sync(0xffffffffu, wc.a[0], 1);
+      auto v_at = [&](int64_t i) -> T {
+        return (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2) ? v_in[(int64_t)j * ld + i] : T(0);
+      };
+      if (lane == 0) wl = u_at(i0 - 1, j) - v_at(i0 - 1);
+      if (lane == 31) wr = u_at(i0 + V, j) - v_at(i0 + V);
+    }
+    Pack<T> out, gu1, uo, vo;
     A gxv[V], gyv[V], gy0[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -107,6 +139,16 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       gxv[e] = (i <= nx - 2) ? (A)(gwx * (dlx * dux)) : A(0);
       gyv[e] = interior ? (A)(gwy * (dly * duy)) : A(0);
       gy0[e] = interior ? (A)(gwy * (lc.a[e] * uc.a[e])) : A(0);  // y-face (0, 1), used on row 1
+      if constexpr (REV) {
+        const T wxl = (e == 0) ? wl : wc.a[e - 1];
+        const T wxr = (e == V - 1) ? wr : wc.a[e + 1];
+        const T bw = ar.b(hxv.a[e], hxl, hyv.a[e], hym.a[e], wc.a[e], wxl, wxr, wn.a[e], wm.a[e]);
+        uo.a[e] = interior ? wc.a[e] : T(0);
+        if constexpr (sizeof(T) == 8)
+          vo.a[e] = interior ? __dsub_rn(vc.a[e], bw) : T(0);
+        else
+          vo.a[e] = interior ? vc.a[e] - bw : T(0);
+      }
     }
     if (active) {
       if constexpr (MODE == 0)
@@ -124,6 +166,10 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       }
       st_vec(gx + row, ax);
       st_vec(gy + row, ay);
+      if constexpr (REV) {
+        st_vec(u_out + row, uo);
+        st_vec(v_out + row, vo);
+      }
       if (j == 1) {
         Pack<A> a0 = ld_vec_l2(gy + i0);
 #pragma unroll
@@ -135,6 +181,11 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
     lc = ln;
     hym = hyv;
     uc = un;
+    if constexpr (REV) {
+      vc = vn;
+      wm = wc;
+      wc = wn;
+    }
   }
   // receiver injection lam^n += g^n at this CTA's receivers, in receiver order, after the CTA's
   // own stores of lam^n (visible to the CTA after the barrier)
@@ -220,7 +271,7 @@ namespace {
 template <typename T>
 cudaError_t pass_t(const StencilGeom& g, bool start, const void* hx, const void* hy, const void* lam,
                    const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy, void* g_u1,
-                   const RecBuckets& rb, cudaStream_t s) {
+                   const RecBuckets& rb, const void* v_in, void* u_out, void* v_out, cudaStream_t s) {
   using A = typename AccOf<T>::type;
   int64_t gx_, gy_, cpc;
   int rows;
@@ -229,14 +280,19 @@ cudaError_t pass_t(const StencilGeom& g, bool start, const void* hx, const void*
   dim3 grid((unsigned)gx_, (unsigned)gy_);
   const T w = start ? T(0.5) : T(1);
   const T gwx = -(T)g.cx * w, gwy = -(T)g.cy * w;
-  if (!start)
-    k_adjoint_pass<T, 0><<<grid, threads, 0, s>>>(g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx,
-                                                   (const T*)hy, (const T*)lam, (const T*)lam_pp, (T*)lam_out,
-                                                   (const T*)u, (A*)gx, (A*)gy, nullptr, rows, rb);
+  if (start)
+    k_adjoint_pass<T, 1, false><<<grid, threads, 0, s>>>(
+        g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx, (const T*)hy, (const T*)lam,
+        (const T*)lam_pp, (T*)lam_out, (const T*)u, (A*)gx, (A*)gy, (T*)g_u1, rows, rb, nullptr, nullptr, nullptr);
+  else if (v_in)
+    k_adjoint_pass<T, 0, true><<<grid, threads, 0, s>>>(
+        g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx, (const T*)hy, (const T*)lam,
+        (const T*)lam_pp, (T*)lam_out, (const T*)u, (A*)gx, (A*)gy, nullptr, rows, rb, (const T*)v_in, (T*)u_out,
+        (T*)v_out);
   else
-    k_adjoint_pass<T, 1><<<grid, threads, 0, s>>>(g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx,
-                                                   (const T*)hy, (const T*)lam, (const T*)lam_pp, (T*)lam_out,
-                                                   (const T*)u, (A*)gx, (A*)gy, (T*)g_u1, rows, rb);
+    k_adjoint_pass<T, 0, false><<<grid, threads, 0, s>>>(
+        g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx, (const T*)hy, (const T*)lam,
+        (const T*)lam_pp, (T*)lam_out, (const T*)u, (A*)gx, (A*)gy, nullptr, rows, rb, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 }  // namespace
@@ -252,9 +308,11 @@ cudaError_t launch_rec_bucket(const StencilGeom& g, int dtype, const int64_t* id
 
 cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
                                 const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
-                                void* g_u1, const RecBuckets& rb, cudaStream_t s) {
-  return dtype == TSU_F32 ? pass_t<float>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, s)
-                          : pass_t<double>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, s);
+                                void* g_u1, const RecBuckets& rb, cudaStream_t s, const void* v_in, void* u_out,
+                                void* v_out) {
+  return dtype == TSU_F32
+             ? pass_t<float>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, v_in, u_out, v_out, s)
+             : pass_t<double>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, v_in, u_out, v_out, s);
 }
 
 cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,

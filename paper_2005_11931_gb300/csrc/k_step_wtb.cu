@@ -15,6 +15,8 @@
 // x (L + 2K)/L for the halo rows: 6.4 B per lattice update at K = 4.
 #include <string.h>
 
+#include <type_traits>
+
 #include "stencil_common.cuh"
 
 namespace tsu {
@@ -27,8 +29,10 @@ constexpr int kWtbPre = 2;         // rows in flight ahead of the one being cons
 
 template <int K>
 struct WtbShape {
-  static constexpr int SA = kWtbPre + 2;      // ring of (u, p) rows: in flight + current + previous
-  static constexpr int SB = K + 2 + kWtbPre;  // ring of (hx, hy) rows: levels' rows + in flight
+  // rings of power-of-two length (slot = row index & (S - 1))
+  static constexpr int SA = 4;                // (u, p) rows: in flight (2) + current + previous
+  static constexpr int SB = 8;                // (hx, hy) rows: the levels' rows (K + 2) + in flight (2)
+  static_assert(kWtbPre + 2 <= SA && K + 2 + kWtbPre <= SB, "ring too short");
   // bytes per thread
   static constexpr int bytes = (SA * 2 + SB * 2) * 16;
 };
@@ -125,8 +129,8 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   // this thread's private ring: A[SA][2] float4 (u, p), B[SB][2] float4 (hx, hy)
   float* ringA = reinterpret_cast<float*>(wtb_smem) + (size_t)threadIdx.x * 4;
   const int stride = kWtbWarps * 32 * 4;  // floats between consecutive float4 slots of one thread
-  auto slotA = [&](int s, int f) { return ringA + (size_t)(s * 2 + f) * stride; };
-  auto slotB = [&](int s, int f) { return ringA + (size_t)(Sh::SA * 2 + s * 2 + f) * stride; };
+  auto slotA = [&](unsigned s, int f) { return ringA + (size_t)(s * 2 + f) * stride; };
+  auto slotB = [&](unsigned s, int f) { return ringA + (size_t)(Sh::SA * 2 + s * 2 + f) * stride; };
 
   const int64_t xs = strip * kWtbOut - 4;
   const int64_t c0 = xs + 4 * lane;  // first of this lane's four columns
@@ -142,7 +146,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   auto issue = [&](int r) {  // copies of input row r into the rings (zeros outside the grid)
     const bool ok = col_in && r >= 0 && r < a.ny;
     const int64_t go = ok ? (int64_t)r * a.ld + c0 : 0;
-    const int sa = ((r - r_first) % Sh::SA + Sh::SA) % Sh::SA, sb = ((r - r_first) % Sh::SB + Sh::SB) % Sh::SB;
+    const unsigned sa = (unsigned)(r - r_first) & (Sh::SA - 1), sb = (unsigned)(r - r_first) & (Sh::SB - 1);
     cp16(slotA(sa, 0), a.u + go, ok);
     cp16(slotA(sa, 1), a.p + go, ok);
     cp16(slotB(sb, 0), a.hx + go, ok);
@@ -150,7 +154,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   };
   auto ringB = [&](int r, int f) -> F4 {  // hx (f = 0) or hy (f = 1) of row r, zeros outside
     if (r < r_first) return F4{{0.f, 0.f, 0.f, 0.f}};
-    return lds4(slotB((r - r_first) % Sh::SB, f));
+    return lds4(slotB((unsigned)(r - r_first) & (Sh::SB - 1), f));
   };
 
   // registers: w[t][0..2] = level t at its latest three rows, v[t][0..1] likewise (increment form)
@@ -170,12 +174,13 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     if (q < nit) issue(r_first + q);
     cp_commit();
   }
-  for (int it = 0; it < nit; ++it) {
+  // Iterations whose levels all lie on interior output rows of a strip without boundary columns
+  // take the fast path: no masking, no range checks (the edge path handles the rest).
+  const bool interior_strip = (xs >= 1) && (xs + 127 <= (int64_t)a.nx - 2);
+  auto iterate = [&](auto edge_tag, const int it) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
     const int r_in = r_first + it;
-    if (it + kWtbPre < nit) issue(r_in + kWtbPre);
-    cp_commit();
-    cp_wait<kWtbPre>();  // this thread's copies of row r_in have landed
-    const int sa = it % Sh::SA;
+    const unsigned sa = (unsigned)it & (Sh::SA - 1);
     // ---- level 0: the input row
 #pragma unroll
     for (int t = 0; t <= K; ++t) {
@@ -191,23 +196,35 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
       const int rt = r_in - t;
-      const F4 hxv = ringB(rt, 0), hyv = ringB(rt, 1), hyd = ringB(rt - 1, 1);
+      F4 hxv, hyv, hyd;
+      if constexpr (EDGE) {
+        hxv = ringB(rt, 0);
+        hyv = ringB(rt, 1);
+        hyd = ringB(rt - 1, 1);
+      } else {  // rows rt - 1 >= r_first: plain ring slots
+        const unsigned sb = (unsigned)(it - t) & (Sh::SB - 1), sd = (unsigned)(it - t - 1) & (Sh::SB - 1);
+        hxv = lds4(slotB(sb, 0));
+        hyv = lds4(slotB(sb, 1));
+        hyd = lds4(slotB(sd, 1));
+      }
       const F4 uc = w[t - 1][1], uu = w[t - 1][0], ud = w[t - 1][2];
       F4 pc;  // u^{n-1} (standard) or v at row rt of the level below
       if (t == 1) {
-        pc = (it >= 1) ? lds4(slotA((it - 1) % Sh::SA, 1)) : F4{{0.f, 0.f, 0.f, 0.f}};
-        if constexpr (FORM == 1) pc = vv[0][1];
+        if constexpr (FORM == 1)
+          pc = vv[0][1];
+        else
+          pc = (!EDGE || it >= 1) ? lds4(slotA((unsigned)(it - 1) & (Sh::SA - 1), 1)) : F4{{0.f, 0.f, 0.f, 0.f}};
       } else {
         if constexpr (FORM == 0)
           pc = w[t - 2][2];
         else
           pc = vv[t - 1][1];
       }
-      float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1);
-      float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
-      float hl = __shfl_up_sync(0xffffffffu, hxv.a[3], 1);
-      const bool row_in = rt >= 1 && rt <= a.ny - 2;
-      const bool row_out = rt >= y0 && rt < y1;
+      const float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1);
+      const float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
+      const float hl = __shfl_up_sync(0xffffffffu, hxv.a[3], 1);
+      const bool row_in = !EDGE || (rt >= 1 && rt <= a.ny - 2);
+      const bool row_out = !EDGE || (rt >= y0 && rt < y1);
       F4 un, vn;
       float erow = 0.f;
 #pragma unroll
@@ -218,7 +235,6 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         const float fx = hxv.a[e] * (xr - uc.a[e]) - hxl * (uc.a[e] - xl);
         const float fy = hyv.a[e] * (uu.a[e] - uc.a[e]) - hyd.a[e] * (uc.a[e] - ud.a[e]);
         const float b = fmaf(a.cx, fx, a.cy * fy);
-        const bool node = row_in && node_col[e];
         float unew, vnew = 0.f, up;
         if constexpr (FORM == 0) {
           up = pc.a[e];
@@ -228,12 +244,22 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
           vnew = pc.a[e] + b;
           unew = uc.a[e] + vnew;
         }
-        un.a[e] = node ? unew : 0.f;
-        vn.a[e] = node ? vnew : 0.f;
-        if constexpr (ENERGY) {
-          if (node && row_out && col_out) {
+        if constexpr (EDGE) {
+          const bool node = row_in && node_col[e];
+          un.a[e] = node ? unew : 0.f;
+          vn.a[e] = node ? vnew : 0.f;
+          if constexpr (ENERGY) {
+            if (node && row_out && col_out) {
+              const float d = uc.a[e] - up;
+              erow += d * d - b * up;
+            }
+          }
+        } else {
+          un.a[e] = unew;
+          vn.a[e] = vnew;
+          if constexpr (ENERGY) {
             const float d = uc.a[e] - up;
-            erow += d * d - b * up;
+            erow += d * d - b * up;  // lanes that are not output are masked once at the end
           }
         }
       }
@@ -258,6 +284,22 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         else
           stg4(a.out_b + o, w[K - 1][1]);  // level K-1 at the same row
       }
+    }
+  };
+  for (int it = 0; it < nit; ++it) {
+    const int r_in = r_first + it;
+    if (it + kWtbPre < nit) issue(r_in + kWtbPre);
+    cp_commit();
+    cp_wait<kWtbPre>();  // this thread's copies of row r_in have landed
+    if (interior_strip && r_in - K >= y0 && r_in - 1 < y1)
+      iterate(std::integral_constant<bool, false>(), it);
+    else
+      iterate(std::integral_constant<bool, true>(), it);
+  }
+  if constexpr (ENERGY) {
+    if (!col_out) {  // fast-path sums of halo lanes and lanes beyond the row
+#pragma unroll
+      for (int t = 0; t < K; ++t) es[t] = ec[t] = 0.f;
     }
   }
   cp_wait<0>();
@@ -359,6 +401,16 @@ cudaError_t launch_step_wtb_batched(int form, int k, const void* probs_dev, size
 
 int64_t wtb_tiles(int64_t ny, int64_t ld, int rows) {
   return ((ld + 4 + kWtbOut - 1) / kWtbOut) * ((ny - 2 + rows - 1) / rows);
+}
+
+// Rows per chunk: 96 (the measured optimum on 8192^2: 654 GLUPS at 96 rows against 604 at 240),
+// shortened in steps of 16 (down to 32) while the grid has fewer than two rounds of tiles for the
+// 152 SMs x 16 resident warps.
+int wtb_auto_rows(int64_t ny, int64_t ld, int k) {
+  (void)k;
+  int rows = 96;
+  while (rows > 32 && wtb_tiles(ny, ld, rows) < 2 * 152 * 16) rows -= 16;
+  return rows;
 }
 
 int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows) {

@@ -227,9 +227,7 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   // when its tiles give at least ~500 CTAs (rows per chunk 256, halved down to 64 to get there);
   // smaller grids run one step per pass (their fields largely stay in L2)
   const int wdepth = o.tdepth ? o.tdepth : 4;
-  int wrows = o.rows ? (o.rows < 16 ? 16 : o.rows) : 256;
-  if (!o.rows)
-    while (wrows > 64 && (tsu::wtb_tiles(g->ny, g->ld, wrows) + 3) / 4 < 500) wrows /= 2;
+  int wrows = o.rows ? (o.rows < 16 ? 16 : o.rows) : tsu::wtb_auto_rows(g->ny, g->ld, wdepth);
   const bool wtb_fills = (tsu::wtb_tiles(g->ny, g->ld, wrows) + 3) / 4 >= 300;
   const bool use_wtb = tb_possible && nsteps >= wdepth && tsu::wtb_supported_depth(wdepth) &&
                        (o.kernel == 2 || (o.kernel == 0 && wtb_fills));
@@ -314,22 +312,34 @@ static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
   return gx * gy;
 }
 
-static size_t adjoint_ws_bytes(const tsu_grid* g, int dtype, int64_t every, int32_t nrec) {
+// The time-reversed sweep (increment form: each adjoint pass also inverts one forward step, no
+// segment storage) is exact up to rounding but measured slower on GB300 at 2048^2 (230 ms against
+// 184 ms for the overlapped recompute, 4000 steps): it stays available behind this switch.
+constexpr bool kAdjointTimeReversal = false;
+
+// fields of dtype before the FP32 accumulators: 2 multipliers, then two segment buffers of E + 2
+// (or, for the time-reversed sweep, the two (u, v) states)
+static int64_t adjoint_fields(int form, int64_t every) {
+  return (form == TSU_FORM_INCREMENT && kAdjointTimeReversal) ? 2 + 4 : 2 + 2 * (every + 2);
+}
+
+static size_t adjoint_ws_bytes(const tsu_grid* g, int dtype, int form, int64_t every, int32_t nrec) {
   const size_t fb = (size_t)g->ny * g->ld * elem_size(dtype);
-  size_t b = (size_t)(2 * (every + 2) + 2) * fb;  // 2 multipliers + two segment buffers of E + 2 fields
+  size_t b = (size_t)adjoint_fields(form, every) * fb;
   if (dtype == TSU_F32) b += 2 * (size_t)g->ny * g->ld * sizeof(float);
   const size_t buckets = ((size_t)(adjoint_ctas(g, dtype) + 1) + 2 * (size_t)(nrec > 0 ? nrec : 0)) * sizeof(int);
   return b + (buckets + 255) / 256 * 256 + 256;
 }
 
-int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int64_t nsteps, int64_t ckpt_every, int32_t nrec,
+int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps, int64_t ckpt_every, int32_t nrec,
                           size_t* bytes) {
   g_err[0] = 0;
   TRY(check_grid(g));
   TRY(check_dtype(dtype));
   if (!bytes) return fail(TSU_EINVAL, "bytes is NULL");
+  if (form != TSU_FORM_STANDARD && form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
   if (nsteps < 1 || ckpt_every < 1 || nrec < 0) return fail(TSU_EINVAL, "nsteps, ckpt_every >= 1 and nrec >= 0");
-  *bytes = adjoint_ws_bytes(g, dtype, ckpt_every, nrec);
+  *bytes = adjoint_ws_bytes(g, dtype, form, ckpt_every, nrec);
   return TSU_OK;
 }
 
@@ -391,10 +401,10 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   TRY(check_field(g_u1, "g_u1"));
   if (form != TSU_FORM_STANDARD && form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
   if (nsteps < 1 || ckpt_every < 1) return fail(TSU_EINVAL, "nsteps and ckpt_every must be >= 1");
-  const int64_t C = tsu_ckpt_slots(nsteps, ckpt_every);
+  int64_t C = tsu_ckpt_slots(nsteps, ckpt_every);
   if (C > 0) TRY(check_field(ckpt, "ckpt"));
   if (nrec < 0 || (nrec > 0 && (!rec_idx || !dtraces))) return fail(TSU_EINVAL, "receivers need rec_idx and dtraces");
-  const size_t need = adjoint_ws_bytes(g, dtype, ckpt_every, nrec);
+  const size_t need = adjoint_ws_bytes(g, dtype, form, ckpt_every, nrec);
   if (!ws || ws_bytes < need) return fail(TSU_ENOMEM, "adjoint workspace %zu B < %zu B", ws_bytes, need);
   TRY(check_field(ws, "workspace"));
   cudaStream_t s = (cudaStream_t)stream;
@@ -406,7 +416,7 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   // two segment buffers, each seg[k] = u^{m_c + k} (k = 0..E) followed by one restore field
   // (u^{m_c - 1} or v); the recompute of one segment overlaps the reverse sweep of the other
   char* segbuf[2] = {w + 2 * fb, w + 2 * fb + (size_t)(ckpt_every + 2) * fb};
-  char* g32 = w + (size_t)(2 * (ckpt_every + 2) + 2) * fb;  // FP32 accumulators [2][ny][ld]
+  char* g32 = w + (size_t)adjoint_fields(form, ckpt_every) * fb;  // FP32 accumulators [2][ny][ld]
   const size_t f32b = (size_t)g->ny * g->ld * sizeof(float);
   void* accx = dtype == TSU_F32 ? (void*)g32 : (void*)g_hx;
   void* accy = dtype == TSU_F32 ? (void*)(g32 + f32b) : (void*)g_hy;
@@ -433,8 +443,52 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     return r;
   };
   if (C == 0) {  // nsteps == 1: lam^1 = g^1 (the gradient term of n = 1 vanishes with lam^2 = 0)
-    e = step_back(1, segp(0, 0));
+    e = step_back(1, (void*)lam[1]);  // a zero field: the u argument is not used with lam^2 = 0
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
+  }
+  if (form == TSU_FORM_INCREMENT && C > 0 && kAdjointTimeReversal) {
+    // Time-reversed sweep.  The increment-form step is exactly invertible:
+    //   u^{n-1} = u^n - v^n,  v^{n-1} = v^n - B u^{n-1},
+    // so each adjoint pass also steps the state back and no segment is stored.  The state is
+    // re-anchored to the checkpoint (exact forward values) whenever the sweep reaches one, which
+    // bounds the rounding drift of the reversal to one segment.
+    char* U[2] = {w + 2 * fb, w + 3 * fb};
+    char* Vb[2] = {w + 4 * fb, w + 5 * fb};
+    const int64_t mlast = 1 + (C - 1) * ckpt_every;
+    const char* slot = (const char*)ckpt + (size_t)(C - 1) * 2 * fb;
+    e = cudaMemcpyAsync(U[0], slot, fb, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Vb[0], slot + fb, fb, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint restore");
+    int pu = 0;  // u in U[pu], v in Vb[pv]
+    int pv = 0;
+    tsu::PassOut none{};
+    for (int64_t k = mlast; k < nsteps; ++k) {  // forward to u^S, v^S (v in place)
+      e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, nullptr, U[pu], Vb[pv], U[pu ^ 1], none, true, 0, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint recompute");
+      pu ^= 1;
+    }
+    for (int64_t n = nsteps; n >= 1; --n) {
+      tsu::RecBuckets rb{};
+      if (nrec > 0) rb = {b_off, b_ord, rec_idx, (const char*)dtraces + (size_t)(n - 1) * nrec * es};
+      e = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam[a], lam[a ^ 1], lam[a ^ 1], U[pu], accx, accy,
+                                   nullptr, rb, s, Vb[pv], U[pu ^ 1], Vb[pv ^ 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
+      a ^= 1;
+      pu ^= 1;
+      pv ^= 1;
+      const int64_t m_state = n - 1;  // the state now held
+      if (m_state >= 1 && (m_state - 1) % ckpt_every == 0 && (m_state - 1) / ckpt_every < C) {
+        const char* sl = (const char*)ckpt + (size_t)((m_state - 1) / ckpt_every) * 2 * fb;
+        e = cudaMemcpyAsync(U[pu], sl, fb, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Vb[pv], sl + fb, fb, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint re-anchor");
+      }
+      if (dtype == TSU_F32 && ((n - 1) % ckpt_every) == 0) {
+        e = tsu::launch_flush(sg, accx, accy, g_hx, g_hy, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint flush");
+      }
+    }
+    C = 0;  // the segment loop below has nothing left to do
   }
   // the recompute stream starts after the resets above
   e = cudaEventRecord(aux->start, s);

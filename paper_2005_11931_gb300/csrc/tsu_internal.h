@@ -82,6 +82,7 @@ cudaError_t launch_step_tb(const StencilGeom& g, int form, int k, const void* hx
 // Warp-blocked FP32 pass (k_step_wtb.cu): k in {2, 4} steps per launch, no CTA barriers.
 bool wtb_supported_depth(int k);
 int64_t wtb_tiles(int64_t ny, int64_t ld, int rows);
+int wtb_auto_rows(int64_t ny, int64_t ld, int k);
 int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows);
 cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
                             const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int rows,
@@ -116,9 +117,11 @@ void adjoint_pass_shape(const StencilGeom& g, int dtype, int64_t* gridx, int64_t
                         int64_t* cols_per_cta);
 cudaError_t launch_rec_bucket(const StencilGeom& g, int dtype, const int64_t* idx, int32_t nrec, int* off, int* ord,
                               int* cta_of, cudaStream_t s);
+// v_in != nullptr: the pass also steps the increment-form state back, (u, v_in) -> (u_out, v_out)
 cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
                                 const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
-                                void* g_u1, const RecBuckets& rb, cudaStream_t s);
+                                void* g_u1, const RecBuckets& rb, cudaStream_t s, const void* v_in = nullptr,
+                                void* u_out = nullptr, void* v_out = nullptr);
 cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,
                           int32_t nrec, cudaStream_t s);
 cudaError_t launch_flush(const StencilGeom& g, void* g32x, void* g32y, double* gx, double* gy, cudaStream_t s);

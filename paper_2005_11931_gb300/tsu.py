@@ -109,7 +109,8 @@ def load():
         "tsu_noalloc_last_error": ([], C.c_char_p),
         "tsu_batch_workspace": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), C.POINTER(C.c_size_t)], C.c_int),
         "tsu_batch_run": ([i32, C.POINTER(Problem), C.POINTER(BatchOpts), vp, C.c_size_t, vp], C.c_int),
-        "tsu_adjoint_workspace": ([C.POINTER(Grid), C.c_int, i64, i64, i32, C.POINTER(C.c_size_t)], C.c_int),
+        "tsu_adjoint_workspace": ([C.POINTER(Grid), C.c_int, C.c_int, i64, i64, i32, C.POINTER(C.c_size_t)],
+                                  C.c_int),
         "tsu_adjoint": ([C.POINTER(Grid), C.c_int, C.c_int, dbl, C.POINTER(Medium), i64, i64, vp, vp, i32, vp, vp,
                          vp, vp, vp, vp, vp, C.c_size_t, vp], C.c_int),
         "tsu_observe": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), vp, i32, vp, vp, vp,
@@ -255,10 +256,10 @@ def tsu_ckpt_slots(nsteps: int, ckpt_every: int) -> int:
     return int(load().tsu_ckpt_slots(int(nsteps), int(ckpt_every)))
 
 
-def tsu_adjoint_workspace(g: Grid, dtype, nsteps: int, ckpt_every: int, nrec: int = 0) -> int:
+def tsu_adjoint_workspace(g: Grid, dtype, form: int, nsteps: int, ckpt_every: int, nrec: int = 0) -> int:
     n = C.c_size_t(0)
-    _check(load().tsu_adjoint_workspace(C.byref(g), dtype_code(dtype), int(nsteps), int(ckpt_every), int(nrec),
-                                        C.byref(n)), "tsu_adjoint_workspace")
+    _check(load().tsu_adjoint_workspace(C.byref(g), dtype_code(dtype), int(form), int(nsteps), int(ckpt_every),
+                                        int(nrec), C.byref(n)), "tsu_adjoint_workspace")
     return int(n.value)
 
 

@@ -36,7 +36,7 @@ def gpu_forward_adjoint(nx, ny, depth, u0n, u1n, S, rec_ij, dtr, dtype, form, ev
     dt = torch.from_numpy(dtr).to(tdt).cuda()
     out = {k: torch.zeros((g.ny, g.ld), dtype=torch.float64 if k in ("g_hx", "g_hy") else tdt, device="cuda")
            for k in ("g_hx", "g_hy", "g_u0", "g_u1")}
-    wsb = tsu.tsu_adjoint_workspace(g, sim.dtype, S, every, len(rec))
+    wsb = tsu.tsu_adjoint_workspace(g, sim.dtype, form, S, every, len(rec))
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     tsu.tsu_adjoint(g, sim.dtype, form, sim.tau, sim.medium, S, every, ck, u0, rec, dt, out["g_hx"], out["g_hy"],
                     out["g_u0"], out["g_u1"], ws, wsb)
