@@ -317,17 +317,26 @@ static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
 // 184 ms for the overlapped recompute, 4000 steps): it stays available behind this switch.
 constexpr bool kAdjointTimeReversal = false;
 
-// fields of dtype before the FP32 accumulators: 2 multipliers, then two segment buffers of E + 2
+// fields of dtype before the FP32 accumulators: 4 multipliers, then two segment buffers of E + 2
 // (or, for the time-reversed sweep, the two (u, v) states)
 static int64_t adjoint_fields(int form, int64_t every) {
-  return (form == TSU_FORM_INCREMENT && kAdjointTimeReversal) ? 2 + 4 : 2 + 2 * (every + 2);
+  return (form == TSU_FORM_INCREMENT && kAdjointTimeReversal) ? 4 + 4 : 4 + 2 * (every + 2);
+}
+
+// receiver tables: the one-step pass's (per CTA) and the two-step pass's (per tile, <= 4 per receiver)
+static size_t adjoint_bucket_bytes(const tsu_grid* g, int dtype, int32_t nrec) {
+  const size_t nr = nrec > 0 ? (size_t)nrec : 0;
+  const size_t one = ((size_t)(adjoint_ctas(g, dtype) + 1) + 2 * nr) * sizeof(int);
+  const int rows2 = tsu::adjoint_wtb2_rows(g->ny, g->ld);
+  const size_t two = ((size_t)tsu::adjoint_wtb2_tiles(g->ny, g->ld, rows2) + 1) * sizeof(int) + 16 + 4 * nr * 16;
+  return (one + 15) / 16 * 16 + two;
 }
 
 static size_t adjoint_ws_bytes(const tsu_grid* g, int dtype, int form, int64_t every, int32_t nrec) {
   const size_t fb = (size_t)g->ny * g->ld * elem_size(dtype);
   size_t b = (size_t)adjoint_fields(form, every) * fb;
   if (dtype == TSU_F32) b += 2 * (size_t)g->ny * g->ld * sizeof(float);
-  const size_t buckets = ((size_t)(adjoint_ctas(g, dtype) + 1) + 2 * (size_t)(nrec > 0 ? nrec : 0)) * sizeof(int);
+  const size_t buckets = adjoint_bucket_bytes(g, dtype, nrec);
   return b + (buckets + 255) / 256 * 256 + 256;
 }
 
@@ -412,10 +421,13 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   const size_t es = elem_size(dtype);
   const size_t fb = (size_t)g->ny * g->ld * es;
   char* w = (char*)ws;
-  char* lam[2] = {w, w + fb};                    // lam^{n+1}, lam^{n+2}
+  // four multiplier fields: lam4[i1] = lam^{n+1}, lam4[i2] = lam^{n+2}, the other two receive the
+  // outputs of a two-step pass (which may not overwrite inputs that neighbouring halos still read)
+  char* lam4[4] = {w, w + fb, w + 2 * fb, w + 3 * fb};
+  int i1 = 0, i2 = 1;
   // two segment buffers, each seg[k] = u^{m_c + k} (k = 0..E) followed by one restore field
   // (u^{m_c - 1} or v); the recompute of one segment overlaps the reverse sweep of the other
-  char* segbuf[2] = {w + 2 * fb, w + 2 * fb + (size_t)(ckpt_every + 2) * fb};
+  char* segbuf[2] = {w + 4 * fb, w + 4 * fb + (size_t)(ckpt_every + 2) * fb};
   char* g32 = w + (size_t)adjoint_fields(form, ckpt_every) * fb;  // FP32 accumulators [2][ny][ld]
   const size_t f32b = (size_t)g->ny * g->ld * sizeof(float);
   void* accx = dtype == TSU_F32 ? (void*)g32 : (void*)g_hx;
@@ -424,26 +436,49 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   int* b_off = (int*)bk;
   int* b_ord = b_off + (adjoint_ctas(g, dtype) + 1);
   int* b_cta = b_ord + (nrec > 0 ? nrec : 0);
+  // two-step pass (FP32): tile table of receivers
+  const bool pairs = dtype == TSU_F32;
+  const int rows2 = tsu::adjoint_wtb2_rows(g->ny, g->ld);
+  char* bk2 = bk + ((((size_t)(adjoint_ctas(g, dtype) + 1) + 2 * (size_t)(nrec > 0 ? nrec : 0)) * sizeof(int) + 15) /
+                    16 * 16);
+  int* t_off = (int*)bk2;
+  int4* t_ent = (int4*)(bk2 + (((size_t)tsu::adjoint_wtb2_tiles(g->ny, g->ld, rows2) + 1) * sizeof(int) + 15) / 16 * 16);
   auto segp = [&](int b, int64_t k) { return (void*)(segbuf[b] + (size_t)k * fb); };
   auto extra = [&](int b) { return (void*)(segbuf[b] + (size_t)(ckpt_every + 1) * fb); };
   AuxStream* aux = aux_stream();
   if (!aux) return fail(TSU_ECUDA, "tsu_adjoint: could not create the recompute stream");
   cudaError_t e = cudaMemsetAsync(ws, 0, need - 256, s);
   if (e == cudaSuccess && nrec > 0) e = tsu::launch_rec_bucket(sg, dtype, rec_idx, nrec, b_off, b_ord, b_cta, s);
+  if (e == cudaSuccess && nrec > 0 && pairs) e = tsu::launch_rec_tiles(sg, rec_idx, nrec, rows2, t_off, t_ent, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hx, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hy, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint reset");
-  int a = 0;  // lam[a] = lam^{n+1}, lam[a^1] = lam^{n+2}
+  // one step back: lam^n written over lam^{n+2}
   auto step_back = [&](int64_t n, const void* un) -> cudaError_t {
     tsu::RecBuckets rb{};
     if (nrec > 0) rb = {b_off, b_ord, rec_idx, (const char*)dtraces + (size_t)(n - 1) * nrec * es};
-    cudaError_t r = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam[a], lam[a ^ 1], lam[a ^ 1], un, accx,
+    cudaError_t r = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam4[i1], lam4[i2], lam4[i2], un, accx,
                                              accy, nullptr, rb, s);
-    a ^= 1;  // lam[a] = lam^n now
+    const int t = i1;  // now lam4[i1] = lam^n, lam4[i2] = lam^{n+1}
+    i1 = i2;
+    i2 = t;
+    return r;
+  };
+  // two steps back (n and n-1): lam^n and lam^{n-1} into the two free multiplier fields
+  auto two_steps_back = [&](int64_t n, const void* un, const void* um) -> cudaError_t {
+    int o1 = -1, o2 = -1;
+    for (int k = 0; k < 4; ++k)
+      if (k != i1 && k != i2) (o1 < 0 ? o1 : o2) = k;
+    const void* g1 = nrec > 0 ? (const char*)dtraces + (size_t)(n - 1) * nrec * es : nullptr;
+    const void* g2 = nrec > 0 ? (const char*)dtraces + (size_t)(n - 2) * nrec * es : nullptr;
+    cudaError_t r = tsu::launch_adjoint_wtb2(sg, rows2, m->hx, m->hy, lam4[i1], lam4[i2], un, um, lam4[o1], lam4[o2],
+                                             accx, accy, nrec > 0 ? t_off : nullptr, t_ent, g1, g2, s);
+    i1 = o2;  // lam^{n-1}
+    i2 = o1;  // lam^n
     return r;
   };
   if (C == 0) {  // nsteps == 1: lam^1 = g^1 (the gradient term of n = 1 vanishes with lam^2 = 0)
-    e = step_back(1, (void*)lam[1]);  // a zero field: the u argument is not used with lam^2 = 0
+    e = step_back(1, (void*)lam4[2]);  // a zero field: the u argument is not used with lam^2 = 0
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
   }
   if (form == TSU_FORM_INCREMENT && C > 0 && kAdjointTimeReversal) {
@@ -452,8 +487,8 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     // so each adjoint pass also steps the state back and no segment is stored.  The state is
     // re-anchored to the checkpoint (exact forward values) whenever the sweep reaches one, which
     // bounds the rounding drift of the reversal to one segment.
-    char* U[2] = {w + 2 * fb, w + 3 * fb};
-    char* Vb[2] = {w + 4 * fb, w + 5 * fb};
+    char* U[2] = {w + 4 * fb, w + 5 * fb};
+    char* Vb[2] = {w + 6 * fb, w + 7 * fb};
     const int64_t mlast = 1 + (C - 1) * ckpt_every;
     const char* slot = (const char*)ckpt + (size_t)(C - 1) * 2 * fb;
     e = cudaMemcpyAsync(U[0], slot, fb, cudaMemcpyDeviceToDevice, s);
@@ -470,10 +505,10 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     for (int64_t n = nsteps; n >= 1; --n) {
       tsu::RecBuckets rb{};
       if (nrec > 0) rb = {b_off, b_ord, rec_idx, (const char*)dtraces + (size_t)(n - 1) * nrec * es};
-      e = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam[a], lam[a ^ 1], lam[a ^ 1], U[pu], accx, accy,
+      e = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam4[i1], lam4[i2], lam4[i2], U[pu], accx, accy,
                                    nullptr, rb, s, Vb[pv], U[pu ^ 1], Vb[pv ^ 1]);
       if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
-      a ^= 1;
+      std::swap(i1, i2);
       pu ^= 1;
       pv ^= 1;
       const int64_t m_state = n - 1;  // the state now held
@@ -527,8 +562,14 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->computed[b], 0);
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint stream order");
     const int64_t nlo = (c == 0) ? 1 : mc + 1;
-    for (int64_t n = mend; n >= nlo; --n) {
-      e = step_back(n, segp(b, n - mc));
+    for (int64_t n = mend; n >= nlo;) {
+      if (pairs && n - 1 >= nlo) {
+        e = two_steps_back(n, segp(b, n - mc), segp(b, n - 1 - mc));
+        n -= 2;
+      } else {
+        e = step_back(n, segp(b, n - mc));
+        n -= 1;
+      }
       if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
     }
     if (dtype == TSU_F32) {
@@ -539,7 +580,7 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint stream order");
   }
   // the start: dJ/du0 = (I + B/2) lam^1 - lam^2, dJ/du1 = tau lam^1, face terms with u^0 and weight 1/2
-  e = tsu::launch_adjoint_pass(sg, dtype, true, m->hx, m->hy, lam[a], lam[a ^ 1], g_u0, u0, accx, accy, g_u1,
+  e = tsu::launch_adjoint_pass(sg, dtype, true, m->hx, m->hy, lam4[i1], lam4[i2], g_u0, u0, accx, accy, g_u1,
                                tsu::RecBuckets{}, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_u0, 0, (size_t)g->ld * es, s);  // boundary rows of the outputs
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)g_u0 + (size_t)(g->ny - 1) * g->ld * es, 0, (size_t)g->ld * es, s);

@@ -82,6 +82,32 @@ def test_fp64_adjoint_independent_of_checkpoint_period():
         assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("form", [tsu.TSU_FORM_STANDARD, tsu.TSU_FORM_INCREMENT])
+@pytest.mark.parametrize("every,S", [(8, 41), (5, 23), (64, 41), (3, 2)])
+def test_fp32_adjoint_matches_oracle_across_tiles(form, every, S):
+    """FP32 sweeps run two adjoint steps per pass on 120-column by 16-row tiles, with single passes
+    for odd segment lengths.  Against the FP64 oracle on a grid of 3 strips and a ragged last
+    chunk, with receivers on and next to strip and chunk edges (where halo copies of a multiplier
+    need the receiver value too), duplicates and a boundary receiver."""
+    nx, ny = 301, 150
+    rng = np.random.default_rng(23)
+    u0 = inputs.random_field(nx, ny, None, rng)
+    u1 = inputs.random_field(nx, ny, None, rng)
+    cols = [1, 3, 4, 116, 119, 120, 123, 124, 236, 239, 240, 243, 299]
+    rows = [1, 2, 15, 16, 17, 18, 32, 33, 144, 145, 147, 148]
+    rec = np.array([[cols[k % len(cols)], rows[k % len(rows)]] for k in range(3 * len(cols))]
+                   + [[120, 17], [0, 40], [150, 149]])
+    dtr = rng.standard_normal((S, len(rec)))
+    gg, tau = gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f32", form, every)
+    og = oracle.grid(nx, ny)
+    hx, hy, ext = oracle.make_depth(og, DEPTH)
+    ref = oracle.adjoint(og, tau, hx, hy, u0, u1, S, inputs.flat_index(rec, nx), dtr)
+    for k in ("g_hx", "g_hy", "g_u0", "g_u1"):
+        # FP32 states and multipliers: rounding of order 1e-7 per step, grown over S steps
+        assert relerr(gg[k], ref[k]) <= 2e-5, (k, relerr(gg[k], ref[k]))
+        assert np.max(np.abs(gg[k] - ref[k])) <= 1e-4 * np.max(np.abs(ref[k])), k
+
+
 def test_fp32_adjoint_directional_derivatives_match_central_differences():
     """FP32 fields, FP64-accumulated face gradients: <dJ/dh, d> against central differences of the
     oracle's FP64 forward map along seeded random directions, relative error <= 1e-4."""
