@@ -30,6 +30,9 @@ METRIC = "grid-point updates/s (GLUPS) and HBM roofline %; adjoint/forward time 
 # DRAM bytes (read + write) per launch of the dominant kernel from ncu captures (profiles/),
 # keyed by (kernel, form, n, steps per launch); only for kernels unchanged since the capture.
 TRAFFIC = {
+    # profiles/k_leapfrog_wtb_increment_8192.md: one launch of the timed configuration (8192^2,
+    # 4 steps per pass, 96 rows per chunk), dram__bytes_read.sum + dram__bytes_write.sum
+    ("k_leapfrog_wtb", "increment", 8192, 4): 1.693221e9,
     # profiles/k_leapfrog_increment_4096.md, scaled by 8190^2/4094^2 (writes under-counted: L2 residency)
     ("k_leapfrog", "increment", 8192, 1): 1.483e9,
     # profiles/k_leapfrog_standard_4096.md, scaled likewise
@@ -49,12 +52,17 @@ def parse():
     ap.add_argument("--nsteps", type=int, default=5000, help="leapfrog steps per bench step")
     ap.add_argument("--form", default="increment", choices=["increment", "standard"])
     ap.add_argument("--rows", type=int, default=0)
-    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one step per pass, 3 temporally blocked")
-    ap.add_argument("--tdepth", type=int, default=0, help="steps per blocked pass (4 or 8; 0 = 8)")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="0 = 2; 1 one step per pass, 2 warp-blocked (tdepth 2/4), 3 CTA-blocked (tdepth 4/8)")
+    ap.add_argument("--tdepth", type=int, default=0, help="steps per blocked pass (0: 4 for kernel 2, 8 for 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched and 16384^2 measurements")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch (from profiles/)")
+    ap.add_argument("--measure", choices=["adjoint", "batched", "large"], default=None,
+                    help="run only this side measurement and print its result (a profiling aid)")
+    ap.add_argument("--measure-n", type=int, default=2048, help="grid side of --measure adjoint")
+    ap.add_argument("--measure-steps", type=int, default=4000, help="leapfrog steps of --measure adjoint/batched")
     return ap.parse_args()
 
 
@@ -63,6 +71,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's figure (a MAX all-reduce); the value itself on one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_glups(world: int, lups_per_rank: float, reps: int, ms: float) -> float:
+    """Lattice updates of all ranks (each runs its own replica) over the slowest rank's time."""
+    return world * lups_per_rank * reps / (ms / 1e3) / 1e9
 
 
 def load_peaks():
@@ -268,13 +293,9 @@ def run_gpu(args):
             kernel_ms.append(ev_k0.elapsed_time(ev_k1))
         t1.record(stream)
         torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), dev)
     lups_step = (p.n - 2) ** 2 * S
-    value = world * lups_step * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_glups(world, lups_step, args.steps, ms)
     tsu.tsu_sync_status(ws, ws_bytes, stream)  # raises if a bounded device wait expired
     # roofline of the dominant kernel.  Algorithmic bytes per launch: one read of the state and
     # the faces and one write of the state: 24 B per node (increment form) / 20 B (standard,
@@ -288,7 +309,9 @@ def run_gpu(args):
         kname = "k_leapfrog"
     launch_ms = sum(kernel_ms) / (len(kernel_ms) * main_launches)
     achieved = bpn * (p.n - 2) ** 2 / (launch_ms / 1e3) / 1e9
-    traffic = args.traffic if args.traffic is not None else TRAFFIC.get((kname, args.form, p.n, K if blocked else 1))
+    traffic = args.traffic
+    if traffic is None and args.rows == 0:  # the captured launches used the automatic rows per chunk
+        traffic = TRAFFIC.get((kname, args.form, p.n, K if blocked else 1))
     peak, peak_kind = load_peaks()
     e_final = energy.cpu().numpy()
     drift = float(np.max(np.abs(e_final - e_final[0])) / e_final[0])
@@ -314,12 +337,8 @@ def run_gpu(args):
             e_host.copy_(energy, non_blocking=True)
         a1.record(stream)
         torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * lups_step * reps / (ems / 1e3) / 1e9, "unit": UNIT,
+        ems = max_over_ranks(a0.elapsed_time(a1), dev)
+        e2e = {"value": whole_job_glups(world, lups_step, reps, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(u0_host.numel() * 4),
                "d2h_bytes_per_step": int(u_host.numel() * 4 + e_host.numel() * 8)}
 
@@ -516,6 +535,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.measure:
+        fn = {"adjoint": lambda: measure_adjoint(args.measure_n, args.measure_steps),
+              "batched": lambda: measure_batched(args.measure_steps), "large": measure_large}[args.measure]
+        print(json.dumps(fn()))
+        return 0
     return run_gpu(args)
 
 

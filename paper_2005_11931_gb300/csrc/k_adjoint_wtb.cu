@@ -304,11 +304,16 @@ __global__ void k_rec_tiles(const int32_t nx, const int32_t ny, const int64_t ld
 
 }  // namespace
 
+// Rows per chunk: the fewest that still fit all tiles into one wave (152 SMs x 3 resident CTAs of
+// 4 warps at 148 registers), between 16 (halo rows cost (rows + 4) / rows) and 64.  Tiles of a
+// second, partly filled wave would leave most SMs idle while it runs.
 int adjoint_wtb2_rows(int64_t ny, int64_t ld) {
   const int64_t strips = (ld + kAwOut - 1) / kAwOut;
-  int rows = 64;
-  while (rows > 16 && strips * ((ny - 2 + rows - 1) / rows) < 2 * 152 * 16) rows -= 8;
-  return rows;
+  const int64_t wave_tiles = 152 * 3 * kAwWarps;
+  const int64_t chunks = wave_tiles / strips;
+  if (chunks < 1) return 64;
+  const int64_t rows = (ny - 2 + chunks - 1) / chunks;
+  return (int)(rows < 16 ? 16 : rows > 64 ? 64 : rows);
 }
 
 int64_t adjoint_wtb2_tiles(int64_t ny, int64_t ld, int rows) {

@@ -13,6 +13,10 @@
 //
 // HBM traffic per K steps: 16 B read + 8 B written per node, x 128/120 for the halo columns and
 // x (L + 2K)/L for the halo rows: 6.4 B per lattice update at K = 4.
+//
+// The segment variant (k_leapfrog_wtb_seg) also writes every intermediate level u^{n+1} ..
+// u^{n+K-1}: the states the reverse sweep of the adjoint reads, recomputed from a checkpoint at
+// 4 + (16 + 4)/K B per node and step instead of 24 B for one step per pass.
 #include <string.h>
 
 #include <type_traits>
@@ -64,6 +68,8 @@ struct alignas(16) WtbArgs {
   double* energy;   // K doubles or nullptr
   EnergyWs ews;
   double escale;
+  float* seg;       // segment variant: u^{n+t} at seg + (t - 1) seg_stride, t = 1 .. K - 1
+  int64_t seg_stride;
 };
 
 struct F4 {
@@ -120,7 +126,7 @@ __device__ void wtb_energy(float (&es)[K], float (&ec)[K], const WtbArgs& a) {
   if (threadIdx.x == 0) *a.ews.counter = 0u;
 }
 
-template <int K, int FORM, bool ENERGY>
+template <int K, int FORM, bool ENERGY, bool ALL>
 __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, const int64_t strip,
                                          const int64_t chunk) {
   using Sh = WtbShape<K>;
@@ -270,6 +276,9 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         es[t - 1] = sum;
       }
       w[t][0] = un;
+      if constexpr (ALL) {
+        if (t < K && row_out && col_out) stg4(a.seg + (int64_t)(t - 1) * a.seg_stride + (int64_t)rt * a.ld + c0, un);
+      }
       if constexpr (FORM == 1) {
         if (t < K) {
           vv[t][1] = vv[t][0];
@@ -281,8 +290,8 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         stg4(a.out_a + o, un);
         if constexpr (FORM == 1)
           stg4(a.out_b + o, vn);
-        else
-          stg4(a.out_b + o, w[K - 1][1]);  // level K-1 at the same row
+        else if constexpr (!ALL)
+          stg4(a.out_b + o, w[K - 1][1]);  // level K-1 at the same row (the segment has it already)
       }
     }
   };
@@ -310,7 +319,14 @@ template <int K, int FORM, bool ENERGY>
 __global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
-  wtb_body<K, FORM, ENERGY>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
+  wtb_body<K, FORM, ENERGY, false>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
+}
+
+template <int K, int FORM>
+__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_seg(const WtbArgs a) {
+  const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
+  const bool ok = tile < a.ntiles;
+  wtb_body<K, FORM, false, true>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
 }
 
 // Batched family: warp w of CTA b works on tile tiles[4 b + w] = (problem, strip, chunk) of
@@ -323,7 +339,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_batched(const W
   const bool ok = tile < ntiles;
   const int4 t = ok ? tiles[tile] : make_int4(0, 0, 0, 0);
   const WtbArgs a = probs[t.x];
-  wtb_body<K, FORM, false>(a, ok, t.y, t.z);
+  wtb_body<K, FORM, false, false>(a, ok, t.y, t.z);
 }
 
 template <int K, int FORM>
@@ -342,6 +358,16 @@ cudaError_t wtb_launch(const WtbArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     kern<<<grid, kWtbWarps * 32, smem, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+template <int K, int FORM>
+cudaError_t wtb_launch_seg(const WtbArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)WtbShape<K>::bytes * kWtbWarps * 32;
+  auto kern = k_leapfrog_wtb_seg<K, FORM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)((a.ntiles + kWtbWarps - 1) / kWtbWarps), kWtbWarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -413,6 +439,16 @@ int wtb_auto_rows(int64_t ny, int64_t ld, int k) {
   return rows;
 }
 
+// Rows per chunk of the segment recompute: the fewest that fit all tiles into one wave (152 SMs x
+// 4 resident CTAs of 4 warps), between 16 and 96.
+int wtb_seg_rows(int64_t ny, int64_t ld) {
+  const int64_t strips = (ld + kWtbOut - 1) / kWtbOut;
+  const int64_t chunks = (int64_t)152 * 4 * kWtbWarps / strips;
+  if (chunks < 1) return 96;
+  const int64_t rows = (ny - 2 + chunks - 1) / chunks;
+  return (int)(rows < 16 ? 16 : rows > 96 ? 96 : rows);
+}
+
 int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows) {
   return ((wtb_tiles(ny, ld, rows) + kWtbWarps - 1) / kWtbWarps) * k;
 }
@@ -439,8 +475,21 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
   a.energy = energy;
   a.ews = ews;
   a.escale = g.dxdy / (2.0 * g.tau * g.tau);
+  a.seg = nullptr;
+  a.seg_stride = 0;
   if (k == 2) return form == TSU_FORM_STANDARD ? wtb_launch<2, 0>(a, s) : wtb_launch<2, 1>(a, s);
   if (k == 4) return form == TSU_FORM_STANDARD ? wtb_launch<4, 0>(a, s) : wtb_launch<4, 1>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
+                                const void* p, void* seg, int64_t seg_stride, void* v_out, int rows, cudaStream_t s) {
+  WtbArgs a{};
+  wtb_fill_args(&a, g, hx, hy, u, p, (float*)seg + (int64_t)(k - 1) * seg_stride, v_out, rows);
+  a.seg = (float*)seg;
+  a.seg_stride = seg_stride;
+  if (k == 2) return form == TSU_FORM_STANDARD ? wtb_launch_seg<2, 0>(a, s) : wtb_launch_seg<2, 1>(a, s);
+  if (k == 4) return form == TSU_FORM_STANDARD ? wtb_launch_seg<4, 0>(a, s) : wtb_launch_seg<4, 1>(a, s);
   return cudaErrorInvalidValue;
 }
 

@@ -316,11 +316,13 @@ static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
 // segment storage) is exact up to rounding but measured slower on GB300 at 2048^2 (230 ms against
 // 184 ms for the overlapped recompute, 4000 steps): it stays available behind this switch.
 constexpr bool kAdjointTimeReversal = false;
+// steps per pass of the FP32 segment recompute (warp-blocked, intermediate states stored)
+constexpr int kRecomputeDepth = 4;
 
-// fields of dtype before the FP32 accumulators: 4 multipliers, then two segment buffers of E + 2
+// fields of dtype before the FP32 accumulators: 4 multipliers, then two segment buffers of E + 3
 // (or, for the time-reversed sweep, the two (u, v) states)
 static int64_t adjoint_fields(int form, int64_t every) {
-  return (form == TSU_FORM_INCREMENT && kAdjointTimeReversal) ? 4 + 4 : 4 + 2 * (every + 2);
+  return (form == TSU_FORM_INCREMENT && kAdjointTimeReversal) ? 4 + 4 : 4 + 2 * (every + 3);
 }
 
 // receiver tables: the one-step pass's (per CTA) and the two-step pass's (per tile, <= 4 per receiver)
@@ -425,9 +427,10 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   // outputs of a two-step pass (which may not overwrite inputs that neighbouring halos still read)
   char* lam4[4] = {w, w + fb, w + 2 * fb, w + 3 * fb};
   int i1 = 0, i2 = 1;
-  // two segment buffers, each seg[k] = u^{m_c + k} (k = 0..E) followed by one restore field
-  // (u^{m_c - 1} or v); the recompute of one segment overlaps the reverse sweep of the other
-  char* segbuf[2] = {w + 4 * fb, w + 4 * fb + (size_t)(ckpt_every + 2) * fb};
+  // two segment buffers, each seg[k] = u^{m_c + k} (k = 0..E) followed by the restore field
+  // (u^{m_c - 1} or v) and a second v field (the blocked recompute writes v to the other one);
+  // the recompute of one segment overlaps the reverse sweep of the other
+  char* segbuf[2] = {w + 4 * fb, w + 4 * fb + (size_t)(ckpt_every + 3) * fb};
   char* g32 = w + (size_t)adjoint_fields(form, ckpt_every) * fb;  // FP32 accumulators [2][ny][ld]
   const size_t f32b = (size_t)g->ny * g->ld * sizeof(float);
   void* accx = dtype == TSU_F32 ? (void*)g32 : (void*)g_hx;
@@ -444,7 +447,8 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   int* t_off = (int*)bk2;
   int4* t_ent = (int4*)(bk2 + (((size_t)tsu::adjoint_wtb2_tiles(g->ny, g->ld, rows2) + 1) * sizeof(int) + 15) / 16 * 16);
   auto segp = [&](int b, int64_t k) { return (void*)(segbuf[b] + (size_t)k * fb); };
-  auto extra = [&](int b) { return (void*)(segbuf[b] + (size_t)(ckpt_every + 1) * fb); };
+  const int recompute_rows = tsu::wtb_seg_rows(g->ny, g->ld);
+  auto extra = [&](int b, int q = 0) { return (void*)(segbuf[b] + (size_t)(ckpt_every + 1 + q) * fb); };
   AuxStream* aux = aux_stream();
   if (!aux) return fail(TSU_ECUDA, "tsu_adjoint: could not create the recompute stream");
   cudaError_t e = cudaMemsetAsync(ws, 0, need - 256, s);
@@ -548,13 +552,25 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     }
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint restore");
     tsu::PassOut none{};
-    for (int64_t k = 0; k < mend - mc; ++k) {
+    int64_t k = 0;
+    int vq = 0;  // increment form: v^{m_c + k} in extra(b, vq)
+    if (dtype == TSU_F32) {  // kRecomputeDepth steps per pass, every intermediate state stored
+      for (; k + kRecomputeDepth <= mend - mc; k += kRecomputeDepth) {
+        const void* p = form == TSU_FORM_STANDARD ? (k == 0 ? extra(b) : segp(b, k - 1)) : extra(b, vq);
+        e = tsu::launch_step_wtb_seg(sg, form, kRecomputeDepth, m->hx, m->hy, segp(b, k), p, segp(b, k + 1),
+                                     (int64_t)(fb / es), form == TSU_FORM_STANDARD ? nullptr : extra(b, vq ^ 1),
+                                     recompute_rows, aux->s);
+        if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint recompute");
+        vq ^= 1;
+      }
+    }
+    for (; k < mend - mc; ++k) {
       if (form == TSU_FORM_STANDARD)
         e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, k == 0 ? extra(b) : segp(b, k - 1), segp(b, k), nullptr,
                              segp(b, k + 1), none, true, 0, aux->s);
       else
-        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, nullptr, segp(b, k), extra(b), segp(b, k + 1), none, true,
-                             0, aux->s);
+        e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, nullptr, segp(b, k), extra(b, vq), segp(b, k + 1), none,
+                             true, 0, aux->s);
       if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint recompute");
     }
     e = cudaEventRecord(aux->computed[b], aux->s);

@@ -87,6 +87,11 @@ int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows);
 cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
                             const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int rows,
                             cudaStream_t s);
+int wtb_seg_rows(int64_t ny, int64_t ld);
+// segment variant: u^{n+t} into seg + (t - 1) seg_stride for t = 1 .. k (elements), v^{n+k} into
+// v_out (increment form; unused in the standard form)
+cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
+                                const void* p, void* seg, int64_t seg_stride, void* v_out, int rows, cudaStream_t s);
 // batched warp-blocked pass: descriptors of wtb_args_bytes() each, int4 tiles (problem, strip, chunk)
 int wtb_strip_width();
 size_t wtb_args_bytes();
