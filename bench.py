@@ -32,7 +32,7 @@ METRIC = "grid-point updates/s (GLUPS) and HBM roofline %; adjoint/forward time 
 TRAFFIC = {
     # profiles/k_leapfrog_wtb_increment_8192.md: one launch of the timed configuration (8192^2,
     # 4 steps per pass, 96 rows per chunk), dram__bytes_read.sum + dram__bytes_write.sum
-    ("k_leapfrog_wtb", "increment", 8192, 4): 1.693221e9,
+    ("k_leapfrog_wtb", "increment", 8192, 4): 1.692158e9,
     # profiles/k_leapfrog_increment_4096.md, scaled by 8190^2/4094^2 (writes under-counted: L2 residency)
     ("k_leapfrog", "increment", 8192, 1): 1.483e9,
     # profiles/k_leapfrog_standard_4096.md, scaled likewise
@@ -456,7 +456,7 @@ def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
             "adjoint_glups": lups / t_a / 1e6, "J": J, "grad_norm_hx": float(gx.norm())}
 
 
-def measure_batched(steps=2000, warm=1):
+def measure_batched(steps=2000, warm=1, rows=0):
     """The 64-problem eps-family: one batched launch per K steps vs the same problems run one
     after the other (one step per pass, and the automatic kernel choice)."""
     import numpy as np
@@ -470,7 +470,7 @@ def measure_batched(steps=2000, warm=1):
         sim = tsu.Simulation.create(pr.n, pr.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
         sims.append((pr, sim, torch.from_numpy(pr.initial(sim.g.ld, np.float32)).cuda()))
     nsteps = [pr.steps - 1 for pr in probs]
-    wsb = tsu.tsu_batch_workspace([s for _, s, _ in sims], nsteps)
+    wsb = tsu.tsu_batch_workspace([s for _, s, _ in sims], nsteps, rows=rows)
     ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
 
     def init_all():
@@ -479,7 +479,7 @@ def measure_batched(steps=2000, warm=1):
 
     def batched():
         init_all()
-        tsu.tsu_batch_run([s for _, s, _ in sims], nsteps, ws, wsb)
+        tsu.tsu_batch_run([s for _, s, _ in sims], nsteps, ws, wsb, rows=rows)
 
     def sequential(kernel):
         init_all()
@@ -537,7 +537,8 @@ def main():
         return run_reference(args)
     if args.measure:
         fn = {"adjoint": lambda: measure_adjoint(args.measure_n, args.measure_steps),
-              "batched": lambda: measure_batched(args.measure_steps), "large": measure_large}[args.measure]
+              "batched": lambda: measure_batched(args.measure_steps, rows=args.rows),
+              "large": measure_large}[args.measure]
         print(json.dumps(fn()))
         return 0
     return run_gpu(args)

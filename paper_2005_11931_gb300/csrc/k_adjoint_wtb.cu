@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
     cp16(slot(s, 7), a.gy + ga, acc);
   };
   const F4 Z{{0.f, 0.f, 0.f, 0.f}};
+  const ArithF32 ar{a.cx, a.cy};
   // windows (index 0 = newest row)
   F4 w0[3] = {Z, Z, Z};      // lam^{n+1} rows r, r-1, r-2
   F4 w1[3] = {Z, Z, Z};      // lam^n rows r-1, r-2, r-3
@@ -191,10 +192,8 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
         const float xl = (e == 0) ? ul : uc.a[e - 1];
         const float xr = (e == 3) ? ur : uc.a[e + 1];
         const float hxl = (e == 0) ? hl : HX[1].a[e - 1];
-        const float fx = HX[1].a[e] * (xr - uc.a[e]) - hxl * (uc.a[e] - xl);
-        const float fy = HY[1].a[e] * (uu.a[e] - uc.a[e]) - HY[2].a[e] * (uc.a[e] - ud.a[e]);
-        const float b = fmaf(a.cx, fx, a.cy * fy);
-        const float v = (2.0f * uc.a[e] - L2[1].a[e]) + b;
+        const float b = ar.b(HX[1].a[e], hxl, HY[1].a[e], HY[2].a[e], uc.a[e], xl, xr, uu.a[e], ud.a[e]);
+        const float v = ar.lf(uc.a[e], L2[1].a[e], b);
         l1.a[e] = (row_in && node_col[e]) ? v : 0.f;
         const float uxr = (e == 3) ? unr : U[1].a[e + 1];
         g1x[e] = face_x[e] ? -a.cx * ((xr - uc.a[e]) * (uxr - U[1].a[e])) : 0.f;
@@ -222,10 +221,8 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
         const float xl = (e == 0) ? ul : uc.a[e - 1];
         const float xr = (e == 3) ? ur : uc.a[e + 1];
         const float hxl = (e == 0) ? hl : HX[2].a[e - 1];
-        const float fx = HX[2].a[e] * (xr - uc.a[e]) - hxl * (uc.a[e] - xl);
-        const float fy = HY[2].a[e] * (uu.a[e] - uc.a[e]) - HY[3].a[e] * (uc.a[e] - ud.a[e]);
-        const float b = fmaf(a.cx, fx, a.cy * fy);
-        const float v = (2.0f * uc.a[e] - w0[2].a[e]) + b;
+        const float b = ar.b(HX[2].a[e], hxl, HY[2].a[e], HY[3].a[e], uc.a[e], xl, xr, uu.a[e], ud.a[e]);
+        const float v = ar.lf(uc.a[e], w0[2].a[e], b);
         l2.a[e] = (row_in && node_col[e]) ? v : 0.f;
         const float uxr = (e == 3) ? umr : M[2].a[e + 1];
         g2x[e] = face_x[e] ? -a.cx * ((xr - uc.a[e]) * (uxr - M[2].a[e])) : 0.f;

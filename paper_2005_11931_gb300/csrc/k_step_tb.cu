@@ -21,6 +21,7 @@
 // drains its own copies (bounded) and returns.
 #include <string.h>
 
+#include "stencil_common.cuh"
 #include "tsu_internal.h"
 
 namespace tsu {
@@ -271,18 +272,17 @@ __device__ __forceinline__ void tb_body(const TbArgs& a, const int strip, const 
       const float hyu = st ? st[3 * WE + tid] : 0.0f;
       const float hyd = sd ? sd[3 * WE + tid] : 0.0f;
       const float uc = w[t - 1][1], uu = w[t - 1][0], ud = w[t - 1][2];
-      const float fx = hxr * (ur - uc) - hxl * (uc - ul);
-      const float fy = hyu * (uu - uc) - hyd * (uc - ud);
-      const float b = fmaf(a.cx, fx, a.cy * fy);
+      const dev::ArithF32 ar{a.cx, a.cy};
+      const float b = ar.b(hxr, hxl, hyu, hyd, uc, ul, ur, uu, ud);
       const bool node = col_interior && rt >= 1 && rt <= a.ny - 2;
       float unew, vnew = 0.0f, upv;
       if constexpr (FORM == 0) {
         upv = up_or_v;
-        unew = (2.0f * uc - upv) + b;
+        unew = ar.lf(uc, upv, b);
       } else {
         upv = uc - up_or_v;
-        vnew = up_or_v + b;
-        unew = uc + vnew;
+        vnew = ar.add(up_or_v, b);
+        unew = ar.add(uc, vnew);
       }
       unew = node ? unew : 0.0f;
       vnew = node ? vnew : 0.0f;

@@ -233,22 +233,21 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       const bool row_out = !EDGE || (rt >= y0 && rt < y1);
       F4 un, vn;
       float erow = 0.f;
+      const ArithF32 ar{a.cx, a.cy};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float xl = (e == 0) ? ul : uc.a[e - 1];
         const float xr = (e == 3) ? ur : uc.a[e + 1];
         const float hxl = (e == 0) ? hl : hxv.a[e - 1];
-        const float fx = hxv.a[e] * (xr - uc.a[e]) - hxl * (uc.a[e] - xl);
-        const float fy = hyv.a[e] * (uu.a[e] - uc.a[e]) - hyd.a[e] * (uc.a[e] - ud.a[e]);
-        const float b = fmaf(a.cx, fx, a.cy * fy);
+        const float b = ar.b(hxv.a[e], hxl, hyv.a[e], hyd.a[e], uc.a[e], xl, xr, uu.a[e], ud.a[e]);
         float unew, vnew = 0.f, up;
         if constexpr (FORM == 0) {
           up = pc.a[e];
-          unew = (2.0f * uc.a[e] - up) + b;
+          unew = ar.lf(uc.a[e], up, b);
         } else {
           up = uc.a[e] - pc.a[e];
-          vnew = pc.a[e] + b;
-          unew = uc.a[e] + vnew;
+          vnew = ar.add(pc.a[e], b);
+          unew = ar.add(uc.a[e], vnew);
         }
         if constexpr (EDGE) {
           const bool node = row_in && node_col[e];
@@ -429,24 +428,23 @@ int64_t wtb_tiles(int64_t ny, int64_t ld, int rows) {
   return ((ld + 4 + kWtbOut - 1) / kWtbOut) * ((ny - 2 + rows - 1) / rows);
 }
 
-// Rows per chunk: 96 (the measured optimum on 8192^2: 654 GLUPS at 96 rows against 604 at 240),
-// shortened in steps of 16 (down to 32) while the grid has fewer than two rounds of tiles for the
-// 152 SMs x 16 resident warps.
-int wtb_auto_rows(int64_t ny, int64_t ld, int k) {
-  (void)k;
-  int rows = 96;
-  while (rows > 32 && wtb_tiles(ny, ld, rows) < 2 * 152 * 16) rows -= 16;
-  return rows;
-}
-
-// Rows per chunk of the segment recompute: the fewest that fit all tiles into one wave (152 SMs x
-// 4 resident CTAs of 4 warps), between 16 and 96.
+// Rows per chunk for one wave of tiles (152 SMs x 4 resident CTAs of 4 warps), between 16 and 96.
 int wtb_seg_rows(int64_t ny, int64_t ld) {
   const int64_t strips = (ld + kWtbOut - 1) / kWtbOut;
   const int64_t chunks = (int64_t)152 * 4 * kWtbWarps / strips;
   if (chunks < 1) return 96;
   const int64_t rows = (ny - 2 + chunks - 1) / chunks;
   return (int)(rows < 16 ? 16 : rows > 96 ? 96 : rows);
+}
+
+// Rows per chunk: the fewest (>= 16) that fit all tiles into one wave of 152 SMs x 4 resident CTAs
+// x 4 warps, at most 96.  Measured FP32 GLUPS (increment form, energy every step, K = 4):
+//   8192^2: 654 at 96 rows (604 at 240);  4096^2: 473 at 64, 467 at 32, 397 at 16 (one step
+//   per pass: 247);  2048^2: 290 at 16, 292 at 32, 227 at 64 (one step: 256);  1024^2: 131 at
+//   16, 93 at 32 (one step: 102).
+int wtb_auto_rows(int64_t ny, int64_t ld, int k) {
+  (void)k;
+  return wtb_seg_rows(ny, ld);
 }
 
 int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows) {

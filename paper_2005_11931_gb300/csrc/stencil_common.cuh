@@ -77,16 +77,20 @@ __device__ __forceinline__ void st_vec(T* p, const Pack<T>& r) {
 }
 
 // ---- arithmetic of one node ------------------------------------------------------------------
+// FP32: every rounding is explicit (the compiler contracts nothing), so every pass that calls these
+// (one step, CTA-blocked, warp-blocked, batched, segment recompute) gives the same bits.
 struct ArithF32 {
   float cx, cy;
   __device__ __forceinline__ float b(float hxr, float hxl, float hyu, float hyd, float uc, float ul, float ur,
                                      float uu, float ud) const {
-    float fx = hxr * (ur - uc) - hxl * (uc - ul);
-    float fy = hyu * (uu - uc) - hyd * (uc - ud);
-    return fmaf(cx, fx, cy * fy);
+    const float fx = __fmaf_rn(hxr, __fsub_rn(ur, uc), -__fmul_rn(hxl, __fsub_rn(uc, ul)));
+    const float fy = __fmaf_rn(hyu, __fsub_rn(uu, uc), -__fmul_rn(hyd, __fsub_rn(uc, ud)));
+    return __fmaf_rn(cx, fx, __fmul_rn(cy, fy));
   }
-  __device__ __forceinline__ float lf(float uc, float up, float b) const { return (2.0f * uc - up) + b; }
-  __device__ __forceinline__ float add(float a, float b) const { return a + b; }
+  __device__ __forceinline__ float lf(float uc, float up, float b) const {
+    return __fadd_rn(__fmaf_rn(2.0f, uc, -up), b);
+  }
+  __device__ __forceinline__ float add(float a, float b) const { return __fadd_rn(a, b); }
 };
 
 struct ArithF64 {  // explicitly rounded, definition order, no contraction

@@ -223,21 +223,17 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   const bool tb_possible = dtype == TSU_F32 && st->nbuf == 4 && have_ws && !o.traces && !o.ckpt;
   if ((o.kernel == 3 || o.kernel == 2) && !tb_possible)
     return fail(TSU_EINVAL, "kernels 2 and 3 need FP32, nbuf = 4, a workspace and no traces/checkpoints");
-  // kernel 2: warp-blocked pass, tdepth steps per launch (default 4).  Auto (kernel 0) takes it
-  // when its tiles give at least ~500 CTAs (rows per chunk 256, halved down to 64 to get there);
-  // smaller grids run one step per pass (their fields largely stay in L2)
+  // kernel 2: warp-blocked pass, tdepth steps per launch (default 4); also the automatic choice
+  // (kernel 0) whenever it is possible: it beat one step per pass at every size measured (1024^2
+  // to 16384^2).  All passes give the same bits, so the choice never changes a result.
   const int wdepth = o.tdepth ? o.tdepth : 4;
   int wrows = o.rows ? (o.rows < 16 ? 16 : o.rows) : tsu::wtb_auto_rows(g->ny, g->ld, wdepth);
-  const bool wtb_fills = (tsu::wtb_tiles(g->ny, g->ld, wrows) + 3) / 4 >= 300;
   const bool use_wtb = tb_possible && nsteps >= wdepth && tsu::wtb_supported_depth(wdepth) &&
-                       (o.kernel == 2 || (o.kernel == 0 && wtb_fills));
+                       (o.kernel == 2 || o.kernel == 0);
+  // kernel 3: CTA-blocked pass, on request only
   const int tdepth = o.tdepth ? o.tdepth : 8;
   int tb_rows = o.rows ? o.rows : 128;
   if (tb_rows < 16) tb_rows = 16;
-  // auto: the blocked pass only when its tiles fill the GPU at least twice over (152 SMs x 2 CTAs);
-  // smaller grids run one step per pass (their fields largely stay in L2)
-  const int64_t tb_ctas = ((g->ld + tsu::tb_strip_width(tdepth) - 1) / tsu::tb_strip_width(tdepth)) *
-                          ((g->ny - 2 + tb_rows - 1) / tb_rows);
   const bool use_tb = !use_wtb && tb_possible && nsteps >= tdepth && o.kernel == 3;
   const tsu::StencilGeom sg = geom(g, tau);
   const size_t field_bytes = (size_t)g->ny * g->ld * elem_size(dtype);
@@ -620,7 +616,9 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
   const int kern = batch_kernel(opts);
   if (kern != 2 && kern != 3) return fail(TSU_EINVAL, "batch kernel must be 2 or 3");
   const int k = (opts && opts->tdepth) ? opts->tdepth : (kern == 2 ? 4 : 8);
-  const int rows = (opts && opts->rows) ? opts->rows : 256;
+  // rows per chunk: 96 (64-problem family, FP32 GLUPS at 32/64/96/128/192/256 rows:
+  // 755/815/818/802/763/725)
+  const int rows = (opts && opts->rows) ? opts->rows : 96;
   if (kern == 3 && !tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 3: tdepth must be 4 or 8");
   if (kern == 2 && !tsu::wtb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 2: tdepth must be 2 or 4");
   if (rows < 16) return fail(TSU_EINVAL, "rows must be >= 16");
