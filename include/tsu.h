@@ -133,8 +133,9 @@ typedef struct {
   int32_t kernel;   /* 0 auto, 1 register-streaming (one step per pass), 2 warp-blocked (tdepth =
                        2 or 4 steps per pass, default 4), 3 CTA-blocked (tdepth = 4 or 8, default 8);
                        2 and 3 need FP32, nbuf = 4, a workspace and no traces/checkpoints; auto picks
-                       a blocked kernel when possible and its tiles fill the GPU */
-  int32_t rows;     /* rows per CTA (0 = auto) */
+                       kernel 2 (tdepth 4) whenever those hold.  All kernels round every operation
+                       the same way, so the FP32 states do not depend on the choice */
+  int32_t rows;     /* rows per CTA (kernels 1, 3) or per warp tile (kernel 2); 0 = auto */
   int32_t tdepth;   /* steps per pass of kernels 2 and 3 (0 = default); leftover steps run one per pass */
   int32_t reserved; /* 0.  Bit 0 is a test hook of the failure detection: kernel 3 then never
                        issues one row copy, its bounded wait (20 ms) expires and tsu_sync_status
@@ -187,8 +188,8 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
 int64_t tsu_ckpt_slots(int64_t nsteps, int64_t ckpt_every);
 
 /* Bytes of device workspace tsu_adjoint needs for a forward run of this form with nrec receivers:
- * 2 ckpt_every + 6 fields of dtype (multipliers and two recompute segments), two FP32 gradient
- * accumulators for FP32 fields and a receiver table. */
+ * 2 ckpt_every + 10 fields of dtype (four multiplier fields and two recompute segments of
+ * ckpt_every + 3 fields), two FP32 gradient accumulators for FP32 fields and receiver tables. */
 int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps, int64_t ckpt_every, int32_t nrec,
                           size_t* bytes);
 
@@ -225,7 +226,7 @@ typedef struct {
 /* Options of tsu_batch_run (NULL = defaults). */
 typedef struct {
   int32_t tdepth; /* steps per batched pass (0 = the kernel's default: 4 for kernel 2, 8 for kernel 3) */
-  int32_t rows;   /* rows per chunk (0 = 256) */
+  int32_t rows;   /* rows per chunk (0 = 96) */
   int32_t kernel; /* 0 or 2: warp-blocked (tdepth 2 or 4); 3: CTA-blocked (tdepth 4 or 8) */
   int32_t reserved;
 } tsu_batch_opts;
@@ -236,8 +237,8 @@ int tsu_batch_workspace(int32_t nprob, const tsu_problem* probs, const tsu_batch
 /* Advance a whole family of regularised problems (the eps-family (u_eps)_eps of Sec. 3.2, with
  * different singularities, widths, grid sizes and time steps) together: every launch of the
  * temporally blocked pass covers the tiles of all problems that still have tdepth steps to go;
- * leftover steps (nsteps % tdepth) run one per pass.  Each problem ends in the same state as
- * tsu_step_n(kernel 3) would leave it.  The call uploads descriptors (it synchronises with the
+ * leftover steps (nsteps % tdepth) run one per pass.  Each problem ends in the same state, bit for
+ * bit, as tsu_step_n would leave it.  The call uploads descriptors (it synchronises with the
  * host once) and updates every state's cur/aux/step; tsu_sync_status(ws) reports expired waits.
  * Errors: TSU_EINVAL (mixed forms, non-FP32 fields, nbuf != 4), TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
 int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, void* ws, size_t ws_bytes,
