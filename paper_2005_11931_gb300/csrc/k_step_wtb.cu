@@ -72,16 +72,59 @@ struct alignas(16) WtbArgs {
   int64_t seg_stride;
 };
 
+// A lane's four consecutive columns as two packed pairs (c0, c1), (c2, c3): the stencil runs on
+// the paired FP32 instructions (add/sub/mul/fma .f32x2), two columns per instruction, each
+// element rounded exactly as the scalar ArithF32 helper rounds it.
+typedef unsigned long long f2x;
 struct F4 {
-  float a[4];
+  f2x p[2];
 };
+__device__ __forceinline__ f2x pk(float lo, float hi) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk(f2x a) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+  return r;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// B u for a pair of columns, in ArithF32's order: fx = fma(hxl, ul - uc, hxr (ur - uc)), fy
+// likewise, B u = fma(cx, fx, cy fy)
+__device__ __forceinline__ f2x stencil2(f2x hxl, f2x hxr, f2x hyd, f2x hyu, f2x uc, f2x ul, f2x ur, f2x uu, f2x ud,
+                                        f2x cx, f2x cy) {
+  const f2x fx = fma2(hxl, sub2(ul, uc), mul2(hxr, sub2(ur, uc)));
+  const f2x fy = fma2(hyd, sub2(ud, uc), mul2(hyu, sub2(uu, uc)));
+  return fma2(cx, fx, mul2(cy, fy));
+}
 __device__ __forceinline__ F4 lds4(const float* s) {
-  const float4 v = *reinterpret_cast<const float4*>(s);
-  return F4{{v.x, v.y, v.z, v.w}};
+  const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(s);
+  return F4{{v.x, v.y}};
 }
 __device__ __forceinline__ void stg4(float* g, const F4& v) {
-  *reinterpret_cast<float4*>(g) = make_float4(v.a[0], v.a[1], v.a[2], v.a[3]);
+  *reinterpret_cast<ulonglong2*>(g) = make_ulonglong2(v.p[0], v.p[1]);
 }
+constexpr F4 kZero4{{0ull, 0ull}};  // +0.0f in every column
 
 template <int K>
 __device__ void wtb_energy(float (&es)[K], float (&ec)[K], const WtbArgs& a) {
@@ -159,7 +202,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     cp16(slotB(sb, 1), a.hy + go, ok);
   };
   auto ringB = [&](int r, int f) -> F4 {  // hx (f = 0) or hy (f = 1) of row r, zeros outside
-    if (r < r_first) return F4{{0.f, 0.f, 0.f, 0.f}};
+    if (r < r_first) return kZero4;
     return lds4(slotB((unsigned)(r - r_first) & (Sh::SB - 1), f));
   };
 
@@ -169,9 +212,10 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 #pragma unroll
   for (int t = 0; t <= K; ++t)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) w[t][q] = F4{{0.f, 0.f, 0.f, 0.f}};
+    for (int q = 0; q < 3; ++q) w[t][q] = kZero4;
 #pragma unroll
-  for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = F4{{0.f, 0.f, 0.f, 0.f}};
+  for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = kZero4;
+  const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
   float es[K], ec[K];  // compensated per-level energy sums of this thread
 #pragma unroll
   for (int t = 0; t < K; ++t) es[t] = ec[t] = 0.f;
@@ -219,53 +263,58 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         if constexpr (FORM == 1)
           pc = vv[0][1];
         else
-          pc = (!EDGE || it >= 1) ? lds4(slotA((unsigned)(it - 1) & (Sh::SA - 1), 1)) : F4{{0.f, 0.f, 0.f, 0.f}};
+          pc = (!EDGE || it >= 1) ? lds4(slotA((unsigned)(it - 1) & (Sh::SA - 1), 1)) : kZero4;
       } else {
         if constexpr (FORM == 0)
           pc = w[t - 2][2];
         else
           pc = vv[t - 1][1];
       }
-      const float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1);
-      const float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
-      const float hl = __shfl_up_sync(0xffffffffu, hxv.a[3], 1);
+      const float2 c01 = upk(uc.p[0]), c23 = upk(uc.p[1]);
+      const float2 h01 = upk(hxv.p[0]), h23 = upk(hxv.p[1]);
+      const float ul = __shfl_up_sync(0xffffffffu, c23.y, 1);
+      const float ur = __shfl_down_sync(0xffffffffu, c01.x, 1);
+      const float hl = __shfl_up_sync(0xffffffffu, h23.y, 1);
       const bool row_in = !EDGE || (rt >= 1 && rt <= a.ny - 2);
       const bool row_out = !EDGE || (rt >= y0 && rt < y1);
-      F4 un, vn;
+      // x-neighbour pairs: (ul, c0) left of pair 0, (c1, c2) between the pairs, (c3, ur) right of pair 1
+      const f2x mid = pk(c01.y, c23.x);
+      F4 bv, un, vn = kZero4;
+      bv.p[0] = stencil2(pk(hl, h01.x), hxv.p[0], hyd.p[0], hyv.p[0], uc.p[0], pk(ul, c01.x), mid, uu.p[0], ud.p[0],
+                         cx2, cy2);
+      bv.p[1] = stencil2(pk(h01.y, h23.x), hxv.p[1], hyd.p[1], hyv.p[1], uc.p[1], mid, pk(c23.y, ur), uu.p[1],
+                         ud.p[1], cx2, cy2);
       float erow = 0.f;
-      const ArithF32 ar{a.cx, a.cy};
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float xl = (e == 0) ? ul : uc.a[e - 1];
-        const float xr = (e == 3) ? ur : uc.a[e + 1];
-        const float hxl = (e == 0) ? hl : hxv.a[e - 1];
-        const float b = ar.b(hxv.a[e], hxl, hyv.a[e], hyd.a[e], uc.a[e], xl, xr, uu.a[e], ud.a[e]);
-        float unew, vnew = 0.f, up;
+      for (int q = 0; q < 2; ++q) {
+        f2x up;
         if constexpr (FORM == 0) {
-          up = pc.a[e];
-          unew = ar.lf(uc.a[e], up, b);
+          up = pc.p[q];
+          un.p[q] = add2(sub2(add2(uc.p[q], uc.p[q]), up), bv.p[q]);  // (2 u - u_prev) + B u, 2 u exact
         } else {
-          up = uc.a[e] - pc.a[e];
-          vnew = ar.add(pc.a[e], b);
-          unew = ar.add(uc.a[e], vnew);
+          if constexpr (ENERGY) up = sub2(uc.p[q], pc.p[q]);
+          vn.p[q] = add2(pc.p[q], bv.p[q]);
+          un.p[q] = add2(uc.p[q], vn.p[q]);
+        }
+        float2 ef = make_float2(0.f, 0.f);
+        if constexpr (ENERGY) {
+          const f2x d = sub2(uc.p[q], up);
+          ef = upk(sub2(mul2(d, d), mul2(bv.p[q], up)));
         }
         if constexpr (EDGE) {
-          const bool node = row_in && node_col[e];
-          un.a[e] = node ? unew : 0.f;
-          vn.a[e] = node ? vnew : 0.f;
-          if constexpr (ENERGY) {
-            if (node && row_out && col_out) {
-              const float d = uc.a[e] - up;
-              erow += d * d - b * up;
-            }
+          const bool n0 = row_in && node_col[2 * q], n1 = row_in && node_col[2 * q + 1];
+          const float2 uq = upk(un.p[q]);
+          un.p[q] = pk(n0 ? uq.x : 0.f, n1 ? uq.y : 0.f);
+          if constexpr (FORM == 1) {
+            const float2 vq = upk(vn.p[q]);
+            vn.p[q] = pk(n0 ? vq.x : 0.f, n1 ? vq.y : 0.f);
           }
-        } else {
-          un.a[e] = unew;
-          vn.a[e] = vnew;
           if constexpr (ENERGY) {
-            const float d = uc.a[e] - up;
-            erow += d * d - b * up;  // lanes that are not output are masked once at the end
+            const bool o = row_out && col_out;
+            erow += (n0 && o ? ef.x : 0.f) + (n1 && o ? ef.y : 0.f);
           }
+        } else if constexpr (ENERGY) {
+          erow += ef.x + ef.y;  // lanes that are not output are masked once at the end
         }
       }
       if constexpr (ENERGY) {
@@ -315,14 +364,14 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 }
 
 template <int K, int FORM, bool ENERGY>
-__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb(const WtbArgs a) {
+__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
   wtb_body<K, FORM, ENERGY, false>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
 }
 
 template <int K, int FORM>
-__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_seg(const WtbArgs a) {
+__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_seg(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
   wtb_body<K, FORM, false, true>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
@@ -331,7 +380,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_seg(const WtbAr
 // Batched family: warp w of CTA b works on tile tiles[4 b + w] = (problem, strip, chunk) of
 // descriptor probs[problem]; one launch advances every problem by K steps.
 template <int K, int FORM>
-__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_batched(const WtbArgs* __restrict__ probs,
+__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_batched(const WtbArgs* __restrict__ probs,
                                                                         const int4* __restrict__ tiles,
                                                                         const int64_t ntiles) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);

@@ -83,8 +83,10 @@ struct ArithF32 {
   float cx, cy;
   __device__ __forceinline__ float b(float hxr, float hxl, float hyu, float hyd, float uc, float ul, float ur,
                                      float uu, float ud) const {
-    const float fx = __fmaf_rn(hxr, __fsub_rn(ur, uc), -__fmul_rn(hxl, __fsub_rn(uc, ul)));
-    const float fy = __fmaf_rn(hyu, __fsub_rn(uu, uc), -__fmul_rn(hyd, __fsub_rn(uc, ud)));
+    // fx = hxr (ur - uc) - hxl (uc - ul) written as hxl (ul - uc) + hxr (ur - uc): the form the
+    // paired .f32x2 instructions evaluate without a negation
+    const float fx = __fmaf_rn(hxl, __fsub_rn(ul, uc), __fmul_rn(hxr, __fsub_rn(ur, uc)));
+    const float fy = __fmaf_rn(hyd, __fsub_rn(ud, uc), __fmul_rn(hyu, __fsub_rn(uu, uc)));
     return __fmaf_rn(cx, fx, __fmul_rn(cy, fy));
   }
   __device__ __forceinline__ float lf(float uc, float up, float b) const {
