@@ -242,21 +242,21 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       vv[0][1] = vv[0][0];
       vv[0][0] = lds4(slotA(sa, 1));
     }
+    // hy of row r_in - t; level t reads the rows rt and rt - 1, level t + 1 the rows rt - 1 and
+    // rt - 2, so each row is read once
+    auto hy_row = [&](int t) -> F4 {
+      if constexpr (EDGE)
+        return ringB(r_in - t, 1);
+      else  // rows >= r_first: plain ring slots
+        return lds4(slotB((unsigned)(it - t) & (Sh::SB - 1), 1));
+    };
+    F4 hyv = hy_row(1);
     // ---- levels 1..K
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
       const int rt = r_in - t;
-      F4 hxv, hyv, hyd;
-      if constexpr (EDGE) {
-        hxv = ringB(rt, 0);
-        hyv = ringB(rt, 1);
-        hyd = ringB(rt - 1, 1);
-      } else {  // rows rt - 1 >= r_first: plain ring slots
-        const unsigned sb = (unsigned)(it - t) & (Sh::SB - 1), sd = (unsigned)(it - t - 1) & (Sh::SB - 1);
-        hxv = lds4(slotB(sb, 0));
-        hyv = lds4(slotB(sb, 1));
-        hyd = lds4(slotB(sd, 1));
-      }
+      const F4 hxv = EDGE ? ringB(rt, 0) : lds4(slotB((unsigned)(it - t) & (Sh::SB - 1), 0));
+      const F4 hyd = hy_row(t + 1);
       const F4 uc = w[t - 1][1], uu = w[t - 1][0], ud = w[t - 1][2];
       F4 pc;  // u^{n-1} (standard) or v at row rt of the level below
       if (t == 1) {
@@ -287,19 +287,20 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       float erow = 0.f;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        f2x up;
+        // energy term of the pair (u^{n-1}, u^n) at this node: (u^n - u^{n-1})^2 - (B u^n) u^{n-1}
+        float2 ef = make_float2(0.f, 0.f);
         if constexpr (FORM == 0) {
-          up = pc.p[q];
+          const f2x up = pc.p[q];
           un.p[q] = add2(sub2(add2(uc.p[q], uc.p[q]), up), bv.p[q]);  // (2 u - u_prev) + B u, 2 u exact
+          if constexpr (ENERGY) {
+            const f2x d = sub2(uc.p[q], up);
+            ef = upk(sub2(mul2(d, d), mul2(bv.p[q], up)));
+          }
         } else {
-          if constexpr (ENERGY) up = sub2(uc.p[q], pc.p[q]);
           vn.p[q] = add2(pc.p[q], bv.p[q]);
           un.p[q] = add2(uc.p[q], vn.p[q]);
-        }
-        float2 ef = make_float2(0.f, 0.f);
-        if constexpr (ENERGY) {
-          const f2x d = sub2(uc.p[q], up);
-          ef = upk(sub2(mul2(d, d), mul2(bv.p[q], up)));
+          // u^n - u^{n-1} is the stored increment v^n; v^n - u^n = -u^{n-1} exactly as rounded
+          if constexpr (ENERGY) ef = upk(fma2(bv.p[q], sub2(pc.p[q], uc.p[q]), mul2(pc.p[q], pc.p[q])));
         }
         if constexpr (EDGE) {
           const bool n0 = row_in && node_col[2 * q], n1 = row_in && node_col[2 * q + 1];
@@ -324,6 +325,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         es[t - 1] = sum;
       }
       w[t][0] = un;
+      hyv = hyd;
       if constexpr (ALL) {
         if (t < K && row_out && col_out) stg4(a.seg + (int64_t)(t - 1) * a.seg_stride + (int64_t)rt * a.ld + c0, un);
       }
