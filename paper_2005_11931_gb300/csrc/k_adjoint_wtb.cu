@@ -28,16 +28,6 @@ constexpr int kAwPre = 2;
 constexpr int kAwRing = 4;  // slots per field: in flight (2) + current, power of two
 constexpr int kAwFields = 8;  // lam^{n+1}, lam^{n+2}, u^n, u^{n-1}, hx, hy, then gx, gy two rows behind
 
-struct F4 {
-  float a[4];
-};
-__device__ __forceinline__ F4 lds4(const float* s) {
-  const float4 v = *reinterpret_cast<const float4*>(s);
-  return F4{{v.x, v.y, v.z, v.w}};
-}
-__device__ __forceinline__ void stg4(float* g, const F4& v) {
-  *reinterpret_cast<float4*>(g) = make_float4(v.a[0], v.a[1], v.a[2], v.a[3]);
-}
 __device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
   const int n = valid ? 16 : 0;
@@ -108,18 +98,27 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
     cp16(slot(s, 6), a.gx + ga, acc);
     cp16(slot(s, 7), a.gy + ga, acc);
   };
-  const F4 Z{{0.f, 0.f, 0.f, 0.f}};
-  const ArithF32 ar{a.cx, a.cy};
+  // per-thread column constants (the columns of a thread never change): node and face masks
+  // folded into the coefficients of the gradient terms
+  f2x node2[2], gcx2[2], gcy2[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = 2 * q;
+    node2[q] = pk(node_col[e] ? 1.f : 0.f, node_col[e + 1] ? 1.f : 0.f);
+    gcx2[q] = pk(face_x[e] ? -a.cx : 0.f, face_x[e + 1] ? -a.cx : 0.f);
+    gcy2[q] = pk(node_col[e] ? -a.cy : 0.f, node_col[e + 1] ? -a.cy : 0.f);
+  }
+  const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
   // windows (index 0 = newest row)
-  F4 w0[3] = {Z, Z, Z};      // lam^{n+1} rows r, r-1, r-2
-  F4 w1[3] = {Z, Z, Z};      // lam^n rows r-1, r-2, r-3
-  F4 L2[2] = {Z, Z};         // lam^{n+2} rows r, r-1
-  F4 U[2] = {Z, Z};          // u^n rows r, r-1
-  F4 M[3] = {Z, Z, Z};       // u^{n-1} rows r, r-1, r-2
-  F4 HX[3] = {Z, Z, Z};      // hx rows r, r-1, r-2
-  F4 HY[4] = {Z, Z, Z, Z};   // hy rows r .. r-3
-  float gpx[4] = {0.f, 0.f, 0.f, 0.f}, gpy[4] = {0.f, 0.f, 0.f, 0.f};  // step n at the previous level-1 row
-  float g0ya[4] = {0.f, 0.f, 0.f, 0.f};  // y-face (0, 1) of step n, carried to the level-2 row 1
+  P4 w0[3] = {kZeroP4, kZeroP4, kZeroP4};  // lam^{n+1} rows r, r-1, r-2
+  P4 w1[3] = {kZeroP4, kZeroP4, kZeroP4};  // lam^n rows r-1, r-2, r-3
+  P4 L2[2] = {kZeroP4, kZeroP4};           // lam^{n+2} rows r, r-1
+  P4 U[2] = {kZeroP4, kZeroP4};            // u^n rows r, r-1
+  P4 M[3] = {kZeroP4, kZeroP4, kZeroP4};   // u^{n-1} rows r, r-1, r-2
+  P4 HX[3] = {kZeroP4, kZeroP4, kZeroP4};  // hx rows r, r-1, r-2
+  P4 HY[4] = {kZeroP4, kZeroP4, kZeroP4, kZeroP4};  // hy rows r .. r-3
+  P4 gpx = kZeroP4, gpy = kZeroP4;  // face gradients of step n at the previous level-1 row
+  P4 g0ya = kZeroP4;                // y-face (0, 1) of step n, carried to the level-2 row 1
   const int q_lo = (tile_ok && a.rec_off) ? a.rec_off[tile] : 0, q_hi = (tile_ok && a.rec_off) ? a.rec_off[tile + 1] : 0;
   // the tile's first 32 receiver entries, one per lane (row -1: none)
   int pr_row = -1, pr_col = 0;
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
     pr_g2 = a.g2[rq.z];
   }
   // add g at the entries on row p to the lane's four multipliers (warp-uniform loop bounds)
-  auto inject = [&](int p, F4& l, bool second) {
+  auto inject = [&](int p, P4& l, bool second) {
     for (int qb = q_lo; qb < q_hi; qb += 32) {
       int row = pr_row, col = pr_col;
       float val = second ? pr_g2 : pr_g1;
@@ -152,9 +151,43 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
         const int c = __shfl_sync(0xffffffffu, col, src_lane);
         const float v = __shfl_sync(0xffffffffu, val, src_lane);
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (c == c0 + e) l.a[e] += v;
+        for (int e = 0; e < 4; ++e) {
+          if (c == c0 + e) {
+            float2 x = upk(l.p[e >> 1]);
+            if (e & 1)
+              x.y += v;
+            else
+              x.x += v;
+            l.p[e >> 1] = pk(x.x, x.y);
+          }
+        }
       }
+    }
+  };
+  // One reverse step at a row: lam_out = (2 lam - lam_pp) + B lam on interior nodes (0 elsewhere),
+  // and the face-gradient terms -cx (lam_{i+1} - lam_i)(u_{i+1} - u_i), -cy (lam_{j+1} - lam_j)
+  // (u_{j+1} - u_j) of that step with the state u (rows: uc, uu = uc + 1 for lam; us, usu for u).
+  auto level = [&](const P4& uc, const P4& uu, const P4& ud, const P4& hx, const P4& hyu, const P4& hyd,
+                   const P4& lpp, const P4& us, const P4& usu, const bool row_in, P4& lout, P4& gx, P4& gy) {
+    const float2 c01 = upk(uc.p[0]), c23 = upk(uc.p[1]);
+    const float2 h01 = upk(hx.p[0]), h23 = upk(hx.p[1]);
+    const float2 s01 = upk(us.p[0]), s23 = upk(us.p[1]);
+    const float ul = __shfl_up_sync(0xffffffffu, c23.y, 1);
+    const float ur = __shfl_down_sync(0xffffffffu, c01.x, 1);
+    const float hl = __shfl_up_sync(0xffffffffu, h23.y, 1);
+    const float sr = __shfl_down_sync(0xffffffffu, s01.x, 1);
+    const f2x mid = pk(c01.y, c23.x), right1 = pk(c23.y, ur);
+    const f2x lpair[2] = {pk(ul, c01.x), mid}, rpair[2] = {mid, right1};
+    const f2x hlpair[2] = {pk(hl, h01.x), pk(h01.y, h23.x)};
+    const f2x srpair[2] = {pk(s01.y, s23.x), pk(s23.y, sr)};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const f2x b = stencil2(hlpair[q], hx.p[q], hyd.p[q], hyu.p[q], uc.p[q], lpair[q], rpair[q], uu.p[q], ud.p[q],
+                             cx2, cy2);
+      const f2x v = add2(sub2(add2(uc.p[q], uc.p[q]), lpp.p[q]), b);  // (2 lam - lam_pp) + B lam
+      lout.p[q] = row_in ? mul2(v, node2[q]) : 0ull;
+      gx.p[q] = mul2(gcx2[q], mul2(sub2(rpair[q], uc.p[q]), sub2(srpair[q], us.p[q])));
+      gy.p[q] = mul2(gcy2[q], mul2(sub2(uu.p[q], uc.p[q]), sub2(usu.p[q], us.p[q])));
     }
   };
 
@@ -169,93 +202,53 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
     cp_wait<kAwPre>();
     const unsigned s = (unsigned)it & (kAwRing - 1);
     // shift histories and take the new row
-    w0[2] = w0[1]; w0[1] = w0[0]; w0[0] = lds4(slot(s, 0));
-    L2[1] = L2[0]; L2[0] = lds4(slot(s, 1));
-    U[1] = U[0]; U[0] = lds4(slot(s, 2));
-    M[2] = M[1]; M[1] = M[0]; M[0] = lds4(slot(s, 3));
-    HX[2] = HX[1]; HX[1] = HX[0]; HX[0] = lds4(slot(s, 4));
-    HY[3] = HY[2]; HY[2] = HY[1]; HY[1] = HY[0]; HY[0] = lds4(slot(s, 5));
+    w0[2] = w0[1]; w0[1] = w0[0]; w0[0] = lds_p4(slot(s, 0));
+    L2[1] = L2[0]; L2[0] = lds_p4(slot(s, 1));
+    U[1] = U[0]; U[0] = lds_p4(slot(s, 2));
+    M[2] = M[1]; M[1] = M[0]; M[0] = lds_p4(slot(s, 3));
+    HX[2] = HX[1]; HX[1] = HX[0]; HX[0] = lds_p4(slot(s, 4));
+    HY[3] = HY[2]; HY[2] = HY[1]; HY[1] = HY[0]; HY[0] = lds_p4(slot(s, 5));
 
     // ---- level 1: lam^n at row p1 = r_in - 1, and the face gradients of step n there
     const int p1 = r_in - 1;
-    F4 l1;
-    float g1x[4], g1y[4];
-    {
-      const F4 uc = w0[1], uu = w0[0], ud = w0[2];
-      const float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1);
-      const float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
-      const float hl = __shfl_up_sync(0xffffffffu, HX[1].a[3], 1);
-      const float unr = __shfl_down_sync(0xffffffffu, U[1].a[0], 1);
-      const bool row_in = p1 >= 1 && p1 <= a.ny - 2;
+    P4 l1, g1x, g1y;
+    level(w0[1], w0[0], w0[2], HX[1], HY[1], HY[2], L2[1], U[1], U[0], p1 >= 1 && p1 <= a.ny - 2, l1, g1x, g1y);
+    if (p1 == 1) {  // y-face (0, 1): lam and u vanish on row 0, the term is -cy lam_1 u_1
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float xl = (e == 0) ? ul : uc.a[e - 1];
-        const float xr = (e == 3) ? ur : uc.a[e + 1];
-        const float hxl = (e == 0) ? hl : HX[1].a[e - 1];
-        const float b = ar.b(HX[1].a[e], hxl, HY[1].a[e], HY[2].a[e], uc.a[e], xl, xr, uu.a[e], ud.a[e]);
-        const float v = ar.lf(uc.a[e], L2[1].a[e], b);
-        l1.a[e] = (row_in && node_col[e]) ? v : 0.f;
-        const float uxr = (e == 3) ? unr : U[1].a[e + 1];
-        g1x[e] = face_x[e] ? -a.cx * ((xr - uc.a[e]) * (uxr - U[1].a[e])) : 0.f;
-        g1y[e] = node_col[e] ? -a.cy * ((uu.a[e] - uc.a[e]) * (U[0].a[e] - U[1].a[e])) : 0.f;
-        if (p1 == 1) g0ya[e] = node_col[e] ? -a.cy * (uc.a[e] * U[1].a[e]) : 0.f;  // face (0, 1)
-      }
+      for (int q = 0; q < 2; ++q) g0ya.p[q] = mul2(gcy2[q], mul2(w0[1].p[q], U[1].p[q]));
     }
     inject(p1, l1, false);  // receivers on this row (extended region)
     w1[2] = w1[1]; w1[1] = w1[0]; w1[0] = l1;
-    if (col_out && p1 >= y0 && p1 < y1) stg4(a.out1 + (int64_t)p1 * a.ld + c0, l1);
+    if (col_out && p1 >= y0 && p1 < y1) stg_p4(a.out1 + (int64_t)p1 * a.ld + c0, l1);
 
     // ---- level 2: lam^{n-1} at row p2 = r_in - 2, and the face gradients of step n-1 there
     const int p2 = r_in - 2;
-    {
-      const F4 uc = w1[1], uu = w1[0], ud = w1[2];
-      const float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1);
-      const float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
-      const float hl = __shfl_up_sync(0xffffffffu, HX[2].a[3], 1);
-      const float umr = __shfl_down_sync(0xffffffffu, M[2].a[0], 1);
-      const bool row_in = p2 >= 1 && p2 <= a.ny - 2;
-      F4 l2;
-      float g2x[4], g2y[4], g0b[4];
+    P4 l2, g2x, g2y;
+    level(w1[1], w1[0], w1[2], HX[2], HY[2], HY[3], w0[2], M[2], M[1], p2 >= 1 && p2 <= a.ny - 2, l2, g2x, g2y);
+    inject(p2, l2, true);
+    if (col_out && p2 >= y0 && p2 < y1) {
+      const int64_t o = (int64_t)p2 * a.ld + c0;
+      stg_p4(a.out2 + o, l2);
+      // both steps' face gradients of row p2: step n was computed one iteration ago
+      P4 ax = lds_p4(slot(s, 6)), ay = lds_p4(slot(s, 7));
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float xl = (e == 0) ? ul : uc.a[e - 1];
-        const float xr = (e == 3) ? ur : uc.a[e + 1];
-        const float hxl = (e == 0) ? hl : HX[2].a[e - 1];
-        const float b = ar.b(HX[2].a[e], hxl, HY[2].a[e], HY[3].a[e], uc.a[e], xl, xr, uu.a[e], ud.a[e]);
-        const float v = ar.lf(uc.a[e], w0[2].a[e], b);
-        l2.a[e] = (row_in && node_col[e]) ? v : 0.f;
-        const float uxr = (e == 3) ? umr : M[2].a[e + 1];
-        g2x[e] = face_x[e] ? -a.cx * ((xr - uc.a[e]) * (uxr - M[2].a[e])) : 0.f;
-        g2y[e] = node_col[e] ? -a.cy * ((uu.a[e] - uc.a[e]) * (M[1].a[e] - M[2].a[e])) : 0.f;
-        g0b[e] = node_col[e] ? -a.cy * (uc.a[e] * M[2].a[e]) : 0.f;
+      for (int q = 0; q < 2; ++q) {
+        ax.p[q] = add2(ax.p[q], add2(gpx.p[q], g2x.p[q]));
+        ay.p[q] = add2(ay.p[q], add2(gpy.p[q], g2y.p[q]));
       }
-      inject(p2, l2, true);
-      if (col_out && p2 >= y0 && p2 < y1) {
-        const int64_t o = (int64_t)p2 * a.ld + c0;
-        stg4(a.out2 + o, l2);
-        // both steps' face gradients of row p2: step n was computed one iteration ago
-        F4 ax = lds4(slot(s, 6)), ay = lds4(slot(s, 7));
+      stg_p4(a.gx + o, ax);
+      stg_p4(a.gy + o, ay);
+      if (p2 == 1) {  // y-face (0, 1) of both steps
+        const ulonglong2 r0 = __ldcg(reinterpret_cast<const ulonglong2*>(a.gy + c0));  // once per tile column
+        P4 a0{{r0.x, r0.y}};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          ax.a[e] += gpx[e] + g2x[e];
-          ay.a[e] += gpy[e] + g2y[e];
-        }
-        stg4(a.gx + o, ax);
-        stg4(a.gy + o, ay);
-        if (p2 == 1) {  // y-face (0, 1): lam and u vanish on row 0
-          const float4 r0 = __ldcg(reinterpret_cast<const float4*>(a.gy + c0));  // once per tile column
-          F4 a0{{r0.x, r0.y, r0.z, r0.w}};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) a0.a[e] += g0ya[e] + g0b[e];
-          stg4(a.gy + c0, a0);
-        }
+        for (int q = 0; q < 2; ++q)
+          a0.p[q] = add2(a0.p[q], add2(g0ya.p[q], mul2(gcy2[q], mul2(w1[1].p[q], M[2].p[q]))));
+        stg_p4(a.gy + c0, a0);
       }
     }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      gpx[e] = g1x[e];
-      gpy[e] = g1y[e];
-    }
+    gpx = g1x;
+    gpy = g1y;
   }
   cp_wait<0>();
 }

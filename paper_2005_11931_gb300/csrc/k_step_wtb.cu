@@ -72,59 +72,7 @@ struct alignas(16) WtbArgs {
   int64_t seg_stride;
 };
 
-// A lane's four consecutive columns as two packed pairs (c0, c1), (c2, c3): the stencil runs on
-// the paired FP32 instructions (add/sub/mul/fma .f32x2), two columns per instruction, each
-// element rounded exactly as the scalar ArithF32 helper rounds it.
-typedef unsigned long long f2x;
-struct F4 {
-  f2x p[2];
-};
-__device__ __forceinline__ f2x pk(float lo, float hi) {
-  f2x r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 upk(f2x a) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
-  return r;
-}
-__device__ __forceinline__ f2x add2(f2x a, f2x b) {
-  f2x d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
-  f2x d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
-  f2x d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
-  f2x d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-// B u for a pair of columns, in ArithF32's order: fx = fma(hxl, ul - uc, hxr (ur - uc)), fy
-// likewise, B u = fma(cx, fx, cy fy)
-__device__ __forceinline__ f2x stencil2(f2x hxl, f2x hxr, f2x hyd, f2x hyu, f2x uc, f2x ul, f2x ur, f2x uu, f2x ud,
-                                        f2x cx, f2x cy) {
-  const f2x fx = fma2(hxl, sub2(ul, uc), mul2(hxr, sub2(ur, uc)));
-  const f2x fy = fma2(hyd, sub2(ud, uc), mul2(hyu, sub2(uu, uc)));
-  return fma2(cx, fx, mul2(cy, fy));
-}
-__device__ __forceinline__ F4 lds4(const float* s) {
-  const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(s);
-  return F4{{v.x, v.y}};
-}
-__device__ __forceinline__ void stg4(float* g, const F4& v) {
-  *reinterpret_cast<ulonglong2*>(g) = make_ulonglong2(v.p[0], v.p[1]);
-}
-constexpr F4 kZero4{{0ull, 0ull}};  // +0.0f in every column
+
 
 template <int K>
 __device__ void wtb_energy(float (&es)[K], float (&ec)[K], const WtbArgs& a) {
@@ -201,20 +149,20 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     cp16(slotB(sb, 0), a.hx + go, ok);
     cp16(slotB(sb, 1), a.hy + go, ok);
   };
-  auto ringB = [&](int r, int f) -> F4 {  // hx (f = 0) or hy (f = 1) of row r, zeros outside
-    if (r < r_first) return kZero4;
-    return lds4(slotB((unsigned)(r - r_first) & (Sh::SB - 1), f));
+  auto ringB = [&](int r, int f) -> P4 {  // hx (f = 0) or hy (f = 1) of row r, zeros outside
+    if (r < r_first) return kZeroP4;
+    return lds_p4(slotB((unsigned)(r - r_first) & (Sh::SB - 1), f));
   };
 
   // registers: w[t][0..2] = level t at its latest three rows, v[t][0..1] likewise (increment form)
-  F4 w[K + 1][3];
-  F4 vv[K][2];
+  P4 w[K + 1][3];
+  P4 vv[K][2];
 #pragma unroll
   for (int t = 0; t <= K; ++t)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) w[t][q] = kZero4;
+    for (int q = 0; q < 3; ++q) w[t][q] = kZeroP4;
 #pragma unroll
-  for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = kZero4;
+  for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = kZeroP4;
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
   float es[K], ec[K];  // compensated per-level energy sums of this thread
 #pragma unroll
@@ -237,33 +185,33 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       w[t][2] = w[t][1];
       w[t][1] = w[t][0];
     }
-    w[0][0] = lds4(slotA(sa, 0));
+    w[0][0] = lds_p4(slotA(sa, 0));
     if constexpr (FORM == 1) {
       vv[0][1] = vv[0][0];
-      vv[0][0] = lds4(slotA(sa, 1));
+      vv[0][0] = lds_p4(slotA(sa, 1));
     }
     // hy of row r_in - t; level t reads the rows rt and rt - 1, level t + 1 the rows rt - 1 and
     // rt - 2, so each row is read once
-    auto hy_row = [&](int t) -> F4 {
+    auto hy_row = [&](int t) -> P4 {
       if constexpr (EDGE)
         return ringB(r_in - t, 1);
       else  // rows >= r_first: plain ring slots
-        return lds4(slotB((unsigned)(it - t) & (Sh::SB - 1), 1));
+        return lds_p4(slotB((unsigned)(it - t) & (Sh::SB - 1), 1));
     };
-    F4 hyv = hy_row(1);
+    P4 hyv = hy_row(1);
     // ---- levels 1..K
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
       const int rt = r_in - t;
-      const F4 hxv = EDGE ? ringB(rt, 0) : lds4(slotB((unsigned)(it - t) & (Sh::SB - 1), 0));
-      const F4 hyd = hy_row(t + 1);
-      const F4 uc = w[t - 1][1], uu = w[t - 1][0], ud = w[t - 1][2];
-      F4 pc;  // u^{n-1} (standard) or v at row rt of the level below
+      const P4 hxv = EDGE ? ringB(rt, 0) : lds_p4(slotB((unsigned)(it - t) & (Sh::SB - 1), 0));
+      const P4 hyd = hy_row(t + 1);
+      const P4 uc = w[t - 1][1], uu = w[t - 1][0], ud = w[t - 1][2];
+      P4 pc;  // u^{n-1} (standard) or v at row rt of the level below
       if (t == 1) {
         if constexpr (FORM == 1)
           pc = vv[0][1];
         else
-          pc = (!EDGE || it >= 1) ? lds4(slotA((unsigned)(it - 1) & (Sh::SA - 1), 1)) : kZero4;
+          pc = (!EDGE || it >= 1) ? lds_p4(slotA((unsigned)(it - 1) & (Sh::SA - 1), 1)) : kZeroP4;
       } else {
         if constexpr (FORM == 0)
           pc = w[t - 2][2];
@@ -279,12 +227,13 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       const bool row_out = !EDGE || (rt >= y0 && rt < y1);
       // x-neighbour pairs: (ul, c0) left of pair 0, (c1, c2) between the pairs, (c3, ur) right of pair 1
       const f2x mid = pk(c01.y, c23.x);
-      F4 bv, un, vn = kZero4;
+      P4 bv, un;
+      [[maybe_unused]] P4 vn = kZeroP4;
       bv.p[0] = stencil2(pk(hl, h01.x), hxv.p[0], hyd.p[0], hyv.p[0], uc.p[0], pk(ul, c01.x), mid, uu.p[0], ud.p[0],
                          cx2, cy2);
       bv.p[1] = stencil2(pk(h01.y, h23.x), hxv.p[1], hyd.p[1], hyv.p[1], uc.p[1], mid, pk(c23.y, ur), uu.p[1],
                          ud.p[1], cx2, cy2);
-      float erow = 0.f;
+      [[maybe_unused]] float erow = 0.f;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         // energy term of the pair (u^{n-1}, u^n) at this node: (u^n - u^{n-1})^2 - (B u^n) u^{n-1}
@@ -327,7 +276,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       w[t][0] = un;
       hyv = hyd;
       if constexpr (ALL) {
-        if (t < K && row_out && col_out) stg4(a.seg + (int64_t)(t - 1) * a.seg_stride + (int64_t)rt * a.ld + c0, un);
+        if (t < K && row_out && col_out) stg_p4(a.seg + (int64_t)(t - 1) * a.seg_stride + (int64_t)rt * a.ld + c0, un);
       }
       if constexpr (FORM == 1) {
         if (t < K) {
@@ -337,11 +286,11 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       }
       if (t == K && row_out && col_out) {
         const int64_t o = (int64_t)rt * a.ld + c0;
-        stg4(a.out_a + o, un);
+        stg_p4(a.out_a + o, un);
         if constexpr (FORM == 1)
-          stg4(a.out_b + o, vn);
+          stg_p4(a.out_b + o, vn);
         else if constexpr (!ALL)
-          stg4(a.out_b + o, w[K - 1][1]);  // level K-1 at the same row (the segment has it already)
+          stg_p4(a.out_b + o, w[K - 1][1]);  // level K-1 at the same row (the segment has it already)
       }
     }
   };

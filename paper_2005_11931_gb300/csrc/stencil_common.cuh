@@ -109,6 +109,60 @@ struct ArithF64 {  // explicitly rounded, definition order, no contraction
   __device__ __forceinline__ double add(double a, double b) const { return __dadd_rn(a, b); }
 };
 
+// Four consecutive columns as two packed pairs (c0, c1), (c2, c3) for the paired FP32
+// instructions of the sm_100 family (add/sub/mul/fma .f32x2): two columns per instruction, each
+// element rounded exactly as the scalar ArithF32 helper rounds it.
+typedef unsigned long long f2x;
+struct P4 {
+  f2x p[2];
+};
+__device__ __forceinline__ f2x pk(float lo, float hi) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk(f2x a) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+  return r;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// B u for a pair of columns, in ArithF32's order: fx = fma(hxl, ul - uc, hxr (ur - uc)), fy
+// likewise, B u = fma(cx, fx, cy fy)
+__device__ __forceinline__ f2x stencil2(f2x hxl, f2x hxr, f2x hyd, f2x hyu, f2x uc, f2x ul, f2x ur, f2x uu, f2x ud,
+                                        f2x cx, f2x cy) {
+  const f2x fx = fma2(hxl, sub2(ul, uc), mul2(hxr, sub2(ur, uc)));
+  const f2x fy = fma2(hyd, sub2(ud, uc), mul2(hyu, sub2(uu, uc)));
+  return fma2(cx, fx, mul2(cy, fy));
+}
+__device__ __forceinline__ P4 lds_p4(const float* s) {
+  const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(s);
+  return P4{{v.x, v.y}};
+}
+__device__ __forceinline__ void stg_p4(float* g, const P4& v) {
+  *reinterpret_cast<ulonglong2*>(g) = make_ulonglong2(v.p[0], v.p[1]);
+}
+constexpr P4 kZeroP4{{0ull, 0ull}};  // +0.0f in every column
+
 template <typename T>
 struct ArithOf;
 template <>
