@@ -226,7 +226,7 @@ typedef struct {
 /* Options of tsu_batch_run (NULL = defaults). */
 typedef struct {
   int32_t tdepth; /* steps per batched pass (0 = the kernel's default: 4 for kernel 2, 8 for kernel 3) */
-  int32_t rows;   /* rows per chunk (0 = 96) */
+  int32_t rows;   /* rows per chunk (0 = 128) */
   int32_t kernel; /* 0 or 2: warp-blocked (tdepth 2 or 4); 3: CTA-blocked (tdepth 4 or 8) */
   int32_t reserved;
 } tsu_batch_opts;

@@ -30,6 +30,9 @@ using namespace dev;
 constexpr int kWtbWarps = 4;       // warps (independent tiles) per CTA
 constexpr int kWtbOut = 120;       // output columns per strip
 constexpr int kWtbPre = 2;         // rows in flight ahead of the one being consumed
+// Resident CTAs per SM: the register file holds three CTAs of these kernels (no launch bound is
+// set, so nothing spills; bounding them to four CTAs forced spills and measured 4-13 % slower).
+constexpr int kWtbCtasPerSm = 3;
 
 template <int K>
 struct WtbShape {
@@ -315,14 +318,14 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 }
 
 template <int K, int FORM, bool ENERGY>
-__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArgs a) {
+__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
   wtb_body<K, FORM, ENERGY, false>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
 }
 
 template <int K, int FORM>
-__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_seg(const WtbArgs a) {
+__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_seg(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
   wtb_body<K, FORM, false, true>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_seg(const Wt
 // Batched family: warp w of CTA b works on tile tiles[4 b + w] = (problem, strip, chunk) of
 // descriptor probs[problem]; one launch advances every problem by K steps.
 template <int K, int FORM>
-__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_batched(const WtbArgs* __restrict__ probs,
+__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_batched(const WtbArgs* __restrict__ probs,
                                                                         const int4* __restrict__ tiles,
                                                                         const int64_t ntiles) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
@@ -428,20 +431,22 @@ int64_t wtb_tiles(int64_t ny, int64_t ld, int rows) {
   return ((ld + 4 + kWtbOut - 1) / kWtbOut) * ((ny - 2 + rows - 1) / rows);
 }
 
-// Rows per chunk for one wave of tiles (152 SMs x 4 resident CTAs of 4 warps), between 16 and 96.
+// Rows per chunk for one wave of tiles (152 SMs x 3 resident CTAs of 4 warps at up to 168
+// registers per thread), between 16 and 160.
 int wtb_seg_rows(int64_t ny, int64_t ld) {
   const int64_t strips = (ld + kWtbOut - 1) / kWtbOut;
-  const int64_t chunks = (int64_t)152 * 4 * kWtbWarps / strips;
-  if (chunks < 1) return 96;
+  const int64_t chunks = (int64_t)152 * kWtbCtasPerSm * kWtbWarps / strips;
+  if (chunks < 1) return 160;
   const int64_t rows = (ny - 2 + chunks - 1) / chunks;
-  return (int)(rows < 16 ? 16 : rows > 96 ? 96 : rows);
+  return (int)(rows < 16 ? 16 : rows > 160 ? 160 : rows);
 }
 
-// Rows per chunk: the fewest (>= 16) that fit all tiles into one wave of 152 SMs x 4 resident CTAs
-// x 4 warps, at most 96.  Measured FP32 GLUPS (increment form, energy every step, K = 4):
-//   8192^2: 654 at 96 rows (604 at 240);  4096^2: 473 at 64, 467 at 32, 397 at 16 (one step
-//   per pass: 247);  2048^2: 290 at 16, 292 at 32, 227 at 64 (one step: 256);  1024^2: 131 at
-//   16, 93 at 32 (one step: 102).
+// Rows per chunk: the fewest (>= 16) that fit all tiles into one wave, at most 160.  Measured FP32
+// GLUPS of this pass (increment form, energy every step, K = 4, 3 CTAs per SM):
+//   16384^2: 891 at 160 rows, 878 at 128, 856 at 96, 815 at 64;  8192^2: 765 at 160, 764 at 96,
+//   744 at 128, 741 at 64;  4096^2: 638 at 79 (the rule's choice), 571 at 64, 542 at 32;
+//   2048^2: 370 at 21 (the rule's) and at 32, 337 at 16, 283 at 48.  One step per pass for
+//   comparison (scalar version): 247 at 4096^2, 256 at 2048^2, 102 at 1024^2.
 int wtb_auto_rows(int64_t ny, int64_t ld, int k) {
   (void)k;
   return wtb_seg_rows(ny, ld);

@@ -616,9 +616,9 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
   const int kern = batch_kernel(opts);
   if (kern != 2 && kern != 3) return fail(TSU_EINVAL, "batch kernel must be 2 or 3");
   const int k = (opts && opts->tdepth) ? opts->tdepth : (kern == 2 ? 4 : 8);
-  // rows per chunk: 96 (64-problem family, FP32 GLUPS at 32/64/96/128/192/256 rows:
-  // 755/815/818/802/763/725)
-  const int rows = (opts && opts->rows) ? opts->rows : 96;
+  // rows per chunk: 128 (64-problem family, FP32 GLUPS at 64/96/128 rows: 801/805/810; an
+  // earlier build of the pass at 32/64/96/128/192/256 rows: 755/815/818/802/763/725)
+  const int rows = (opts && opts->rows) ? opts->rows : 128;
   if (kern == 3 && !tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 3: tdepth must be 4 or 8");
   if (kern == 2 && !tsu::wtb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 2: tdepth must be 2 or 4");
   if (rows < 16) return fail(TSU_EINVAL, "rows must be >= 16");
