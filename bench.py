@@ -54,9 +54,9 @@ def parse():
     ap.add_argument("--tdepth", type=int, default=0, help="steps per blocked pass (0: 4 for kernel 2, 8 for 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched and 16384^2 measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched, 16384^2 and paper Case 1 measurements")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch (from profiles/)")
-    ap.add_argument("--measure", choices=["adjoint", "batched", "large"], default=None,
+    ap.add_argument("--measure", choices=["adjoint", "batched", "large", "paper_case1"], default=None,
                     help="run only this side measurement and print its result (a profiling aid)")
     ap.add_argument("--measure-n", type=int, default=2048, help="grid side of --measure adjoint")
     ap.add_argument("--measure-steps", type=int, default=4000, help="leapfrog steps of --measure adjoint/batched")
@@ -349,6 +349,7 @@ def run_gpu(args):
         extras["adjoint"] = measure_adjoint()
         extras["batched"] = measure_batched()
         extras["large"] = measure_large()
+        extras["paper_case1"] = measure_paper_case1()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         r = oracle_sample(p.n, 64 if p.n >= 4096 else 256)
@@ -528,6 +529,35 @@ def measure_large(n=16384, steps=2000, warm=1):
             "energy_drift": float(np.max(np.abs(en - en[0])) / en[0])}
 
 
+def measure_paper_case1(n=4097, steps=2000, warm=1):
+    """The paper's own 2D workload (Sec. 3.3, rescaled to the unit box): Friedrichs-mollified
+    depth step 100 -> 10 at x = 0.75, eps = 0.8/100, hump 50 exp(-r^2/8) at (0.40, 0.50); FP32,
+    energy every step."""
+    import numpy as np
+    import torch
+
+    from paper_2005_11931_gb300 import inputs, tsu
+
+    p = inputs.paper_case1_2d(n=n, steps=steps)["problem"]
+    sim = tsu.Simulation.create(n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+    u0 = torch.from_numpy(p.initial(sim.g.ld, np.float32)).cuda()
+    e = torch.zeros(steps, dtype=torch.float64, device="cuda")
+
+    def run():
+        sim.init(u0)
+        sim.step(steps - 1, energy=e[: steps - 1])
+
+    for _ in range(warm):
+        run()
+    t = _events_ms(run)
+    tsu.tsu_sync_status(sim.ws, sim.ws.numel())
+    en = e[: steps - 1].cpu().numpy()
+    return {"workload": f"paper_case1_{n}: {n}^2, depth step 100 -> 10 at x = 0.75 (Friedrichs, eps 0.008), "
+                        f"hump 50 exp(-r^2/8) at (0.40, 0.50) in paper units, {steps} steps, energy every step",
+            "ms": t, "glups": (n - 2) ** 2 * steps / t / 1e6,
+            "energy_drift": float(np.max(np.abs(en - en[0])) / en[0])}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -535,7 +565,7 @@ def main():
     if args.measure:
         fn = {"adjoint": lambda: measure_adjoint(args.measure_n, args.measure_steps),
               "batched": lambda: measure_batched(args.measure_steps, rows=args.rows),
-              "large": measure_large}[args.measure]
+              "large": measure_large, "paper_case1": measure_paper_case1}[args.measure]
         print(json.dumps(fn()))
         return 0
     return run_gpu(args)

@@ -35,26 +35,41 @@ __device__ double friedrichs_cdf(double c1, double t) {
   return c1 * s * h * half;
 }
 
+// Far from a singularity the mollifier's value is exactly 0 in FP64 (exp(-q^2) underflows for
+// q^2 > 745.2; the bump vanishes for |t| >= 1) and the mollified step is exactly 0 or 1; those
+// faces skip the transcendental functions, with the same results.  kFar = 750 keeps a margin over
+// the rounding of the squared distances.
+constexpr double kFar = 750.0;
+
 __device__ __forceinline__ double phi1(const DepthParams& p, double s) {
   const double e = p.eps;
   if (p.mollifier == TSU_GAUSS) {
+    if (s * s > kFar * (e * e)) return 0.0;
     double q = s / e;
     return exp(-q * q) / (e * sqrt(kPi));
   }
+  if (s * s >= e * e * 1.0000001) return 0.0;
   return p.c1 / e * bump(s / e);
 }
 
-__device__ __forceinline__ double phi2(const DepthParams& p, double r) {
-  const double e = p.eps;
+__device__ __forceinline__ double phi2(const DepthParams& p, double dx, double dy) {
+  const double e = p.eps, r2 = dx * dx + dy * dy;
   if (p.mollifier == TSU_GAUSS) {
-    double q = r / e;
+    if (r2 > kFar * (e * e)) return 0.0;
+    double q = sqrt(r2) / e;
     return exp(-q * q) / (kPi * e * e);
   }
-  return p.c2 / (e * e) * bump(r / e);
+  if (r2 >= e * e * 1.0000001) return 0.0;
+  return p.c2 / (e * e) * bump(sqrt(r2) / e);
 }
 
 __device__ __forceinline__ double step1(const DepthParams& p, double s) {
-  if (p.mollifier == TSU_GAUSS) return 0.5 * erfc(-s / p.eps);
+  if (p.mollifier == TSU_GAUSS) {
+    // 0.5 erfc(-s/eps): erfc(t) = 2 exactly below t = -6 and 0 above t = 27.3
+    if (s > 7.0 * p.eps) return 1.0;
+    if (s < -28.0 * p.eps) return 0.0;
+    return 0.5 * erfc(-s / p.eps);
+  }
   return friedrichs_cdf(p.c1, s / p.eps);
 }
 
@@ -66,11 +81,7 @@ __device__ double depth_at(const DepthParams& p, double x, double y) {
     switch (s.kind) {
       case TSU_LINE_X: v = phi1(p, x - s.cx); break;
       case TSU_LINE_Y: v = phi1(p, y - s.cy); break;
-      case TSU_POINT: {
-        double dx = x - s.cx, dy = y - s.cy;
-        v = phi2(p, sqrt(dx * dx + dy * dy));
-        break;
-      }
+      case TSU_POINT: v = phi2(p, x - s.cx, y - s.cy); break;
       case TSU_STEP_X: v = step1(p, s.cx - x); break;
       default: v = step1(p, s.cy - y); break;
     }

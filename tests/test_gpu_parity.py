@@ -79,6 +79,23 @@ def test_line_fp64_201_full_parity():
     assert np.abs(gpu["u"]).max() > 0.05
 
 
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_paper_case1_workload(dtype, tol):
+    """The paper's own 2D workload (Sec. 3.3): a Friedrichs-mollified depth step from 100 to 10 at
+    x = 75 (here 0.75) and the hump 50 exp(-((x-40)^2 + (y-50)^2)/8), on the unit box; 513^2
+    nodes, 600 steps (the wave crosses the step and part of it is reflected)."""
+    case = inputs.paper_case1_2d(n=513, steps=600)
+    p = case["problem"]
+    u0 = p.initial()
+    gpu = run_gpu(p.n, p.depth, u0, p.steps, dtype=dtype, form=tsu.TSU_FORM_INCREMENT)
+    orc = run_oracle(p.n, p.depth, u0, p.steps)
+    assert relerr(gpu["u"], orc["u"]) <= tol
+    assert np.max(np.abs(gpu["energy"] - orc["energy"]) / orc["energy"]) <= (1e-12 if dtype == "f64" else 1e-6)
+    # the hump (width 0.028 at x = 0.40) has spread: the field left of the step is no longer the
+    # initial one, and something has passed the step at x = 0.75
+    assert np.abs(gpu["u"][:, int(0.8 * (p.n - 1)):]).max() > 1e-3 * 50
+
+
 @pytest.mark.parametrize("form,dtype,steps,tol", [
     (tsu.TSU_FORM_STANDARD, "f64", 300, 1e-12), (tsu.TSU_FORM_INCREMENT, "f64", 300, 1e-12),
     (tsu.TSU_FORM_INCREMENT, "f32", 400, 1e-5),
