@@ -1,19 +1,21 @@
-// Two adjoint steps per pass (the paper has no adjoint; this is the exact reverse of the scheme of
-// k_step.cu, arXiv:2005.11931 Sec. 2 eq. (2.1) on the Sec. 3.3 box), warp-blocked like
-// k_step_wtb.cu:
-//   lam^n     = g^n     + 2 lam^{n+1} - lam^{n+2} + B lam^{n+1}
-//   lam^{n-1} = g^{n-1} + 2 lam^n     - lam^{n+1} + B lam^n
-//   dJ/dhx_ij += -cx [ (lam^{n+1}_{i+1}-lam^{n+1}_i)(u^n_{i+1}-u^n_i)
-//                    + (lam^n_{i+1}  -lam^n_i  )(u^{n-1}_{i+1}-u^{n-1}_i) ]   (dJ/dhy likewise)
-// Every warp owns a tile: 128 columns (one float4 per lane; the middle 120 are output, a
-// 4-column halo covers the two-step cone) by a chunk of rows it streams down.  Each thread copies
-// its own float4 of the six input rows (lam^{n+1}, lam^{n+2}, u^n, u^{n-1}, hx, hy) through a
-// private cp.async ring; level 1 (lam^n) lags the input by one row, level 2 (lam^{n-1}) by two.
-// The face gradients of both steps are added in registers, so the FP32 accumulators are read and
-// written once per two steps; their rows travel through the same ring, two rows behind the
-// inputs, so no load waits inside the row loop.  Receiver values g^n, g^{n-1} are added to the
-// multipliers in registers, in every tile whose extended region holds the receiver (halo copies
-// included): the lanes hold the tile's entries and a ballot per row finds the ones on it.
+// K adjoint steps per pass, K = 2 or 4 (the paper has no adjoint; this is the exact reverse of
+// the scheme of k_step.cu, arXiv:2005.11931 Sec. 2 eq. (2.1) on the Sec. 3.3 box), warp-blocked
+// like k_step_wtb.cu.  Level k = 1..K computes lam^{n-k+1} from the two levels before it:
+//   lam^{n-k+1} = g^{n-k+1} + 2 lam^{n-k+2} - lam^{n-k+3} + B lam^{n-k+2}
+//   dJ/dhx_ij  += -cx (lam^{n-k+2}_{i+1} - lam^{n-k+2}_i)(u^{n-k+1}_{i+1} - u^{n-k+1}_i)   (hy likewise)
+// (level 0 = lam^{n+1} and level -1 = lam^{n+2} are the inputs).  Every warp owns a tile: 128
+// columns (one float4 per lane; the middle 120 are output, a 4-column halo covers the K-step
+// cone) by a chunk of rows it streams down; level k lags the input row by k rows.  Each thread
+// copies its own float4 of every input row through a private cp.async ring: lam^{n+1},
+// lam^{n+2}, hx and hy at the input row (the faces one row behind), u^{n-f} f rows behind, where
+// level f + 1 needs it, and the FP32 gradient accumulators K rows behind, where the last level
+// finishes a row; so nothing in the row loop waits on memory.  The face gradients of a row are
+// summed over the K steps in registers (carried from level to level) and added to the
+// accumulators once per pass.  Only the last two levels are stored: they are lam^{n'+2} and
+// lam^{n'+1} of the next pass.  Receiver values are added to the multipliers in registers, in
+// every tile whose extended region holds the receiver (halo copies included): the lanes hold the
+// tile's entries and a ballot per row and level finds the ones on it.  Arithmetic runs on paired
+// FP32 instructions with the rounding order of the scalar one-step adjoint pass.
 #include <string.h>
 
 #include "stencil_common.cuh"
@@ -26,7 +28,13 @@ constexpr int kAwWarps = 4;
 constexpr int kAwOut = 120;
 constexpr int kAwPre = 2;
 constexpr int kAwRing = 4;  // slots per field: in flight (2) + current, power of two
-constexpr int kAwFields = 8;  // lam^{n+1}, lam^{n+2}, u^n, u^{n-1}, hx, hy, then gx, gy two rows behind
+// resident CTAs per SM (register-limited; checked against -Xptxas -v): K = 2 at <= 168
+// registers per thread, K = 4 at <= 255
+template <int K>
+constexpr int aw_ctas_per_sm() { return K == 2 ? 3 : 2; }
+// ring fields: lam^{n+1}, lam^{n+2}, hx, hy, u^n .. u^{n-K+1}, gx, gy
+template <int K>
+constexpr int aw_fields() { return K + 6; }
 
 __device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
@@ -39,29 +47,31 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+template <int K>
 struct AwArgs {
   int32_t nx, ny;
   int64_t ld;
   float cx, cy;
   const float* hx;
   const float* hy;
-  const float* lam1;  // lam^{n+1}
-  const float* lam2;  // lam^{n+2}
-  const float* un;    // u^n
-  const float* um;    // u^{n-1}
-  float* out1;        // lam^n
-  float* out2;        // lam^{n-1}
-  float* gx;          // FP32 face-gradient accumulators
+  const float* lam1;   // lam^{n+1}
+  const float* lam2;   // lam^{n+2}
+  const float* u[K];   // u^n, u^{n-1}, ..., u^{n-K+1}
+  float* out_a;        // lam^{n-K+2} (level K - 1)
+  float* out_b;        // lam^{n-K+1} (level K)
+  float* gx;           // FP32 face-gradient accumulators
   float* gy;
   int rows;
   int64_t nstrips, ntiles;
   const int* rec_off;  // per tile [ntiles + 1], or nullptr
   const int4* rec;     // (row, col, receiver, 0)
-  const float* g1;     // g^n at the receivers
-  const float* g2;     // g^{n-1}
+  const float* g[K];   // g^n, g^{n-1}, ... at the receivers
 };
 
-__global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) {
+template <int K>
+__global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a) {
+  constexpr int NF = aw_fields<K>();
+  constexpr int F_L1 = 0, F_L2 = 1, F_HX = 2, F_HY = 3, F_U = 4, F_GX = 4 + K, F_GY = 5 + K;
   extern __shared__ __align__(16) unsigned char aw_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kAwWarps + warp;
@@ -71,7 +81,7 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
   const int64_t c0 = xs + 4 * lane;
   const int y0 = 1 + (int)chunk * a.rows;
   const int y1 = tile_ok ? min(y0 + a.rows, a.ny - 1) : y0;
-  const int r_first = y0 - 2, nit = tile_ok ? (y1 - y0) + 4 : 0;
+  const int r_first = y0 - K, nit = tile_ok ? (y1 - y0) + 2 * K : 0;
   const bool col_in = c0 >= 0 && c0 < a.ld;
   const bool col_out = lane >= 1 && lane <= 30 && col_in;
   bool node_col[4], face_x[4];
@@ -80,23 +90,28 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
     node_col[e] = (c0 + e >= 1) && (c0 + e <= a.nx - 2);
     face_x[e] = (c0 + e <= a.nx - 2);  // x-face (i, i+1) exists
   }
-  // per-thread ring: [kAwRing][kAwFields] float4
+  // per-thread ring: [kAwRing][NF] float4
   float* ring = reinterpret_cast<float*>(aw_smem) + (size_t)threadIdx.x * 4;
   const int stride = kAwWarps * 32 * 4;
-  auto slot = [&](unsigned s, int f) { return ring + (size_t)(s * kAwFields + f) * stride; };
-  const float* src[6] = {a.lam1, a.lam2, a.un, a.um, a.hx, a.hy};
-  auto issue = [&](int r) {
-    const bool ok = col_in && r >= 0 && r < a.ny;
-    const int64_t go = ok ? (int64_t)r * a.ld + c0 : 0;
-    const unsigned s = (unsigned)(r - r_first) & (kAwRing - 1);
+  auto slot = [&](unsigned s, int f) { return ring + (size_t)(s * NF + f) * stride; };
+  auto issue = [&](int q) {  // the copies consumed at iteration q (input row r_first + q)
+    const int r = r_first + q;
+    const unsigned s = (unsigned)q & (kAwRing - 1);
+    auto copy = [&](int f, const float* src, int row, bool extra) {
+      const bool ok = extra && col_in && row >= 0 && row < a.ny;
+      cp16(slot(s, f), src + (ok ? (int64_t)row * a.ld + c0 : 0), ok);
+    };
+    copy(F_L1, a.lam1, r, true);
+    copy(F_L2, a.lam2, r, true);
+    copy(F_HX, a.hx, r - 1, true);
+    copy(F_HY, a.hy, r - 1, true);
 #pragma unroll
-    for (int f = 0; f < 6; ++f) cp16(slot(s, f), src[f] + go, ok);
-    // accumulators of row r - 2, the row level 2 finishes when row r is consumed; only rows this
+    for (int f = 0; f < K; ++f) copy(F_U + f, a.u[f], r - f, true);
+    // accumulators of row r - K, the row the last level finishes at iteration q; only rows this
     // tile owns are read (no other tile writes them, and this tile writes each once)
-    const bool acc = col_out && r - 2 >= y0 && r - 2 < y1;
-    const int64_t ga = acc ? (int64_t)(r - 2) * a.ld + c0 : 0;
-    cp16(slot(s, 6), a.gx + ga, acc);
-    cp16(slot(s, 7), a.gy + ga, acc);
+    const bool acc = col_out && r - K >= y0 && r - K < y1;
+    copy(F_GX, a.gx, r - K, acc);
+    copy(F_GY, a.gy, r - K, acc);
   };
   // per-thread column constants (the columns of a thread never change): node and face masks
   // folded into the coefficients of the gradient terms
@@ -109,39 +124,52 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
     gcy2[q] = pk(node_col[e] ? -a.cy : 0.f, node_col[e + 1] ? -a.cy : 0.f);
   }
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
-  // windows (index 0 = newest row)
-  P4 w0[3] = {kZeroP4, kZeroP4, kZeroP4};  // lam^{n+1} rows r, r-1, r-2
-  P4 w1[3] = {kZeroP4, kZeroP4, kZeroP4};  // lam^n rows r-1, r-2, r-3
-  P4 L2[2] = {kZeroP4, kZeroP4};           // lam^{n+2} rows r, r-1
-  P4 U[2] = {kZeroP4, kZeroP4};            // u^n rows r, r-1
-  P4 M[3] = {kZeroP4, kZeroP4, kZeroP4};   // u^{n-1} rows r, r-1, r-2
-  P4 HX[3] = {kZeroP4, kZeroP4, kZeroP4};  // hx rows r, r-1, r-2
-  P4 HY[4] = {kZeroP4, kZeroP4, kZeroP4, kZeroP4};  // hy rows r .. r-3
-  P4 gpx = kZeroP4, gpy = kZeroP4;  // face gradients of step n at the previous level-1 row
-  P4 g0ya = kZeroP4;                // y-face (0, 1) of step n, carried to the level-2 row 1
+  // register windows, index 0 = newest row
+  P4 W[K][3];       // level k = 0..K-1 (level 0 = lam^{n+1}) at rows r - k, r - k - 1, r - k - 2
+  P4 LP[2];         // lam^{n+2} at rows r, r - 1
+  P4 UW[K][2];      // u^{n-f} at rows r - f, r - f - 1
+  P4 HXW[K];        // hx at rows r - 1 .. r - K
+  P4 HYW[K + 1];    // hy at rows r - 1 .. r - K - 1
+  P4 cx_[K], cy_[K];  // gradient sums of levels 1..j at the row level j + 1 reaches next
+  P4 g0 = kZeroP4;    // y-face (0, 1) terms of the levels that have passed row 1
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    W[k][0] = W[k][1] = W[k][2] = kZeroP4;
+    UW[k][0] = UW[k][1] = kZeroP4;
+    HXW[k] = kZeroP4;
+    cx_[k] = cy_[k] = kZeroP4;
+  }
+#pragma unroll
+  for (int k = 0; k <= K; ++k) HYW[k] = kZeroP4;
+  LP[0] = LP[1] = kZeroP4;
+
   const int q_lo = (tile_ok && a.rec_off) ? a.rec_off[tile] : 0, q_hi = (tile_ok && a.rec_off) ? a.rec_off[tile + 1] : 0;
-  // the tile's first 32 receiver entries, one per lane (row -1: none)
+  // the tile's first 32 receiver entries, one per lane (row -1: none), with their K values
   int pr_row = -1, pr_col = 0;
-  float pr_g1 = 0.f, pr_g2 = 0.f;
+  float pr_g[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) pr_g[k] = 0.f;
   if (q_lo + lane < q_hi) {
     const int4 rq = a.rec[q_lo + lane];
     pr_row = rq.x;
     pr_col = rq.y;
-    pr_g1 = a.g1[rq.z];
-    pr_g2 = a.g2[rq.z];
+#pragma unroll
+    for (int k = 0; k < K; ++k) pr_g[k] = a.g[k][rq.z];
   }
-  // add g at the entries on row p to the lane's four multipliers (warp-uniform loop bounds)
-  auto inject = [&](int p, P4& l, bool second) {
+  // add g^{n-k} (k = kg) at the entries on row p to the lane's four multipliers (warp-uniform
+  // loop bounds)
+  // (kg is a constant once the level loop is unrolled)
+  auto inject = [&](int p, P4& l, const int kg) {
     for (int qb = q_lo; qb < q_hi; qb += 32) {
       int row = pr_row, col = pr_col;
-      float val = second ? pr_g2 : pr_g1;
+      float val = pr_g[kg];
       if (qb != q_lo) {  // more than 32 entries: the rest from memory
         row = -1;
         if (qb + lane < q_hi) {
           const int4 rq = a.rec[qb + lane];
           row = rq.x;
           col = rq.y;
-          val = second ? a.g2[rq.z] : a.g1[rq.z];
+          val = a.g[kg][rq.z];
         }
       }
       unsigned m = __ballot_sync(0xffffffffu, row == p);
@@ -192,73 +220,102 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb2(const AwArgs a) 
   };
 
   for (int q = 0; q < kAwPre; ++q) {
-    if (q < nit) issue(r_first + q);
+    if (q < nit) issue(q);
     cp_commit();
   }
   for (int it = 0; it < nit; ++it) {
     const int r_in = r_first + it;
-    if (it + kAwPre < nit) issue(r_in + kAwPre);
+    if (it + kAwPre < nit) issue(it + kAwPre);
     cp_commit();
     cp_wait<kAwPre>();
     const unsigned s = (unsigned)it & (kAwRing - 1);
-    // shift histories and take the new row
-    w0[2] = w0[1]; w0[1] = w0[0]; w0[0] = lds_p4(slot(s, 0));
-    L2[1] = L2[0]; L2[0] = lds_p4(slot(s, 1));
-    U[1] = U[0]; U[0] = lds_p4(slot(s, 2));
-    M[2] = M[1]; M[1] = M[0]; M[0] = lds_p4(slot(s, 3));
-    HX[2] = HX[1]; HX[1] = HX[0]; HX[0] = lds_p4(slot(s, 4));
-    HY[3] = HY[2]; HY[2] = HY[1]; HY[1] = HY[0]; HY[0] = lds_p4(slot(s, 5));
-
-    // ---- level 1: lam^n at row p1 = r_in - 1, and the face gradients of step n there
-    const int p1 = r_in - 1;
-    P4 l1, g1x, g1y;
-    level(w0[1], w0[0], w0[2], HX[1], HY[1], HY[2], L2[1], U[1], U[0], p1 >= 1 && p1 <= a.ny - 2, l1, g1x, g1y);
-    if (p1 == 1) {  // y-face (0, 1): lam and u vanish on row 0, the term is -cy lam_1 u_1
+    // shift the input windows and take the new rows
+    W[0][2] = W[0][1];
+    W[0][1] = W[0][0];
+    W[0][0] = lds_p4(slot(s, F_L1));
+    LP[1] = LP[0];
+    LP[0] = lds_p4(slot(s, F_L2));
 #pragma unroll
-      for (int q = 0; q < 2; ++q) g0ya.p[q] = mul2(gcy2[q], mul2(w0[1].p[q], U[1].p[q]));
+    for (int f = 0; f < K; ++f) {
+      UW[f][1] = UW[f][0];
+      UW[f][0] = lds_p4(slot(s, F_U + f));
     }
-    inject(p1, l1, false);  // receivers on this row (extended region)
-    w1[2] = w1[1]; w1[1] = w1[0]; w1[0] = l1;
-    if (col_out && p1 >= y0 && p1 < y1) stg_p4(a.out1 + (int64_t)p1 * a.ld + c0, l1);
+#pragma unroll
+    for (int k = K - 1; k >= 1; --k) HXW[k] = HXW[k - 1];
+    HXW[0] = lds_p4(slot(s, F_HX));
+#pragma unroll
+    for (int k = K; k >= 1; --k) HYW[k] = HYW[k - 1];
+    HYW[0] = lds_p4(slot(s, F_HY));
 
-    // ---- level 2: lam^{n-1} at row p2 = r_in - 2, and the face gradients of step n-1 there
-    const int p2 = r_in - 2;
-    P4 l2, g2x, g2y;
-    level(w1[1], w1[0], w1[2], HX[2], HY[2], HY[3], w0[2], M[2], M[1], p2 >= 1 && p2 <= a.ny - 2, l2, g2x, g2y);
-    inject(p2, l2, true);
-    if (col_out && p2 >= y0 && p2 < y1) {
-      const int64_t o = (int64_t)p2 * a.ld + c0;
-      stg_p4(a.out2 + o, l2);
-      // both steps' face gradients of row p2: step n was computed one iteration ago
-      P4 ax = lds_p4(slot(s, 6)), ay = lds_p4(slot(s, 7));
+    P4 pend_x = kZeroP4, pend_y = kZeroP4;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        ax.p[q] = add2(ax.p[q], add2(gpx.p[q], g2x.p[q]));
-        ay.p[q] = add2(ay.p[q], add2(gpy.p[q], g2y.p[q]));
+    for (int k = 1; k <= K; ++k) {
+      const int pk_row = r_in - k;
+      const P4& lpp = (k == 1) ? LP[1] : W[k >= 2 ? k - 2 : 0][2];
+      P4 lk, gxk, gyk;
+      level(W[k - 1][1], W[k - 1][0], W[k - 1][2], HXW[k - 1], HYW[k - 1], HYW[k], lpp, UW[k - 1][1], UW[k - 1][0],
+            pk_row >= 1 && pk_row <= a.ny - 2, lk, gxk, gyk);
+      if (pk_row == 1) {  // y-face (0, 1): lam and u vanish on row 0, the term is -cy lam_1 u_1
+#pragma unroll
+        for (int q = 0; q < 2; ++q) g0.p[q] = add2(g0.p[q], mul2(gcy2[q], mul2(W[k - 1][1].p[q], UW[k - 1][1].p[q])));
       }
-      stg_p4(a.gx + o, ax);
-      stg_p4(a.gy + o, ay);
-      if (p2 == 1) {  // y-face (0, 1) of both steps
-        const ulonglong2 r0 = __ldcg(reinterpret_cast<const ulonglong2*>(a.gy + c0));  // once per tile column
-        P4 a0{{r0.x, r0.y}};
+      inject(pk_row, lk, k - 1);
+      const bool store_row = col_out && pk_row >= y0 && pk_row < y1;
+      if (k < K) {
+        W[k][2] = W[k][1];
+        W[k][1] = W[k][0];
+        W[k][0] = lk;
+      }
+      if (k == K - 1 && store_row) stg_p4(a.out_a + (int64_t)pk_row * a.ld + c0, lk);
+      // gradient sums: level k adds to the sum of levels 1..k-1 at this row (carried from the
+      // previous iteration); the new sum is kept until level k + 1 has read the old one
+      P4 sx, sy;
+      if (k == 1) {
+        sx = gxk;
+        sy = gyk;
+      } else {
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-          a0.p[q] = add2(a0.p[q], add2(g0ya.p[q], mul2(gcy2[q], mul2(w1[1].p[q], M[2].p[q]))));
-        stg_p4(a.gy + c0, a0);
+        for (int q = 0; q < 2; ++q) {
+          sx.p[q] = add2(cx_[k - 1].p[q], gxk.p[q]);
+          sy.p[q] = add2(cy_[k - 1].p[q], gyk.p[q]);
+        }
+        cx_[k - 1] = pend_x;
+        cy_[k - 1] = pend_y;
+      }
+      if (k < K) {
+        pend_x = sx;
+        pend_y = sy;
+      } else if (store_row) {
+        const int64_t o = (int64_t)pk_row * a.ld + c0;
+        stg_p4(a.out_b + o, lk);
+        P4 ax = lds_p4(slot(s, F_GX)), ay = lds_p4(slot(s, F_GY));
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          ax.p[q] = add2(ax.p[q], sx.p[q]);
+          ay.p[q] = add2(ay.p[q], sy.p[q]);
+        }
+        stg_p4(a.gx + o, ax);
+        stg_p4(a.gy + o, ay);
+        if (pk_row == 1) {  // y-face (0, 1) of all K steps
+          const ulonglong2 r0 = __ldcg(reinterpret_cast<const ulonglong2*>(a.gy + c0));  // once per tile column
+          P4 a0{{r0.x, r0.y}};
+#pragma unroll
+          for (int q = 0; q < 2; ++q) a0.p[q] = add2(a0.p[q], g0.p[q]);
+          stg_p4(a.gy + c0, a0);
+        }
       }
     }
-    gpx = g1x;
-    gpy = g1y;
   }
   cp_wait<0>();
 }
 
-// Receivers of the two-step pass: for every tile whose extended region (columns 120 s - 4 ..
-// 120 s + 123, rows y0 - 1 .. y1) holds a receiver's interior node, one entry (row, col, r, 0),
-// tiles in order, receivers in order within a tile.  One thread; nrec is small.
+// Receivers of the K-step pass: for every tile whose extended region (columns 120 s - 4 ..
+// 120 s + 123, rows y0 - (K - 1) .. y1 + (K - 2), where the levels before the last need the
+// values) holds a receiver's interior node, one entry (row, col, r, 0), tiles in order,
+// receivers in order within a tile (at most 4 per receiver).  One thread; nrec is small.
 __global__ void k_rec_tiles(const int32_t nx, const int32_t ny, const int64_t ld, const int64_t* idx,
-                            const int32_t nrec, const int rows, const int64_t nstrips, const int64_t ntiles, int* off,
-                            int4* ent) {
+                            const int32_t nrec, const int rows, const int above, const int below,
+                            const int64_t nstrips, const int64_t ntiles, int* off, int4* ent) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int64_t nchunks = ntiles / nstrips;
   for (int64_t t = 0; t <= ntiles; ++t) off[t] = 0;
@@ -274,7 +331,7 @@ __global__ void k_rec_tiles(const int32_t nx, const int32_t ny, const int64_t ld
         for (int64_t ch = c_lo; ch <= c_lo + 2; ++ch) {
           if (ch < 0 || ch >= nchunks) continue;
           const int64_t y0 = 1 + ch * rows, y1 = (y0 + rows < ny - 1) ? y0 + rows : ny - 1;
-          if (j < y0 - 1 || j > y1) continue;
+          if (j < y0 - above || j > y1 + below) continue;
           const int64_t t = ch * nstrips + sc;
           if (pass == 0)
             off[t + 1] += 1;
@@ -292,37 +349,43 @@ __global__ void k_rec_tiles(const int32_t nx, const int32_t ny, const int64_t ld
   }
 }
 
+template <int K>
+cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void* hy, const void* lam1,
+                      const void* lam2, const void* const* u, void* out_a, void* out_b, void* gx, void* gy,
+                      const int* rec_off, const int4* rec, const void* const* gv, cudaStream_t s);
+
 }  // namespace
 
-// Rows per chunk: the fewest that still fit all tiles into one wave (152 SMs x 3 resident CTAs of
-// 4 warps at 148 registers), between 16 (halo rows cost (rows + 4) / rows) and 64.  Tiles of a
-// second, partly filled wave would leave most SMs idle while it runs.
-int adjoint_wtb2_rows(int64_t ny, int64_t ld) {
+// Rows per chunk: the fewest that still fit all tiles into one wave (152 SMs x the resident CTAs
+// of 4 warps), between 16 (halo rows cost (rows + 2K) / rows) and 64.  Tiles of a second, partly
+// filled wave would leave most SMs idle while it runs.
+int adjoint_wtb_rows(int k, int64_t ny, int64_t ld) {
   const int64_t strips = (ld + kAwOut - 1) / kAwOut;
-  const int64_t wave_tiles = 152 * 3 * kAwWarps;
+  const int64_t wave_tiles = (int64_t)152 * (k == 2 ? aw_ctas_per_sm<2>() : aw_ctas_per_sm<4>()) * kAwWarps;
   const int64_t chunks = wave_tiles / strips;
   if (chunks < 1) return 64;
   const int64_t rows = (ny - 2 + chunks - 1) / chunks;
   return (int)(rows < 16 ? 16 : rows > 64 ? 64 : rows);
 }
 
-int64_t adjoint_wtb2_tiles(int64_t ny, int64_t ld, int rows) {
+int64_t adjoint_wtb_tiles(int64_t ny, int64_t ld, int rows) {
   return ((ld + kAwOut - 1) / kAwOut) * ((ny - 2 + rows - 1) / rows);
 }
 
-cudaError_t launch_rec_tiles(const StencilGeom& g, const int64_t* idx, int32_t nrec, int rows, int* off, int4* ent,
-                             cudaStream_t s) {
+cudaError_t launch_rec_tiles(const StencilGeom& g, int k, const int64_t* idx, int32_t nrec, int rows, int* off,
+                             int4* ent, cudaStream_t s) {
   const int64_t nstrips = (g.ld + kAwOut - 1) / kAwOut;
-  k_rec_tiles<<<1, 32, 0, s>>>(g.nx, g.ny, g.ld, idx, nrec, rows, nstrips, adjoint_wtb2_tiles(g.ny, g.ld, rows), off,
-                               ent);
+  k_rec_tiles<<<1, 32, 0, s>>>(g.nx, g.ny, g.ld, idx, nrec, rows, k - 1, k - 2, nstrips,
+                               adjoint_wtb_tiles(g.ny, g.ld, rows), off, ent);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_wtb2(const StencilGeom& g, int rows, const void* hx, const void* hy, const void* lam1,
-                                const void* lam2, const void* un, const void* um, void* out1, void* out2, void* gx,
-                                void* gy, const int* rec_off, const int4* rec, const void* g1, const void* g2,
-                                cudaStream_t s) {
-  AwArgs a;
+namespace {
+template <int K>
+cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void* hy, const void* lam1,
+                      const void* lam2, const void* const* u, void* out_a, void* out_b, void* gx, void* gy,
+                      const int* rec_off, const int4* rec, const void* const* gv, cudaStream_t s) {
+  AwArgs<K> a;
   a.nx = g.nx;
   a.ny = g.ny;
   a.ld = g.ld;
@@ -332,24 +395,34 @@ cudaError_t launch_adjoint_wtb2(const StencilGeom& g, int rows, const void* hx, 
   a.hy = (const float*)hy;
   a.lam1 = (const float*)lam1;
   a.lam2 = (const float*)lam2;
-  a.un = (const float*)un;
-  a.um = (const float*)um;
-  a.out1 = (float*)out1;
-  a.out2 = (float*)out2;
+  for (int f = 0; f < K; ++f) {
+    a.u[f] = (const float*)u[f];
+    a.g[f] = gv ? (const float*)gv[f] : nullptr;
+  }
+  a.out_a = (float*)out_a;
+  a.out_b = (float*)out_b;
   a.gx = (float*)gx;
   a.gy = (float*)gy;
   a.rows = rows;
   a.nstrips = (g.ld + kAwOut - 1) / kAwOut;
-  a.ntiles = adjoint_wtb2_tiles(g.ny, g.ld, rows);
+  a.ntiles = adjoint_wtb_tiles(g.ny, g.ld, rows);
   a.rec_off = rec_off;
   a.rec = rec;
-  a.g1 = (const float*)g1;
-  a.g2 = (const float*)g2;
-  const size_t smem = (size_t)kAwRing * kAwFields * 16 * kAwWarps * 32;
-  cudaError_t e = cudaFuncSetAttribute(k_adjoint_wtb2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (size_t)kAwRing * aw_fields<K>() * 16 * kAwWarps * 32;
+  cudaError_t e = cudaFuncSetAttribute(k_adjoint_wtb<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_adjoint_wtb2<<<(unsigned)((a.ntiles + kAwWarps - 1) / kAwWarps), kAwWarps * 32, smem, s>>>(a);
+  k_adjoint_wtb<K><<<(unsigned)((a.ntiles + kAwWarps - 1) / kAwWarps), kAwWarps * 32, smem, s>>>(a);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_adjoint_wtb(const StencilGeom& g, int k, int rows, const void* hx, const void* hy,
+                               const void* lam1, const void* lam2, const void* const* u, void* out_a, void* out_b,
+                               void* gx, void* gy, const int* rec_off, const int4* rec, const void* const* gv,
+                               cudaStream_t s) {
+  if (k == 2) return aw_launch<2>(g, rows, hx, hy, lam1, lam2, u, out_a, out_b, gx, gy, rec_off, rec, gv, s);
+  if (k == 4) return aw_launch<4>(g, rows, hx, hy, lam1, lam2, u, out_a, out_b, gx, gy, rec_off, rec, gv, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace tsu

@@ -314,6 +314,8 @@ static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
 constexpr bool kAdjointTimeReversal = false;
 // steps per pass of the FP32 segment recompute (warp-blocked, intermediate states stored)
 constexpr int kRecomputeDepth = 4;
+// steps per pass of the FP32 reverse sweep (2 or 4); leftover steps of a segment run one per pass
+constexpr int kAdjointDepth = 4;
 
 // fields of dtype before the FP32 accumulators: 4 multipliers, then two segment buffers of E + 3
 // (or, for the time-reversed sweep, the two (u, v) states)
@@ -321,13 +323,13 @@ static int64_t adjoint_fields(int form, int64_t every) {
   return (form == TSU_FORM_INCREMENT && kAdjointTimeReversal) ? 4 + 4 : 4 + 2 * (every + 3);
 }
 
-// receiver tables: the one-step pass's (per CTA) and the two-step pass's (per tile, <= 4 per receiver)
+// receiver tables: the one-step pass's (per CTA) and the K-step pass's (per tile, <= 4 per receiver)
 static size_t adjoint_bucket_bytes(const tsu_grid* g, int dtype, int32_t nrec) {
   const size_t nr = nrec > 0 ? (size_t)nrec : 0;
   const size_t one = ((size_t)(adjoint_ctas(g, dtype) + 1) + 2 * nr) * sizeof(int);
-  const int rows2 = tsu::adjoint_wtb2_rows(g->ny, g->ld);
-  const size_t two = ((size_t)tsu::adjoint_wtb2_tiles(g->ny, g->ld, rows2) + 1) * sizeof(int) + 16 + 4 * nr * 16;
-  return (one + 15) / 16 * 16 + two;
+  const int rowsk = tsu::adjoint_wtb_rows(kAdjointDepth, g->ny, g->ld);
+  const size_t blk = ((size_t)tsu::adjoint_wtb_tiles(g->ny, g->ld, rowsk) + 1) * sizeof(int) + 16 + 4 * nr * 16;
+  return (one + 15) / 16 * 16 + blk;
 }
 
 static size_t adjoint_ws_bytes(const tsu_grid* g, int dtype, int form, int64_t every, int32_t nrec) {
@@ -435,13 +437,13 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   int* b_off = (int*)bk;
   int* b_ord = b_off + (adjoint_ctas(g, dtype) + 1);
   int* b_cta = b_ord + (nrec > 0 ? nrec : 0);
-  // two-step pass (FP32): tile table of receivers
-  const bool pairs = dtype == TSU_F32;
-  const int rows2 = tsu::adjoint_wtb2_rows(g->ny, g->ld);
+  // K-step pass (FP32): tile table of receivers
+  const bool blocked = dtype == TSU_F32;
+  const int rowsk = tsu::adjoint_wtb_rows(kAdjointDepth, g->ny, g->ld);
   char* bk2 = bk + ((((size_t)(adjoint_ctas(g, dtype) + 1) + 2 * (size_t)(nrec > 0 ? nrec : 0)) * sizeof(int) + 15) /
                     16 * 16);
   int* t_off = (int*)bk2;
-  int4* t_ent = (int4*)(bk2 + (((size_t)tsu::adjoint_wtb2_tiles(g->ny, g->ld, rows2) + 1) * sizeof(int) + 15) / 16 * 16);
+  int4* t_ent = (int4*)(bk2 + (((size_t)tsu::adjoint_wtb_tiles(g->ny, g->ld, rowsk) + 1) * sizeof(int) + 15) / 16 * 16);
   auto segp = [&](int b, int64_t k) { return (void*)(segbuf[b] + (size_t)k * fb); };
   const int recompute_rows = tsu::wtb_seg_rows(g->ny, g->ld);
   auto extra = [&](int b, int q = 0) { return (void*)(segbuf[b] + (size_t)(ckpt_every + 1 + q) * fb); };
@@ -449,7 +451,8 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   if (!aux) return fail(TSU_ECUDA, "tsu_adjoint: could not create the recompute stream");
   cudaError_t e = cudaMemsetAsync(ws, 0, need - 256, s);
   if (e == cudaSuccess && nrec > 0) e = tsu::launch_rec_bucket(sg, dtype, rec_idx, nrec, b_off, b_ord, b_cta, s);
-  if (e == cudaSuccess && nrec > 0 && pairs) e = tsu::launch_rec_tiles(sg, rec_idx, nrec, rows2, t_off, t_ent, s);
+  if (e == cudaSuccess && nrec > 0 && blocked)
+    e = tsu::launch_rec_tiles(sg, kAdjointDepth, rec_idx, nrec, rowsk, t_off, t_ent, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hx, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hy, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint reset");
@@ -464,17 +467,20 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     i2 = t;
     return r;
   };
-  // two steps back (n and n-1): lam^n and lam^{n-1} into the two free multiplier fields
-  auto two_steps_back = [&](int64_t n, const void* un, const void* um) -> cudaError_t {
-    int o1 = -1, o2 = -1;
+  // kAdjointDepth steps back (n .. n-K+1) in one pass, u[f] = u^{n-f}: lam^{n-K+2} and lam^{n-K+1}
+  // into the two free multiplier fields
+  auto steps_back = [&](int64_t n, const void* const* u) -> cudaError_t {
+    int oa = -1, ob = -1;
     for (int k = 0; k < 4; ++k)
-      if (k != i1 && k != i2) (o1 < 0 ? o1 : o2) = k;
-    const void* g1 = nrec > 0 ? (const char*)dtraces + (size_t)(n - 1) * nrec * es : nullptr;
-    const void* g2 = nrec > 0 ? (const char*)dtraces + (size_t)(n - 2) * nrec * es : nullptr;
-    cudaError_t r = tsu::launch_adjoint_wtb2(sg, rows2, m->hx, m->hy, lam4[i1], lam4[i2], un, um, lam4[o1], lam4[o2],
-                                             accx, accy, nrec > 0 ? t_off : nullptr, t_ent, g1, g2, s);
-    i1 = o2;  // lam^{n-1}
-    i2 = o1;  // lam^n
+      if (k != i1 && k != i2) (oa < 0 ? oa : ob) = k;
+    const void* gv[kAdjointDepth];
+    for (int f = 0; f < kAdjointDepth; ++f)
+      gv[f] = nrec > 0 ? (const char*)dtraces + (size_t)(n - 1 - f) * nrec * es : nullptr;
+    cudaError_t r = tsu::launch_adjoint_wtb(sg, kAdjointDepth, rowsk, m->hx, m->hy, lam4[i1], lam4[i2], u, lam4[oa],
+                                            lam4[ob], accx, accy, nrec > 0 ? t_off : nullptr, t_ent,
+                                            nrec > 0 ? gv : nullptr, s);
+    i1 = ob;  // lam^{n-K+1}
+    i2 = oa;  // lam^{n-K+2}
     return r;
   };
   if (C == 0) {  // nsteps == 1: lam^1 = g^1 (the gradient term of n = 1 vanishes with lam^2 = 0)
@@ -575,9 +581,11 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint stream order");
     const int64_t nlo = (c == 0) ? 1 : mc + 1;
     for (int64_t n = mend; n >= nlo;) {
-      if (pairs && n - 1 >= nlo) {
-        e = two_steps_back(n, segp(b, n - mc), segp(b, n - 1 - mc));
-        n -= 2;
+      if (blocked && n - (kAdjointDepth - 1) >= nlo) {
+        const void* u[kAdjointDepth];
+        for (int f = 0; f < kAdjointDepth; ++f) u[f] = segp(b, n - f - mc);
+        e = steps_back(n, u);
+        n -= kAdjointDepth;
       } else {
         e = step_back(n, segp(b, n - mc));
         n -= 1;

@@ -129,17 +129,19 @@ cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, con
                                 void* u_out = nullptr, void* v_out = nullptr);
 cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,
                           int32_t nrec, cudaStream_t s);
-// Two adjoint steps per pass, FP32 (k_adjoint_wtb.cu): lam^n into out1 and lam^{n-1} into out2
-// from lam^{n+1}, lam^{n+2}, u^n, u^{n-1}; receivers through a per-tile table (off[ntiles+1],
-// int4 (row, col, receiver, 0) entries, <= 4 per receiver) built by launch_rec_tiles.
-int adjoint_wtb2_rows(int64_t ny, int64_t ld);
-int64_t adjoint_wtb2_tiles(int64_t ny, int64_t ld, int rows);
-cudaError_t launch_rec_tiles(const StencilGeom& g, const int64_t* idx, int32_t nrec, int rows, int* off, int4* ent,
-                             cudaStream_t s);
-cudaError_t launch_adjoint_wtb2(const StencilGeom& g, int rows, const void* hx, const void* hy, const void* lam1,
-                                const void* lam2, const void* un, const void* um, void* out1, void* out2, void* gx,
-                                void* gy, const int* rec_off, const int4* rec, const void* g1, const void* g2,
-                                cudaStream_t s);
+// K = 2 or 4 adjoint steps per pass, FP32 (k_adjoint_wtb.cu): from lam^{n+1}, lam^{n+2} and
+// u[f] = u^{n-f} (f < K), the levels lam^n .. lam^{n-K+1}; stores lam^{n-K+2} into out_a and
+// lam^{n-K+1} into out_b and adds the K steps' face gradients into gx, gy.  Receivers through a
+// per-tile table (off[ntiles+1], int4 (row, col, receiver, 0) entries, <= 4 per receiver) built by
+// launch_rec_tiles for the same K and rows; gv[f] = g^{n-f} at the receivers.
+int adjoint_wtb_rows(int k, int64_t ny, int64_t ld);
+int64_t adjoint_wtb_tiles(int64_t ny, int64_t ld, int rows);
+cudaError_t launch_rec_tiles(const StencilGeom& g, int k, const int64_t* idx, int32_t nrec, int rows, int* off,
+                             int4* ent, cudaStream_t s);
+cudaError_t launch_adjoint_wtb(const StencilGeom& g, int k, int rows, const void* hx, const void* hy,
+                               const void* lam1, const void* lam2, const void* const* u, void* out_a, void* out_b,
+                               void* gx, void* gy, const int* rec_off, const int4* rec, const void* const* gv,
+                               cudaStream_t s);
 cudaError_t launch_flush(const StencilGeom& g, void* g32x, void* g32y, double* gx, double* gy, cudaStream_t s);
 
 }  // namespace tsu

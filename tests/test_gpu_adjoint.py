@@ -85,16 +85,17 @@ def test_fp64_adjoint_independent_of_checkpoint_period():
 @pytest.mark.parametrize("form", [tsu.TSU_FORM_STANDARD, tsu.TSU_FORM_INCREMENT])
 @pytest.mark.parametrize("every,S", [(8, 41), (5, 23), (64, 41), (3, 2)])
 def test_fp32_adjoint_matches_oracle_across_tiles(form, every, S):
-    """FP32 sweeps run two adjoint steps per pass on 120-column by 16-row tiles, with single passes
-    for odd segment lengths.  Against the FP64 oracle on a grid of 3 strips and a ragged last
-    chunk, with receivers on and next to strip and chunk edges (where halo copies of a multiplier
-    need the receiver value too), duplicates and a boundary receiver."""
+    """FP32 sweeps run four adjoint steps per pass on 120-column by 16-row tiles, with single
+    passes for the rest of a segment.  Against the FP64 oracle on a grid of 3 strips and a ragged
+    last chunk, with receivers on and up to three rows and four columns beyond strip and chunk
+    edges (where halo copies of a multiplier need the receiver value too), duplicates and a
+    boundary receiver."""
     nx, ny = 301, 150
     rng = np.random.default_rng(23)
     u0 = inputs.random_field(nx, ny, None, rng)
     u1 = inputs.random_field(nx, ny, None, rng)
     cols = [1, 3, 4, 116, 119, 120, 123, 124, 236, 239, 240, 243, 299]
-    rows = [1, 2, 15, 16, 17, 18, 32, 33, 144, 145, 147, 148]
+    rows = [1, 2, 3, 13, 14, 15, 16, 17, 18, 19, 20, 32, 33, 144, 145, 147, 148]
     rec = np.array([[cols[k % len(cols)], rows[k % len(rows)]] for k in range(3 * len(cols))]
                    + [[120, 17], [0, 40], [150, 149]])
     dtr = rng.standard_normal((S, len(rec)))
