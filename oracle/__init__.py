@@ -83,6 +83,8 @@ def _load():
         lib.orc_friedrichs_c2.restype = C.c_double
         lib.orc_make_depth.argtypes = [g, C.POINTER(_Depth), d, d, d]
         lib.orc_make_depth.restype = C.c_int
+        lib.orc_depth_deps.argtypes = [g, C.POINTER(_Depth), d, d]
+        lib.orc_depth_deps.restype = C.c_int
         lib.orc_apply_B.argtypes = [g, C.c_double, C.c_double, d, d, d, d]
         lib.orc_init.argtypes = [g, C.c_double, d, d, d, d, d, d]
         lib.orc_step.argtypes = [g, C.c_double, d, d, d, d]
@@ -145,6 +147,21 @@ def make_depth(g: _Grid, depth: dict):
     if rc != 0:
         raise ValueError("oracle make_depth: bad arguments")
     return hx, hy, ext
+
+
+def depth_deps(g: _Grid, depth: dict):
+    """d h_eps / d eps at the faces (same layout as make_depth's hx, hy): the derivative of the
+    regularised depth with respect to the regularisation width (Sec. 2.1).  Returns (dhx, dhy)."""
+    lib = _load()
+    sings = depth.get("sings", [])
+    arr = (_Sing * max(1, len(sings)))(*[_Sing(*s) for s in sings])
+    d = _Depth(float(depth["background"]), float(depth["eps"]), int(depth.get("mollifier", GAUSS)),
+               len(sings), C.cast(arr, C.POINTER(_Sing)))
+    dhx = np.zeros((g.ny, g.ld))
+    dhy = np.zeros((g.ny, g.ld))
+    if lib.orc_depth_deps(C.byref(g), C.byref(d), _p(dhx), _p(dhy)) != 0:
+        raise ValueError("oracle depth_deps: bad arguments")
+    return dhx, dhy
 
 
 def coefs(g: _Grid, tau: float) -> tuple[float, float]:

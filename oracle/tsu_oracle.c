@@ -14,6 +14,7 @@
  *   depth    h_eps = background + sum_s amp_s * phi_eps(dist_s)^p_s,
  *            phi_eps a unit-mass mollifier of width eps        -- Sec. 2.1 (h * psi_eps), Sec. 3.1
  *   energy   d/dt (||u_t||^2 + sum_j ||h_j^1/2 d_j u||^2) = 0   -- Theorem 2.1, identity (CL-01)
+ *   d h_eps / d eps, the depth's derivative in the regularisation width  -- Sec. 2.1
  *
  * The scheme is the explicit leapfrog written out exactly as defined:
  *   fx(u)_ij = hx_ij (u_i+1,j - u_ij) - hx_i-1,j (u_ij - u_i-1,j)
@@ -185,6 +186,101 @@ int orc_make_depth(const orc_grid* g, const orc_depth* d, double* hx, double* hy
   ext[1] = mxx;
   ext[2] = mny;
   ext[3] = mxy;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* d h_eps / d eps at the faces: how the regularised depth moves with the    */
+/* regularisation width (Sec. 2.1, h_eps = h * psi_eps).  Differentiating    */
+/* psi_eps(s) = eps^-d psi(s/eps) in eps (t = s/eps):                        */
+/*   d/deps [eps^-d psi(t)] = -eps^-(d+1) [d psi(t) + t psi'(t)],            */
+/* with psi the Gaussian exp(-t^2)/sqrt(pi)^d or c_d bump(t),                */
+/*   Gaussian: t psi' = -2 t^2 psi;   bump: t psi' = -2 t^2/(t^2-1)^2 psi,   */
+/* and for the mollified step S = int_{-inf}^{s/eps} psi: dS/deps = -t/eps   */
+/* psi(t).  A power p > 1 brings the factor p phi^{p-1}.                     */
+/* ------------------------------------------------------------------------- */
+static double dphi_deps(int moll, double c, int d, double eps, double s) {
+  const double t = s / eps;
+  double psi, tdpsi;
+  if (moll == ORC_GAUSS) {
+    psi = exp(-t * t) / (d == 1 ? sqrt(M_PI) : M_PI);
+    tdpsi = -2.0 * t * t * psi;
+  } else {
+    if (!(fabs(t) < 1.0)) return 0.0;
+    psi = c * bump(t);
+    const double w = t * t - 1.0;
+    tdpsi = -2.0 * t * t / (w * w) * psi;
+  }
+  return -(d * psi + tdpsi) / pow(eps, d + 1);
+}
+
+static double dstep_deps(int moll, double c1, double eps, double s) {
+  const double t = s / eps;
+  double psi;
+  if (moll == ORC_GAUSS)
+    psi = exp(-t * t) / sqrt(M_PI);
+  else
+    psi = (fabs(t) < 1.0) ? c1 * bump(t) : 0.0;
+  return -t / eps * psi;
+}
+
+static double depth_deps_at(const orc_depth* d, double c1, double c2, double x, double y) {
+  double acc = 0.0;
+  for (int k = 0; k < d->nsing; ++k) {
+    const orc_sing* s = &d->sing[k];
+    double v, dv;
+    switch (s->kind) {
+      case ORC_LINE_X:
+        v = phi1(d->mollifier, c1, d->eps, x - s->cx);
+        dv = dphi_deps(d->mollifier, c1, 1, d->eps, x - s->cx);
+        break;
+      case ORC_LINE_Y:
+        v = phi1(d->mollifier, c1, d->eps, y - s->cy);
+        dv = dphi_deps(d->mollifier, c1, 1, d->eps, y - s->cy);
+        break;
+      case ORC_POINT: {
+        double r = sqrt((x - s->cx) * (x - s->cx) + (y - s->cy) * (y - s->cy));
+        v = phi2(d->mollifier, c2, d->eps, r);
+        dv = dphi_deps(d->mollifier, c2, 2, d->eps, r);
+        break;
+      }
+      case ORC_STEP_X:
+        v = step1(d->mollifier, c1, d->eps, s->cx - x);
+        dv = dstep_deps(d->mollifier, c1, d->eps, s->cx - x);
+        break;
+      case ORC_STEP_Y:
+        v = step1(d->mollifier, c1, d->eps, s->cy - y);
+        dv = dstep_deps(d->mollifier, c1, d->eps, s->cy - y);
+        break;
+      default: return NAN;
+    }
+    double pw = 1.0; /* v^(power-1) */
+    for (int q = 1; q < s->power; ++q) pw = pw * v;
+    acc = acc + s->amp * (s->power * pw) * dv;
+  }
+  return acc;
+}
+
+/* dhx[j][i] = d h_eps / d eps at the x-face (x_i + dx/2, y_j), i <= nx-2, and dhy likewise;
+ * every other entry 0.  Returns 0, or 1 on bad arguments. */
+int orc_depth_deps(const orc_grid* g, const orc_depth* d, double* dhx, double* dhy) {
+  if (g->nx < 3 || g->ny < 3 || g->ld < g->nx || !(d->eps > 0.0)) return 1;
+  if (d->nsing > 0 && !d->sing) return 1;
+  for (int k = 0; k < d->nsing; ++k) {
+    if (d->sing[k].kind < 0 || d->sing[k].kind > 4 || d->sing[k].power < 1) return 1;
+  }
+  const double c1 = orc_friedrichs_c1(), c2 = orc_friedrichs_c2();
+  const int64_t n = (int64_t)g->ny * g->ld;
+  memset(dhx, 0, sizeof(double) * n);
+  memset(dhy, 0, sizeof(double) * n);
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < g->ny; ++j) {
+    for (int i = 0; i < g->nx; ++i) {
+      double x = i * g->dx, y = j * g->dy;
+      if (i <= g->nx - 2) dhx[IDX(g, i, j)] = depth_deps_at(d, c1, c2, (i + 0.5) * g->dx, y);
+      if (j <= g->ny - 2) dhy[IDX(g, i, j)] = depth_deps_at(d, c1, c2, x, (j + 0.5) * g->dy);
+    }
+  }
   return 0;
 }
 

@@ -407,3 +407,50 @@ def test_eps_family_is_cauchy():
     sols = [oracle.forward(g, tau, hx, hy, u0, None, S, want_energy=False)["u"] for hx, hy, _ in exts]
     d = [np.linalg.norm(sols[k] - sols[k + 1]) * g.dx for k in range(3)]
     assert d[0] > d[1] > d[2], d
+
+
+EPS_DEPTHS = {
+    "line_gauss": dict(background=1.0, eps=0.03, mollifier=0, sings=[(0, 1, 1.0, 0.5, 0.5)]),
+    "line_y_friedrichs": dict(background=1.0, eps=0.05, mollifier=1, sings=[(1, 1, 0.7, 0.5, 0.43)]),
+    "point_gauss": dict(background=0.5, eps=0.04, mollifier=0, sings=[(2, 1, 0.01, 0.47, 0.52)]),
+    "point_friedrichs": dict(background=0.5, eps=0.06, mollifier=1, sings=[(2, 1, 0.01, 0.5, 0.5)]),
+    "delta2": dict(background=1.0, eps=0.05, mollifier=0, sings=[(1, 2, 0.002, 0.5, 0.6)]),
+    "step_gauss": dict(background=10.0, eps=0.02, mollifier=0, sings=[(3, 1, 90.0, 0.75, 0.5)]),
+    "step_friedrichs_y": dict(background=2.0, eps=0.04, mollifier=1, sings=[(4, 1, 3.0, 0.5, 0.33)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EPS_DEPTHS))
+def test_depth_eps_derivative_matches_central_differences(name):
+    """d h_eps / d eps (the analytic derivative of Sec. 2.1's regularisation in its width) against
+    central differences of the face depth in eps, for every singularity kind, both mollifiers and
+    the delta^2 power."""
+    depth = EPS_DEPTHS[name]
+    g = oracle.grid(97, 89)
+    dhx, dhy = oracle.depth_deps(g, depth)
+    eps, st = depth["eps"], 1e-5 * depth["eps"]
+    hp = oracle.make_depth(g, dict(depth, eps=eps + st))
+    hm = oracle.make_depth(g, dict(depth, eps=eps - st))
+    fdx, fdy = (hp[0] - hm[0]) / (2 * st), (hp[1] - hm[1]) / (2 * st)
+    assert np.abs(dhx).max() + np.abs(dhy).max() > 0
+    assert relerr(dhx, fdx) <= 1e-7, relerr(dhx, fdx)
+    assert relerr(dhy, fdy) <= 1e-7, relerr(dhy, fdy)
+
+
+@pytest.mark.parametrize("moll", [0, 1])
+def test_depth_eps_derivative_keeps_the_mass(moll):
+    """A unit-mass mollifier keeps unit mass at every width, so d/deps of its integral is 0: the
+    face sums of d h / d eps vanish for a line (1D sum across it) and a point (2D sum).  The
+    bump's derivative is steep near the edge of its support, so it gets a wider eps (the sums
+    converge spectrally: 1.2e-3, 4e-6, 8e-9, 2e-11 at eps = 0.02, 0.05, 0.1, 0.15 on this grid)."""
+    n = 801
+    g = oracle.grid(n, n)
+    eps = 0.02 if moll == 0 else 0.15
+    line = dict(background=1.0, eps=eps, mollifier=moll, sings=[(0, 1, 1.0, 0.5, 0.5)])
+    dhx, _ = oracle.depth_deps(g, line)
+    row = dhx[n // 2, : n - 1]
+    assert abs(row.sum() * g.dx) <= 1e-9 * np.abs(row).sum() * g.dx
+    point = dict(background=1.0, eps=1.5 * eps, mollifier=moll, sings=[(2, 1, 1.0, 0.5, 0.5)])
+    _, dhy = oracle.depth_deps(g, point)
+    tot = dhy[: n - 1, :n]
+    assert abs(tot.sum()) <= 1e-8 * np.abs(tot).sum()
