@@ -158,6 +158,29 @@ const char* tsu_last_error(void);
 int tsu_make_depth(const tsu_grid* g, const tsu_depth* d, int dtype, void* hx, void* hy,
                    double* ext_dev, double* ext_host, void* stream);
 
+/* d h_eps / d eps: the derivative of the regularised depth in its width (Sec. 2.1, h_eps = h *
+ * psi_eps with psi_eps(s) = eps^-d psi(s/eps), so d/deps psi_eps = -eps^-(d+1) (d psi + t psi'(t)),
+ * t = s/eps; for a mollified step S = int^{s/eps} psi, dS/deps = -(t/eps) psi(t)), sampled at
+ * the faces exactly like tsu_make_depth's hx, hy (same layout, element type dtype, entries
+ * outside the faces 0).  Evaluated in FP64.  Asynchronous.  Errors: TSU_EINVAL, TSU_ECUDA. */
+int tsu_depth_eps_derivative(const tsu_grid* g, const tsu_depth* d, int dtype, void* dhx, void* dhy, void* stream);
+
+/* Bytes of device workspace (16-byte aligned) of the reductions below. */
+size_t tsu_reduce_workspace(void);
+
+/* dJ/deps = sum over faces of g_hx dhx/deps + g_hy dhy/deps: chains face gradients (device double
+ * [ny][ld], e.g. tsu_adjoint's g_hx, g_hy) through the regularised depth, without storing the
+ * derivative fields.  Deterministic FP64 sum (fixed grid, fixed order) into out_dev[0] (device
+ * double).  Asynchronous.  Errors: TSU_EINVAL, TSU_ENOMEM (workspace), TSU_ECUDA. */
+int tsu_depth_eps_gradient(const tsu_grid* g, const tsu_depth* d, const double* g_hx, const double* g_hy,
+                           double* out_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* How far apart two fields are (the eps-family comparisons of Sec. 3.2): out_dev[0] = sum (a - b)^2,
+ * out_dev[1] = sum b^2 over the nodes i < nx of two device fields of element type dtype.
+ * Deterministic FP64 sums.  Asynchronous.  Errors: TSU_EINVAL, TSU_ENOMEM, TSU_ECUDA. */
+int tsu_diff_norms(const tsu_grid* g, int dtype, const void* a, const void* b, double* out_dev, void* ws,
+                   size_t ws_bytes, void* stream);
+
 /* Largest tau allowed by the leapfrog bound tau^2 (hx_max/dx^2 + hy_max/dy^2) <= 1, times cfl
  * (0 < cfl <= 1).  Host only.  Returns 0 on bad input. */
 double tsu_tau_for(const tsu_grid* g, double hx_max, double hy_max, double cfl);

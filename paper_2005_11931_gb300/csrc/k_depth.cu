@@ -92,6 +92,76 @@ __device__ double depth_at(const DepthParams& p, double x, double y) {
   return h;
 }
 
+// d h_eps / d eps (Sec. 2.1, the regularised depth's derivative in its width).  With
+// psi_eps(s) = eps^-d psi(s/eps) and t = s/eps:  d/deps psi_eps = -eps^-(d+1) (d psi + t psi'(t)),
+// where t psi' = -2 t^2 psi (Gaussian) or -2 t^2/(t^2-1)^2 psi (bump); for the mollified step
+// S(s) = int^{s/eps} psi:  dS/deps = -(t/eps) psi(t); a power p > 1 brings p phi^{p-1}.
+__device__ __forceinline__ double dphi_deps(const DepthParams& p, int d, double c, double s2) {
+  const double e = p.eps;
+  if (p.mollifier == TSU_GAUSS && s2 > kFar * (e * e)) return 0.0;
+  if (p.mollifier != TSU_GAUSS && s2 >= e * e * 1.0000001) return 0.0;
+  const double t2 = s2 / (e * e);
+  double psi, tdpsi;
+  if (p.mollifier == TSU_GAUSS) {
+    psi = exp(-t2) / (d == 1 ? sqrt(kPi) : kPi);
+    tdpsi = -2.0 * t2 * psi;
+  } else {
+    psi = c * exp(1.0 / (t2 - 1.0));
+    const double w = t2 - 1.0;
+    tdpsi = -2.0 * t2 / (w * w) * psi;
+  }
+  const double ed = d == 1 ? e * e : e * e * e;
+  return -(d * psi + tdpsi) / ed;
+}
+
+__device__ __forceinline__ double dstep_deps(const DepthParams& p, double s) {
+  const double e = p.eps, t = s / e;
+  double psi;
+  if (p.mollifier == TSU_GAUSS) {
+    if (t * t > kFar) return 0.0;
+    psi = exp(-t * t) / sqrt(kPi);
+  } else {
+    psi = fabs(t) < 1.0 ? p.c1 * exp(1.0 / (t * t - 1.0)) : 0.0;
+  }
+  return -t / e * psi;
+}
+
+__device__ double depth_deps_at(const DepthParams& p, double x, double y) {
+  double acc = 0.0;
+  for (int k = 0; k < p.nsing; ++k) {
+    const tsu_sing& s = p.sing[k];
+    double v, dv;
+    switch (s.kind) {
+      case TSU_LINE_X:
+        v = phi1(p, x - s.cx);
+        dv = dphi_deps(p, 1, p.c1, (x - s.cx) * (x - s.cx));
+        break;
+      case TSU_LINE_Y:
+        v = phi1(p, y - s.cy);
+        dv = dphi_deps(p, 1, p.c1, (y - s.cy) * (y - s.cy));
+        break;
+      case TSU_POINT: {
+        const double dx = x - s.cx, dy = y - s.cy;
+        v = phi2(p, dx, dy);
+        dv = dphi_deps(p, 2, p.c2, dx * dx + dy * dy);
+        break;
+      }
+      case TSU_STEP_X:
+        v = step1(p, s.cx - x);
+        dv = dstep_deps(p, s.cx - x);
+        break;
+      default:
+        v = step1(p, s.cy - y);
+        dv = dstep_deps(p, s.cy - y);
+        break;
+    }
+    double pw = 1.0;  // v^(power-1)
+    for (int q = 1; q < s.power; ++q) pw *= v;
+    acc += s.amp * (s.power * pw) * dv;
+  }
+  return acc;
+}
+
 // Order-preserving map of doubles to unsigned 64-bit integers (for atomicMin/Max).
 __device__ __forceinline__ unsigned long long ord_enc(double d) {
   unsigned long long b = (unsigned long long)__double_as_longlong(d);
@@ -171,7 +241,63 @@ __global__ void __launch_bounds__(256) k_make_depth(int32_t nx, int32_t ny, int6
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_depth_deps(int32_t nx, int32_t ny, int64_t ld, double dx, double dy,
+                                                    const DepthParams p, T* __restrict__ dhx, T* __restrict__ dhy) {
+  const int64_t total = (int64_t)ny * ld;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = k / ld, i = k - j * ld;
+    dhx[k] = (i <= nx - 2) ? T(depth_deps_at(p, (i + 0.5) * dx, j * dy)) : T(0);
+    dhy[k] = (i < nx && j <= ny - 2) ? T(depth_deps_at(p, i * dx, (j + 0.5) * dy)) : T(0);
+  }
+}
+
+// Per-block FP64 partial sums of g_hx dhx/deps + g_hy dhy/deps (fixed grid, fixed order).
+__global__ void __launch_bounds__(256) k_eps_gradient(int32_t nx, int32_t ny, int64_t ld, double dx, double dy,
+                                                      const DepthParams p, const double* __restrict__ gx,
+                                                      const double* __restrict__ gy, double* partials) {
+  const int64_t total = (int64_t)ny * ld;
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = k / ld, i = k - j * ld;
+    if (i <= nx - 2 && gx[k] != 0.0) acc += gx[k] * depth_deps_at(p, (i + 0.5) * dx, j * dy);
+    if (i < nx && j <= ny - 2 && gy[k] != 0.0) acc += gy[k] * depth_deps_at(p, i * dx, (j + 0.5) * dy);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q];
+    partials[blockIdx.x] = t;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_depth_deps(const tsu_grid& g, const DepthParams& p, int dtype, void* dhx, void* dhy,
+                              cudaStream_t s) {
+  const int64_t total = (int64_t)g.ny * g.ld;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (dtype == TSU_F32)
+    k_depth_deps<float><<<(unsigned)blocks, 256, 0, s>>>(g.nx, g.ny, g.ld, g.dx, g.dy, p, (float*)dhx, (float*)dhy);
+  else
+    k_depth_deps<double><<<(unsigned)blocks, 256, 0, s>>>(g.nx, g.ny, g.ld, g.dx, g.dy, p, (double*)dhx,
+                                                         (double*)dhy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eps_gradient(const tsu_grid& g, const DepthParams& p, const double* gx, const double* gy,
+                                double* partials, double* out, cudaStream_t s) {
+  k_eps_gradient<<<kReduceBlocks, 256, 0, s>>>(g.nx, g.ny, g.ld, g.dx, g.dy, p, gx, gy, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_partials(partials, kReduceBlocks, 1, out, s);
+}
 
 cudaError_t launch_make_depth(const tsu_grid& g, const DepthParams& p, int dtype, void* hx, void* hy,
                               double* ext_dev, cudaStream_t s) {

@@ -117,14 +117,8 @@ double tsu_tau_for(const tsu_grid* g, double hx_max, double hy_max, double cfl) 
   return cfl / sqrt(s);
 }
 
-int tsu_make_depth(const tsu_grid* g, const tsu_depth* d, int dtype, void* hx, void* hy, double* ext_dev,
-                   double* ext_host, void* stream) {
-  g_err[0] = 0;
-  TRY(check_grid(g));
-  TRY(check_dtype(dtype));
-  TRY(check_field(hx, "hx"));
-  TRY(check_field(hy, "hy"));
-  if (!ext_dev || ((uintptr_t)ext_dev & 7u)) return fail(TSU_EINVAL, "ext_dev must be a device double[4]");
+// validated depth descriptor -> device parameters
+static int depth_params(const tsu_depth* d, tsu::DepthParams* p_out) {
   if (!d) return fail(TSU_EINVAL, "depth is NULL");
   if (!(d->eps > 0.0) || !isfinite(d->eps)) return fail(TSU_EINVAL, "eps must be positive");
   if (d->nsing < 0 || d->nsing > tsu::kMaxSing) return fail(TSU_EINVAL, "nsing must be in [0, %d]", tsu::kMaxSing);
@@ -144,6 +138,20 @@ int tsu_make_depth(const tsu_grid* g, const tsu_depth* d, int dtype, void* hx, v
     if (s.power < 1 || s.power > 8) return fail(TSU_EINVAL, "sing[%d]: power must be in [1, 8]", k);
     p.sing[k] = s;
   }
+  *p_out = p;
+  return TSU_OK;
+}
+
+int tsu_make_depth(const tsu_grid* g, const tsu_depth* d, int dtype, void* hx, void* hy, double* ext_dev,
+                   double* ext_host, void* stream) {
+  g_err[0] = 0;
+  TRY(check_grid(g));
+  TRY(check_dtype(dtype));
+  TRY(check_field(hx, "hx"));
+  TRY(check_field(hy, "hy"));
+  if (!ext_dev || ((uintptr_t)ext_dev & 7u)) return fail(TSU_EINVAL, "ext_dev must be a device double[4]");
+  tsu::DepthParams p;
+  TRY(depth_params(d, &p));
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = tsu::launch_make_depth(*g, p, dtype, hx, hy, ext_dev, s);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_make_depth launch");
@@ -154,6 +162,57 @@ int tsu_make_depth(const tsu_grid* g, const tsu_depth* d, int dtype, void* hx, v
     if (!(ext_host[0] > 0.0) || !(ext_host[2] > 0.0))
       return fail(TSU_ENONPOS, "face depth minimum <= 0 (min hx = %.6g, min hy = %.6g)", ext_host[0], ext_host[2]);
   }
+  return TSU_OK;
+}
+
+int tsu_depth_eps_derivative(const tsu_grid* g, const tsu_depth* d, int dtype, void* dhx, void* dhy, void* stream) {
+  g_err[0] = 0;
+  TRY(check_grid(g));
+  TRY(check_dtype(dtype));
+  TRY(check_field(dhx, "dhx"));
+  TRY(check_field(dhy, "dhy"));
+  tsu::DepthParams p;
+  TRY(depth_params(d, &p));
+  cudaError_t e = tsu::launch_depth_deps(*g, p, dtype, dhx, dhy, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_depth_eps_derivative launch");
+  return TSU_OK;
+}
+
+size_t tsu_reduce_workspace(void) { return 256 + 2 * (size_t)tsu::kReduceBlocks * sizeof(double); }
+
+static int check_reduce(double* out_dev, void* ws, size_t ws_bytes) {
+  if (!out_dev || ((uintptr_t)out_dev & 7u)) return fail(TSU_EINVAL, "out_dev must be a device double array");
+  if (!ws || ws_bytes < tsu_reduce_workspace())
+    return fail(TSU_ENOMEM, "reduction workspace %zu B < %zu B", ws_bytes, tsu_reduce_workspace());
+  if ((uintptr_t)ws & 15u) return fail(TSU_EINVAL, "workspace must be 16-byte aligned");
+  return TSU_OK;
+}
+
+int tsu_depth_eps_gradient(const tsu_grid* g, const tsu_depth* d, const double* g_hx, const double* g_hy,
+                           double* out_dev, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  TRY(check_grid(g));
+  TRY(check_field(g_hx, "g_hx"));
+  TRY(check_field(g_hy, "g_hy"));
+  TRY(check_reduce(out_dev, ws, ws_bytes));
+  tsu::DepthParams p;
+  TRY(depth_params(d, &p));
+  cudaError_t e = tsu::launch_eps_gradient(*g, p, g_hx, g_hy, (double*)((char*)ws + 256), out_dev,
+                                           (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_depth_eps_gradient launch");
+  return TSU_OK;
+}
+
+int tsu_diff_norms(const tsu_grid* g, int dtype, const void* a, const void* b, double* out_dev, void* ws,
+                   size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  TRY(check_grid(g));
+  TRY(check_dtype(dtype));
+  TRY(check_field(a, "a"));
+  TRY(check_field(b, "b"));
+  TRY(check_reduce(out_dev, ws, ws_bytes));
+  cudaError_t e = tsu::launch_diff_norms(*g, dtype, a, b, (double*)((char*)ws + 256), out_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_diff_norms launch");
   return TSU_OK;
 }
 

@@ -52,6 +52,18 @@ double friedrichs_c2();
 cudaError_t launch_make_depth(const tsu_grid& g, const DepthParams& p, int dtype, void* hx, void* hy,
                               double* ext_dev, cudaStream_t s);
 
+// Deterministic reductions (k_reduce.cu): kReduceBlocks per-block FP64 partials, then one block.
+constexpr int kReduceBlocks = 152 * 4;
+cudaError_t launch_sum_partials(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s);
+// out[0] = sum (a - b)^2, out[1] = sum b^2 over nodes i < nx; partials: 2 kReduceBlocks doubles
+cudaError_t launch_diff_norms(const tsu_grid& g, int dtype, const void* a, const void* b, double* partials,
+                              double* out, cudaStream_t s);
+// d h_eps / d eps at the faces (k_depth.cu), and its contraction with face gradients
+cudaError_t launch_depth_deps(const tsu_grid& g, const DepthParams& p, int dtype, void* dhx, void* dhy,
+                              cudaStream_t s);
+cudaError_t launch_eps_gradient(const tsu_grid& g, const DepthParams& p, const double* gx, const double* gy,
+                                double* partials, double* out, cudaStream_t s);
+
 // Optional per-step side outputs of a stencil pass.
 struct PassOut {
   double* energy;           // one double, or nullptr

@@ -98,6 +98,10 @@ def load():
         "tsu_last_error": ([], C.c_char_p),
         "tsu_make_depth": ([C.POINTER(Grid), C.POINTER(Depth), C.c_int, vp, vp, vp, C.POINTER(C.c_double), vp], C.c_int),
         "tsu_tau_for": ([C.POINTER(Grid), dbl, dbl, dbl], dbl),
+        "tsu_depth_eps_derivative": ([C.POINTER(Grid), C.POINTER(Depth), C.c_int, vp, vp, vp], C.c_int),
+        "tsu_reduce_workspace": ([], C.c_size_t),
+        "tsu_depth_eps_gradient": ([C.POINTER(Grid), C.POINTER(Depth), vp, vp, vp, vp, C.c_size_t, vp], C.c_int),
+        "tsu_diff_norms": ([C.POINTER(Grid), C.c_int, vp, vp, vp, vp, C.c_size_t, vp], C.c_int),
         "tsu_init": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), vp, vp, C.POINTER(State), vp], C.c_int),
         "tsu_step_workspace": ([C.POINTER(Grid), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
         "tsu_step_n": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), i64,
@@ -129,7 +133,7 @@ def declared_symbols() -> list[str]:
     import re
     hdr = os.path.join(os.path.dirname(_HERE), "include", "tsu.h")
     text = open(hdr).read()
-    return sorted(set(re.findall(r"^\s*(?:int|int64_t|double|const char\*)\s+(tsu_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|double|size_t|const char\*)\s+(tsu_\w+)\s*\(", text, re.M)))
 
 
 def _check(rc: int, func: str):
@@ -185,6 +189,33 @@ def tsu_make_depth(g: Grid, depth: dict, dtype, hx: torch.Tensor, hy: torch.Tens
                                ext, _stream(stream))
     _check(rc, "tsu_make_depth")
     return np.array(list(ext)) if sync else None
+
+
+def tsu_depth_eps_derivative(g: Grid, depth: dict, dtype, dhx: torch.Tensor, dhy: torch.Tensor, stream=None):
+    """d h_eps / d eps at the faces, same layout as tsu_make_depth's hx, hy."""
+    d = depth_struct(depth)
+    _check(load().tsu_depth_eps_derivative(C.byref(g), C.byref(d), dtype_code(dtype), _ptr(dhx), _ptr(dhy),
+                                           _stream(stream)), "tsu_depth_eps_derivative")
+
+
+def tsu_reduce_workspace() -> int:
+    return int(load().tsu_reduce_workspace())
+
+
+def tsu_depth_eps_gradient(g: Grid, depth: dict, g_hx: torch.Tensor, g_hy: torch.Tensor, out: torch.Tensor,
+                           ws: torch.Tensor, stream=None):
+    """out[0] = dJ/deps = sum g_hx dhx/deps + g_hy dhy/deps (device double)."""
+    d = depth_struct(depth)
+    _check(load().tsu_depth_eps_gradient(C.byref(g), C.byref(d), _ptr(g_hx), _ptr(g_hy), _ptr(out), _ptr(ws),
+                                         int(ws.numel() * ws.element_size()), _stream(stream)),
+           "tsu_depth_eps_gradient")
+
+
+def tsu_diff_norms(g: Grid, dtype, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor, ws: torch.Tensor,
+                   stream=None):
+    """out[0] = sum (a - b)^2, out[1] = sum b^2 over nodes i < nx (device double[2])."""
+    _check(load().tsu_diff_norms(C.byref(g), dtype_code(dtype), _ptr(a), _ptr(b), _ptr(out), _ptr(ws),
+                                 int(ws.numel() * ws.element_size()), _stream(stream)), "tsu_diff_norms")
 
 
 def tsu_tau_for(g: Grid, hx_max: float, hy_max: float, cfl: float) -> float:
