@@ -91,28 +91,31 @@ def mollifier_gap(eps_list, n: int = 1025, T: float = 0.15, kind: str = "line_x"
 def reflected_pulse(eps: float, n: int = 769, T: float = 0.45, amp: float = 1.0, x_src: float = 0.30,
                     x_rec: float = 0.40, width: float = 0.03) -> dict:
     """A hump at (x_src, 0.5), a line singularity amp phi_eps(x - 0.5) on background 1 and a
-    receiver at (x_rec, 0.5) between them.  The receiver sees the outgoing pulse first and the
-    one reflected by the line later; returns both peaks (signed) and their arrival times."""
-    depth = dict(background=1.0, eps=float(eps), mollifier=inputs.GAUSS, sings=[(inputs.LINE_X, 1, amp, 0.5, 0.5)])
-    sim = tsu.Simulation.create(n, depth, dtype="f32", nbuf=3)
+    receiver at (x_rec, 0.5) between them.  The same run without the singularity (same tau) gives
+    the free wave; the difference of the two receiver traces is the wave the line sends back.
+    Returns the free wave's peak and arrival and the reflected wave's signed peak and arrival."""
+    line = dict(background=1.0, eps=float(eps), mollifier=inputs.GAUSS, sings=[(inputs.LINE_X, 1, amp, 0.5, 0.5)])
+    free = dict(background=1.0, eps=float(eps), mollifier=inputs.GAUSS, sings=[])
+    sim = tsu.Simulation.create(n, line, dtype="f32", nbuf=3)
+    ref = tsu.Simulation.create(n, free, dtype="f32", nbuf=3, tau=sim.tau)
     steps = max(2, int(math.ceil(T / sim.tau)))
     u0 = torch.from_numpy(inputs.gaussian_hump(n, n, sim.g.ld, x_src, 0.5, width, 1.0, np.float32)).cuda()
     i, j = round(x_rec * (n - 1)), round(0.5 * (n - 1))
     rec = torch.tensor([j * sim.g.ld + i], dtype=torch.int64, device="cuda")
-    tr = torch.zeros((steps, 1), dtype=torch.float32, device="cuda")
-    sim.init(u0)
-    sim.step(steps - 1, rec_idx=rec, traces=tr[: steps - 1])
-    sim.observe(rec_idx=rec, trace=tr[steps - 1])
-    trace = tr[:, 0].double().cpu().numpy()
+    traces = []
+    for s in (sim, ref):
+        tr = torch.zeros((steps, 1), dtype=torch.float32, device="cuda")
+        s.init(u0)
+        s.step(steps - 1, rec_idx=rec, traces=tr[: steps - 1])
+        s.observe(rec_idx=rec, trace=tr[steps - 1])
+        traces.append(tr[:, 0].double().cpu().numpy())
     t = sim.tau * np.arange(1, steps + 1)
-    # the background wave speed is 1: the outgoing pulse passes the receiver around
-    # (x_rec - x_src), the reflection arrives around (0.5 - x_src) + (0.5 - x_rec)
-    split = 0.5 * ((x_rec - x_src) + (1.0 - x_src - x_rec))
-    inc = np.argmax(np.abs(np.where(t < split, trace, 0.0)))
-    ref = np.argmax(np.abs(np.where(t >= split, trace, 0.0)))
-    return {"eps": float(eps), "n": n, "tau": sim.tau, "steps": steps, "trace": trace,
-            "incident_peak": float(trace[inc]), "incident_arrival": float(t[inc]),
-            "reflected_peak": float(trace[ref]), "reflected_arrival": float(t[ref])}
+    scattered = traces[0] - traces[1]
+    inc = int(np.argmax(np.abs(traces[1])))
+    rfl = int(np.argmax(np.abs(scattered)))
+    return {"eps": float(eps), "n": n, "tau": sim.tau, "steps": steps, "trace": traces[0], "free_trace": traces[1],
+            "incident_peak": float(traces[1][inc]), "incident_arrival": float(t[inc]),
+            "reflected_peak": float(scattered[rfl]), "reflected_arrival": float(t[rfl])}
 
 
 def misfit_eps_gradient(n: int, depth: dict, u0: np.ndarray, S: int, rec_ij: np.ndarray, eps_obs: float,

@@ -121,9 +121,14 @@ def test_mollifier_choice_fades_as_eps_decreases():
 
 
 def test_reflected_pulse_from_a_line_singularity():
-    """Sec. 3.2: a wave meeting the line singularity is partly reflected; the receivers left of
-    the line see the incident pulse and, later, a reflected one of opposite-side origin."""
-    r = study.reflected_pulse(0.02, n=769, T=0.45)
-    assert r["incident_peak"] > 0
-    assert abs(r["reflected_peak"]) > 1e-3 * r["incident_peak"]
-    assert r["reflected_arrival"] > r["incident_arrival"]
+    """Sec. 3.2: a wave meeting the line singularity is partly reflected.  The receiver between
+    the source and the line sees the free wave first; the difference to the run without the line
+    arrives after the time to the line and back (0.2 + 0.1 at speed 1, less the line's width), is
+    a fraction of the incident pulse, and its size settles as eps decreases."""
+    r = [study.reflected_pulse(e, n=769, T=0.45) for e in (0.02, 0.01)]
+    for q in r:
+        assert q["incident_peak"] > 0 and abs(q["incident_arrival"] - 0.1) < 0.03
+        assert 0.2 < q["reflected_arrival"] < 0.32
+        assert 1e-2 * q["incident_peak"] < abs(q["reflected_peak"]) < q["incident_peak"]
+    assert np.sign(r[0]["reflected_peak"]) == np.sign(r[1]["reflected_peak"])
+    assert abs(r[1]["reflected_peak"] / r[0]["reflected_peak"] - 1) < 0.5
