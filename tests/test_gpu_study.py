@@ -132,3 +132,24 @@ def test_reflected_pulse_from_a_line_singularity():
         assert 1e-2 * q["incident_peak"] < abs(q["reflected_peak"]) < q["incident_peak"]
     assert np.sign(r[0]["reflected_peak"]) == np.sign(r[1]["reflected_peak"])
     assert abs(r[1]["reflected_peak"] / r[0]["reflected_peak"] - 1) < 0.5
+
+
+def test_argument_errors_of_the_study_entry_points():
+    g = tsu.grid(65, 65)
+    depth = EPS_DEPTHS["line_gauss"]
+    f = tsu.empty_field(g, "f64")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    small = torch.empty(64, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(tsu.tsu_reduce_workspace(), dtype=torch.uint8, device="cuda")
+    with pytest.raises(tsu.TsuError) as e:
+        tsu.tsu_diff_norms(g, "f64", f, f, out, small)
+    assert e.value.code == tsu.TSU_ENOMEM
+    with pytest.raises(tsu.TsuError) as e:
+        tsu.tsu_depth_eps_gradient(g, depth, f, f, out, small)
+    assert e.value.code == tsu.TSU_ENOMEM
+    with pytest.raises(tsu.TsuError) as e:
+        tsu.tsu_depth_eps_derivative(g, dict(depth, eps=-1.0), "f64", f, f)
+    assert e.value.code == tsu.TSU_EINVAL
+    with pytest.raises(tsu.TsuError) as e:
+        tsu.tsu_diff_norms(g, "f64", f, f.view(-1)[1:], out, ws)  # second field 8 bytes off alignment
+    assert e.value.code == tsu.TSU_EINVAL
