@@ -179,6 +179,17 @@ def oracle_sample(n: int, steps_sample: int):
                        f"interior updates), {threads} OpenMP threads", seconds=dt)
 
 
+def workload_config(n: int, S: int, form: str, world: int) -> dict:
+    """The config both arms report: the workload they measure (the reference arm times a bounded
+    sample of it, described in its cpu_baseline)."""
+    return {"workload": f"point_fp32_{n}: {n}x{n} grid, depth 0.5 + 0.01 phi_eps(|r-(0.5,0.5)|), eps = 4dx, "
+                        f"Gaussian hump width 0.02 at (0.3,0.5), {S} steps, energy every step",
+            "n": n, "leapfrog_steps": S, "form": form,
+            "l2": (f"inputs larger than L2 (four {n * ((n + 31) // 32 * 32) * 4 / 2**20:.0f} MiB fields), no flush"
+                   if 4 * n * n * 4 > 129e6 else "inputs smaller than L2 (129 MB)"),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -196,7 +207,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"point_fp32_{args.n} sample", "n": args.n, "leapfrog_steps": steps_sample},
+            "config": workload_config(args.n, args.nsteps, args.form, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -361,13 +372,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"point_fp32_{p.n}: {p.n}x{p.n} grid, depth 0.5 + 0.01 phi_eps(|r-(0.5,0.5)|), "
-                               f"eps = 4dx, Gaussian hump width 0.02 at (0.3,0.5), {S} steps, "
-                               f"{'increment' if form else 'standard'} form, energy every step, "
-                               f"{'%d steps per blocked pass' % K if blocked else 'one step per pass'}",
-                   "n": p.n, "leapfrog_steps": S, "form": args.form, "tau": tau,
-                   "l2": "inputs larger than L2 (four 256 MiB fields), no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(p.n, S, args.form, world),
+        "kernel": f"{'%d steps per blocked pass' % K if blocked else 'one step per pass'}, tau = {tau:.6g}",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "bytes_per_launch_per_node": bpn,
                      "steps_per_launch": K if blocked else 1, "kernel": kname, "launch_ms": launch_ms,
