@@ -457,10 +457,19 @@ def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
     t_a = _events_ms(adjoint, reps)
     lups = (n - 2) ** 2 * S
     J = 0.5 * float(((traces - obs).double() ** 2).sum())
+    # algorithmic bytes: the forward reads u, v, hx, hy and writes u, v every step (6 fields); the
+    # adjoint moves 23 fields per 4 reverse steps (the 4-step sweep 14: lam^{n+1}, lam^{n+2},
+    # u^n..u^{n-3}, hx, hy and the two accumulators read, two multipliers and the accumulators
+    # written; the 4-step recompute 9: u, v, hx, hy read, 4 states and v written)
+    fb = g.ny * g.ld * 4
+    peak, _ = load_peaks()
     return {"workload": f"adjoint_{n}: {n}^2 FP32 (increment form), depth 1 + 0.5 phi_eps(x-0.5), eps 0.01, "
                         f"{S} steps, {nrec} receivers on y = 0.8, checkpoints every {every}",
             "forward_ms": t_f, "adjoint_ms": t_a, "ratio": t_a / t_f, "forward_glups": lups / t_f / 1e6,
-            "adjoint_glups": lups / t_a / 1e6, "J": J, "grad_norm_hx": float(gx.norm())}
+            "adjoint_glups": lups / t_a / 1e6, "J": J, "grad_norm_hx": float(gx.norm()),
+            "forward_gbs_algorithmic": 6 * fb * S / (t_f / 1e3) / 1e9,
+            "adjoint_gbs_algorithmic": 23 / 4 * fb * S / (t_a / 1e3) / 1e9,
+            "adjoint_frac_of_measured_peak": 23 / 4 * fb * S / (t_a / 1e3) / 1e9 / peak}
 
 
 def measure_batched(steps=2000, warm=1, rows=0):
@@ -504,10 +513,15 @@ def measure_batched(steps=2000, warm=1, rows=0):
     t_s0 = _events_ms(lambda: sequential(0))
     tsu.tsu_sync_status(ws, wsb)
     lups = sum((pr.n - 2) ** 2 * pr.steps for pr in probs)
+    # algorithmic bytes of the 4-step batched pass: u, v, hx, hy read and u, v written once per
+    # 4 steps (1.5 fields per step) for every problem
+    peak, _ = load_peaks()
+    gbs = sum(1.5 * s.g.ny * s.g.ld * 4 * (pr.steps - 1) for (pr, s, _) in sims) / (t_b / 1e3) / 1e9
     return {"workload": f"eps-family: {len(probs)} problems (16 eps x line-x, line-y, point, line+point), "
                         f"N in {{512..2048}}, {steps} steps each, FP32 increment form",
             "lups": lups, "batched_ms": t_b, "sequential_one_step_ms": t_s1, "sequential_auto_ms": t_s0,
-            "init_ms": t_init, "batched_glups": lups / t_b / 1e6, "speedup_vs_sequential_one_step": t_s1 / t_b,
+            "init_ms": t_init, "batched_glups": lups / t_b / 1e6, "batched_gbs_algorithmic": gbs,
+            "batched_frac_of_measured_peak": gbs / peak, "speedup_vs_sequential_one_step": t_s1 / t_b,
             "speedup_vs_sequential_auto": t_s0 / t_b, "max_rel_diff_batched_vs_sequential": diff}
 
 
