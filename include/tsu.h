@@ -218,7 +218,8 @@ int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps
 
 /* Reverse-time discrete adjoint of the forward run "tsu_init(u0, u1) then tsu_step_n(nsteps-1)"
  * for a receiver functional J(traces) (the paper has no adjoint; it is the exact reverse of the
- * scheme above, with multipliers lam^n = g^n + (2I + B) lam^{n+1} - lam^{n+2}).
+ * scheme above, with multipliers lam^n = g^n + (2I + B) lam^{n+1} - lam^{n+2}; FP32 fields run the
+ * same recursion in increment form, mu^n = lam^n - lam^{n+1} = mu^{n+1} + B lam^{n+1} + g^n).
  *   form      the form of that forward run (its checkpoints hold that form's two fields)
  *   nsteps    S (final state u^S); ckpt_every, ckpt: the checkpoint store the forward filled
  *             (tsu_ckpt_slots(S, every) slots); segments are recomputed from it
@@ -251,7 +252,8 @@ typedef struct {
   int32_t tdepth; /* steps per batched pass (0 = the kernel's default: 4 for kernel 2, 8 for kernel 3) */
   int32_t rows;   /* rows per chunk (0 = 128) */
   int32_t kernel; /* 0 or 2: warp-blocked (tdepth 2 or 4); 3: CTA-blocked (tdepth 4 or 8) */
-  int32_t reserved;
+  int32_t graph;  /* 1: capture every launch of the call into one CUDA graph and launch that (needs a
+                     non-default stream); 0: launch on the stream directly */
 } tsu_batch_opts;
 
 /* Bytes of device workspace tsu_batch_run needs for these problems (descriptors and tile table). */

@@ -8,8 +8,13 @@
 //                with -cx/2, lam^1 and u^0 for the start), dJ/dhy likewise in j.
 // k_adjoint_pass computes lam^n from lam^{n+1} (5-point) and lam^{n+2} (centre), written over
 // lam^{n+2}, with the same register-streaming layout as the forward pass, and accumulates both
-// face gradients from lam^{n+1} and the recomputed forward state u^n.  In FP32 the face
-// gradients are summed in FP32 over one checkpoint segment and flushed into FP64 per segment.
+// face gradients from lam^{n+1} and the recomputed forward state u^n.  FP32 runs the recursion in
+// increment form, mu^n = lam^n - lam^{n+1}:
+//   mu^n = mu^{n+1} + B lam^{n+1} + g^n,  lam^n = lam^{n+1} + mu^n,  dJ/du0 = mu^1 + B lam^1 / 2,
+// algebraically the same recursion; it keeps the multipliers accurate over thousands of steps in
+// FP32 for the reason the forward's increment form does (the change per step is far below one ulp
+// of lam).  In FP32 the face gradients are summed in FP32 over one checkpoint segment and flushed
+// into FP64 per segment.
 #include "stencil_common.cuh"
 
 namespace tsu {
@@ -23,19 +28,19 @@ struct AccOf<float> { using type = float; };
 template <>
 struct AccOf<double> { using type = double; };
 
-// MODE 0: lam_out = (2 lam_c - lam_pp) + B lam_c          (the recursion)
-// MODE 1: lam_out = (lam_c - lam_pp) + B lam_c / 2 = dJ/du0; g_u1 = tau lam_c   (the start)
-// REV: the pass also steps the increment-form state backwards, the exact inverse of the forward
-//      step: u^{n-1} = u^n - v^n, v^{n-1} = v^n - B u^{n-1}, from (u, v_in) into (u_out, v_out).
-template <typename T, int MODE, bool REV>
+// MODE 0 (kAdjStep):     lam_out = (2 lam_c - lam_pp) + B lam_c          (the recursion)
+// MODE 1 (kAdjStart):    lam_out = (lam_c - lam_pp) + B lam_c / 2 = dJ/du0; g_u1 = tau lam_c
+// MODE 2 (kAdjStepInc):  lam_pp holds mu^{n+1}: mu_out = mu^{n+1} + B lam_c (may be lam_pp itself:
+//                        every node reads only its own mu), lam_out = lam_c + mu_out
+// MODE 3 (kAdjStartInc): lam_pp holds mu^1: lam_out = mu^1 + B lam_c / 2 = dJ/du0; g_u1 = tau lam_c
+template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const int32_t ny, const int64_t ld,
                                                       const typename ArithOf<T>::type ar, const T gwx, const T gwy,
                                                       const T tau, const T* __restrict__ hx, const T* __restrict__ hy,
-                                                      const T* __restrict__ lam, const T* lam_pp, T* lam_out,
+                                                      const T* __restrict__ lam, const T* lam_pp, T* lam_out, T* mu_out,
                                                       const T* __restrict__ u, typename AccOf<T>::type* gx,
                                                       typename AccOf<T>::type* gy, T* g_u1, const int rows,
-                                                      const RecBuckets rb, const T* __restrict__ v_in,
-                                                      T* __restrict__ u_out, T* __restrict__ v_out) {
+                                                      const RecBuckets rb) {
   using A = typename AccOf<T>::type;
   constexpr int V = Vec<T>::V;
   const int lane = threadIdx.x & 31;
@@ -63,20 +68,6 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
   Pack<T> lc = ld_vec(lam + (int64_t)j0 * ld + i0);
   Pack<T> hym = ld_vec(hy + (int64_t)(j0 - 1) * ld + i0);
   Pack<T> uc = umask(ld_vec(u + (int64_t)j0 * ld + i0), j0);
-  // reverse state step: w = u^{n-1} = u^n - v^n on rows j-1, j, j+1
-  Pack<T> vc, wm, wc;
-  auto wdiff = [&](const Pack<T>& a, const Pack<T>& b) {
-    Pack<T> r;
-#pragma unroll
-    for (int e = 0; e < V; ++e) r.a[e] = a.a[e] - b.a[e];
-    return r;
-  };
-  if constexpr (REV) {
-    vc = umask(ld_vec(v_in + (int64_t)j0 * ld + i0), j0);
-    wm = wdiff(umask(ld_vec(u + (int64_t)(j0 - 1) * ld + i0), j0 - 1),
-               umask(ld_vec(v_in + (int64_t)(j0 - 1) * ld + i0), j0 - 1));
-    wc = wdiff(uc, vc);
-  }
   for (int j = j0; j < j1; ++j) {
     const int64_t row = (int64_t)j * ld + i0;
     const Pack<T> ln = ld_vec(lam + row + ld);
@@ -84,11 +75,6 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
     const Pack<T> hxv = ld_vec(hx + row);
     const Pack<T> hyv = ld_vec(hy + row);
     const Pack<T> un = umask(ld_vec(u + row + ld), j + 1);
-    Pack<T> vn, wn;
-    if constexpr (REV) {
-      vn = umask(ld_vec(v_in + row + ld), j + 1);
-      wn = wdiff(un, vn);
-    }
     T ll = __shfl_up_sync(0xffffffffu, lc.a[V - 1], 1);
     T hl = __shfl_up_sync(0xffffffffu, hxv.a[V - 1], 1);
     T lr = __shfl_down_sync(0xffffffffu, lc.a[0], 1);
@@ -101,17 +87,7 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       lr = (i0 + V < ld) ? lam[row + V] : T(0);
       ur = u_at(i0 + V, j);
     }
-    T wl = T(0), wr = T(0);
-    if constexpr (REV) {
-      wl = __shfl_up_sync(0xffffffffu, wc.a[V - 1], 1);
-      wr = __shfl_down_sync(0xffffffffu, wc.a[0], 1);
-      auto v_at = [&](int64_t i) -> T {
-        return (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2) ? v_in[(int64_t)j * ld + i] : T(0);
-      };
-      if (lane == 0) wl = u_at(i0 - 1, j) - v_at(i0 - 1);
-      if (lane == 31) wr = u_at(i0 + V, j) - v_at(i0 + V);
-    }
-    Pack<T> out, gu1, uo, vo;
+    Pack<T> out, gu1, mo;
     A gxv[V], gyv[V], gy0[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) {
@@ -124,11 +100,16 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       T val;
       if constexpr (MODE == 0) {
         val = ar.lf(lc.a[e], lp.a[e], b);
+      } else if constexpr (MODE == 2) {
+        const T mu = ar.add(lp.a[e], b);
+        mo.a[e] = interior ? mu : T(0);
+        val = ar.add(lc.a[e], mu);
       } else {
+        const T d = (MODE == 1) ? lc.a[e] - lp.a[e] : lp.a[e];  // lam^1 - lam^2 = mu^1
         if constexpr (sizeof(T) == 8)
-          val = __dadd_rn(__dsub_rn(lc.a[e], lp.a[e]), __dmul_rn(0.5, b));
+          val = __dadd_rn(MODE == 1 ? __dsub_rn(lc.a[e], lp.a[e]) : lp.a[e], __dmul_rn(0.5, b));
         else
-          val = (lc.a[e] - lp.a[e]) + 0.5f * b;
+          val = d + 0.5f * b;
         gu1.a[e] = interior ? tau * lc.a[e] : T(0);
       }
       out.a[e] = interior ? val : T(0);
@@ -139,24 +120,11 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       gxv[e] = (i <= nx - 2) ? (A)(gwx * (dlx * dux)) : A(0);
       gyv[e] = interior ? (A)(gwy * (dly * duy)) : A(0);
       gy0[e] = interior ? (A)(gwy * (lc.a[e] * uc.a[e])) : A(0);  // y-face (0, 1), used on row 1
-      if constexpr (REV) {
-        const T wxl = (e == 0) ? wl : wc.a[e - 1];
-        const T wxr = (e == V - 1) ? wr : wc.a[e + 1];
-        const T bw = ar.b(hxv.a[e], hxl, hyv.a[e], hym.a[e], wc.a[e], wxl, wxr, wn.a[e], wm.a[e]);
-        uo.a[e] = interior ? wc.a[e] : T(0);
-        if constexpr (sizeof(T) == 8)
-          vo.a[e] = interior ? __dsub_rn(vc.a[e], bw) : T(0);
-        else
-          vo.a[e] = interior ? vc.a[e] - bw : T(0);
-      }
     }
     if (active) {
-      if constexpr (MODE == 0)
-        st_vec(lam_out + row, out);
-      else {
-        st_vec(lam_out + row, out);
-        st_vec(g_u1 + row, gu1);
-      }
+      st_vec(lam_out + row, out);
+      if constexpr (MODE == 2) st_vec(mu_out + row, mo);
+      if constexpr (MODE == 1 || MODE == 3) st_vec(g_u1 + row, gu1);
       // the accumulators have the field's vector width (float4 / double2): 16-byte read-modify-write
       Pack<A> ax = ld_vec_l2(gx + row), ay = ld_vec_l2(gy + row);
 #pragma unroll
@@ -166,10 +134,6 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
       }
       st_vec(gx + row, ax);
       st_vec(gy + row, ay);
-      if constexpr (REV) {
-        st_vec(u_out + row, uo);
-        st_vec(v_out + row, vo);
-      }
       if (j == 1) {
         Pack<A> a0 = ld_vec_l2(gy + i0);
 #pragma unroll
@@ -181,21 +145,18 @@ __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const in
     lc = ln;
     hym = hyv;
     uc = un;
-    if constexpr (REV) {
-      vc = vn;
-      wm = wc;
-      wc = wn;
-    }
   }
-  // receiver injection lam^n += g^n at this CTA's receivers, in receiver order, after the CTA's
-  // own stores of lam^n (visible to the CTA after the barrier)
+  // receiver injection lam^n += g^n (and mu^n += g^n in increment form) at this CTA's receivers,
+  // in receiver order, after the CTA's own stores (visible to the CTA after the barrier)
   if (rb.off) {
     __syncthreads();
     if (threadIdx.x == 0) {
       const int64_t cta = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
       for (int q = rb.off[cta]; q < rb.off[cta + 1]; ++q) {
         const int r = rb.ord[q];
-        lam_out[rb.idx[r]] += ((const T*)rb.g)[r];
+        const T gv = ((const T*)rb.g)[r];
+        lam_out[rb.idx[r]] += gv;
+        if constexpr (MODE == 2) mu_out[rb.idx[r]] += gv;
       }
     }
   }
@@ -268,31 +229,43 @@ void adjoint_pass_shape(const StencilGeom& g, int dtype, int64_t* gridx, int64_t
 }
 
 namespace {
-template <typename T>
-cudaError_t pass_t(const StencilGeom& g, bool start, const void* hx, const void* hy, const void* lam,
-                   const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy, void* g_u1,
-                   const RecBuckets& rb, const void* v_in, void* u_out, void* v_out, cudaStream_t s) {
+template <typename T, int MODE>
+void pass_mode(dim3 grid, const StencilGeom& g, T gwx, T gwy, const void* hx, const void* hy, const void* lam,
+               const void* lam_pp, void* lam_out, void* mu_out, const void* u, void* gx, void* gy, void* g_u1,
+               int rows, const RecBuckets& rb, cudaStream_t s) {
   using A = typename AccOf<T>::type;
+  k_adjoint_pass<T, MODE><<<grid, 128, 0, s>>>(g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx,
+                                               (const T*)hy, (const T*)lam, (const T*)lam_pp, (T*)lam_out,
+                                               (T*)mu_out, (const T*)u, (A*)gx, (A*)gy, (T*)g_u1, rows, rb);
+}
+
+template <typename T>
+cudaError_t pass_t(const StencilGeom& g, int mode, const void* hx, const void* hy, const void* lam,
+                   const void* lam_pp, void* lam_out, void* mu_out, const void* u, void* gx, void* gy, void* g_u1,
+                   const RecBuckets& rb, cudaStream_t s) {
   int64_t gx_, gy_, cpc;
   int rows;
   adjoint_pass_shape(g, sizeof(T) == 4 ? TSU_F32 : TSU_F64, &gx_, &gy_, &rows, &cpc);
-  const int threads = 128;
   dim3 grid((unsigned)gx_, (unsigned)gy_);
+  const bool start = mode == kAdjStart || mode == kAdjStartInc;
   const T w = start ? T(0.5) : T(1);
   const T gwx = -(T)g.cx * w, gwy = -(T)g.cy * w;
-  if (start)
-    k_adjoint_pass<T, 1, false><<<grid, threads, 0, s>>>(
-        g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx, (const T*)hy, (const T*)lam,
-        (const T*)lam_pp, (T*)lam_out, (const T*)u, (A*)gx, (A*)gy, (T*)g_u1, rows, rb, nullptr, nullptr, nullptr);
-  else if (v_in)
-    k_adjoint_pass<T, 0, true><<<grid, threads, 0, s>>>(
-        g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx, (const T*)hy, (const T*)lam,
-        (const T*)lam_pp, (T*)lam_out, (const T*)u, (A*)gx, (A*)gy, nullptr, rows, rb, (const T*)v_in, (T*)u_out,
-        (T*)v_out);
-  else
-    k_adjoint_pass<T, 0, false><<<grid, threads, 0, s>>>(
-        g.nx, g.ny, g.ld, arith<T>(g), gwx, gwy, (T)g.tau, (const T*)hx, (const T*)hy, (const T*)lam,
-        (const T*)lam_pp, (T*)lam_out, (const T*)u, (A*)gx, (A*)gy, nullptr, rows, rb, nullptr, nullptr, nullptr);
+  switch (mode) {
+    case kAdjStep:
+      pass_mode<T, 0>(grid, g, gwx, gwy, hx, hy, lam, lam_pp, lam_out, mu_out, u, gx, gy, g_u1, rows, rb, s);
+      break;
+    case kAdjStart:
+      pass_mode<T, 1>(grid, g, gwx, gwy, hx, hy, lam, lam_pp, lam_out, mu_out, u, gx, gy, g_u1, rows, rb, s);
+      break;
+    case kAdjStepInc:
+      pass_mode<T, 2>(grid, g, gwx, gwy, hx, hy, lam, lam_pp, lam_out, mu_out, u, gx, gy, g_u1, rows, rb, s);
+      break;
+    case kAdjStartInc:
+      pass_mode<T, 3>(grid, g, gwx, gwy, hx, hy, lam, lam_pp, lam_out, mu_out, u, gx, gy, g_u1, rows, rb, s);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 }  // namespace
@@ -306,13 +279,11 @@ cudaError_t launch_rec_bucket(const StencilGeom& g, int dtype, const int64_t* id
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
-                                const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
-                                void* g_u1, const RecBuckets& rb, cudaStream_t s, const void* v_in, void* u_out,
-                                void* v_out) {
-  return dtype == TSU_F32
-             ? pass_t<float>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, v_in, u_out, v_out, s)
-             : pass_t<double>(g, start, hx, hy, lam, lam_pp, lam_out, u, gx, gy, g_u1, rb, v_in, u_out, v_out, s);
+cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, int mode, const void* hx, const void* hy,
+                                const void* lam, const void* lam_pp, void* lam_out, void* mu_out, const void* u,
+                                void* gx, void* gy, void* g_u1, const RecBuckets& rb, cudaStream_t s) {
+  return dtype == TSU_F32 ? pass_t<float>(g, mode, hx, hy, lam, lam_pp, lam_out, mu_out, u, gx, gy, g_u1, rb, s)
+                          : pass_t<double>(g, mode, hx, hy, lam, lam_pp, lam_out, mu_out, u, gx, gy, g_u1, rb, s);
 }
 
 cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,

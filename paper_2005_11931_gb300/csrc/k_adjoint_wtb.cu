@@ -1,18 +1,19 @@
 // K adjoint steps per pass, K = 2 or 4 (the paper has no adjoint; this is the exact reverse of
 // the scheme of k_step.cu, arXiv:2005.11931 Sec. 2 eq. (2.1) on the Sec. 3.3 box), warp-blocked
-// like k_step_wtb.cu.  Level k = 1..K computes lam^{n-k+1} from the two levels before it:
-//   lam^{n-k+1} = g^{n-k+1} + 2 lam^{n-k+2} - lam^{n-k+3} + B lam^{n-k+2}
-//   dJ/dhx_ij  += -cx (lam^{n-k+2}_{i+1} - lam^{n-k+2}_i)(u^{n-k+1}_{i+1} - u^{n-k+1}_i)   (hy likewise)
-// (level 0 = lam^{n+1} and level -1 = lam^{n+2} are the inputs).  Every warp owns a tile: 128
+// like k_step_wtb.cu, in the increment form of the recursion (mu^n = lam^n - lam^{n+1}, see
+// k_adjoint.cu).  Level k = 1..K computes step m = n - k + 1 from level k - 1:
+//   mu^m  = mu^{m+1} + B lam^{m+1} + g^m,   lam^m = lam^{m+1} + mu^m
+//   dJ/dhx_ij  += -cx (lam^{m+1}_{i+1} - lam^{m+1}_i)(u^m_{i+1} - u^m_i)   (hy likewise)
+// (level 0 = (lam^{n+1}, mu^{n+1}) is the input).  Every warp owns a tile: 128
 // columns (one float4 per lane; the middle 120 are output, a 4-column halo covers the K-step
 // cone) by a chunk of rows it streams down; level k lags the input row by k rows.  Each thread
 // copies its own float4 of every input row through a private cp.async ring: lam^{n+1},
-// lam^{n+2}, hx and hy at the input row (the faces one row behind), u^{n-f} f rows behind, where
+// mu^{n+1}, hx and hy at the input row (the faces one row behind), u^{n-f} f rows behind, where
 // level f + 1 needs it, and the FP32 gradient accumulators K rows behind, where the last level
 // finishes a row; so nothing in the row loop waits on memory.  The face gradients of a row are
 // summed over the K steps in registers (carried from level to level) and added to the
-// accumulators once per pass.  Only the last two levels are stored: they are lam^{n'+2} and
-// lam^{n'+1} of the next pass.  Receiver values are added to the multipliers in registers, in
+// accumulators once per pass.  Only the last level is stored (lam and mu: the next pass's
+// input).  Receiver values are added to mu (and so to lam) in registers, in
 // every tile whose extended region holds the receiver (halo copies included): the lanes hold the
 // tile's entries and a ballot per row and level finds the ones on it.  Arithmetic runs on paired
 // FP32 instructions with the rounding order of the scalar one-step adjoint pass.
@@ -32,7 +33,7 @@ constexpr int kAwRing = 4;  // slots per field: in flight (2) + current, power o
 // registers per thread, K = 4 at <= 255
 template <int K>
 constexpr int aw_ctas_per_sm() { return K == 2 ? 3 : 2; }
-// ring fields: lam^{n+1}, lam^{n+2}, hx, hy, u^n .. u^{n-K+1}, gx, gy
+// ring fields: lam^{n+1}, mu^{n+1}, hx, hy, u^n .. u^{n-K+1}, gx, gy
 template <int K>
 constexpr int aw_fields() { return K + 6; }
 
@@ -55,10 +56,10 @@ struct AwArgs {
   const float* hx;
   const float* hy;
   const float* lam1;   // lam^{n+1}
-  const float* lam2;   // lam^{n+2}
+  const float* mu1;    // mu^{n+1} = lam^{n+1} - lam^{n+2}
   const float* u[K];   // u^n, u^{n-1}, ..., u^{n-K+1}
-  float* out_a;        // lam^{n-K+2} (level K - 1)
-  float* out_b;        // lam^{n-K+1} (level K)
+  float* out_a;        // lam^{n-K+1} (level K)
+  float* out_b;        // mu^{n-K+1}
   float* gx;           // FP32 face-gradient accumulators
   float* gy;
   int rows;
@@ -71,7 +72,7 @@ struct AwArgs {
 template <int K>
 __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a) {
   constexpr int NF = aw_fields<K>();
-  constexpr int F_L1 = 0, F_L2 = 1, F_HX = 2, F_HY = 3, F_U = 4, F_GX = 4 + K, F_GY = 5 + K;
+  constexpr int F_L1 = 0, F_MU = 1, F_HX = 2, F_HY = 3, F_U = 4, F_GX = 4 + K, F_GY = 5 + K;
   extern __shared__ __align__(16) unsigned char aw_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kAwWarps + warp;
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
       cp16(slot(s, f), src + (ok ? (int64_t)row * a.ld + c0 : 0), ok);
     };
     copy(F_L1, a.lam1, r, true);
-    copy(F_L2, a.lam2, r, true);
+    copy(F_MU, a.mu1, r, true);
     copy(F_HX, a.hx, r - 1, true);
     copy(F_HY, a.hy, r - 1, true);
 #pragma unroll
@@ -125,8 +126,8 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
   }
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
   // register windows, index 0 = newest row
-  P4 W[K][3];       // level k = 0..K-1 (level 0 = lam^{n+1}) at rows r - k, r - k - 1, r - k - 2
-  P4 LP[2];         // lam^{n+2} at rows r, r - 1
+  P4 W[K][3];       // lam of level k = 0..K-1 (level 0 = lam^{n+1}) at rows r - k, r - k - 1, r - k - 2
+  P4 MW[K][2];      // mu of level k at rows r - k, r - k - 1
   P4 UW[K][2];      // u^{n-f} at rows r - f, r - f - 1
   P4 HXW[K];        // hx at rows r - 1 .. r - K
   P4 HYW[K + 1];    // hy at rows r - 1 .. r - K - 1
@@ -135,13 +136,13 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     W[k][0] = W[k][1] = W[k][2] = kZeroP4;
+    MW[k][0] = MW[k][1] = kZeroP4;
     UW[k][0] = UW[k][1] = kZeroP4;
     HXW[k] = kZeroP4;
     cx_[k] = cy_[k] = kZeroP4;
   }
 #pragma unroll
   for (int k = 0; k <= K; ++k) HYW[k] = kZeroP4;
-  LP[0] = LP[1] = kZeroP4;
 
   const int q_lo = (tile_ok && a.rec_off) ? a.rec_off[tile] : 0, q_hi = (tile_ok && a.rec_off) ? a.rec_off[tile + 1] : 0;
   // the tile's first 32 receiver entries, one per lane (row -1: none), with their K values
@@ -192,11 +193,11 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
       }
     }
   };
-  // One reverse step at a row: lam_out = (2 lam - lam_pp) + B lam on interior nodes (0 elsewhere),
-  // and the face-gradient terms -cx (lam_{i+1} - lam_i)(u_{i+1} - u_i), -cy (lam_{j+1} - lam_j)
+  // One reverse step at a row: b = B lam and mu_out = mu + b on interior nodes (0 elsewhere), and
+  // the face-gradient terms -cx (lam_{i+1} - lam_i)(u_{i+1} - u_i), -cy (lam_{j+1} - lam_j)
   // (u_{j+1} - u_j) of that step with the state u (rows: uc, uu = uc + 1 for lam; us, usu for u).
   auto level = [&](const P4& uc, const P4& uu, const P4& ud, const P4& hx, const P4& hyu, const P4& hyd,
-                   const P4& lpp, const P4& us, const P4& usu, const bool row_in, P4& lout, P4& gx, P4& gy) {
+                   const P4& mu, const P4& us, const P4& usu, const bool row_in, P4& mout, P4& gx, P4& gy) {
     const float2 c01 = upk(uc.p[0]), c23 = upk(uc.p[1]);
     const float2 h01 = upk(hx.p[0]), h23 = upk(hx.p[1]);
     const float2 s01 = upk(us.p[0]), s23 = upk(us.p[1]);
@@ -212,8 +213,7 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     for (int q = 0; q < 2; ++q) {
       const f2x b = stencil2(hlpair[q], hx.p[q], hyd.p[q], hyu.p[q], uc.p[q], lpair[q], rpair[q], uu.p[q], ud.p[q],
                              cx2, cy2);
-      const f2x v = add2(sub2(add2(uc.p[q], uc.p[q]), lpp.p[q]), b);  // (2 lam - lam_pp) + B lam
-      lout.p[q] = row_in ? mul2(v, node2[q]) : 0ull;
+      mout.p[q] = row_in ? mul2(add2(mu.p[q], b), node2[q]) : 0ull;
       gx.p[q] = mul2(gcx2[q], mul2(sub2(rpair[q], uc.p[q]), sub2(srpair[q], us.p[q])));
       gy.p[q] = mul2(gcy2[q], mul2(sub2(uu.p[q], uc.p[q]), sub2(usu.p[q], us.p[q])));
     }
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     W[0][2] = W[0][1];
     W[0][1] = W[0][0];
     W[0][0] = lds_p4(slot(s, F_L1));
-    LP[1] = LP[0];
-    LP[0] = lds_p4(slot(s, F_L2));
+    MW[0][1] = MW[0][0];
+    MW[0][0] = lds_p4(slot(s, F_MU));
 #pragma unroll
     for (int f = 0; f < K; ++f) {
       UW[f][1] = UW[f][0];
@@ -251,22 +251,25 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
 #pragma unroll
     for (int k = 1; k <= K; ++k) {
       const int pk_row = r_in - k;
-      const P4& lpp = (k == 1) ? LP[1] : W[k >= 2 ? k - 2 : 0][2];
-      P4 lk, gxk, gyk;
-      level(W[k - 1][1], W[k - 1][0], W[k - 1][2], HXW[k - 1], HYW[k - 1], HYW[k], lpp, UW[k - 1][1], UW[k - 1][0],
-            pk_row >= 1 && pk_row <= a.ny - 2, lk, gxk, gyk);
+      P4 mk, gxk, gyk;
+      level(W[k - 1][1], W[k - 1][0], W[k - 1][2], HXW[k - 1], HYW[k - 1], HYW[k], MW[k - 1][1], UW[k - 1][1],
+            UW[k - 1][0], pk_row >= 1 && pk_row <= a.ny - 2, mk, gxk, gyk);
       if (pk_row == 1) {  // y-face (0, 1): lam and u vanish on row 0, the term is -cy lam_1 u_1
 #pragma unroll
         for (int q = 0; q < 2; ++q) g0.p[q] = add2(g0.p[q], mul2(gcy2[q], mul2(W[k - 1][1].p[q], UW[k - 1][1].p[q])));
       }
-      inject(pk_row, lk, k - 1);
+      inject(pk_row, mk, k - 1);  // g^m into mu^m (receivers are interior nodes)
+      P4 lk;  // lam^m = lam^{m+1} + mu^m (0 wherever mu^m and lam^{m+1} are)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) lk.p[q] = add2(W[k - 1][1].p[q], mk.p[q]);
       const bool store_row = col_out && pk_row >= y0 && pk_row < y1;
       if (k < K) {
         W[k][2] = W[k][1];
         W[k][1] = W[k][0];
         W[k][0] = lk;
+        MW[k][1] = MW[k][0];
+        MW[k][0] = mk;
       }
-      if (k == K - 1 && store_row) stg_p4(a.out_a + (int64_t)pk_row * a.ld + c0, lk);
       // gradient sums: level k adds to the sum of levels 1..k-1 at this row (carried from the
       // previous iteration); the new sum is kept until level k + 1 has read the old one
       P4 sx, sy;
@@ -287,7 +290,8 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
         pend_y = sy;
       } else if (store_row) {
         const int64_t o = (int64_t)pk_row * a.ld + c0;
-        stg_p4(a.out_b + o, lk);
+        stg_p4(a.out_a + o, lk);
+        stg_p4(a.out_b + o, mk);
         P4 ax = lds_p4(slot(s, F_GX)), ay = lds_p4(slot(s, F_GY));
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -351,7 +355,7 @@ __global__ void k_rec_tiles(const int32_t nx, const int32_t ny, const int64_t ld
 
 template <int K>
 cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void* hy, const void* lam1,
-                      const void* lam2, const void* const* u, void* out_a, void* out_b, void* gx, void* gy,
+                      const void* mu1, const void* const* u, void* out_a, void* out_b, void* gx, void* gy,
                       const int* rec_off, const int4* rec, const void* const* gv, cudaStream_t s);
 
 }  // namespace
@@ -383,7 +387,7 @@ cudaError_t launch_rec_tiles(const StencilGeom& g, int k, const int64_t* idx, in
 namespace {
 template <int K>
 cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void* hy, const void* lam1,
-                      const void* lam2, const void* const* u, void* out_a, void* out_b, void* gx, void* gy,
+                      const void* mu1, const void* const* u, void* out_a, void* out_b, void* gx, void* gy,
                       const int* rec_off, const int4* rec, const void* const* gv, cudaStream_t s) {
   AwArgs<K> a;
   a.nx = g.nx;
@@ -394,7 +398,7 @@ cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void
   a.hx = (const float*)hx;
   a.hy = (const float*)hy;
   a.lam1 = (const float*)lam1;
-  a.lam2 = (const float*)lam2;
+  a.mu1 = (const float*)mu1;
   for (int f = 0; f < K; ++f) {
     a.u[f] = (const float*)u[f];
     a.g[f] = gv ? (const float*)gv[f] : nullptr;
@@ -417,11 +421,11 @@ cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void
 }  // namespace
 
 cudaError_t launch_adjoint_wtb(const StencilGeom& g, int k, int rows, const void* hx, const void* hy,
-                               const void* lam1, const void* lam2, const void* const* u, void* out_a, void* out_b,
+                               const void* lam1, const void* mu1, const void* const* u, void* out_lam, void* out_mu,
                                void* gx, void* gy, const int* rec_off, const int4* rec, const void* const* gv,
                                cudaStream_t s) {
-  if (k == 2) return aw_launch<2>(g, rows, hx, hy, lam1, lam2, u, out_a, out_b, gx, gy, rec_off, rec, gv, s);
-  if (k == 4) return aw_launch<4>(g, rows, hx, hy, lam1, lam2, u, out_a, out_b, gx, gy, rec_off, rec, gv, s);
+  if (k == 2) return aw_launch<2>(g, rows, hx, hy, lam1, mu1, u, out_lam, out_mu, gx, gy, rec_off, rec, gv, s);
+  if (k == 4) return aw_launch<4>(g, rows, hx, hy, lam1, mu1, u, out_lam, out_mu, gx, gy, rec_off, rec, gv, s);
   return cudaErrorInvalidValue;
 }
 

@@ -370,16 +370,16 @@ static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
 // The time-reversed sweep (increment form: each adjoint pass also inverts one forward step, no
 // segment storage) is exact up to rounding but measured slower on GB300 at 2048^2 (230 ms against
 // 184 ms for the overlapped recompute, 4000 steps): it stays available behind this switch.
-constexpr bool kAdjointTimeReversal = false;
 // steps per pass of the FP32 segment recompute (warp-blocked, intermediate states stored)
 constexpr int kRecomputeDepth = 4;
 // steps per pass of the FP32 reverse sweep (2 or 4); leftover steps of a segment run one per pass
 constexpr int kAdjointDepth = 4;
 
-// fields of dtype before the FP32 accumulators: 4 multipliers, then two segment buffers of E + 3
-// (or, for the time-reversed sweep, the two (u, v) states)
+// fields of dtype before the FP32 accumulators: 4 multiplier fields, then two segment buffers of
+// E + 3
 static int64_t adjoint_fields(int form, int64_t every) {
-  return (form == TSU_FORM_INCREMENT && kAdjointTimeReversal) ? 4 + 4 : 4 + 2 * (every + 3);
+  (void)form;
+  return 4 + 2 * (every + 3);
 }
 
 // receiver tables: the one-step pass's (per CTA) and the K-step pass's (per tile, <= 4 per receiver)
@@ -480,10 +480,13 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   const size_t es = elem_size(dtype);
   const size_t fb = (size_t)g->ny * g->ld * es;
   char* w = (char*)ws;
-  // four multiplier fields: lam4[i1] = lam^{n+1}, lam4[i2] = lam^{n+2}, the other two receive the
-  // outputs of a two-step pass (which may not overwrite inputs that neighbouring halos still read)
+  // four multiplier fields.  FP64 (standard form): lam4[i1] = lam^{n+1}, lam4[i2] = lam^{n+2}.
+  // FP32 (increment form): lam4[i1] = lam^{n+1}, lam4[i2] = mu^{n+1} = lam^{n+1} - lam^{n+2}.  The
+  // other two receive the outputs of a K-step pass (which may not overwrite inputs that
+  // neighbouring tiles' halos still read).
   char* lam4[4] = {w, w + fb, w + 2 * fb, w + 3 * fb};
   int i1 = 0, i2 = 1;
+  const bool inc = dtype == TSU_F32;
   // two segment buffers, each seg[k] = u^{m_c + k} (k = 0..E) followed by the restore field
   // (u^{m_c - 1} or v) and a second v field (the blocked recompute writes v to the other one);
   // the recompute of one segment overlaps the reverse sweep of the other
@@ -515,80 +518,48 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hx, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_hy, 0, (size_t)g->ny * g->ld * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint reset");
-  // one step back: lam^n written over lam^{n+2}
+  auto free_pair = [&](int* oa, int* ob) {
+    *oa = *ob = -1;
+    for (int k = 0; k < 4; ++k)
+      if (k != i1 && k != i2) (*oa < 0 ? *oa : *ob) = k;
+  };
+  // one step back.  FP64: lam^n written over lam^{n+2}.  FP32: mu^n in place, lam^n into a free field.
   auto step_back = [&](int64_t n, const void* un) -> cudaError_t {
     tsu::RecBuckets rb{};
     if (nrec > 0) rb = {b_off, b_ord, rec_idx, (const char*)dtraces + (size_t)(n - 1) * nrec * es};
-    cudaError_t r = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam4[i1], lam4[i2], lam4[i2], un, accx,
-                                             accy, nullptr, rb, s);
+    if (inc) {
+      int oa, ob;
+      free_pair(&oa, &ob);
+      cudaError_t r = tsu::launch_adjoint_pass(sg, dtype, tsu::kAdjStepInc, m->hx, m->hy, lam4[i1], lam4[i2],
+                                               lam4[oa], lam4[i2], un, accx, accy, nullptr, rb, s);
+      i1 = oa;  // lam^n; mu^n stays in lam4[i2]
+      return r;
+    }
+    cudaError_t r = tsu::launch_adjoint_pass(sg, dtype, tsu::kAdjStep, m->hx, m->hy, lam4[i1], lam4[i2], lam4[i2],
+                                             nullptr, un, accx, accy, nullptr, rb, s);
     const int t = i1;  // now lam4[i1] = lam^n, lam4[i2] = lam^{n+1}
     i1 = i2;
     i2 = t;
     return r;
   };
-  // kAdjointDepth steps back (n .. n-K+1) in one pass, u[f] = u^{n-f}: lam^{n-K+2} and lam^{n-K+1}
-  // into the two free multiplier fields
+  // kAdjointDepth steps back (n .. n-K+1) in one pass (FP32), u[f] = u^{n-f}: lam^{n-K+1} and
+  // mu^{n-K+1} into the two free multiplier fields
   auto steps_back = [&](int64_t n, const void* const* u) -> cudaError_t {
-    int oa = -1, ob = -1;
-    for (int k = 0; k < 4; ++k)
-      if (k != i1 && k != i2) (oa < 0 ? oa : ob) = k;
+    int oa, ob;
+    free_pair(&oa, &ob);
     const void* gv[kAdjointDepth];
     for (int f = 0; f < kAdjointDepth; ++f)
       gv[f] = nrec > 0 ? (const char*)dtraces + (size_t)(n - 1 - f) * nrec * es : nullptr;
     cudaError_t r = tsu::launch_adjoint_wtb(sg, kAdjointDepth, rowsk, m->hx, m->hy, lam4[i1], lam4[i2], u, lam4[oa],
                                             lam4[ob], accx, accy, nrec > 0 ? t_off : nullptr, t_ent,
                                             nrec > 0 ? gv : nullptr, s);
-    i1 = ob;  // lam^{n-K+1}
-    i2 = oa;  // lam^{n-K+2}
+    i1 = oa;  // lam^{n-K+1}
+    i2 = ob;  // mu^{n-K+1}
     return r;
   };
   if (C == 0) {  // nsteps == 1: lam^1 = g^1 (the gradient term of n = 1 vanishes with lam^2 = 0)
-    e = step_back(1, (void*)lam4[2]);  // a zero field: the u argument is not used with lam^2 = 0
+    e = step_back(1, (void*)lam4[3]);  // a zero field no pass writes here: u is not used with lam^2 = 0
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
-  }
-  if (form == TSU_FORM_INCREMENT && C > 0 && kAdjointTimeReversal) {
-    // Time-reversed sweep.  The increment-form step is exactly invertible:
-    //   u^{n-1} = u^n - v^n,  v^{n-1} = v^n - B u^{n-1},
-    // so each adjoint pass also steps the state back and no segment is stored.  The state is
-    // re-anchored to the checkpoint (exact forward values) whenever the sweep reaches one, which
-    // bounds the rounding drift of the reversal to one segment.
-    char* U[2] = {w + 4 * fb, w + 5 * fb};
-    char* Vb[2] = {w + 6 * fb, w + 7 * fb};
-    const int64_t mlast = 1 + (C - 1) * ckpt_every;
-    const char* slot = (const char*)ckpt + (size_t)(C - 1) * 2 * fb;
-    e = cudaMemcpyAsync(U[0], slot, fb, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Vb[0], slot + fb, fb, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint restore");
-    int pu = 0;  // u in U[pu], v in Vb[pv]
-    int pv = 0;
-    tsu::PassOut none{};
-    for (int64_t k = mlast; k < nsteps; ++k) {  // forward to u^S, v^S (v in place)
-      e = tsu::launch_step(sg, dtype, form, m->hx, m->hy, nullptr, U[pu], Vb[pv], U[pu ^ 1], none, true, 0, s);
-      if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint recompute");
-      pu ^= 1;
-    }
-    for (int64_t n = nsteps; n >= 1; --n) {
-      tsu::RecBuckets rb{};
-      if (nrec > 0) rb = {b_off, b_ord, rec_idx, (const char*)dtraces + (size_t)(n - 1) * nrec * es};
-      e = tsu::launch_adjoint_pass(sg, dtype, false, m->hx, m->hy, lam4[i1], lam4[i2], lam4[i2], U[pu], accx, accy,
-                                   nullptr, rb, s, Vb[pv], U[pu ^ 1], Vb[pv ^ 1]);
-      if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint pass");
-      std::swap(i1, i2);
-      pu ^= 1;
-      pv ^= 1;
-      const int64_t m_state = n - 1;  // the state now held
-      if (m_state >= 1 && (m_state - 1) % ckpt_every == 0 && (m_state - 1) / ckpt_every < C) {
-        const char* sl = (const char*)ckpt + (size_t)((m_state - 1) / ckpt_every) * 2 * fb;
-        e = cudaMemcpyAsync(U[pu], sl, fb, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(Vb[pv], sl + fb, fb, cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint re-anchor");
-      }
-      if (dtype == TSU_F32 && ((n - 1) % ckpt_every) == 0) {
-        e = tsu::launch_flush(sg, accx, accy, g_hx, g_hy, s);
-        if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint flush");
-      }
-    }
-    C = 0;  // the segment loop below has nothing left to do
   }
   // the recompute stream starts after the resets above
   e = cudaEventRecord(aux->start, s);
@@ -658,9 +629,10 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
     e = cudaEventRecord(aux->swept[b], s);
     if (e != cudaSuccess) return cuda_fail(e, "tsu_adjoint stream order");
   }
-  // the start: dJ/du0 = (I + B/2) lam^1 - lam^2, dJ/du1 = tau lam^1, face terms with u^0 and weight 1/2
-  e = tsu::launch_adjoint_pass(sg, dtype, true, m->hx, m->hy, lam4[i1], lam4[i2], g_u0, u0, accx, accy, g_u1,
-                               tsu::RecBuckets{}, s);
+  // the start: dJ/du0 = (I + B/2) lam^1 - lam^2 (= mu^1 + B lam^1 / 2), dJ/du1 = tau lam^1, face
+  // terms with u^0 and weight 1/2
+  e = tsu::launch_adjoint_pass(sg, dtype, inc ? tsu::kAdjStartInc : tsu::kAdjStart, m->hx, m->hy, lam4[i1], lam4[i2],
+                               g_u0, nullptr, u0, accx, accy, g_u1, tsu::RecBuckets{}, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_u0, 0, (size_t)g->ld * es, s);  // boundary rows of the outputs
   if (e == cudaSuccess) e = cudaMemsetAsync((char*)g_u0 + (size_t)(g->ny - 1) * g->ld * es, 0, (size_t)g->ld * es, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(g_u1, 0, (size_t)g->ld * es, s);
@@ -798,37 +770,62 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
   if (e == cudaSuccess) e = cudaMemcpyAsync(tdev, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffers go out of scope
   if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run upload");
-  const int64_t rounds_max = probs[order[0]].nsteps / k;
-  for (int64_t r = 0; r < rounds_max; ++r) {
-    // tiles of the problems that still have a full round
-    int64_t nt = 0;
-    for (int oi = 0; oi < nprob; ++oi)
-      if (probs[order[oi]].nsteps / k > r) nt = prefix[oi];
-    const int set = r == 0 ? 0 : ((r & 1) ? 1 : 2);
-    e = kern == 2 ? tsu::launch_step_wtb_batched(form, k, desc + (size_t)set * nprob * ab, ab, tdev, nt, s)
-                  : tsu::launch_step_tb_batched(form, k, desc + (size_t)set * nprob * ab, tdev, nt, s);
-    if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run launch");
-  }
-  // host-side roles after the blocked rounds, then the leftover single steps per problem
-  for (int i = 0; i < nprob; ++i) {
-    tsu_state* st = probs[i].state;
-    const int64_t rounds = probs[i].nsteps / k;
-    for (int64_t r = 0; r < rounds; ++r) {
-      const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
-      st->cur = f1;
-      st->aux = f2;
+  // every launch of the run: the blocked rounds, then the leftover single steps per problem
+  auto enqueue = [&]() -> int {
+    const int64_t rounds_max = probs[order[0]].nsteps / k;
+    for (int64_t r = 0; r < rounds_max; ++r) {
+      // tiles of the problems that still have a full round
+      int64_t nt = 0;
+      for (int oi = 0; oi < nprob; ++oi)
+        if (probs[order[oi]].nsteps / k > r) nt = prefix[oi];
+      const int set = r == 0 ? 0 : ((r & 1) ? 1 : 2);
+      cudaError_t le = kern == 2
+                           ? tsu::launch_step_wtb_batched(form, k, desc + (size_t)set * nprob * ab, ab, tdev, nt, s)
+                           : tsu::launch_step_tb_batched(form, k, desc + (size_t)set * nprob * ab, tdev, nt, s);
+      if (le != cudaSuccess) return cuda_fail(le, "tsu_batch_run launch");
     }
-    st->step += rounds * k;
-    const int64_t left = probs[i].nsteps - rounds * k;
-    if (left > 0) {
-      tsu_step_opts o;
-      memset(&o, 0, sizeof o);
-      o.kernel = 1;
-      const int rc = tsu_step_n(&probs[i].grid, TSU_F32, probs[i].tau, &probs[i].medium, st, left, &o, nullptr, 0,
-                                stream);
-      if (rc != TSU_OK) return rc;
+    for (int i = 0; i < nprob; ++i) {
+      tsu_state* st = probs[i].state;
+      const int64_t rounds = probs[i].nsteps / k;
+      for (int64_t r = 0; r < rounds; ++r) {
+        const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
+        st->cur = f1;
+        st->aux = f2;
+      }
+      st->step += rounds * k;
+      const int64_t left = probs[i].nsteps - rounds * k;
+      if (left > 0) {
+        tsu_step_opts o;
+        memset(&o, 0, sizeof o);
+        o.kernel = 1;
+        const int rc = tsu_step_n(&probs[i].grid, TSU_F32, probs[i].tau, &probs[i].medium, st, left, &o, nullptr, 0,
+                                  stream);
+        if (rc != TSU_OK) return rc;
+      }
     }
+    return TSU_OK;
+  };
+  if (!(opts && opts->graph)) return enqueue();
+  // the same launches captured into one CUDA graph and launched once (the executable graph is
+  // released right away; CUDA frees it when the launch completes)
+  if (!s) return fail(TSU_EINVAL, "graph launch needs a non-default stream");
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run capture");
+  const int rc = enqueue();
+  cudaGraph_t gr = nullptr;
+  e = cudaStreamEndCapture(s, &gr);
+  if (rc != TSU_OK) {
+    if (gr) cudaGraphDestroy(gr);
+    return rc;
   }
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run capture");
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run graph instantiate");
+  e = cudaGraphLaunch(ge, s);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_batch_run graph launch");
   return TSU_OK;
 }
 

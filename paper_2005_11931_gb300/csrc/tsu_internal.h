@@ -134,24 +134,27 @@ void adjoint_pass_shape(const StencilGeom& g, int dtype, int64_t* gridx, int64_t
                         int64_t* cols_per_cta);
 cudaError_t launch_rec_bucket(const StencilGeom& g, int dtype, const int64_t* idx, int32_t nrec, int* off, int* ord,
                               int* cta_of, cudaStream_t s);
-// v_in != nullptr: the pass also steps the increment-form state back, (u, v_in) -> (u_out, v_out)
-cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, bool start, const void* hx, const void* hy,
-                                const void* lam, const void* lam_pp, void* lam_out, const void* u, void* gx, void* gy,
-                                void* g_u1, const RecBuckets& rb, cudaStream_t s, const void* v_in = nullptr,
-                                void* u_out = nullptr, void* v_out = nullptr);
+// One reverse step (mode kAdjStep / kAdjStepInc) or the start (kAdjStart / kAdjStartInc).  The
+// increment modes read mu = lam^{n+1} - lam^{n+2} from lam_pp and write mu^n into mu_out (which may
+// be lam_pp); see k_adjoint.cu.
+enum { kAdjStep = 0, kAdjStart = 1, kAdjStepInc = 2, kAdjStartInc = 3 };
+cudaError_t launch_adjoint_pass(const StencilGeom& g, int dtype, int mode, const void* hx, const void* hy,
+                                const void* lam, const void* lam_pp, void* lam_out, void* mu_out, const void* u,
+                                void* gx, void* gy, void* g_u1, const RecBuckets& rb, cudaStream_t s);
 cudaError_t launch_inject(const StencilGeom& g, int dtype, void* lam, const void* gvals, const int64_t* idx,
                           int32_t nrec, cudaStream_t s);
-// K = 2 or 4 adjoint steps per pass, FP32 (k_adjoint_wtb.cu): from lam^{n+1}, lam^{n+2} and
-// u[f] = u^{n-f} (f < K), the levels lam^n .. lam^{n-K+1}; stores lam^{n-K+2} into out_a and
-// lam^{n-K+1} into out_b and adds the K steps' face gradients into gx, gy.  Receivers through a
-// per-tile table (off[ntiles+1], int4 (row, col, receiver, 0) entries, <= 4 per receiver) built by
-// launch_rec_tiles for the same K and rows; gv[f] = g^{n-f} at the receivers.
+// K = 2 or 4 adjoint steps per pass, FP32, increment form (k_adjoint_wtb.cu): from lam^{n+1},
+// mu^{n+1} = lam^{n+1} - lam^{n+2} and u[f] = u^{n-f} (f < K), the steps n .. n-K+1; stores
+// lam^{n-K+1} into out_lam and mu^{n-K+1} into out_mu and adds the K steps' face gradients into
+// gx, gy.  Receivers through a per-tile table (off[ntiles+1], int4 (row, col, receiver, 0)
+// entries, <= 4 per receiver) built by launch_rec_tiles for the same K and rows; gv[f] = g^{n-f}
+// at the receivers.
 int adjoint_wtb_rows(int k, int64_t ny, int64_t ld);
 int64_t adjoint_wtb_tiles(int64_t ny, int64_t ld, int rows);
 cudaError_t launch_rec_tiles(const StencilGeom& g, int k, const int64_t* idx, int32_t nrec, int rows, int* off,
                              int4* ent, cudaStream_t s);
 cudaError_t launch_adjoint_wtb(const StencilGeom& g, int k, int rows, const void* hx, const void* hy,
-                               const void* lam1, const void* lam2, const void* const* u, void* out_a, void* out_b,
+                               const void* lam1, const void* mu1, const void* const* u, void* out_lam, void* out_mu,
                                void* gx, void* gy, const int* rec_off, const int4* rec, const void* const* gv,
                                cudaStream_t s);
 cudaError_t launch_flush(const StencilGeom& g, void* g32x, void* g32y, double* gx, double* gy, cudaStream_t s);

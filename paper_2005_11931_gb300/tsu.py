@@ -78,7 +78,7 @@ class Problem(C.Structure):
 
 
 class BatchOpts(C.Structure):
-    _fields_ = [("tdepth", C.c_int32), ("rows", C.c_int32), ("kernel", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("tdepth", C.c_int32), ("rows", C.c_int32), ("kernel", C.c_int32), ("graph", C.c_int32)]
 
 
 _lib = None
@@ -265,10 +265,12 @@ def tsu_batch_workspace(sims, nsteps, tdepth: int = 0, rows: int = 0, kernel: in
     return int(n.value)
 
 
-def tsu_batch_run(sims, nsteps, ws, ws_bytes: int, tdepth: int = 0, rows: int = 0, kernel: int = 0, stream=None):
-    """Advance every Simulation in ``sims`` by its entry of ``nsteps`` in batched launches."""
+def tsu_batch_run(sims, nsteps, ws, ws_bytes: int, tdepth: int = 0, rows: int = 0, kernel: int = 0,
+                  graph: bool = False, stream=None):
+    """Advance every Simulation in ``sims`` by its entry of ``nsteps`` in batched launches (captured
+    into one CUDA graph when ``graph``; that needs a non-default stream)."""
     arr = _problems(sims, nsteps)
-    o = BatchOpts(int(tdepth), int(rows), int(kernel))
+    o = BatchOpts(int(tdepth), int(rows), int(kernel), int(bool(graph)))
     rc = load().tsu_batch_run(len(sims), arr, C.byref(o), _ptr(ws), int(ws_bytes), _stream(stream))
     _check(rc, "tsu_batch_run")
 
@@ -375,6 +377,17 @@ class Simulation:
     def observe(self, energy: torch.Tensor | None = None, rec_idx=None, trace=None, stream=None):
         tsu_observe(self.g, self.dtype, self.tau, self.medium, self.state, energy, rec_idx, trace, self.ws,
                     self.ws.numel(), stream)
+
+    def clone(self) -> "Simulation":
+        """A copy with its own state buffers and workspace (same medium, tau and roles)."""
+        bufs = [b.clone() for b in self.bufs]
+        st = State()
+        for k, b in enumerate(bufs):
+            st.buf[k] = b.data_ptr()
+        st.nbuf, st.form, st.cur, st.aux, st.step = (self.state.nbuf, self.state.form, self.state.cur,
+                                                     self.state.aux, self.state.step)
+        return Simulation(self.g, self.dtype, self.form, self.hx, self.hy, self.ext, self.tau, self.medium, bufs, st,
+                          torch.zeros_like(self.ws))
 
     @property
     def u_prev(self) -> torch.Tensor | None:

@@ -67,3 +67,76 @@ def test_batched_problem_matches_oracle():
     for p, sim in zip(probs, bat):
         orc = run_oracle(p.n, p.depth, p.initial(), p.steps, energy=False)
         assert relerr(sim.u[:, : p.n].double().cpu().numpy(), orc["u"]) <= 1e-5, p.name
+
+
+def test_graph_launch_equals_stream_launch():
+    """The whole call captured into one CUDA graph (uneven step counts, so blocked rounds of
+    shrinking tile prefixes and single leftover steps are all in the graph)."""
+    probs = family(steps=40)
+    rng = np.random.default_rng(8)
+    steps = [int(s) for s in rng.integers(0, 60, size=len(probs))]
+    a = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    b = [s.clone() for s in a]
+    wsb = tsu.tsu_batch_workspace(a, steps)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    tsu.tsu_batch_run(a, steps, ws, wsb)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    ws2 = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(side):
+        tsu.tsu_batch_run(b, steps, ws2, wsb, graph=True, stream=side)
+    side.synchronize()
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert (x.state.cur, x.state.aux, x.state.step) == (y.state.cur, y.state.aux, y.state.step)
+        assert torch.equal(x.u, y.u)
+        assert torch.equal(x.bufs[x.state.aux], y.bufs[y.state.aux])
+
+
+def test_graph_launch_needs_a_stream():
+    probs = family(steps=9)
+    sims = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    steps = [8] * len(sims)
+    wsb = tsu.tsu_batch_workspace(sims, steps)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tsu.TsuError) as e:
+        tsu.tsu_batch_run(sims, steps, ws, wsb, graph=True, stream=0)
+    assert e.value.code == tsu.TSU_EINVAL
+
+
+def test_autotuned_choices_keep_the_results(tmp_path):
+    from paper_2005_11931_gb300 import autotune
+
+    cache = autotune.Cache(str(tmp_path / "tune.json"))
+    probs = family(steps=50)
+    sims = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    ref = [s.clone() for s in sims]
+    c = autotune.tune_batch(sims, rounds=2, cache=cache)
+    assert isinstance(c, autotune.Choice)
+    # tuning ran on scratch copies: the states did not move
+    for x, y in zip(sims, ref):
+        assert x.state.step == y.state.step and torch.equal(x.u, y.u)
+    assert autotune.tune_batch(sims, cache=cache) == c  # cached
+    steps = [p.steps - 1 for p in probs]
+    wsb = tsu.tsu_batch_workspace(sims, steps, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        tsu.tsu_batch_run(sims, steps, ws, wsb, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel, graph=c.graph,
+                          stream=side)
+    side.synchronize()
+    for s, n in zip(ref, steps):
+        s.step(n, kernel=1)
+    torch.cuda.synchronize()
+    for x, y in zip(sims, ref):
+        assert torch.equal(x.u, y.u)
+    # one problem: the tuned stepping choice
+    big = tsu.Simulation.create(1025, probs[0].depth, dtype="f32")
+    big.init(torch.from_numpy(inputs.gaussian_hump(1025, 1025, big.g.ld, 0.4, 0.5, 0.03, 1.0, np.float32)).cuda())
+    other = big.clone()
+    cs = autotune.tune_step(big, steps=16, cache=cache)
+    big.step(37, kernel=cs.kernel, tdepth=cs.tdepth, rows=cs.rows)
+    other.step(37, kernel=1)
+    torch.cuda.synchronize()
+    assert torch.equal(big.u, other.u)
