@@ -655,13 +655,23 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
   const int kern = batch_kernel(opts);
   if (kern != 2 && kern != 3) return fail(TSU_EINVAL, "batch kernel must be 2 or 3");
   const int k = (opts && opts->tdepth) ? opts->tdepth : (kern == 2 ? 4 : 8);
-  // rows per chunk: 128 (64-problem family, FP32 GLUPS at 64/96/128 rows: 801/805/810; an
-  // earlier build of the pass at 32/64/96/128/192/256 rows: 755/815/818/802/763/725)
-  const int rows = (opts && opts->rows) ? opts->rows : 128;
   if (kern == 3 && !tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 3: tdepth must be 4 or 8");
   if (kern == 2 && !tsu::wtb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 2: tdepth must be 2 or 4");
-  if (rows < 16) return fail(TSU_EINVAL, "rows must be >= 16");
   const int W = kern == 2 ? tsu::wtb_strip_width() : tsu::tb_strip_width(k);
+  auto tiles_at = [&](int r) {
+    int64_t t = 0;
+    for (int i = 0; i < nprob; ++i) t += ((probs[i].grid.ld + W - 1) / W) * ((probs[i].grid.ny - 2 + r - 1) / r);
+    return t;
+  };
+  // rows per chunk: 128 (64-problem family, FP32 GLUPS at 64/96/128 rows: 801/805/810; an
+  // earlier build of the pass at 32/64/96/128/192/256 rows: 755/815/818/802/763/725), fewer
+  // (down to 16) while the family's tiles would not fill one wave of the GPU (small problems)
+  int rows = (opts && opts->rows) ? opts->rows : 128;
+  if (!(opts && opts->rows) && kern == 2) {
+    for (int i = 0; i < nprob; ++i) TRY(check_grid(&probs[i].grid));
+    while (rows > 16 && tiles_at(rows) < (int64_t)152 * 3 * 4) rows = rows > 32 ? rows / 2 : 16;
+  }
+  if (rows < 16) return fail(TSU_EINVAL, "rows must be >= 16");
   const size_t ab = kern == 2 ? tsu::wtb_args_bytes() : tsu::tb_args_bytes();
   int64_t ntiles = 0;
   for (int i = 0; i < nprob; ++i) {
