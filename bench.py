@@ -377,7 +377,11 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind, "bytes_per_launch_per_node": bpn,
                      "steps_per_launch": K if blocked else 1, "kernel": kname, "launch_ms": launch_ms,
-                     "launches_per_step": main_launches},
+                     "launches_per_step": main_launches,
+                     # DRAM bytes the ncu capture counted per launch over the live launch time, and the
+                     # algorithmic rate against the 8 TB/s nominal figure (context)
+                     "dram_frac": (traffic / (launch_ms / 1e3) / 1e9 / peak) if traffic else None,
+                     "frac_of_nominal_8tbs": achieved / 8000.0},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),

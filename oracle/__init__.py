@@ -83,6 +83,8 @@ def _load():
         lib.orc_friedrichs_c2.restype = C.c_double
         lib.orc_make_depth.argtypes = [g, C.POINTER(_Depth), d, d, d]
         lib.orc_make_depth.restype = C.c_int
+        lib.orc_forward_f32.argtypes = [g, C.c_double, d, d, d, d, C.c_int64, C.c_int, d]
+        lib.orc_forward_f32.restype = C.c_int
         lib.orc_depth_deps.argtypes = [g, C.POINTER(_Depth), d, d]
         lib.orc_depth_deps.restype = C.c_int
         lib.orc_apply_B.argtypes = [g, C.c_double, C.c_double, d, d, d, d]
@@ -147,6 +149,18 @@ def make_depth(g: _Grid, depth: dict):
     if rc != 0:
         raise ValueError("oracle make_depth: bad arguments")
     return hx, hy, ext
+
+
+def forward_f32(g, tau, hx, hy, u0, u1, steps: int, increment: bool):
+    """The start and ``steps-1`` leapfrog steps in FP32 arithmetic (no fused multiply-add), in the
+    standard or the increment form; returns u^S widened to FP64.  Shows the FP32 rounding of each
+    form without any GPU code."""
+    out = np.zeros((g.ny, g.ld))
+    rc = _load().orc_forward_f32(C.byref(g), tau, _p(_field(g, hx)), _p(_field(g, hy)), _p(_field(g, u0)),
+                                 _p(_field(g, u1)), int(steps), int(bool(increment)), _p(out))
+    if rc != 0:
+        raise ValueError("oracle forward_f32: bad arguments")
+    return out
 
 
 def depth_deps(g: _Grid, depth: dict):

@@ -15,6 +15,7 @@
  *            phi_eps a unit-mass mollifier of width eps        -- Sec. 2.1 (h * psi_eps), Sec. 3.1
  *   energy   d/dt (||u_t||^2 + sum_j ||h_j^1/2 d_j u||^2) = 0   -- Theorem 2.1, identity (CL-01)
  *   d h_eps / d eps, the depth's derivative in the regularisation width  -- Sec. 2.1
+ *   and an FP32 emulation of the stepping in both forms (rounding study only)
  *
  * The scheme is the explicit leapfrog written out exactly as defined:
  *   fx(u)_ij = hx_ij (u_i+1,j - u_ij) - hx_i-1,j (u_ij - u_i-1,j)
@@ -186,6 +187,95 @@ int orc_make_depth(const orc_grid* g, const orc_depth* d, double* hx, double* hy
   ext[1] = mxx;
   ext[2] = mny;
   ext[3] = mxy;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP32 emulation: the same start and leapfrog in float arithmetic, in the   */
+/* order written (no fused multiply-add), in the standard form               */
+/*   u^{n+1} = (2 u^n - u^{n-1}) + B u^n                                     */
+/* or the increment form                                                     */
+/*   v^1 = tau u1 + B u^0 / 2,  u^1 = u^0 + v^1,  v^{n+1} = v^n + B u^n,     */
+/*   u^{n+1} = u^n + v^{n+1}                                                 */
+/* (algebraically the same scheme).  It shows how FP32 rounding grows in     */
+/* each form, independently of any GPU code.  Inputs are FP64 and rounded to */
+/* float once; the final u^S is returned widened to double.                  */
+/* ------------------------------------------------------------------------- */
+static inline float fxf(const orc_grid* g, const float* hx, const float* u, int i, int j) {
+  return hx[IDX(g, i, j)] * (u[IDX(g, i + 1, j)] - u[IDX(g, i, j)]) -
+         hx[IDX(g, i - 1, j)] * (u[IDX(g, i, j)] - u[IDX(g, i - 1, j)]);
+}
+static inline float fyf(const orc_grid* g, const float* hy, const float* u, int i, int j) {
+  return hy[IDX(g, i, j)] * (u[IDX(g, i, j + 1)] - u[IDX(g, i, j)]) -
+         hy[IDX(g, i, j - 1)] * (u[IDX(g, i, j)] - u[IDX(g, i, j - 1)]);
+}
+
+int orc_forward_f32(const orc_grid* g, double tau, const double* hx, const double* hy, const double* u0,
+                    const double* u1, int64_t S, int increment, double* u_out) {
+  if (S < 1) return 1;
+  const int64_t n = (int64_t)g->ny * g->ld;
+  float* fhx = (float*)calloc(n, sizeof(float));
+  float* fhy = (float*)calloc(n, sizeof(float));
+  float* a = (float*)calloc(n, sizeof(float)); /* u^{n-1} (standard) or v^n (increment) */
+  float* b = (float*)calloc(n, sizeof(float)); /* u^n */
+  if (!fhx || !fhy || !a || !b) {
+    free(fhx); free(fhy); free(a); free(b);
+    return 2;
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    fhx[k] = (float)hx[k];
+    fhy[k] = (float)hy[k];
+  }
+  const float cx = (float)(tau * tau / (g->dx * g->dx)), cy = (float)(tau * tau / (g->dy * g->dy));
+  const float ftau = (float)tau;
+  /* u^0 with zero boundary into a (standard: u^{n-1} slot) or b (increment: u slot) */
+  float* u = increment ? b : a;
+  for (int j = 1; j < g->ny - 1; ++j)
+    for (int i = 1; i < g->nx - 1; ++i) u[IDX(g, i, j)] = (float)u0[IDX(g, i, j)];
+  /* start */
+  if (increment) {
+    for (int j = 1; j < g->ny - 1; ++j)
+      for (int i = 1; i < g->nx - 1; ++i) {
+        const float bu = cx * fxf(g, fhx, b, i, j) + cy * fyf(g, fhy, b, i, j);
+        const float v1 = u1 ? (float)u1[IDX(g, i, j)] : 0.0f;
+        a[IDX(g, i, j)] = ftau * v1 + 0.5f * bu;
+      }
+    for (int j = 1; j < g->ny - 1; ++j)
+      for (int i = 1; i < g->nx - 1; ++i) b[IDX(g, i, j)] = b[IDX(g, i, j)] + a[IDX(g, i, j)];
+  } else {
+    for (int j = 1; j < g->ny - 1; ++j)
+      for (int i = 1; i < g->nx - 1; ++i) {
+        const float bu = cx * fxf(g, fhx, a, i, j) + cy * fyf(g, fhy, a, i, j);
+        const float v1 = u1 ? (float)u1[IDX(g, i, j)] : 0.0f;
+        b[IDX(g, i, j)] = (a[IDX(g, i, j)] + ftau * v1) + 0.5f * bu;
+      }
+  }
+  /* steps 2..S */
+  float* bu = (float*)calloc(n, sizeof(float));
+  if (!bu) {
+    free(fhx); free(fhy); free(a); free(b);
+    return 2;
+  }
+  for (int64_t step = 2; step <= S; ++step) {
+#pragma omp parallel for schedule(static)
+    for (int j = 1; j < g->ny - 1; ++j)
+      for (int i = 1; i < g->nx - 1; ++i) bu[IDX(g, i, j)] = cx * fxf(g, fhx, b, i, j) + cy * fyf(g, fhy, b, i, j);
+#pragma omp parallel for schedule(static)
+    for (int j = 1; j < g->ny - 1; ++j)
+      for (int i = 1; i < g->nx - 1; ++i) {
+        const int64_t k = IDX(g, i, j);
+        if (increment) {
+          a[k] = a[k] + bu[k];
+          b[k] = b[k] + a[k];
+        } else {
+          const float next = (2.0f * b[k] - a[k]) + bu[k];
+          a[k] = b[k];
+          b[k] = next;
+        }
+      }
+  }
+  for (int64_t k = 0; k < n; ++k) u_out[k] = (double)b[k];
+  free(fhx); free(fhy); free(a); free(b); free(bu);
   return 0;
 }
 

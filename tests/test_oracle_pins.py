@@ -454,3 +454,41 @@ def test_depth_eps_derivative_keeps_the_mass(moll):
     _, dhy = oracle.depth_deps(g, point)
     tot = dhy[: n - 1, :n]
     assert abs(tot.sum()) <= 1e-8 * np.abs(tot).sum()
+
+
+@pytest.mark.parametrize("increment", [False, True])
+def test_fp32_emulation_is_exact_at_courant_one(increment):
+    """The oracle's FP32 mode is pinned like its FP64 one: at Courant 1 in x (hy = 0, tau = dx,
+    even integer data) every operation is exact in FP32 as well, so both forms reproduce
+    d'Alembert's solution bit for bit."""
+    nx, ny, S = 129, 6, 77
+    g = oracle.grid(nx, ny)
+    hx = np.zeros((ny, nx))
+    hx[:, : nx - 1] = 1.0
+    hy = np.zeros((ny, nx))
+    rng = np.random.default_rng(4)
+    u0 = np.zeros((ny, nx))
+    u0[1:-1, 1:-1] = 2.0 * rng.integers(-50, 50, size=(ny - 2, nx - 2))
+    out = oracle.forward_f32(g, g.dx, hx, hy, u0, None, S, increment)
+    for j in range(1, ny - 1):
+        F = odd_periodic(u0[j])
+        idx = np.arange(nx)
+        assert np.array_equal(out[j], 0.5 * (F[(idx - S) % len(F)] + F[(idx + S) % len(F)]))
+
+
+def test_fp32_rounding_of_the_two_forms():
+    """Why FP32 runs use the increment form: with small steps the per-step change falls far
+    below one ulp of u, and the standard form (which recomputes the velocity from two rounded
+    levels) drifts, while the increment form stays at the FP32 bar.  Point singularity on 257^2,
+    CFL 0.02, 2000 steps, against the FP64 oracle."""
+    n, S = 257, 2000
+    g = oracle.grid(n, n)
+    depth = dict(background=0.5, eps=4 / (n - 1), mollifier=0, sings=[(2, 1, 0.01, 0.5, 0.5)])
+    hx, hy, ext = oracle.make_depth(g, depth)
+    u0 = inputs.gaussian_hump(n, n, None, 0.3, 0.5, 0.05)
+    tau = 0.02 * g.dx / math.sqrt(max(ext[1], ext[3]))
+    ref = oracle.forward(g, tau, hx, hy, u0, None, S, want_energy=False)["u"]
+    e_std = relerr(oracle.forward_f32(g, tau, hx, hy, u0, None, S, False), ref)
+    e_inc = relerr(oracle.forward_f32(g, tau, hx, hy, u0, None, S, True), ref)
+    assert e_inc <= 1e-5, e_inc
+    assert e_std >= 100 * e_inc, (e_std, e_inc)
