@@ -110,8 +110,8 @@ struct ArithF64 {  // explicitly rounded, definition order, no contraction
 };
 
 // Four consecutive columns as two packed pairs (c0, c1), (c2, c3) for the paired FP32
-// instructions of the sm_100 family (add/sub/mul/fma .f32x2): two columns per instruction, each
-// element rounded exactly as the scalar ArithF32 helper rounds it.
+// instructions of the sm_100 family (mul/fma .f32x2): two columns per instruction, each element
+// rounded exactly as the scalar ArithF32 helper rounds it.
 typedef unsigned long long f2x;
 struct P4 {
   f2x p[2];
@@ -126,15 +126,16 @@ __device__ __forceinline__ float2 upk(f2x a) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
   return r;
 }
+// Additions and subtractions run as two scalar instructions: on the warp-blocked pass that
+// measured faster than the paired forms (8192^2: 793 against 767 GLUPS; paired multiplies and
+// fused multiply-adds do pay: 770 with scalar multiplies, 692 with everything scalar).
 __device__ __forceinline__ f2x add2(f2x a, f2x b) {
-  f2x d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
+  const float2 x = upk(a), y = upk(b);
+  return pk(__fadd_rn(x.x, y.x), __fadd_rn(x.y, y.y));
 }
 __device__ __forceinline__ f2x sub2(f2x a, f2x b) {
-  f2x d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
+  const float2 x = upk(a), y = upk(b);
+  return pk(__fsub_rn(x.x, y.x), __fsub_rn(x.y, y.y));
 }
 __device__ __forceinline__ f2x mul2(f2x a, f2x b) {
   f2x d;
