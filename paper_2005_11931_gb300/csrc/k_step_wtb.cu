@@ -30,8 +30,9 @@ using namespace dev;
 constexpr int kWtbWarps = 4;       // warps (independent tiles) per CTA
 constexpr int kWtbOut = 120;       // output columns per strip
 constexpr int kWtbPre = 2;         // rows in flight ahead of the one being consumed
-// Resident CTAs per SM: the register file holds three CTAs of these kernels (no launch bound is
-// set, so nothing spills; bounding them to four CTAs forced spills and measured 4-13 % slower).
+// Tiles are sized for one wave of three CTAs per SM (the kernels are bounded to 128 registers so
+// that four fit: 8192^2 801 against 792 GLUPS unbounded at 130 registers, 16384^2 952 against
+// 922; sizing the tiles for four CTAs instead lost 4-8 % on 2048^2 and 4096^2).
 constexpr int kWtbCtasPerSm = 3;
 
 template <int K>
@@ -318,14 +319,14 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 }
 
 template <int K, int FORM, bool ENERGY>
-__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb(const WtbArgs a) {
+__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
   wtb_body<K, FORM, ENERGY, false>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
 }
 
 template <int K, int FORM>
-__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_seg(const WtbArgs a) {
+__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_seg(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
   wtb_body<K, FORM, false, true>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_seg(const WtbAr
 // Batched family: warp w of CTA b works on tile tiles[4 b + w] = (problem, strip, chunk) of
 // descriptor probs[problem]; one launch advances every problem by K steps.
 template <int K, int FORM>
-__global__ void __launch_bounds__(kWtbWarps * 32) k_leapfrog_wtb_batched(const WtbArgs* __restrict__ probs,
+__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_batched(const WtbArgs* __restrict__ probs,
                                                                         const int4* __restrict__ tiles,
                                                                         const int64_t ntiles) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
