@@ -357,8 +357,9 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
 }
 
 // ---------------------------------------------------------------------------------------------
-// Adjoint: workspace = 2 multiplier fields + (E+1) recomputed states + 1 restore field
-// (u^{m-1} or v^m) [+ 2 FP32 gradient accumulators for FP32 fields] + receiver buckets
+// Adjoint: workspace = 4 multiplier fields + 2 segment buffers of (E+1) recomputed states, the
+// restore field (u^{m-1} or v^m) and a second v [+ 2 FP32 gradient accumulators for FP32 fields]
+// + receiver tables
 // ---------------------------------------------------------------------------------------------
 static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
   int64_t gx, gy, cpc;
@@ -367,9 +368,6 @@ static int64_t adjoint_ctas(const tsu_grid* g, int dtype) {
   return gx * gy;
 }
 
-// The time-reversed sweep (increment form: each adjoint pass also inverts one forward step, no
-// segment storage) is exact up to rounding but measured slower on GB300 at 2048^2 (230 ms against
-// 184 ms for the overlapped recompute, 4000 steps): it stays available behind this switch.
 // steps per pass of the FP32 segment recompute (warp-blocked, intermediate states stored)
 constexpr int kRecomputeDepth = 4;
 // steps per pass of the FP32 reverse sweep (2 or 4); leftover steps of a segment run one per pass
