@@ -153,3 +153,42 @@ def test_adjoint_2048_full_size_directional_derivatives():
         fd = (J(hx64 + st * dx_, hy64 + st * dy_) - J(hx64 - st * dx_, hy64 - st * dy_)) / (2 * st)
         ad = float((out["gx"] * dx_).sum() + (out["gy"] * dy_).sum())
         assert abs(fd - ad) <= 1e-4 * abs(fd), (trial, fd, ad)
+
+
+def test_grid_beyond_2_31_elements():
+    """47000^2 nodes (ld 47008: 2.21e9 elements per field, past 2^31; six FP32 fields = 53 GB):
+    64-bit indexing in the depth, start, blocked and single-step passes.  The input is a hump of
+    compact support (zero outside a 401^2 block) so that the oracle's window stays small."""
+    n, S, half = 47000, 11, 60
+    p = inputs.Problem("big", n, dict(background=1.0, eps=8.0 / (n - 1), mollifier=0,
+                                      sings=[(0, 1, 1.0, 0.9, 0.5), (1, 1, 1.0, 0.5, 0.9)]),
+                       (0.9, 0.9, 0.0, 1.0), S)
+    sim = tsu.Simulation.create(n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+    assert sim.g.ny * sim.g.ld > 2**31
+    # hump of width 40 dx at the node nearest (0.9, 0.9), i.e. near the far corner of the arrays
+    ic = jc = round(0.9 * (n - 1))
+    blk = 200
+    w = 40.0 / (n - 1)
+    small = inputs.gaussian_hump(2 * blk + 1, 2 * blk + 1, None, 0.5, 0.5, w * (n - 1) / (2 * blk), 1.0)
+    u0 = torch.zeros((sim.g.ny, sim.g.ld), dtype=torch.float32, device="cuda")
+    u0[jc - blk:jc + blk + 1, ic - blk:ic + blk + 1] = torch.from_numpy(small).float()
+    sim.init(u0)
+    sim.step(S - 1, kernel=2, tdepth=4)  # two blocked passes and two single steps
+    torch.cuda.synchronize()
+    # oracle on a window around the hump with the same input block
+    m = half + S + 2
+    i0, j0, nw = ic - m, jc - m, 2 * m
+    og = oracle.grid(nw, nw)
+    og.dx = og.dy = 1.0 / (n - 1)
+    depth = dict(p.depth)
+    depth["sings"] = [(k, pw, a, cx - i0 * og.dx, cy - j0 * og.dx) for (k, pw, a, cx, cy) in p.depth["sings"]]
+    hx, hy, _ = oracle.make_depth(og, depth)
+    u0w = u0[j0:j0 + nw, i0:i0 + nw].double().cpu().numpy()
+    r = oracle.forward(og, sim.tau, hx, hy, u0w, None, S, want_energy=False)
+    ref = r["u"][m - half:m + half, m - half:m + half]
+    got = sim.u[jc - half:jc + half, ic - half:ic + half].double().cpu().numpy()
+    assert relerr(got, ref) <= 1e-5
+    # the far end of the arrays is written (zeros), the last interior row holds finite values
+    assert torch.isfinite(sim.u[-2, :n]).all()
+    del sim, u0
+    torch.cuda.empty_cache()
