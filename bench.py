@@ -422,7 +422,7 @@ def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
     case = inputs.adjoint_case(n, steps)
     p, every = case["problem"], case["ckpt_every"]
     S = p.steps
-    sim = tsu.Simulation.create(p.n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT, nbuf=3)
+    sim = tsu.Simulation.create(p.n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
     g = sim.g
     u0 = torch.from_numpy(p.initial(g.ld, np.float32)).cuda()
     rec = torch.from_numpy(inputs.flat_index(case["receivers"], g.ld)).cuda()
@@ -438,7 +438,7 @@ def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
         sim.observe(rec_idx=rec, trace=tr[S - 1])
 
     # observations: the same run with eps = 0.012 (a different medium)
-    osim = tsu.Simulation.create(p.n, case["depth_obs"], dtype="f32", form=tsu.TSU_FORM_INCREMENT, nbuf=3,
+    osim = tsu.Simulation.create(p.n, case["depth_obs"], dtype="f32", form=tsu.TSU_FORM_INCREMENT,
                                  tau=sim.tau)
     osim.init(u0)
     osim.step(S - 1, rec_idx=rec, traces=obs[: S - 1])
@@ -461,8 +461,9 @@ def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
     t_a = _events_ms(adjoint, reps)
     lups = (n - 2) ** 2 * S
     J = 0.5 * float(((traces - obs).double() ** 2).sum())
-    # algorithmic bytes: the forward reads u, v, hx, hy and writes u, v every step (6 fields); the
-    # adjoint moves 23 fields per 4 reverse steps (the 4-step sweep 14: lam^{n+1}, lam^{n+2},
+    # algorithmic bytes: the forward (warp-blocked, receivers and checkpoints recorded in it) reads
+    # u, v, hx, hy and writes u, v once per 4 steps (1.5 fields per step); the adjoint moves 23
+    # fields per 4 reverse steps (the 4-step sweep 14: lam^{n+1}, lam^{n+2},
     # u^n..u^{n-3}, hx, hy and the two accumulators read, two multipliers and the accumulators
     # written; the 4-step recompute 9: u, v, hx, hy read, 4 states and v written)
     fb = g.ny * g.ld * 4
@@ -471,7 +472,7 @@ def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
                         f"{S} steps, {nrec} receivers on y = 0.8, checkpoints every {every}",
             "forward_ms": t_f, "adjoint_ms": t_a, "ratio": t_a / t_f, "forward_glups": lups / t_f / 1e6,
             "adjoint_glups": lups / t_a / 1e6, "J": J, "grad_norm_hx": float(gx.norm()),
-            "forward_gbs_algorithmic": 6 * fb * S / (t_f / 1e3) / 1e9,
+            "forward_gbs_algorithmic": 1.5 * fb * S / (t_f / 1e3) / 1e9,
             "adjoint_gbs_algorithmic": 23 / 4 * fb * S / (t_a / 1e3) / 1e9,
             "adjoint_frac_of_measured_peak": 23 / 4 * fb * S / (t_a / 1e3) / 1e9 / peak}
 

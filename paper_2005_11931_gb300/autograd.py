@@ -35,11 +35,13 @@ class TsunamiFn(torch.autograd.Function):
         code = tsu.dtype_code(u0.dtype)
         dev = u0.device
         med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), float(cfg.hx_max), float(cfg.hy_max))
-        bufs = [torch.zeros_like(u0) for _ in range(3)]
+        # four state buffers: FP32 runs then take the warp-blocked pass (receivers and checkpoints
+        # recorded by it), FP64 runs one step per pass
+        bufs = [torch.zeros_like(u0) for _ in range(4)]
         st = tsu.State()
         for k, b in enumerate(bufs):
             st.buf[k] = b.data_ptr()
-        st.nbuf, st.form = 3, cfg.form
+        st.nbuf, st.form = 4, cfg.form
         nrec = int(cfg.rec_idx.numel())
         traces = torch.zeros((S, nrec), dtype=u0.dtype, device=dev)
         slots = max(tsu.tsu_ckpt_slots(S, cfg.ckpt_every), 1)

@@ -74,6 +74,9 @@ struct alignas(16) WtbArgs {
   double escale;
   float* seg;       // segment variant: u^{n+t} at seg + (t - 1) seg_stride, t = 1 .. K - 1
   int64_t seg_stride;
+  const int64_t* rec_idx;  // receivers (flat node indices) or nullptr
+  float* traces;           // traces[t * nrec + r] = u^{n+t}[rec_idx[r]], t = 0 .. K - 1
+  int32_t nrec;
 };
 
 
@@ -121,7 +124,7 @@ __device__ void wtb_energy(float (&es)[K], float (&ec)[K], const WtbArgs& a) {
   if (threadIdx.x == 0) *a.ews.counter = 0u;
 }
 
-template <int K, int FORM, bool ENERGY, bool ALL>
+template <int K, int FORM, bool ENERGY, bool ALL, bool REC = false>
 __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, const int64_t strip,
                                          const int64_t chunk) {
   using Sh = WtbShape<K>;
@@ -168,6 +171,61 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 #pragma unroll
   for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = kZeroP4;
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
+  // receivers whose node this tile owns (output columns and rows), one per lane; more than 32
+  // in one tile are read back from memory at every record
+  int rec_row = -1, rec_col = 0, rec_r = 0, rec_count = 0;
+  if constexpr (REC) {
+    const int64_t lo = xs + 4, hi = xs + 123;  // this strip's output columns
+    for (int base = 0; base < a.nrec; base += 32) {
+      const int q = base + lane;
+      int64_t j = -1, i = 0;
+      if (tile_ok && q < a.nrec) {
+        const int64_t idx = a.rec_idx[q];
+        if (idx >= 0 && idx < (int64_t)a.ny * a.ld) {
+          j = idx / a.ld;
+          i = idx - j * a.ld;
+        }
+      }
+      const bool mine = j >= y0 && j < y1 && i >= lo && i <= hi && i >= 1 && i <= a.nx - 2;
+      unsigned m = __ballot_sync(0xffffffffu, mine);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int rj = __shfl_sync(0xffffffffu, (int)j, src), ri = __shfl_sync(0xffffffffu, (int)i, src);
+        if (lane == rec_count) {
+          rec_row = rj;
+          rec_col = ri;
+          rec_r = base + src;
+        }
+        ++rec_count;
+      }
+    }
+  }
+  // trace of level t (u^{n+t}) at row r: the owning lane stores its element
+  auto record = [&](int t, int r, const P4& v) {
+    if constexpr (REC) {
+      if (rec_count == 0) return;
+      const float2 v01 = upk(v.p[0]), v23 = upk(v.p[1]);
+      auto put = [&](int col, int rr) {
+        const int64_t e = col - c0;
+        if (e >= 0 && e < 4)  // selects, not an indexed register array
+          a.traces[(int64_t)t * a.nrec + rr] = e == 0 ? v01.x : e == 1 ? v01.y : e == 2 ? v23.x : v23.y;
+      };
+      if (rec_count <= 32) {
+        unsigned m = __ballot_sync(0xffffffffu, rec_row == r);
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          put(__shfl_sync(0xffffffffu, rec_col, src), __shfl_sync(0xffffffffu, rec_r, src));
+        }
+      } else {
+        for (int q = 0; q < a.nrec; ++q) {
+          const int64_t idx = a.rec_idx[q];
+          if (idx >= 0 && idx < (int64_t)a.ny * a.ld && idx / a.ld == r) put((int)(idx % a.ld), q);
+        }
+      }
+    }
+  };
   float es[K], ec[K];  // compensated per-level energy sums of this thread
 #pragma unroll
   for (int t = 0; t < K; ++t) es[t] = ec[t] = 0.f;
@@ -190,6 +248,9 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       w[t][1] = w[t][0];
     }
     w[0][0] = lds_p4(slotA(sa, 0));
+    if constexpr (REC) {
+      if (r_in >= y0 && r_in < y1) record(0, r_in, w[0][0]);
+    }
     if constexpr (FORM == 1) {
       vv[0][1] = vv[0][0];
       vv[0][0] = lds_p4(slotA(sa, 1));
@@ -279,6 +340,9 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       }
       w[t][0] = un;
       hyv = hyd;
+      if constexpr (REC) {
+        if (t < K && row_out) record(t, rt, un);
+      }
       if constexpr (ALL) {
         if (t < K && row_out && col_out) stg_p4(a.seg + (int64_t)(t - 1) * a.seg_stride + (int64_t)rt * a.ld + c0, un);
       }
@@ -318,11 +382,11 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   if constexpr (ENERGY) wtb_energy<K>(es, ec, a);
 }
 
-template <int K, int FORM, bool ENERGY>
+template <int K, int FORM, bool ENERGY, bool REC>
 __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
-  wtb_body<K, FORM, ENERGY, false>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
+  wtb_body<K, FORM, ENERGY, false, REC>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
 }
 
 template <int K, int FORM>
@@ -345,23 +409,27 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_batched(cons
   wtb_body<K, FORM, false, false>(a, ok, t.y, t.z);
 }
 
+template <int K, int FORM, bool ENERGY, bool REC>
+cudaError_t wtb_launch_kernel(const WtbArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  auto kern = k_leapfrog_wtb<K, FORM, ENERGY, REC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kWtbWarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int K, int FORM>
 cudaError_t wtb_launch(const WtbArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)WtbShape<K>::bytes * kWtbWarps * 32;
   const unsigned grid = (unsigned)((a.ntiles + kWtbWarps - 1) / kWtbWarps);
+  const bool rec = a.traces && a.nrec > 0;
   if (a.energy) {
     if ((int64_t)grid * K > a.ews.capacity) return cudaErrorInvalidValue;
-    auto kern = k_leapfrog_wtb<K, FORM, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, kWtbWarps * 32, smem, s>>>(a);
-  } else {
-    auto kern = k_leapfrog_wtb<K, FORM, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, kWtbWarps * 32, smem, s>>>(a);
+    return rec ? wtb_launch_kernel<K, FORM, true, true>(a, grid, smem, s)
+               : wtb_launch_kernel<K, FORM, true, false>(a, grid, smem, s);
   }
-  return cudaGetLastError();
+  return rec ? wtb_launch_kernel<K, FORM, false, true>(a, grid, smem, s)
+             : wtb_launch_kernel<K, FORM, false, false>(a, grid, smem, s);
 }
 
 template <int K, int FORM>
@@ -459,8 +527,8 @@ int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows) {
 
 cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
                             const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int rows,
-                            cudaStream_t s) {
-  WtbArgs a;
+                            cudaStream_t s, int32_t nrec, const int64_t* rec_idx, void* traces) {
+  WtbArgs a{};
   a.nx = g.nx;
   a.ny = g.ny;
   a.ld = g.ld;
@@ -481,6 +549,9 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
   a.escale = g.dxdy / (2.0 * g.tau * g.tau);
   a.seg = nullptr;
   a.seg_stride = 0;
+  a.nrec = traces ? nrec : 0;
+  a.rec_idx = rec_idx;
+  a.traces = (float*)traces;
   if (k == 2) return form == TSU_FORM_STANDARD ? wtb_launch<2, 0>(a, s) : wtb_launch<2, 1>(a, s);
   if (k == 4) return form == TSU_FORM_STANDARD ? wtb_launch<4, 0>(a, s) : wtb_launch<4, 1>(a, s);
   return cudaErrorInvalidValue;

@@ -277,17 +277,25 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
     cudaError_t e = cudaMemsetAsync(ews.counter, 0, sizeof(unsigned int), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n workspace reset");
   }
-  // kernel choice: the temporally blocked pass needs FP32 fields, four state buffers, a workspace
-  // (status word), and no per-step side outputs other than the energy
-  const bool tb_possible = dtype == TSU_F32 && st->nbuf == 4 && have_ws && !o.traces && !o.ckpt;
-  if ((o.kernel == 3 || o.kernel == 2) && !tb_possible)
-    return fail(TSU_EINVAL, "kernels 2 and 3 need FP32, nbuf = 4, a workspace and no traces/checkpoints");
+  // kernel choice: the temporally blocked passes need FP32 fields, four state buffers and a
+  // workspace (status word).  The warp-blocked pass records receivers itself and takes
+  // checkpoints between its launches, so checkpoint steps must fall on launch boundaries
+  // (ckpt_every a multiple of its depth, the call starting on a checkpoint's residue); the
+  // CTA-blocked pass takes neither.
+  const int wdepth = o.tdepth ? o.tdepth : 4;
+  const bool blocked_base = dtype == TSU_F32 && st->nbuf == 4 && have_ws;
+  const bool ckpt_aligned = !o.ckpt || (o.ckpt_every % wdepth == 0 && ((st->step - 1) % wdepth + wdepth) % wdepth == 0);
+  const bool wtb_possible = blocked_base && ckpt_aligned;
+  const bool tb_possible = blocked_base && !o.traces && !o.ckpt;
+  if (o.kernel == 2 && !wtb_possible)
+    return fail(TSU_EINVAL, "kernel 2 needs FP32, nbuf = 4, a workspace and checkpoints on its launch boundaries");
+  if (o.kernel == 3 && !tb_possible)
+    return fail(TSU_EINVAL, "kernel 3 needs FP32, nbuf = 4, a workspace and no traces/checkpoints");
   // kernel 2: warp-blocked pass, tdepth steps per launch (default 4); also the automatic choice
   // (kernel 0) whenever it is possible: it beat one step per pass at every size measured (1024^2
   // to 16384^2).  All passes give the same bits, so the choice never changes a result.
-  const int wdepth = o.tdepth ? o.tdepth : 4;
   int wrows = o.rows ? (o.rows < 16 ? 16 : o.rows) : tsu::wtb_auto_rows(g->ny, g->ld, wdepth);
-  const bool use_wtb = tb_possible && nsteps >= wdepth && tsu::wtb_supported_depth(wdepth) &&
+  const bool use_wtb = wtb_possible && nsteps >= wdepth && tsu::wtb_supported_depth(wdepth) &&
                        (o.kernel == 2 || o.kernel == 0);
   // kernel 3: CTA-blocked pass, on request only
   const int tdepth = o.tdepth ? o.tdepth : 8;
@@ -300,9 +308,20 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   int64_t k = 0;
   if (use_wtb) {
     for (; k + wdepth <= nsteps; k += wdepth) {
+      const int64_t n = st->step;  // state holds u^n: checkpoint (u^{n-1}, u^n) or (u^n, v^n)
+      if (o.ckpt && ((n - 1) % o.ckpt_every) == 0 && (n - 1) / o.ckpt_every < o.ckpt_slots) {
+        char* slot = (char*)o.ckpt + (size_t)((n - 1) / o.ckpt_every) * 2 * field_bytes;
+        const void* a0 = st->form == TSU_FORM_STANDARD ? st->buf[st->aux] : st->buf[st->cur];
+        const void* a1 = st->form == TSU_FORM_STANDARD ? st->buf[st->cur] : st->buf[st->aux];
+        cudaError_t e = cudaMemcpyAsync(slot, a0, field_bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(slot + field_bytes, a1, field_bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n checkpoint");
+      }
       const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
+      void* tr = o.traces ? (char*)o.traces + (size_t)k * o.nrec * elem_size(dtype) : nullptr;
       cudaError_t e = tsu::launch_step_wtb(sg, st->form, wdepth, m->hx, m->hy, st->buf[st->cur], st->buf[st->aux],
-                                           st->buf[f1], st->buf[f2], o.energy ? o.energy + k : nullptr, ews, wrows, s);
+                                           st->buf[f1], st->buf[f2], o.energy ? o.energy + k : nullptr, ews, wrows, s,
+                                           o.nrec, o.rec_idx, tr);
       if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n warp-blocked launch");
       st->cur = f1;
       st->aux = f2;

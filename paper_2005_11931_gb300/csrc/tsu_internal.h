@@ -96,9 +96,11 @@ bool wtb_supported_depth(int k);
 int64_t wtb_tiles(int64_t ny, int64_t ld, int rows);
 int wtb_auto_rows(int64_t ny, int64_t ld, int k);
 int64_t wtb_energy_slots(int64_t ny, int64_t ld, int k, int rows);
+// traces (optional): traces[t * nrec + r] = u^{n+t}[rec_idx[r]] for t = 0 .. k-1
 cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
                             const void* p, void* out_a, void* out_b, double* energy, const EnergyWs& ews, int rows,
-                            cudaStream_t s);
+                            cudaStream_t s, int32_t nrec = 0, const int64_t* rec_idx = nullptr,
+                            void* traces = nullptr);
 int wtb_seg_rows(int64_t ny, int64_t ld);
 // segment variant: u^{n+t} into seg + (t - 1) seg_stride for t = 1 .. k (elements), v^{n+k} into
 // v_out (increment form; unused in the standard form)

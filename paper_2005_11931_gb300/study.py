@@ -96,8 +96,8 @@ def reflected_pulse(eps: float, n: int = 769, T: float = 0.45, amp: float = 1.0,
     Returns the free wave's peak and arrival and the reflected wave's signed peak and arrival."""
     line = dict(background=1.0, eps=float(eps), mollifier=inputs.GAUSS, sings=[(inputs.LINE_X, 1, amp, 0.5, 0.5)])
     free = dict(background=1.0, eps=float(eps), mollifier=inputs.GAUSS, sings=[])
-    sim = tsu.Simulation.create(n, line, dtype="f32", nbuf=3)
-    ref = tsu.Simulation.create(n, free, dtype="f32", nbuf=3, tau=sim.tau)
+    sim = tsu.Simulation.create(n, line, dtype="f32")
+    ref = tsu.Simulation.create(n, free, dtype="f32", tau=sim.tau)
     steps = max(2, int(math.ceil(T / sim.tau)))
     u0 = torch.from_numpy(inputs.gaussian_hump(n, n, sim.g.ld, x_src, 0.5, width, 1.0, np.float32)).cuda()
     i, j = round(x_rec * (n - 1)), round(0.5 * (n - 1))
@@ -124,9 +124,9 @@ def misfit_eps_gradient(n: int, depth: dict, u0: np.ndarray, S: int, rec_ij: np.
     eps_obs, and dJ/deps = sum_faces (dJ/dhx dhx/deps + dJ/dhy dhy/deps): forward with traces and
     checkpoints, tsu_adjoint, then tsu_depth_eps_gradient.  Same tau for both runs."""
     form = tsu.TSU_FORM_STANDARD if dtype == "f64" else tsu.TSU_FORM_INCREMENT
-    sim = tsu.Simulation.create(n, depth, dtype=dtype, form=form, nbuf=3)
+    sim = tsu.Simulation.create(n, depth, dtype=dtype, form=form)
     g, tdt = sim.g, tsu.DTYPES[sim.dtype]
-    obs_sim = tsu.Simulation.create(n, dict(depth, eps=float(eps_obs)), dtype=dtype, form=form, nbuf=3, tau=sim.tau)
+    obs_sim = tsu.Simulation.create(n, dict(depth, eps=float(eps_obs)), dtype=dtype, form=form, tau=sim.tau)
     u0p = np.zeros((g.ny, g.ld))
     u0p[:, :n] = u0[:, :n]
     u0d = torch.from_numpy(u0p).to(tdt).cuda()

@@ -97,7 +97,7 @@ def test_point_8192_full_run_conserves_energy():
 
 def _forward_traces(p, depth, dtype, tau, rec_ij, hx=None, hy=None, ck=None, every=64):
     form = tsu.TSU_FORM_INCREMENT if dtype == "f32" else tsu.TSU_FORM_STANDARD
-    sim = tsu.Simulation.create(p.n, depth, dtype=dtype, form=form, tau=tau, nbuf=3)
+    sim = tsu.Simulation.create(p.n, depth, dtype=dtype, form=form, tau=tau)
     if hx is not None:
         sim.hx.copy_(hx)
         sim.hy.copy_(hy)

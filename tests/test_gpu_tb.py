@@ -132,3 +132,55 @@ def test_tb_bounded_wait_reports_timeout_and_context_survives():
     tsu.tsu_sync_status(sim2.ws, sim2.ws.numel())
     ref = run_gpu(n, depth, u0.cpu().numpy(), 17, dtype="f32", kernel=1)
     assert relerr(sim2.u[:, :n].double().cpu().numpy(), ref["u"]) <= 1e-5
+
+
+def _trace_run(kernel, n=1001, ny=777, S=61, every=8, rec=None, energy=True, form=tsu.TSU_FORM_INCREMENT):
+    depth = dict(background=1.0, eps=0.015, mollifier=0, sings=[(0, 1, 1.0, 0.5, 0.5), (2, 1, 0.01, 0.5, 0.5)])
+    sim = tsu.Simulation.create(n, depth, dtype="f32", form=form, ny=ny)
+    u0 = torch.from_numpy(inputs.gaussian_hump(n, ny, sim.g.ld, 0.45, 0.55, 0.03, 1.0, np.float32)).cuda()
+    sim.init(u0)
+    idx = torch.from_numpy(inputs.flat_index(rec, sim.g.ld)).cuda()
+    tr = torch.zeros((S - 1, len(rec)), dtype=torch.float32, device="cuda")
+    ck = torch.zeros((tsu.tsu_ckpt_slots(S, every), 2, sim.g.ny, sim.g.ld), dtype=torch.float32, device="cuda")
+    e = torch.zeros(S - 1, dtype=torch.float64, device="cuda") if energy else None
+    sim.step(S - 1, energy=e, rec_idx=idx, traces=tr, ckpt=ck, ckpt_every=every, kernel=kernel, tdepth=4)
+    torch.cuda.synchronize()
+    return sim, tr, ck, e
+
+
+@pytest.mark.parametrize("form", [tsu.TSU_FORM_INCREMENT, tsu.TSU_FORM_STANDARD])
+@pytest.mark.parametrize("energy", [True, False])
+def test_wtb_records_traces_and_checkpoints_like_one_step_passes(form, energy):
+    """Receivers on and next to strip edges (columns 119/120/121, 239/240), chunk edges, the
+    corners, duplicates and boundary nodes; checkpoints every 8 steps.  The warp-blocked pass
+    records them itself and copies checkpoints between launches: traces, checkpoints and states
+    equal the one-step passes' bit for bit."""
+    rng = np.random.default_rng(12)
+    rec = [[c, r] for c in (1, 2, 119, 120, 121, 239, 240, 998) for r in (1, 2, 96, 97, 160, 161, 500, 775)]
+    rec += [[120, 97], [0, 300], [500, 0], [999, 776]] + [[int(x), int(y)] for x, y in zip(
+        rng.integers(1, 999, 60), rng.integers(1, 775, 60))]
+    rec = np.array(rec)
+    a, tra, cka, ea = _trace_run(2, rec=rec, energy=energy, form=form)
+    b, trb, ckb, eb = _trace_run(1, rec=rec, energy=energy, form=form)
+    assert torch.equal(tra, trb)
+    assert torch.equal(cka, ckb)
+    assert torch.equal(a.u, b.u)
+    if energy:
+        assert np.max(np.abs(ea.cpu().numpy() - eb.cpu().numpy()) / np.abs(eb.cpu().numpy())) <= 1e-6
+
+
+def test_unaligned_checkpoints_fall_back_or_are_refused():
+    rec = np.array([[10, 10], [500, 300]])
+    depth = dict(background=1.0, eps=0.02, mollifier=0, sings=[(0, 1, 1.0, 0.5, 0.5)])
+    sim = tsu.Simulation.create(301, depth, dtype="f32")
+    sim.init(torch.from_numpy(inputs.gaussian_hump(301, 301, sim.g.ld, 0.4, 0.5, 0.05, 1.0, np.float32)).cuda())
+    ck = torch.zeros((8, 2, sim.g.ny, sim.g.ld), dtype=torch.float32, device="cuda")
+    with pytest.raises(tsu.TsuError) as e:  # every 6 is not a multiple of 4
+        sim.step(20, ckpt=ck, ckpt_every=6, kernel=2, tdepth=4)
+    assert e.value.code == tsu.TSU_EINVAL
+    ref = sim.clone()
+    sim.step(20, ckpt=ck, ckpt_every=6)  # automatic choice: one step per pass
+    ck2 = torch.zeros_like(ck)
+    ref.step(20, ckpt=ck2, ckpt_every=6, kernel=1)
+    torch.cuda.synchronize()
+    assert torch.equal(ck, ck2) and torch.equal(sim.u, ref.u)
