@@ -132,10 +132,10 @@ typedef struct {
   int64_t ckpt_every, ckpt_slots;
   int32_t kernel;   /* 0 auto, 1 register-streaming (one step per pass), 2 warp-blocked (tdepth =
                        2 or 4 steps per pass, default 4), 3 CTA-blocked (tdepth = 4 or 8, default 8);
-                       2 and 3 need FP32, nbuf = 4 and a workspace; 2 records receivers and takes
-                       checkpoints when ckpt_every is a multiple of tdepth and the call starts at
-                       step 1 + j tdepth; 3 takes neither; auto picks kernel 2 (tdepth 4) whenever
-                       it can.  All kernels round every operation the same way, so the FP32
+                       2 and 3 need FP32, nbuf = 4 and a workspace; 2 records up to 2048
+                       receivers and takes checkpoints when ckpt_every is a multiple of tdepth and
+                       the call starts at step 1 + j tdepth; 3 takes neither; auto picks kernel 2
+                       (tdepth 4) whenever it can.  All kernels round every operation the same way, so the FP32
                        states do not depend on the choice */
   int32_t rows;     /* rows per CTA (kernels 1, 3) or per warp tile (kernel 2); 0 = auto */
   int32_t tdepth;   /* steps per pass of kernels 2 and 3 (0 = default); leftover steps run one per pass */

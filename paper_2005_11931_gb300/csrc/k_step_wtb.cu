@@ -186,7 +186,12 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
           i = idx - j * a.ld;
         }
       }
-      const bool mine = j >= y0 && j < y1 && i >= lo && i <= hi && i >= 1 && i <= a.nx - 2;
+      const bool interior = j >= 1 && j <= a.ny - 2 && i >= 1 && i <= a.nx - 2;
+      const bool mine = interior && j >= y0 && j < y1 && i >= lo && i <= hi;
+      // receivers on the boundary or outside the grid record 0 (the field's value there); the
+      // first tile writes those
+      if (tile_ok && strip == 0 && chunk == 0 && q < a.nrec && !interior)
+        for (int t = 0; t < K; ++t) a.traces[(int64_t)t * a.nrec + q] = 0.f;
       unsigned m = __ballot_sync(0xffffffffu, mine);
       while (m) {
         const int src = __ffs(m) - 1;

@@ -244,6 +244,9 @@ int tsu_step_workspace(const tsu_grid* g, int dtype, size_t* bytes) {
   return TSU_OK;
 }
 
+// longest receiver list the warp-blocked pass records itself
+constexpr int32_t kWtbMaxReceivers = 2048;
+
 int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, tsu_state* st, int64_t nsteps,
                const tsu_step_opts* opts, void* ws, size_t ws_bytes, void* stream) {
   g_err[0] = 0;
@@ -285,7 +288,9 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   const int wdepth = o.tdepth ? o.tdepth : 4;
   const bool blocked_base = dtype == TSU_F32 && st->nbuf == 4 && have_ws;
   const bool ckpt_aligned = !o.ckpt || (o.ckpt_every % wdepth == 0 && ((st->step - 1) % wdepth + wdepth) % wdepth == 0);
-  const bool wtb_possible = blocked_base && ckpt_aligned;
+  // receivers: every warp of the blocked pass scans the whole list once per launch, so long lists
+  // go one step per pass (whose first CTA gathers them)
+  const bool wtb_possible = blocked_base && ckpt_aligned && (!o.traces || o.nrec <= kWtbMaxReceivers);
   const bool tb_possible = blocked_base && !o.traces && !o.ckpt;
   if (o.kernel == 2 && !wtb_possible)
     return fail(TSU_EINVAL, "kernel 2 needs FP32, nbuf = 4, a workspace and checkpoints on its launch boundaries");

@@ -134,13 +134,15 @@ def test_tb_bounded_wait_reports_timeout_and_context_survives():
     assert relerr(sim2.u[:, :n].double().cpu().numpy(), ref["u"]) <= 1e-5
 
 
-def _trace_run(kernel, n=1001, ny=777, S=61, every=8, rec=None, energy=True, form=tsu.TSU_FORM_INCREMENT):
+def _trace_run(kernel, n=1001, ny=777, S=61, every=8, rec=None, energy=True, form=tsu.TSU_FORM_INCREMENT,
+               extra_idx=()):
     depth = dict(background=1.0, eps=0.015, mollifier=0, sings=[(0, 1, 1.0, 0.5, 0.5), (2, 1, 0.01, 0.5, 0.5)])
     sim = tsu.Simulation.create(n, depth, dtype="f32", form=form, ny=ny)
     u0 = torch.from_numpy(inputs.gaussian_hump(n, ny, sim.g.ld, 0.45, 0.55, 0.03, 1.0, np.float32)).cuda()
     sim.init(u0)
-    idx = torch.from_numpy(inputs.flat_index(rec, sim.g.ld)).cuda()
-    tr = torch.zeros((S - 1, len(rec)), dtype=torch.float32, device="cuda")
+    flat = np.concatenate([inputs.flat_index(rec, sim.g.ld), np.array(extra_idx, dtype=np.int64)])
+    idx = torch.from_numpy(flat).cuda()
+    tr = torch.full((S - 1, len(flat)), 7.0, dtype=torch.float32, device="cuda")  # every entry gets written
     ck = torch.zeros((tsu.tsu_ckpt_slots(S, every), 2, sim.g.ny, sim.g.ld), dtype=torch.float32, device="cuda")
     e = torch.zeros(S - 1, dtype=torch.float64, device="cuda") if energy else None
     sim.step(S - 1, energy=e, rec_idx=idx, traces=tr, ckpt=ck, ckpt_every=every, kernel=kernel, tdepth=4)
@@ -160,8 +162,10 @@ def test_wtb_records_traces_and_checkpoints_like_one_step_passes(form, energy):
     rec += [[120, 97], [0, 300], [500, 0], [999, 776]] + [[int(x), int(y)] for x, y in zip(
         rng.integers(1, 999, 60), rng.integers(1, 775, 60))]
     rec = np.array(rec)
-    a, tra, cka, ea = _trace_run(2, rec=rec, energy=energy, form=form)
-    b, trb, ckb, eb = _trace_run(1, rec=rec, energy=energy, form=form)
+    far = (-5, 10**12)  # receivers outside the grid record 0
+    a, tra, cka, ea = _trace_run(2, rec=rec, energy=energy, form=form, extra_idx=far)
+    b, trb, ckb, eb = _trace_run(1, rec=rec, energy=energy, form=form, extra_idx=far)
+    assert not (tra == 7.0).any()
     assert torch.equal(tra, trb)
     assert torch.equal(cka, ckb)
     assert torch.equal(a.u, b.u)
@@ -184,3 +188,12 @@ def test_unaligned_checkpoints_fall_back_or_are_refused():
     ref.step(20, ckpt=ck2, ckpt_every=6, kernel=1)
     torch.cuda.synchronize()
     assert torch.equal(ck, ck2) and torch.equal(sim.u, ref.u)
+
+
+def test_long_receiver_lists_go_one_step_per_pass():
+    """More receivers than the blocked pass scans (2048) take the one-step passes automatically."""
+    rng = np.random.default_rng(21)
+    rec = np.stack([rng.integers(0, 1001, 3000), rng.integers(0, 777, 3000)], axis=1)
+    a, tra, cka, _ = _trace_run(0, rec=rec, energy=False)
+    b, trb, ckb, _ = _trace_run(1, rec=rec, energy=False)
+    assert torch.equal(tra, trb) and torch.equal(cka, ckb) and torch.equal(a.u, b.u)
