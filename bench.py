@@ -33,10 +33,6 @@ TRAFFIC = {
     # profiles/k_leapfrog_wtb_increment_8192.md: one launch of the timed configuration (8192^2,
     # 4 steps per pass, 160 rows per chunk), dram__bytes_read.sum + dram__bytes_write.sum
     ("k_leapfrog_wtb", "increment", 8192, 4): 1.649802e9,
-    # profiles/k_leapfrog_increment_4096.md, scaled by 8190^2/4094^2 (writes under-counted: L2 residency)
-    ("k_leapfrog", "increment", 8192, 1): 1.483e9,
-    # profiles/k_leapfrog_standard_4096.md, scaled likewise
-    ("k_leapfrog", "standard", 8192, 1): 1.280e9,
 }
 UNIT = "GLUPS"
 DEFAULT_KERNEL = 2  # warp-blocked pass, 4 steps per HBM pass
