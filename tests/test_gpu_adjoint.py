@@ -194,3 +194,36 @@ def test_tsunami_fn_autograd_matches_oracle_adjoint():
     assert relerr(hy.grad[:, :n].cpu().numpy(), ref["g_hy"]) <= 1e-11
     assert relerr(u0.grad[:, :n].cpu().numpy(), ref["g_u0"]) <= 1e-11
     assert relerr(u1.grad[:, :n].cpu().numpy(), ref["g_u1"]) <= 1e-11
+
+
+def test_tsunami_fn_autograd_fp32():
+    """The autograd wrapper on FP32 fields (warp-blocked forward recording receivers and
+    checkpoints, four-step reverse passes): traces and gradients against the FP64 oracle."""
+    n, S = 161, 130
+    depth = dict(background=1.0, eps=0.05, mollifier=0, sings=[(0, 1, 0.5, 0.5, 0.5)])
+    sim = tsu.Simulation.create(n, depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+    g = sim.g
+    rng = np.random.default_rng(14)
+    rec = inputs.receivers_on_row(n, 0.8, 10, rng)
+    u0n = inputs.gaussian_hump(n, n, g.ld, 0.45, 0.6, 0.08)
+    obs = torch.from_numpy(rng.standard_normal((S, len(rec))) * 1e-3).float().cuda()
+    hx = sim.hx.clone().requires_grad_(True)
+    hy = sim.hy.clone().requires_grad_(True)
+    u0 = torch.from_numpy(u0n).float().cuda().requires_grad_(True)
+    u1 = torch.zeros_like(u0).requires_grad_(True)
+    cfg = TsunamiConfig(g, sim.tau, S, torch.from_numpy(inputs.flat_index(rec, g.ld)).cuda(), sim.ext[1], sim.ext[3],
+                        form=tsu.TSU_FORM_INCREMENT, ckpt_every=16)
+    tr = tsunami_traces(hx, hy, u0, u1, cfg)
+    loss = 0.5 * ((tr - obs) ** 2).sum()
+    loss.backward()
+    og = oracle.grid(n, n)
+    ohx, ohy, _ = oracle.make_depth(og, depth)
+    fwd = oracle.forward(og, sim.tau, ohx, ohy, u0n[:, :n], None, S, want_energy=False,
+                         rec_idx=inputs.flat_index(rec, n))
+    assert relerr(tr.detach().double().cpu().numpy(), fwd["traces"]) <= 1e-5
+    ref = oracle.adjoint(og, sim.tau, ohx, ohy, u0n[:, :n], None, S, inputs.flat_index(rec, n),
+                         tr.detach().double().cpu().numpy() - obs.double().cpu().numpy())
+    assert relerr(hx.grad[:, :n].double().cpu().numpy(), ref["g_hx"]) <= 2e-5
+    assert relerr(hy.grad[:, :n].double().cpu().numpy(), ref["g_hy"]) <= 2e-5
+    assert relerr(u0.grad[:, :n].double().cpu().numpy(), ref["g_u0"]) <= 2e-5
+    assert relerr(u1.grad[:, :n].double().cpu().numpy(), ref["g_u1"]) <= 2e-5
