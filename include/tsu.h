@@ -230,9 +230,9 @@ int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps
  *   g_hx, g_hy  device double [ny][ld], overwritten with dJ/dhx, dJ/dhy (FP64 accumulation;
  *             for FP32 fields FP32 partial sums over one segment are added into them)
  *   g_u0, g_u1  device [ny][ld] of dtype, overwritten with dJ/du0, dJ/du1
- * Every segment is recomputed from its checkpoint on a library-owned stream (one per device,
- * created by the first call) concurrently with the reverse sweep of the previous one; all of it is
- * ordered before the call's last work on the caller's stream.
+ * Every segment is recomputed from its checkpoint on a library-owned stream (one per device and
+ * host thread, created by that thread's first call) concurrently with the reverse sweep of the
+ * previous one; all of it is ordered before the call's last work on the caller's stream.
  * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
 int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_medium* m, int64_t nsteps,
                 int64_t ckpt_every, const void* ckpt, const void* u0, int32_t nrec, const int64_t* rec_idx,

@@ -435,20 +435,19 @@ int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps
 
 }  // extern "C"
 
-// One auxiliary (non-blocking) stream per device with its events, created on first use, for
-// overlapping the adjoint's segment recompute with its reverse sweep.
+// One auxiliary (non-blocking) stream per device and host thread with its events, created on
+// first use, for overlapping the adjoint's segment recompute with its reverse sweep.  Per thread,
+// so that adjoints enqueued from several host threads never share the events that order them.
 namespace {
 struct AuxStream {
   cudaStream_t s;
   cudaEvent_t start, computed[2], swept[2];
 };
-std::mutex g_aux_mu;
-AuxStream* g_aux[64] = {};
+thread_local AuxStream* g_aux[64] = {};
 
 AuxStream* aux_stream() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(g_aux_mu);
   if (!g_aux[dev]) {
     AuxStream* a = new AuxStream();
     bool ok = cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking) == cudaSuccess;

@@ -227,3 +227,38 @@ def test_tsunami_fn_autograd_fp32():
     assert relerr(hy.grad[:, :n].double().cpu().numpy(), ref["g_hy"]) <= 2e-5
     assert relerr(u0.grad[:, :n].double().cpu().numpy(), ref["g_u0"]) <= 2e-5
     assert relerr(u1.grad[:, :n].double().cpu().numpy(), ref["g_u1"]) <= 2e-5
+
+
+def test_adjoints_from_two_host_threads():
+    """Two host threads enqueue adjoints on their own streams at the same time; each gets the
+    result of a run alone (the recompute streams and their events are per thread)."""
+    import threading
+
+    nx, ny, S, every = 150, 120, 45, 8
+    rng = np.random.default_rng(31)
+    u0 = inputs.random_field(nx, ny, None, rng)
+    u1 = inputs.random_field(nx, ny, None, rng)
+    rec = receivers(nx, ny)
+    dtr = rng.standard_normal((S, len(rec)))
+    alone = gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f32", tsu.TSU_FORM_INCREMENT, every)[0]
+    out, errs = [None, None], []
+
+    def work(k):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                for _ in range(3):
+                    out[k] = gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f32",
+                                                 tsu.TSU_FORM_INCREMENT, every)[0]
+        except Exception as ex:  # pragma: no cover - reported below
+            errs.append(ex)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for k in range(2):
+        for name in alone:
+            assert np.array_equal(out[k][name], alone[name]), (k, name)
