@@ -170,7 +170,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     for (int q = 0; q < 3; ++q) w[t][q] = kZeroP4;
 #pragma unroll
   for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = kZeroP4;
-  const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
+  const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy), ncx2 = pk(-a.cx, -a.cx), ncy2 = pk(-a.cy, -a.cy);
   // receivers whose node this tile owns (output columns and rows), one per lane; more than 32
   // in one tile are read back from memory at every record
   int rec_row = -1, rec_col = 0, rec_r = 0, rec_count = 0;
@@ -299,10 +299,13 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       const f2x mid = pk(c01.y, c23.x);
       P4 bv, un;
       [[maybe_unused]] P4 vn = kZeroP4;
+      // increment form: -B u from the negated coefficients (negation is exact, so v - (-B u)
+      // rounds as v + B u), which the energy term below uses without another negation
+      const f2x ccx = FORM == 1 ? ncx2 : cx2, ccy = FORM == 1 ? ncy2 : cy2;
       bv.p[0] = stencil2(pk(hl, h01.x), hxv.p[0], hyd.p[0], hyv.p[0], uc.p[0], pk(ul, c01.x), mid, uu.p[0], ud.p[0],
-                         cx2, cy2);
+                         ccx, ccy);
       bv.p[1] = stencil2(pk(h01.y, h23.x), hxv.p[1], hyd.p[1], hyv.p[1], uc.p[1], mid, pk(c23.y, ur), uu.p[1],
-                         ud.p[1], cx2, cy2);
+                         ud.p[1], ccx, ccy);
       [[maybe_unused]] float erow = 0.f;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -316,10 +319,11 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
             ef = upk(sub2(mul2(d, d), mul2(bv.p[q], up)));
           }
         } else {
-          vn.p[q] = add2(pc.p[q], bv.p[q]);
+          vn.p[q] = sub2(pc.p[q], bv.p[q]);  // v^{n+1} = v^n + B u^n (bv holds -B u^n)
           un.p[q] = add2(uc.p[q], vn.p[q]);
-          // u^n - u^{n-1} is the stored increment v^n; v^n - u^n = -u^{n-1} exactly as rounded
-          if constexpr (ENERGY) ef = upk(fma2(bv.p[q], sub2(pc.p[q], uc.p[q]), mul2(pc.p[q], pc.p[q])));
+          // (u^n - u^{n-1})^2 - (B u^n) u^{n-1} with u^n - u^{n-1} = v^n and u^{n-1} = u^n - v^n:
+          // v^n (v^n + B u^n) - (B u^n) u^n = v^n v^{n+1} + (-B u^n) u^n
+          if constexpr (ENERGY) ef = upk(fma2(bv.p[q], uc.p[q], mul2(pc.p[q], vn.p[q])));
         }
         if constexpr (EDGE) {
           const bool n0 = row_in && node_col[2 * q], n1 = row_in && node_col[2 * q + 1];
