@@ -116,6 +116,7 @@ def tune_batch(sims, rounds: int = 4, cache: Cache | None = None, timer=wall_tim
         return hit
     scratch = [s.clone() for s in sims]
     side = stream or torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())  # the clones are made on the current stream
     work = {}  # per candidate: step counts and workspace, made before any timing
 
     def run(c: Choice):
@@ -125,6 +126,7 @@ def tune_batch(sims, rounds: int = 4, cache: Cache | None = None, timer=wall_tim
             wsb = tsu.tsu_batch_workspace(scratch, nsteps, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel)
             work[c] = (nsteps, torch.zeros(wsb, dtype=torch.uint8, device="cuda"), wsb)
         nsteps, ws, wsb = work[c]
+        side.wait_stream(torch.cuda.current_stream())  # the workspace is zeroed on the current stream
         with torch.cuda.stream(side):
             tsu.tsu_batch_run(scratch, nsteps, ws, wsb, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel, graph=c.graph,
                               stream=side)

@@ -80,9 +80,9 @@ def test_graph_launch_equals_stream_launch():
     wsb = tsu.tsu_batch_workspace(a, steps)
     ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
     tsu.tsu_batch_run(a, steps, ws, wsb)
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
     ws2 = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())  # after every allocation and fill above
     with torch.cuda.stream(side):
         tsu.tsu_batch_run(b, steps, ws2, wsb, graph=True, stream=side)
     side.synchronize()
