@@ -35,7 +35,7 @@ struct AccOf<double> { using type = double; };
 // MODE 3 (kAdjStartInc): lam_pp holds mu^1: lam_out = mu^1 + B lam_c / 2 = dJ/du0; g_u1 = tau lam_c
 template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_adjoint_pass(const int32_t nx, const int32_t ny, const int64_t ld,
-                                                      const typename ArithOf<T>::type ar, const T gwx, const T gwy,
+                                                      const typename AdjArithOf<T>::type ar, const T gwx, const T gwy,
                                                       const T tau, const T* __restrict__ hx, const T* __restrict__ hy,
                                                       const T* __restrict__ lam, const T* lam_pp, T* lam_out, T* mu_out,
                                                       const T* __restrict__ u, typename AccOf<T>::type* gx,
@@ -209,8 +209,8 @@ __global__ void k_flush(const int64_t total, float* g32x, float* g32y, double* g
 }
 
 template <typename T>
-typename ArithOf<T>::type arith(const StencilGeom& g) {
-  typename ArithOf<T>::type a;
+typename AdjArithOf<T>::type arith(const StencilGeom& g) {
+  typename AdjArithOf<T>::type a;
   a.cx = (T)g.cx;
   a.cy = (T)g.cy;
   return a;

@@ -7,9 +7,10 @@
 // (u^n, u^{n-1} or v^n, hx, hy) through a private ring in shared memory with 16-byte cp.async
 // copies, P rows ahead, and reads back only what it copied itself (cp.async.wait_group), so no
 // thread waits for another.  Time level t lags the input by t rows; for each level the thread
-// keeps the last three rows of its four columns in registers (y-neighbours), and takes the
-// x-neighbours of its two edge columns from the adjacent lanes with shuffles.  Level K is written
-// with level K-1 (standard form) or v (increment form) of the same row.
+// keeps its four columns of the latest rows in registers, with the y face fluxes below the current
+// row, and evaluates every face flux once: the x flux left of its first column comes from the
+// lane on the left, the right neighbour of its last column from the lane on the right (shuffles).
+// Level K is written with level K-1 (standard form) or v (increment form) of the same row.
 //
 // HBM traffic per K steps: 16 B read + 8 B written per node, x 128/120 for the halo columns and
 // x (L + 2K)/L for the halo rows: 6.4 B per lattice update at K = 4.
@@ -39,8 +40,8 @@ template <int K>
 struct WtbShape {
   // rings of power-of-two length (slot = row index & (S - 1))
   static constexpr int SA = 4;                // (u, p) rows: in flight (2) + current + previous
-  static constexpr int SB = 8;                // (hx, hy) rows: the levels' rows (K + 2) + in flight (2)
-  static_assert(kWtbPre + 2 <= SA && K + 2 + kWtbPre <= SB, "ring too short");
+  static constexpr int SB = 8;                // (hx, hy) rows: the levels' rows (K), the input row, in flight (2)
+  static_assert(kWtbPre + 2 <= SA && K + 1 + kWtbPre <= SB, "ring too short");
   // bytes per thread
   static constexpr int bytes = (SA * 2 + SB * 2) * 16;
 };
@@ -164,12 +165,13 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   // registers: w[t][0..2] = level t at its latest three rows, v[t][0..1] likewise (increment form)
   P4 w[K + 1][3];
   P4 vv[K][2];
+  P4 gb[K];  // gb[t - 1]: level t's y flux at the faces below its current row
 #pragma unroll
   for (int t = 0; t <= K; ++t)
 #pragma unroll
     for (int q = 0; q < 3; ++q) w[t][q] = kZeroP4;
 #pragma unroll
-  for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = kZeroP4;
+  for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = gb[t] = kZeroP4;
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy), ncx2 = pk(-a.cx, -a.cx), ncy2 = pk(-a.cy, -a.cy);
   // receivers whose node this tile owns (output columns and rows), one per lane; more than 32
   // in one tile are read back from memory at every record
@@ -260,22 +262,14 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       vv[0][1] = vv[0][0];
       vv[0][0] = lds_p4(slotA(sa, 1));
     }
-    // hy of row r_in - t; level t reads the rows rt and rt - 1, level t + 1 the rows rt - 1 and
-    // rt - 2, so each row is read once
-    auto hy_row = [&](int t) -> P4 {
-      if constexpr (EDGE)
-        return ringB(r_in - t, 1);
-      else  // rows >= r_first: plain ring slots
-        return lds_p4(slotB((unsigned)(it - t) & (Sh::SB - 1), 1));
-    };
-    P4 hyv = hy_row(1);
     // ---- levels 1..K
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
       const int rt = r_in - t;
-      const P4 hxv = EDGE ? ringB(rt, 0) : lds_p4(slotB((unsigned)(it - t) & (Sh::SB - 1), 0));
-      const P4 hyd = hy_row(t + 1);
-      const P4 uc = w[t - 1][1], uu = w[t - 1][0], ud = w[t - 1][2];
+      const unsigned sb = (unsigned)(it - t) & (Sh::SB - 1);  // ring slot of row rt (rows >= r_first)
+      const P4 hxv = EDGE ? ringB(rt, 0) : lds_p4(slotB(sb, 0));
+      const P4 hyv = EDGE ? ringB(rt, 1) : lds_p4(slotB(sb, 1));  // the faces above row rt
+      const P4 uc = w[t - 1][1], uu = w[t - 1][0];
       P4 pc;  // u^{n-1} (standard) or v at row rt of the level below
       if (t == 1) {
         if constexpr (FORM == 1)
@@ -289,23 +283,29 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
           pc = vv[t - 1][1];
       }
       const float2 c01 = upk(uc.p[0]), c23 = upk(uc.p[1]);
-      const float2 h01 = upk(hxv.p[0]), h23 = upk(hxv.p[1]);
-      const float ul = __shfl_up_sync(0xffffffffu, c23.y, 1);
       const float ur = __shfl_down_sync(0xffffffffu, c01.x, 1);
-      const float hl = __shfl_up_sync(0xffffffffu, h23.y, 1);
+      // x fluxes at the faces right of the four columns, F = hx (u_right - u), and the one left
+      // of column 0 from the lane on the left (its fourth flux)
+      const f2x fr01 = mul2(hxv.p[0], pk(__fsub_rn(c01.y, c01.x), __fsub_rn(c23.x, c01.y)));
+      const f2x fr23 = mul2(hxv.p[1], pk(__fsub_rn(c23.y, c23.x), __fsub_rn(ur, c23.y)));
+      const float2 F01 = upk(fr01), F23 = upk(fr23);
+      const float fl = __shfl_up_sync(0xffffffffu, F23.y, 1);
       const bool row_in = !EDGE || (rt >= 1 && rt <= a.ny - 2);
       const bool row_out = !EDGE || (rt >= y0 && rt < y1);
-      // x-neighbour pairs: (ul, c0) left of pair 0, (c1, c2) between the pairs, (c3, ur) right of pair 1
-      const f2x mid = pk(c01.y, c23.x);
-      P4 bv, un;
+      P4 bv, un, fx, gy;
+      fx.p[0] = pk(__fsub_rn(F01.x, fl), __fsub_rn(F01.y, F01.x));
+      fx.p[1] = pk(__fsub_rn(F23.x, F01.y), __fsub_rn(F23.y, F23.x));
       [[maybe_unused]] P4 vn = kZeroP4;
       // increment form: -B u from the negated coefficients (negation is exact, so v - (-B u)
       // rounds as v + B u), which the energy term below uses without another negation
       const f2x ccx = FORM == 1 ? ncx2 : cx2, ccy = FORM == 1 ? ncy2 : cy2;
-      bv.p[0] = stencil2(pk(hl, h01.x), hxv.p[0], hyd.p[0], hyv.p[0], uc.p[0], pk(ul, c01.x), mid, uu.p[0], ud.p[0],
-                         ccx, ccy);
-      bv.p[1] = stencil2(pk(h01.y, h23.x), hxv.p[1], hyd.p[1], hyv.p[1], uc.p[1], mid, pk(c23.y, ur), uu.p[1],
-                         ud.p[1], ccx, ccy);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        // y flux at the faces above row rt; the one below is this level's flux of the row before
+        gy.p[q] = mul2(hyv.p[q], sub2(uu.p[q], uc.p[q]));
+        bv.p[q] = fma2(ccx, fx.p[q], mul2(ccy, sub2(gy.p[q], gb[t - 1].p[q])));
+      }
+      gb[t - 1] = gy;
       [[maybe_unused]] float erow = 0.f;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -348,7 +348,6 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         es[t - 1] = sum;
       }
       w[t][0] = un;
-      hyv = hyd;
       if constexpr (REC) {
         if (t < K && row_out) record(t, rt, un);
       }

@@ -79,12 +79,31 @@ __device__ __forceinline__ void st_vec(T* p, const Pack<T>& r) {
 // ---- arithmetic of one node ------------------------------------------------------------------
 // FP32: every rounding is explicit (the compiler contracts nothing), so every pass that calls these
 // (one step, CTA-blocked, warp-blocked, batched, segment recompute) gives the same bits.
+//
+// Forward passes: the face fluxes F = h (u_right - u_left) are rounded once each and B u is their
+// difference, fx = F(i+1/2) - F(i-1/2), so that neighbouring nodes share each face's flux (the
+// warp-blocked pass computes every flux once and takes the one left of a lane from its
+// neighbour), then B u = fma(cx, fx, cy fy).
 struct ArithF32 {
   float cx, cy;
   __device__ __forceinline__ float b(float hxr, float hxl, float hyu, float hyd, float uc, float ul, float ur,
                                      float uu, float ud) const {
-    // fx = hxr (ur - uc) - hxl (uc - ul) written as hxl (ul - uc) + hxr (ur - uc): the form the
-    // paired .f32x2 instructions evaluate without a negation
+    const float fx = __fsub_rn(__fmul_rn(hxr, __fsub_rn(ur, uc)), __fmul_rn(hxl, __fsub_rn(uc, ul)));
+    const float fy = __fsub_rn(__fmul_rn(hyu, __fsub_rn(uu, uc)), __fmul_rn(hyd, __fsub_rn(uc, ud)));
+    return __fmaf_rn(cx, fx, __fmul_rn(cy, fy));
+  }
+  __device__ __forceinline__ float lf(float uc, float up, float b) const {
+    return __fadd_rn(__fmaf_rn(2.0f, uc, -up), b);
+  }
+  __device__ __forceinline__ float add(float a, float b) const { return __fadd_rn(a, b); }
+};
+
+// Adjoint passes (one-step and four-step, which agree with each other): B lambda with one fused
+// multiply-add per direction, fx = fma(hxl, ul - uc, hxr (ur - uc)), B = fma(cx, fx, cy fy).
+struct ArithF32Fma {
+  float cx, cy;
+  __device__ __forceinline__ float b(float hxr, float hxl, float hyu, float hyd, float uc, float ul, float ur,
+                                     float uu, float ud) const {
     const float fx = __fmaf_rn(hxl, __fsub_rn(ul, uc), __fmul_rn(hxr, __fsub_rn(ur, uc)));
     const float fy = __fmaf_rn(hyd, __fsub_rn(ud, uc), __fmul_rn(hyu, __fsub_rn(uu, uc)));
     return __fmaf_rn(cx, fx, __fmul_rn(cy, fy));
@@ -147,8 +166,8 @@ __device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
-// B u for a pair of columns, in ArithF32's order: fx = fma(hxl, ul - uc, hxr (ur - uc)), fy
-// likewise, B u = fma(cx, fx, cy fy)
+// B lambda for a pair of columns, in ArithF32Fma's order (the adjoint's): fx = fma(hxl, ul - uc,
+// hxr (ur - uc)), fy likewise, B = fma(cx, fx, cy fy)
 __device__ __forceinline__ f2x stencil2(f2x hxl, f2x hxr, f2x hyd, f2x hyu, f2x uc, f2x ul, f2x ur, f2x uu, f2x ud,
                                         f2x cx, f2x cy) {
   const f2x fx = fma2(hxl, sub2(ul, uc), mul2(hxr, sub2(ur, uc)));
@@ -170,6 +189,12 @@ template <>
 struct ArithOf<float> { using type = ArithF32; };
 template <>
 struct ArithOf<double> { using type = ArithF64; };
+template <typename T>
+struct AdjArithOf;
+template <>
+struct AdjArithOf<float> { using type = ArithF32Fma; };
+template <>
+struct AdjArithOf<double> { using type = ArithF64; };
 
 }  // namespace dev
 }  // namespace tsu
