@@ -508,22 +508,34 @@ int64_t wtb_tiles(int64_t ny, int64_t ld, int rows) {
   return ((ld + 4 + kWtbOut - 1) / kWtbOut) * ((ny - 2 + rows - 1) / rows);
 }
 
-// Rows per chunk for one wave of tiles (152 SMs x 3 resident CTAs of 4 warps at up to 168
-// registers per thread), between 16 and 160.
+// Rows per chunk.  When one wave of 152 SMs x 3 CTAs x 4 warps holds every tile at no more than
+// 160 rows each, the fewest rows (>= 16) that do so.  Larger grids take several waves; the chunk
+// count is then the largest that keeps the tiles within m whole waves of 4 CTAs per SM (the
+// register bound lets four reside), for the smallest m whose chunks have at most 160 rows, so
+// that the last wave is full.
 int wtb_seg_rows(int64_t ny, int64_t ld) {
-  const int64_t strips = (ld + kWtbOut - 1) / kWtbOut;
-  const int64_t chunks = (int64_t)152 * kWtbCtasPerSm * kWtbWarps / strips;
-  if (chunks < 1) return 160;
-  const int64_t rows = (ny - 2 + chunks - 1) / chunks;
-  return (int)(rows < 16 ? 16 : rows > 160 ? 160 : rows);
+  const int64_t strips = (ld + 4 + kWtbOut - 1) / kWtbOut;
+  const int64_t inner = ny - 2;
+  const int64_t one_wave = (int64_t)152 * kWtbCtasPerSm * kWtbWarps / strips;
+  if (one_wave >= 1) {
+    const int64_t rows = (inner + one_wave - 1) / one_wave;
+    if (rows <= 160) return (int)(rows < 16 ? 16 : rows);
+  }
+  const int64_t wave4 = (int64_t)152 * 4 * kWtbWarps;
+  for (int64_t m = 1;; ++m) {
+    const int64_t chunks = m * wave4 / strips;
+    if (chunks < 1) continue;
+    const int64_t rows = (inner + chunks - 1) / chunks;
+    if (rows <= 160) return (int)(rows < 16 ? 16 : rows);
+  }
 }
 
-// Rows per chunk: the fewest (>= 16) that fit all tiles into one wave, at most 160.  Measured FP32
-// GLUPS of this pass (increment form, energy every step, K = 4, 3 CTAs per SM):
-//   16384^2: 891 at 160 rows, 878 at 128, 856 at 96, 815 at 64;  8192^2: 765 at 160, 764 at 96,
-//   744 at 128, 741 at 64;  4096^2: 638 at 79 (the rule's choice), 571 at 64, 542 at 32;
-//   2048^2: 370 at 21 (the rule's) and at 32, 337 at 16, 283 at 48.  One step per pass for
-//   comparison (scalar version): 247 at 4096^2, 256 at 2048^2, 102 at 1024^2.
+// Measured FP32 GLUPS of this pass (increment form, energy every step, K = 4):
+//   8192^2 (69 strips): 894 at 117 rows (the rule's: 4830 tiles, 2 full waves of 4 CTAs per SM),
+//   883 at 96, 869 at 140, 866 at 240 (one wave), 858 at 160 (1.48 waves), 850 at 128;
+//   16384^2: 1012-1023 at every row count from 96 to 240;  4096^2: 709 at 79 (the rule's, one
+//   wave of 3 CTAs per SM), 615 at 96, 502 at 160;  2048^2: 407 at 21 (the rule's).  One step per
+//   pass for comparison (scalar version): 247 at 4096^2, 256 at 2048^2, 102 at 1024^2.
 int wtb_auto_rows(int64_t ny, int64_t ld, int k) {
   (void)k;
   return wtb_seg_rows(ny, ld);
