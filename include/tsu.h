@@ -252,7 +252,7 @@ typedef struct {
 /* Options of tsu_batch_run (NULL = defaults). */
 typedef struct {
   int32_t tdepth; /* steps per batched pass (0 = the kernel's default: 4 for kernel 2, 8 for kernel 3) */
-  int32_t rows;   /* rows per chunk (0 = 128, halved down to 16 while the tiles do not fill the GPU) */
+  int32_t rows;   /* rows per chunk (0 = 80, halved down to 16 while the tiles do not fill the GPU) */
   int32_t kernel; /* 0 or 2: warp-blocked (tdepth 2 or 4); 3: CTA-blocked (tdepth 4 or 8) */
   int32_t graph;  /* 1: capture every launch of the call into one CUDA graph and launch that (needs a
                      non-default stream); 0: launch on the stream directly */

@@ -684,10 +684,11 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
     for (int i = 0; i < nprob; ++i) t += ((probs[i].grid.ld + W - 1) / W) * ((probs[i].grid.ny - 2 + r - 1) / r);
     return t;
   };
-  // rows per chunk: 128 (64-problem family, FP32 GLUPS at 64/96/128 rows: 801/805/810; an
-  // earlier build of the pass at 32/64/96/128/192/256 rows: 755/815/818/802/763/725), fewer
-  // (down to 16) while the family's tiles would not fill one wave of the GPU (small problems)
-  int rows = (opts && opts->rows) ? opts->rows : 128;
+  // rows per chunk: 80 (64-problem family of 512^2..2048^2, FP32 GLUPS of the flux-form pass at
+  // 56/64/80/128 rows: 927/932/934/889; ordering the tile table longest tile first instead of
+  // problem by problem lost 2-3 % at every row count), fewer (down to 16) while the family's
+  // tiles would not fill one wave of the GPU (small problems)
+  int rows = (opts && opts->rows) ? opts->rows : 80;
   if (!(opts && opts->rows) && kern == 2) {
     for (int i = 0; i < nprob; ++i) TRY(check_grid(&probs[i].grid));
     while (rows > 16 && tiles_at(rows) < (int64_t)152 * 3 * 4) rows = rows > 32 ? rows / 2 : 16;
