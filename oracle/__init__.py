@@ -16,6 +16,8 @@ Paper passages followed (arXiv:2005.11931):
 * Sec. 3.3: the 2D box with zero Dirichlet edges and the grid omega.
 * Theorem 2.1, identity (CL-01): conservation of ``||u_t||^2 + sum ||h_j^1/2 d_j u||^2``,
   whose leapfrog analogue is ``energy``.
+* Sec. 3.3: the implicit scheme solved line by line with tridiagonal systems, read as the
+  factorized scheme ``(I - sigma B_x)(I - sigma B_y) w = B u`` (``implicit_forward``).
 
 Arrays are float64, shape ``(ny, ld)`` with ``ld >= nx``, row-major (x fastest).
 """
@@ -98,6 +100,8 @@ def _load():
         lib.orc_adjoint.argtypes = [g, C.c_double, d, d, d, d, C.c_int64, C.c_int32,
                                     C.POINTER(C.c_int64), d, d, d, d, d]
         lib.orc_adjoint.restype = C.c_int
+        lib.orc_implicit_forward.argtypes = [g, C.c_double, C.c_double, d, d, d, d, C.c_int64, d, d]
+        lib.orc_implicit_forward.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -252,3 +256,17 @@ def adjoint(g, tau, hx, hy, u0, u1, steps: int, rec_idx, dtraces):
     if rc != 0:
         raise ValueError(f"oracle adjoint failed ({rc})")
     return out
+
+
+def implicit_forward(g, tau, sigma, hx, hy, u0, u1, steps: int):
+    """The implicit comparator (Sec. 3.3, read as the factorized scheme with weight ``sigma``):
+    ``(I - sigma B_x)(I - sigma B_y) w^n = B u^n``, ``v^{n+1} = v^n + w^n``, ``u^{n+1} = u^n +
+    v^{n+1}``, started by ``v^1 = tau u1 + w^0 / 2``.  Every factor is solved line by line with
+    Thomas elimination.  Returns (u^S, v^S) after the start and ``steps - 1`` steps."""
+    u = np.zeros((g.ny, g.ld))
+    v = np.zeros((g.ny, g.ld))
+    rc = _load().orc_implicit_forward(C.byref(g), float(tau), float(sigma), _p(_field(g, hx)), _p(_field(g, hy)),
+                                      _p(_field(g, u0)), _p(_field(g, u1)), int(steps), _p(u), _p(v))
+    if rc != 0:
+        raise ValueError(f"oracle implicit_forward failed ({rc})")
+    return u, v

@@ -15,7 +15,10 @@
  *            phi_eps a unit-mass mollifier of width eps        -- Sec. 2.1 (h * psi_eps), Sec. 3.1
  *   energy   d/dt (||u_t||^2 + sum_j ||h_j^1/2 d_j u||^2) = 0   -- Theorem 2.1, identity (CL-01)
  *   d h_eps / d eps, the depth's derivative in the regularisation width  -- Sec. 2.1
- *   and an FP32 emulation of the stepping in both forms (rounding study only)
+ *   an FP32 emulation of the stepping in both forms (rounding study only)
+ *   and the implicit comparator: a factorized scheme with line-wise tridiagonal
+ *   systems (Sec. 3.3 names an implicit scheme solved along lines; the scheme
+ *   itself is a reading, written out at its section below)
  *
  * The scheme is the explicit leapfrog written out exactly as defined:
  *   fx(u)_ij = hx_ij (u_i+1,j - u_ij) - hx_i-1,j (u_ij - u_i-1,j)
@@ -593,4 +596,157 @@ int orc_adjoint(const orc_grid* g, double tau, const double* hx, const double* h
   add_face_grads(g, -0.5 * cx, -0.5 * cy, lam1, U + 0 * m, g_hx, g_hy);
   free(U); free(lam1); free(lam2); free(lam); free(Bl);
   return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Implicit comparator.  Sec. 3.3 solves the 2D problem with an implicit       */
+/* finite-difference scheme whose systems are tridiagonal along grid lines     */
+/* (cyclic reduction), without writing the scheme out.  The reading taken     */
+/* here is the factorized scheme with weight sigma (sigma = 1/4: stable for    */
+/* every tau):                                                                 */
+/*   (I - sigma B_x)(I - sigma B_y) w^n = B u^n,   B_x u = cx fx(u),           */
+/*                                                 B_y u = cy fy(u)            */
+/* in increment form                                                           */
+/*   v^{n+1} = v^n + w^n,   u^{n+1} = u^n + v^{n+1},                            */
+/* started by w^0 from the same systems with B u^0 and                          */
+/*   v^1 = tau u1 + w^0 / 2,   u^1 = u^0 + v^1.                                 */
+/* Each factor is one independent tridiagonal system per grid line over the    */
+/* interior nodes (zero Dirichlet ends), solved by plain Thomas elimination.   */
+/* ------------------------------------------------------------------------- */
+
+/* Thomas elimination of a tridiagonal system of n >= 1 rows: sub-diagonal a   */
+/* (a[0] unused), diagonal b, super-diagonal c (c[n-1] unused); d holds the     */
+/* right-hand side on entry and the solution on return; cp is scratch.        */
+static void thomas(int n, const double* a, const double* b, const double* c, double* d, double* cp) {
+  cp[0] = c[0] / b[0];
+  d[0] = d[0] / b[0];
+  for (int k = 1; k < n; ++k) {
+    const double p = b[k] - a[k] * cp[k - 1];
+    cp[k] = c[k] / p;
+    d[k] = (d[k] - a[k] * d[k - 1]) / p;
+  }
+  for (int k = n - 2; k >= 0; --k) d[k] = d[k] - cp[k] * d[k + 1];
+}
+
+static int team_size(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+static int team_rank(void) {
+#ifdef _OPENMP
+  return omp_get_thread_num();
+#else
+  return 0;
+#endif
+}
+
+/* r <- (I - s B_x)^{-1} r on every interior row (s = sigma): the system of row */
+/* j couples the interior nodes i = 1..nx-2 through the x faces of that row.    */
+static int solve_x(const orc_grid* g, double s, double cx, const double* hx, double* r) {
+  const int n = g->nx - 2, nt = team_size();
+  double* all = (double*)malloc(sizeof(double) * 5 * (size_t)n * (size_t)nt);
+  if (!all) return 1;
+#pragma omp parallel num_threads(nt)
+  {
+    double* a = all + (size_t)5 * n * team_rank();
+    double *b = a + n, *c = a + 2 * n, *d = a + 3 * n, *cp = a + 4 * n;
+#pragma omp for schedule(static)
+    for (int j = 1; j < g->ny - 1; ++j) {
+      for (int k = 0; k < n; ++k) {
+        const int i = k + 1;
+        const double hl = hx[IDX(g, i - 1, j)], hr = hx[IDX(g, i, j)];
+        a[k] = -(s * cx * hl);
+        b[k] = 1.0 + s * cx * (hl + hr);
+        c[k] = -(s * cx * hr);
+        d[k] = r[IDX(g, i, j)];
+      }
+      thomas(n, a, b, c, d, cp);
+      for (int k = 0; k < n; ++k) r[IDX(g, k + 1, j)] = d[k];
+    }
+  }
+  free(all);
+  return 0;
+}
+
+/* r <- (I - s B_y)^{-1} r on every interior column. */
+static int solve_y(const orc_grid* g, double s, double cy, const double* hy, double* r) {
+  const int n = g->ny - 2, nt = team_size();
+  double* all = (double*)malloc(sizeof(double) * 5 * (size_t)n * (size_t)nt);
+  if (!all) return 1;
+#pragma omp parallel num_threads(nt)
+  {
+    double* a = all + (size_t)5 * n * team_rank();
+    double *b = a + n, *c = a + 2 * n, *d = a + 3 * n, *cp = a + 4 * n;
+#pragma omp for schedule(static)
+    for (int i = 1; i < g->nx - 1; ++i) {
+      for (int k = 0; k < n; ++k) {
+        const int j = k + 1;
+        const double hd = hy[IDX(g, i, j - 1)], hu = hy[IDX(g, i, j)];
+        a[k] = -(s * cy * hd);
+        b[k] = 1.0 + s * cy * (hd + hu);
+        c[k] = -(s * cy * hu);
+        d[k] = r[IDX(g, i, j)];
+      }
+      thomas(n, a, b, c, d, cp);
+      for (int k = 0; k < n; ++k) r[IDX(g, i, k + 1)] = d[k];
+    }
+  }
+  free(all);
+  return 0;
+}
+
+/* w <- A^{-1} B u with A = (I - s B_x)(I - s B_y): first z = (I - s B_x)^{-1}  */
+/* B u, then w = (I - s B_y)^{-1} z.                                            */
+static int implicit_w(const orc_grid* g, double s, double cx, double cy, const double* hx, const double* hy,
+                      const double* u, double* w) {
+  orc_apply_B(g, cx, cy, hx, hy, u, w);
+  if (solve_x(g, s, cx, hx, w)) return 2;
+  if (solve_y(g, s, cy, hy, w)) return 2;
+  return 0;
+}
+
+/* The start and S - 1 steps of the factorized scheme; u_out = u^S, and, when  */
+/* v_out is not NULL, v_out = v^S = u^S - u^{S-1}.                              */
+int orc_implicit_forward(const orc_grid* g, double tau, double sigma, const double* hx, const double* hy,
+                         const double* u0, const double* u1, int64_t S, double* u_out, double* v_out) {
+  if (S < 1 || g->nx < 3 || g->ny < 3 || !(sigma >= 0.0)) return 1;
+  const int64_t n = (int64_t)g->ny * g->ld;
+  const double cx = tau * tau / (g->dx * g->dx), cy = tau * tau / (g->dy * g->dy);
+  double* u = (double*)calloc(n, sizeof(double));
+  double* v = (double*)calloc(n, sizeof(double));
+  double* w = (double*)calloc(n, sizeof(double));
+  int rc = 0;
+  if (!u || !v || !w) {
+    rc = 2;
+    goto out;
+  }
+  memcpy(u, u0, sizeof(double) * n);
+  zero_boundary(g, u);
+  if ((rc = implicit_w(g, sigma, cx, cy, hx, hy, u, w))) goto out;
+  for (int j = 1; j < g->ny - 1; ++j)
+    for (int i = 1; i < g->nx - 1; ++i) {
+      const int64_t k = IDX(g, i, j);
+      v[k] = tau * (u1 ? u1[k] : 0.0) + 0.5 * w[k];
+      u[k] = u[k] + v[k];
+    }
+  for (int64_t step = 2; step <= S; ++step) {
+    if ((rc = implicit_w(g, sigma, cx, cy, hx, hy, u, w))) goto out;
+#pragma omp parallel for schedule(static)
+    for (int j = 1; j < g->ny - 1; ++j)
+      for (int i = 1; i < g->nx - 1; ++i) {
+        const int64_t k = IDX(g, i, j);
+        v[k] = v[k] + w[k];
+        u[k] = u[k] + v[k];
+      }
+  }
+  memcpy(u_out, u, sizeof(double) * n);
+  if (v_out) memcpy(v_out, v, sizeof(double) * n);
+out:
+  free(u);
+  free(v);
+  free(w);
+  return rc;
 }
