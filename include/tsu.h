@@ -301,6 +301,40 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
                 double* energy_dev, int32_t nrec, const int64_t* rec_idx, void* trace, void* ws,
                 size_t ws_bytes, void* stream);
 
+/* ---- Implicit comparator (Sec. 3.3) -------------------------------------------------------
+ * The paper solves its 2D problem with an implicit finite-difference scheme whose systems are
+ * tridiagonal along grid lines (cyclic reduction), without writing the scheme out.  Read here as
+ * the factorized scheme with weight sigma, in increment form:
+ *   (I - sigma B_x)(I - sigma B_y) w^n = B u^n,   v^{n+1} = v^n + w^n,   u^{n+1} = u^n + v^{n+1},
+ *   start: the same systems with B u^0, then v^1 = tau u1 + w^0 / 2, u^1 = u^0 + v^1,
+ * where B_x u = tau^2/dx^2 fx(u) and B_y u = tau^2/dy^2 fy(u) are the two halves of B = tau^2 L_h
+ * of the explicit scheme.  sigma >= 1/4 is stable for every tau (no Courant bound); sigma = 0 is
+ * the explicit leapfrog.  Each factor is one tridiagonal system per grid line over the interior
+ * nodes (zero Dirichlet ends).
+ *
+ * tsu_implicit_sizes: bytes of the factor buffer and of the workspace for this grid and dtype.
+ *   Transposed fields have nx rows of ldT = roundup(ny, 32) elements; the factor holds
+ *   [ny][ld] + 2 [nx][ldT] elements, the workspace [nx][ldT] + max(ny ld, nx ldT) elements.
+ * tsu_implicit_factor: the line systems' pivots for (tau, sigma, medium), computed once on the
+ *   device into `factor` (caller-owned, 16-byte aligned, factor_bytes >= the size above).  Any
+ *   change of tau, sigma or the depth needs a new factor.
+ * tsu_implicit_init: u0 (device [ny][ld]; boundary nodes ignored) and u1 (device or NULL = 0) ->
+ *   buf[0] = u^1, buf[1] = v^1 (st->form must be TSU_FORM_INCREMENT, nbuf >= 2; u0 may be
+ *   buf[0]); sets cur = 0, aux = 1, step = 1.
+ * tsu_implicit_step_n: nsteps steps in place on buf[cur] (u) and buf[aux] (v); step += nsteps.
+ * Every call is asynchronous on `stream`; the workspace (16-byte aligned, >= the size above) is
+ * scratch that must not be shared by calls in flight at the same time.
+ * Errors: TSU_EINVAL (arguments, form, alignment), TSU_ECFL (sigma < 1/4 and
+ * tau^2 (hx_max/dx^2 + hy_max/dy^2) (1 - 4 sigma) > 1), TSU_ENOMEM (factor or workspace too
+ * small), TSU_ECUDA. */
+int tsu_implicit_sizes(const tsu_grid* g, int dtype, size_t* factor_bytes, size_t* ws_bytes);
+int tsu_implicit_factor(const tsu_grid* g, int dtype, double tau, double sigma, const tsu_medium* m, void* factor,
+                        size_t factor_bytes, void* stream);
+int tsu_implicit_init(const tsu_grid* g, int dtype, double tau, double sigma, const tsu_medium* m, const void* factor,
+                      const void* u0, const void* u1, tsu_state* st, void* ws, size_t ws_bytes, void* stream);
+int tsu_implicit_step_n(const tsu_grid* g, int dtype, double tau, double sigma, const tsu_medium* m,
+                        const void* factor, tsu_state* st, int64_t nsteps, void* ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,429 @@
+// Implicit comparator (arXiv:2005.11931 Sec. 3.3: the 2D problem solved by an implicit scheme
+// whose systems are tridiagonal along grid lines).  The scheme is read as the factorized scheme
+// with weight s:
+//   (I - s B_x)(I - s B_y) w^n = B u^n,   v^{n+1} = v^n + w^n,   u^{n+1} = u^n + v^{n+1},
+// started by w^0 from B u^0 and v^1 = tau u1 + w^0 / 2, u^1 = u^0 + v^1.  B_x u = cx fx(u) and
+// B_y u = cy fy(u) are the two halves of the explicit operator (flux form).
+//
+// Each factor is one tridiagonal system per grid line.  Their LU factors do not change in time,
+// so the pivots are computed once (k_imp_factor_x / _y: m = 1 / pivot).  A step is then two
+// passes, one per direction, each a forward and a backward substitution over every line:
+//   forward   d_k = alpha_k d_{k-1} + beta_k,   alpha_k = s c h_{k-1/2} m_k, beta_k = m_k r_k
+//   backward  z_k = gamma_k z_{k+1} + d_k,      gamma_k = s c h_{k+1/2} m_k
+// Both are first-order linear recurrences, i.e. compositions of affine maps.  One warp owns a
+// line and walks it in segments of 128 nodes (4 consecutive nodes per lane, one 16-byte load
+// per field and lane): each lane composes its four maps, a 5-step warp scan (Kogge-Stone, by
+// shuffles) composes the lanes' maps, and the value carried in from the previous segment turns
+// them into the 128 results.  So every line is solved by 32 threads with coalesced loads instead
+// of one thread, and the cyclic reduction of the paper's GPU code is not needed.
+//
+// The x pass (k_imp_x) reads rows of the row-major fields and computes r = B u^n on the way; the
+// y pass (k_imp_y) needs columns, so the x pass writes its result z transposed (zT[i][j]) through
+// a shared-memory tile of R rows x 128 columns, and the y pass reads rows of zT, then writes w
+// back to row-major order through the same kind of tile, fused with the update of v and u.
+// Forward results wait for the backward substitution in a global scratch line (mostly L2).
+#include "stencil_common.cuh"
+
+namespace tsu {
+namespace {
+using namespace dev;
+
+constexpr int kImpSeg = 128;  // nodes per warp segment
+
+template <typename T>
+struct V4 {
+  T a[4];
+};
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  return V4<float>{{v.x, v.y, v.z, v.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p);
+  const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+  return V4<double>{{v0.x, v0.y, v1.x, v1.y}};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.a[0], v.a[1], v.a[2], v.a[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v.a[0], v.a[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v.a[2], v.a[3]);
+}
+template <typename T>
+__device__ __forceinline__ V4<T> zero4() {
+  return V4<T>{{T(0), T(0), T(0), T(0)}};
+}
+
+// explicitly rounded arithmetic (no contraction left to the compiler)
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// An affine map x -> A x + B, composed over a segment by a warp scan.  `up`: maps of lower lanes
+// come first (forward substitution); otherwise higher lanes come first (backward).
+template <typename T, bool UP>
+__device__ __forceinline__ void warp_scan(T& A, T& B, const int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T A2 = UP ? __shfl_up_sync(0xffffffffu, A, off) : __shfl_down_sync(0xffffffffu, A, off);
+    const T B2 = UP ? __shfl_up_sync(0xffffffffu, B, off) : __shfl_down_sync(0xffffffffu, B, off);
+    if (UP ? lane >= off : lane + off < 32) {
+      B = fma_(A, B2, B);
+      A = mul_(A, A2);
+    }
+  }
+}
+
+// Solve x_e = c_e x_{prev} + d_e over the 4 nodes of each lane and the 32 lanes of a segment
+// (node order e = 0..3, lane 0..31 when UP, the reverse otherwise), starting from `carry` (the
+// value before the segment); returns the 4 results and updates carry to the segment's last.
+template <typename T, bool UP>
+__device__ __forceinline__ V4<T> segment_solve(const V4<T>& c, const V4<T>& d, T& carry, const int lane) {
+  T A = T(1), B = T(0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = UP ? q : 3 - q;
+    B = fma_(c.a[e], B, d.a[e]);
+    A = mul_(c.a[e], A);
+  }
+  warp_scan<T, UP>(A, B, lane);
+  // the value entering this lane: the scanned map of the neighbour before it applied to carry
+  const T A1 = UP ? __shfl_up_sync(0xffffffffu, A, 1) : __shfl_down_sync(0xffffffffu, A, 1);
+  const T B1 = UP ? __shfl_up_sync(0xffffffffu, B, 1) : __shfl_down_sync(0xffffffffu, B, 1);
+  const bool first = UP ? lane == 0 : lane == 31;
+  T x = first ? carry : fma_(A1, carry, B1);
+  V4<T> out;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = UP ? q : 3 - q;
+    x = fma_(c.a[e], x, d.a[e]);
+    out.a[e] = x;
+  }
+  carry = __shfl_sync(0xffffffffu, x, UP ? 31 : 0);
+  return out;
+}
+
+template <typename T>
+struct ImpArgs {
+  int32_t nx, ny;
+  int64_t ld, ldT;
+  T cx, cy, sx;      // tau^2/dx^2, tau^2/dy^2, s cx
+  T tau;
+  const T* hx;
+  const T* hy;
+  const T* mx;       // [ny][ld]  1 / pivot of the x systems (0 off the unknowns)
+  const T* myT;      // [nx][ldT] 1 / pivot of the y systems
+  const T* kyT;      // [nx][ldT] s cy hy (face j+1/2 of column i)
+  const T* u;        // u^n (read by the x pass)
+  T* zT;             // [nx][ldT] (I - s B_x)^{-1} B u^n, transposed
+  T* scratch;        // forward results, one line per warp
+  T* v;              // updated in place by the y pass
+  T* uo;             // updated in place by the y pass
+  const T* u1;       // start only: initial velocity or nullptr
+  int start;
+};
+
+// x pass: one warp per row j; R rows per CTA.
+template <typename T, int R>
+__global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
+  __shared__ T tile[R][kImpSeg + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j0 = blockIdx.x * R, j = j0 + w;
+  const bool row_in = j >= 1 && j <= a.ny - 2;  // rows with unknowns
+  const int nseg = (a.nx - 1 + kImpSeg - 1) / kImpSeg;
+  const int64_t base = (int64_t)j * a.ld;
+  T* line = a.scratch + (row_in ? base : 0);
+  // forward: r = B u, then d_k = alpha_k d_{k-1} + beta_k
+  T carry = T(0), cu = T(0), ch = T(0);  // d, u and hx at the node before the segment
+  for (int s = 0; s < nseg; ++s) {
+    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+    const bool in = row_in && c0 < a.ld;
+    V4<T> uc = zero4<T>(), uu = zero4<T>(), ud = zero4<T>(), hxv = zero4<T>(), hyu = zero4<T>(),
+          hyd = zero4<T>(), m = zero4<T>();
+    T ur_own = T(0);
+    if (in) {
+      uc = ld4(a.u + base + c0);
+      uu = ld4(a.u + base + a.ld + c0);
+      ud = ld4(a.u + base - a.ld + c0);
+      hxv = ld4(a.hx + base + c0);
+      hyu = ld4(a.hy + base + c0);
+      hyd = ld4(a.hy + base - a.ld + c0);
+      m = ld4(a.mx + base + c0);
+      if (lane == 31 && c0 + 4 < a.ld) ur_own = a.u[base + c0 + 4];
+    }
+    T ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1), hl = __shfl_up_sync(0xffffffffu, hxv.a[3], 1);
+    T ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
+    if (lane == 0) {
+      ul = cu;
+      hl = ch;
+    }
+    if (lane == 31) ur = ur_own;
+    V4<T> alpha, beta;
+    T fl = mul_(hl, sub_(uc.a[0], ul));  // x flux left of the lane's first node
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const T right = e < 3 ? uc.a[e + 1] : ur;
+      const T fr = mul_(hxv.a[e], sub_(right, uc.a[e]));
+      const T fx = sub_(fr, fl);
+      const T fy = sub_(mul_(hyu.a[e], sub_(uu.a[e], uc.a[e])), mul_(hyd.a[e], sub_(uc.a[e], ud.a[e])));
+      const T r = fma_(a.cx, fx, mul_(a.cy, fy));
+      const T hprev = e == 0 ? hl : hxv.a[e - 1];
+      const bool unk = m.a[e] != T(0);  // off the unknowns m = 0: the node holds 0
+      alpha.a[e] = unk ? mul_(mul_(a.sx, hprev), m.a[e]) : T(0);
+      beta.a[e] = unk ? mul_(m.a[e], r) : T(0);
+      fl = fr;
+    }
+    const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
+    if (in) st4(line + c0, d);
+    cu = __shfl_sync(0xffffffffu, uc.a[3], 31);
+    ch = __shfl_sync(0xffffffffu, hxv.a[3], 31);
+  }
+  // backward: z_k = gamma_k z_{k+1} + d_k, written transposed through the tile
+  carry = T(0);
+  for (int s = nseg - 1; s >= 0; --s) {
+    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+    const bool in = row_in && c0 < a.ld;
+    V4<T> d = zero4<T>(), m = zero4<T>(), hxv = zero4<T>();
+    if (in) {
+      d = ld4(line + c0);
+      m = ld4(a.mx + base + c0);
+      hxv = ld4(a.hx + base + c0);
+    }
+    V4<T> gamma;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(a.sx, hxv.a[e]), m.a[e]) : T(0);
+    const V4<T> z = segment_solve<T, false>(gamma, d, carry, lane);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tile[w][4 * lane + e] = z.a[e];
+    __syncthreads();
+    // column c of the segment, rows j0 .. j0 + R - 1: R consecutive elements of zT
+    for (int q = threadIdx.x; q < kImpSeg * R; q += R * 32) {
+      const int cc = q / R, rr = q - cc * R;
+      const int64_t c = (int64_t)s * kImpSeg + cc;
+      if (c < a.nx) a.zT[c * a.ldT + j0 + rr] = tile[rr][cc];
+    }
+    __syncthreads();
+  }
+}
+
+// y pass: one warp per column i (a row of zT); R columns per CTA; w written back row-major and
+// folded into v and u.
+template <typename T, int R>
+__global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
+  __shared__ T tile[R][kImpSeg + 1];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * R, i = i0 + wp;
+  const bool col_in = i >= 1 && i <= a.nx - 2;
+  const int nseg = (a.ny - 1 + kImpSeg - 1) / kImpSeg;
+  const int64_t base = (int64_t)i * a.ldT;
+  T* line = a.scratch + (col_in ? base : 0);
+  T carry = T(0), ck = T(0);  // d and s cy hy at the node before the segment
+  for (int s = 0; s < nseg; ++s) {
+    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+    const bool in = col_in && c0 < a.ldT;
+    V4<T> z = zero4<T>(), m = zero4<T>(), k = zero4<T>();
+    if (in) {
+      z = ld4(a.zT + base + c0);
+      m = ld4(a.myT + base + c0);
+      k = ld4(a.kyT + base + c0);
+    }
+    T kl = __shfl_up_sync(0xffffffffu, k.a[3], 1);
+    if (lane == 0) kl = ck;
+    V4<T> alpha, beta;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const T kprev = e == 0 ? kl : k.a[e - 1];
+      const bool unk = m.a[e] != T(0);
+      alpha.a[e] = unk ? mul_(kprev, m.a[e]) : T(0);
+      beta.a[e] = unk ? mul_(m.a[e], z.a[e]) : T(0);
+    }
+    const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
+    if (in) st4(line + c0, d);
+    ck = __shfl_sync(0xffffffffu, k.a[3], 31);
+  }
+  carry = T(0);
+  for (int s = nseg - 1; s >= 0; --s) {
+    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+    const bool in = col_in && c0 < a.ldT;
+    V4<T> d = zero4<T>(), m = zero4<T>(), k = zero4<T>();
+    if (in) {
+      d = ld4(line + c0);
+      m = ld4(a.myT + base + c0);
+      k = ld4(a.kyT + base + c0);
+    }
+    V4<T> gamma;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(k.a[e], m.a[e]) : T(0);
+    const V4<T> w = segment_solve<T, false>(gamma, d, carry, lane);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tile[wp][4 * lane + e] = w.a[e];
+    __syncthreads();
+    // row j of the segment, columns i0 .. i0 + R - 1: v += w (or the start), u += v
+    for (int q = threadIdx.x; q < kImpSeg * R; q += R * 32) {
+      const int cc = q / R, rr = q - cc * R;
+      const int jj = s * kImpSeg + cc, ii = i0 + rr;
+      if (jj >= 1 && jj <= a.ny - 2 && ii >= 1 && ii <= a.nx - 2) {
+        const int64_t o = (int64_t)jj * a.ld + ii;
+        const T wv = tile[rr][cc];
+        T vn;
+        if (a.start) {
+          const T u1 = a.u1 ? a.u1[o] : T(0);
+          vn = fma_(a.tau, u1, mul_(T(0.5), wv));
+        } else {
+          vn = a.v[o] + wv;
+        }
+        a.v[o] = vn;
+        a.uo[o] = a.uo[o] + vn;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Pivots of the x systems, one thread per row (once per medium and tau): for the unknowns
+// i = 1..nx-2 of row j, a_i = -s cx hx_{i-1}, b_i = 1 + s cx (hx_{i-1} + hx_i), c_i = -s cx hx_i,
+// p_i = b_i - a_i c_{i-1} / p_{i-1}; stores 1 / p_i (FP64 arithmetic).
+template <typename T>
+__global__ void k_imp_factor_x(int32_t nx, int32_t ny, int64_t ld, double sx, const T* hx, T* mx) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < 1 || j > ny - 2) return;
+  const int64_t base = (int64_t)j * ld;
+  double cprev = 0.0;  // c_{i-1} / p_{i-1}
+  for (int i = 1; i <= nx - 2; ++i) {
+    const double hl = (double)hx[base + i - 1], hr = (double)hx[base + i];
+    const double p = (1.0 + sx * (hl + hr)) - (-(sx * hl)) * cprev;
+    mx[base + i] = (T)(1.0 / p);
+    cprev = -(sx * hr) / p;
+  }
+}
+
+// Pivots of the y systems, one thread per column, stored transposed, with s cy hy transposed.
+template <typename T>
+__global__ void k_imp_factor_y(int32_t nx, int32_t ny, int64_t ld, int64_t ldT, double sy, const T* hy, T* myT,
+                               T* kyT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const int64_t base = (int64_t)i * ldT;
+  for (int j = 0; j + 1 < ny; ++j) kyT[base + j] = (T)(sy * (double)hy[(int64_t)j * ld + i]);
+  if (i < 1 || i > nx - 2) return;
+  double cprev = 0.0;
+  for (int j = 1; j <= ny - 2; ++j) {
+    const double hd = (double)hy[(int64_t)(j - 1) * ld + i], hu = (double)hy[(int64_t)j * ld + i];
+    const double p = (1.0 + sy * (hd + hu)) - (-(sy * hd)) * cprev;
+    myT[base + j] = (T)(1.0 / p);
+    cprev = -(sy * hu) / p;
+  }
+}
+
+template <typename T>
+__global__ void k_imp_prepare(int32_t nx, int32_t ny, int64_t ld, const T* u0, T* u, T* v) {
+  const int64_t total = (int64_t)ny * ld;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = k / ld, i = k - j * ld;
+    const bool interior = i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2;
+    u[k] = interior ? u0[k] : T(0);
+    v[k] = T(0);
+  }
+}
+
+template <typename T, int R>
+cudaError_t launch_pair(const ImpArgs<T>& a, cudaStream_t s) {
+  k_imp_x<T, R><<<(unsigned)((a.ny + R - 1) / R), R * 32, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_imp_y<T, R><<<(unsigned)((a.nx + R - 1) / R), R * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const void* fac, void* u, void* v,
+                    const void* u1, int64_t nsteps, bool start, void* ws, cudaStream_t s) {
+  ImpArgs<T> a;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.ld = g.ld;
+  a.ldT = g.ldT;
+  a.cx = (T)g.cx;
+  a.cy = (T)g.cy;
+  a.sx = (T)(g.sigma * g.cx);
+  a.tau = (T)g.tau;
+  a.hx = (const T*)hx;
+  a.hy = (const T*)hy;
+  a.mx = (const T*)fac;
+  a.myT = a.mx + (int64_t)g.ny * g.ld;
+  a.kyT = a.myT + (int64_t)g.nx * g.ldT;
+  a.u = (const T*)u;
+  a.zT = (T*)ws;
+  a.scratch = a.zT + (int64_t)g.nx * g.ldT;
+  a.v = (T*)v;
+  a.uo = (T*)u;
+  a.u1 = (const T*)u1;
+  // 8 lines per CTA (a 32-byte run per transposed column); 16 (64-byte runs) once both passes
+  // have work for at least two CTAs of 16 lines per SM
+  const bool wide = g.nx >= 16 * 2 * 152 && g.ny >= 16 * 2 * 152;
+  for (int64_t n = 0; n < (start ? 1 : nsteps); ++n) {
+    a.start = start ? 1 : 0;
+    const cudaError_t e = wide ? launch_pair<T, 16>(a, s) : launch_pair<T, 8>(a, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int64_t implicit_ldT(int32_t ny) { return ((int64_t)ny + 31) / 32 * 32; }
+
+size_t implicit_factor_elems(const tsu_grid& g) {
+  return (size_t)g.ny * g.ld + 2 * (size_t)g.nx * implicit_ldT(g.ny);
+}
+
+size_t implicit_ws_elems(const tsu_grid& g) {
+  const size_t t = (size_t)g.nx * implicit_ldT(g.ny), r = (size_t)g.ny * g.ld;
+  return t + (t > r ? t : r);
+}
+
+cudaError_t launch_implicit_factor(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, void* fac,
+                                   cudaStream_t s) {
+  const size_t es = dtype == TSU_F32 ? 4 : 8;
+  tsu_grid tg{g.nx, g.ny, g.ld, 0.0, 0.0};
+  cudaError_t e = cudaMemsetAsync(fac, 0, implicit_factor_elems(tg) * es, s);
+  if (e != cudaSuccess) return e;
+  const double sx = g.sigma * g.cx, sy = g.sigma * g.cy;
+  const unsigned bx = (unsigned)((g.ny + 127) / 128), by = (unsigned)((g.nx + 127) / 128);
+  if (dtype == TSU_F32) {
+    float* mx = (float*)fac;
+    float* myT = mx + (int64_t)g.ny * g.ld;
+    float* kyT = myT + (int64_t)g.nx * g.ldT;
+    k_imp_factor_x<float><<<bx, 128, 0, s>>>(g.nx, g.ny, g.ld, sx, (const float*)hx, mx);
+    k_imp_factor_y<float><<<by, 128, 0, s>>>(g.nx, g.ny, g.ld, g.ldT, sy, (const float*)hy, myT, kyT);
+  } else {
+    double* mx = (double*)fac;
+    double* myT = mx + (int64_t)g.ny * g.ld;
+    double* kyT = myT + (int64_t)g.nx * g.ldT;
+    k_imp_factor_x<double><<<bx, 128, 0, s>>>(g.nx, g.ny, g.ld, sx, (const double*)hx, mx);
+    k_imp_factor_y<double><<<by, 128, 0, s>>>(g.nx, g.ny, g.ld, g.ldT, sy, (const double*)hy, myT, kyT);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_implicit_prepare(const ImplicitGeom& g, int dtype, const void* u0, void* u, void* v,
+                                    cudaStream_t s) {
+  if (dtype == TSU_F32)
+    k_imp_prepare<float><<<152 * 8, 256, 0, s>>>(g.nx, g.ny, g.ld, (const float*)u0, (float*)u, (float*)v);
+  else
+    k_imp_prepare<double><<<152 * 8, 256, 0, s>>>(g.nx, g.ny, g.ld, (const double*)u0, (double*)u, (double*)v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_implicit(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, const void* fac,
+                            void* u, void* v, const void* u1, int64_t nsteps, bool start, void* ws,
+                            cudaStream_t s) {
+  return dtype == TSU_F32 ? imp_run<float>(g, hx, hy, fac, u, v, u1, nsteps, start, ws, s)
+                          : imp_run<double>(g, hx, hy, fac, u, v, u1, nsteps, start, ws, s);
+}
+
+}  // namespace tsu

@@ -907,4 +907,113 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
   return TSU_OK;
 }
 
+// ---- implicit comparator (Sec. 3.3) -------------------------------------------------------------
+
+static tsu::ImplicitGeom implicit_geom(const tsu_grid* g, double tau, double sigma) {
+  tsu::ImplicitGeom ig;
+  ig.nx = g->nx;
+  ig.ny = g->ny;
+  ig.ld = g->ld;
+  ig.ldT = tsu::implicit_ldT(g->ny);
+  ig.cx = tau * tau / (g->dx * g->dx);
+  ig.cy = tau * tau / (g->dy * g->dy);
+  ig.tau = tau;
+  ig.sigma = sigma;
+  return ig;
+}
+
+// sigma >= 1/4: stable for every tau; below, the explicit bound scaled by (1 - 4 sigma)
+static int check_implicit(const tsu_grid* g, int dtype, double tau, double sigma, const tsu_medium* m) {
+  TRY(check_grid(g));
+  TRY(check_dtype(dtype));
+  if (!m) return fail(TSU_EINVAL, "medium is NULL");
+  TRY(check_field(m->hx, "hx"));
+  TRY(check_field(m->hy, "hy"));
+  if (!(tau > 0.0) || !isfinite(tau)) return fail(TSU_EINVAL, "tau must be positive and finite");
+  if (!(sigma >= 0.0) || !isfinite(sigma)) return fail(TSU_EINVAL, "sigma must be >= 0 and finite");
+  if (!(m->hx_max >= 0.0) || !(m->hy_max >= 0.0)) return fail(TSU_EINVAL, "medium maxima must be >= 0");
+  if (sigma < 0.25) {
+    const double q = tau * tau * (m->hx_max / (g->dx * g->dx) + m->hy_max / (g->dy * g->dy));
+    if (q * (1.0 - 4.0 * sigma) > 1.0)
+      return fail(TSU_ECFL, "sigma = %.6g < 1/4 and tau^2 (hx_max/dx^2 + hy_max/dy^2) (1 - 4 sigma) = %.6g > 1",
+                  sigma, q * (1.0 - 4.0 * sigma));
+  }
+  return TSU_OK;
+}
+
+static int check_implicit_state(const tsu_state* st, bool need_roles) {
+  if (!st) return fail(TSU_EINVAL, "state is NULL");
+  if (st->form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "the implicit scheme runs in the increment form");
+  if (st->nbuf < 2 || st->nbuf > 4) return fail(TSU_EINVAL, "state needs 2..4 buffers (nbuf = %d)", st->nbuf);
+  for (int b = 0; b < st->nbuf; ++b)
+    if (!st->buf[b] || !aligned16(st->buf[b])) return fail(TSU_EINVAL, "state buf[%d] NULL or misaligned", b);
+  if (need_roles && (st->cur < 0 || st->cur >= st->nbuf || st->aux < 0 || st->aux >= st->nbuf || st->cur == st->aux))
+    return fail(TSU_EINVAL, "state cur/aux invalid (%d, %d)", st->cur, st->aux);
+  return TSU_OK;
+}
+
+int tsu_implicit_sizes(const tsu_grid* g, int dtype, size_t* factor_bytes, size_t* ws_bytes) {
+  g_err[0] = 0;
+  TRY(check_grid(g));
+  TRY(check_dtype(dtype));
+  if (!factor_bytes || !ws_bytes) return fail(TSU_EINVAL, "output pointer is NULL");
+  *factor_bytes = tsu::implicit_factor_elems(*g) * elem_size(dtype);
+  *ws_bytes = tsu::implicit_ws_elems(*g) * elem_size(dtype);
+  return TSU_OK;
+}
+
+int tsu_implicit_factor(const tsu_grid* g, int dtype, double tau, double sigma, const tsu_medium* m, void* factor,
+                        size_t factor_bytes, void* stream) {
+  g_err[0] = 0;
+  TRY(check_implicit(g, dtype, tau, sigma, m));
+  TRY(check_field(factor, "factor"));
+  const size_t need = tsu::implicit_factor_elems(*g) * elem_size(dtype);
+  if (factor_bytes < need) return fail(TSU_ENOMEM, "factor needs %zu B (got %zu)", need, factor_bytes);
+  cudaError_t e = tsu::launch_implicit_factor(implicit_geom(g, tau, sigma), dtype, m->hx, m->hy, factor,
+                                              (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_implicit_factor launch");
+  return TSU_OK;
+}
+
+int tsu_implicit_init(const tsu_grid* g, int dtype, double tau, double sigma, const tsu_medium* m, const void* factor,
+                      const void* u0, const void* u1, tsu_state* st, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  TRY(check_implicit(g, dtype, tau, sigma, m));
+  TRY(check_field(factor, "factor"));
+  TRY(check_field(u0, "u0"));
+  if (u1) TRY(check_field(u1, "u1"));
+  TRY(check_implicit_state(st, false));
+  TRY(check_field(ws, "workspace"));
+  const size_t need = tsu::implicit_ws_elems(*g) * elem_size(dtype);
+  if (ws_bytes < need) return fail(TSU_ENOMEM, "workspace needs %zu B (got %zu)", need, ws_bytes);
+  const tsu::ImplicitGeom ig = implicit_geom(g, tau, sigma);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = tsu::launch_implicit_prepare(ig, dtype, u0, st->buf[0], st->buf[1], s);
+  if (e == cudaSuccess)
+    e = tsu::launch_implicit(ig, dtype, m->hx, m->hy, factor, st->buf[0], st->buf[1], u1, 1, true, ws, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_implicit_init launch");
+  st->cur = 0;
+  st->aux = 1;
+  st->step = 1;
+  return TSU_OK;
+}
+
+int tsu_implicit_step_n(const tsu_grid* g, int dtype, double tau, double sigma, const tsu_medium* m,
+                        const void* factor, tsu_state* st, int64_t nsteps, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  TRY(check_implicit(g, dtype, tau, sigma, m));
+  TRY(check_field(factor, "factor"));
+  TRY(check_implicit_state(st, true));
+  if (nsteps < 0) return fail(TSU_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return TSU_OK;
+  TRY(check_field(ws, "workspace"));
+  const size_t need = tsu::implicit_ws_elems(*g) * elem_size(dtype);
+  if (ws_bytes < need) return fail(TSU_ENOMEM, "workspace needs %zu B (got %zu)", need, ws_bytes);
+  cudaError_t e = tsu::launch_implicit(implicit_geom(g, tau, sigma), dtype, m->hx, m->hy, factor, st->buf[st->cur],
+                                       st->buf[st->aux], nullptr, nsteps, false, ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tsu_implicit_step_n launch");
+  st->step += nsteps;
+  return TSU_OK;
+}
+
 }  // extern "C"

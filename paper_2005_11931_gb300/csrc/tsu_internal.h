@@ -161,4 +161,26 @@ cudaError_t launch_adjoint_wtb(const StencilGeom& g, int k, int rows, const void
                                cudaStream_t s);
 cudaError_t launch_flush(const StencilGeom& g, void* g32x, void* g32y, double* gx, double* gy, cudaStream_t s);
 
+// Implicit comparator (k_implicit.cu): the factorized scheme (I - s B_x)(I - s B_y) w = B u.
+// Transposed fields have nx rows of ldT = roundup(ny, 32) elements.  Factor layout (elements):
+// mx [ny][ld], myT [nx][ldT], kyT [nx][ldT]; workspace: zT [nx][ldT] then one scratch field of
+// max(ny ld, nx ldT) elements.
+struct ImplicitGeom {
+  int32_t nx, ny;
+  int64_t ld, ldT;
+  double cx, cy, tau, sigma;
+};
+int64_t implicit_ldT(int32_t ny);
+size_t implicit_factor_elems(const tsu_grid& g);
+size_t implicit_ws_elems(const tsu_grid& g);
+cudaError_t launch_implicit_factor(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, void* fac,
+                                   cudaStream_t s);
+// u <- u0 on interior nodes and 0 elsewhere, v <- 0 (u0 may be u)
+cudaError_t launch_implicit_prepare(const ImplicitGeom& g, int dtype, const void* u0, void* u, void* v,
+                                    cudaStream_t s);
+// start (start = true: v = tau u1 + w^0 / 2, u += v) or nsteps steps (v += w^n, u += v), in place
+cudaError_t launch_implicit(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, const void* fac,
+                            void* u, void* v, const void* u1, int64_t nsteps, bool start, void* ws,
+                            cudaStream_t s);
+
 }  // namespace tsu

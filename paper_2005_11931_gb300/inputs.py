@@ -196,5 +196,15 @@ def paper_case1_2d(n: int = 513, eps: float = 0.8, steps: int = 200) -> dict:
                                 steps, "f64"))
 
 
+def paper_table1(n: int, steps: int = 100, dtype: str = "f64") -> Problem:
+    """The paper's GPU timing runs (Sec. 4, Table 1): the 2D Case 1 problem of paper_case1_2d on
+    n x n nodes (the paper's 256 .. 4096), dt = 0.05 in paper units, T = 5.0, so 100 steps.  In
+    the unit box the step is tau = 0.05 / 100 (time rescales with length); its Courant number
+    tau sqrt(100) / dx grows from 1.3 (256) to 20 (4096), beyond any explicit scheme, which is
+    why the paper's scheme is implicit."""
+    p = paper_case1_2d(n=n, steps=steps)["problem"]
+    return Problem(f"paper_table1_{n}", n, p.depth, p.u0, steps, dtype, extra=dict(tau=0.05 / 100.0))
+
+
 def random_directions(shape, count: int, rng: np.random.Generator) -> np.ndarray:
     return rng.standard_normal((count,) + tuple(shape))

@@ -119,6 +119,12 @@ def load():
                          vp, vp, vp, vp, vp, C.c_size_t, vp], C.c_int),
         "tsu_observe": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), vp, i32, vp, vp, vp,
                          C.c_size_t, vp], C.c_int),
+        "tsu_implicit_sizes": ([C.POINTER(Grid), C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
+        "tsu_implicit_factor": ([C.POINTER(Grid), C.c_int, dbl, dbl, C.POINTER(Medium), vp, C.c_size_t, vp], C.c_int),
+        "tsu_implicit_init": ([C.POINTER(Grid), C.c_int, dbl, dbl, C.POINTER(Medium), vp, vp, vp, C.POINTER(State),
+                               vp, C.c_size_t, vp], C.c_int),
+        "tsu_implicit_step_n": ([C.POINTER(Grid), C.c_int, dbl, dbl, C.POINTER(Medium), vp, C.POINTER(State), i64,
+                                 vp, C.c_size_t, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -316,6 +322,82 @@ def tsu_observe(g: Grid, dtype, tau: float, medium: Medium, state: State, energy
 # ---------------------------------------------------------------------------------------------
 # Convenience: one forward problem with torch-owned buffers
 # ---------------------------------------------------------------------------------------------
+def tsu_implicit_sizes(g: Grid, dtype) -> tuple[int, int]:
+    fb, wb = C.c_size_t(0), C.c_size_t(0)
+    _check(load().tsu_implicit_sizes(C.byref(g), dtype_code(dtype), C.byref(fb), C.byref(wb)), "tsu_implicit_sizes")
+    return int(fb.value), int(wb.value)
+
+
+def tsu_implicit_factor(g: Grid, dtype, tau: float, sigma: float, medium: Medium, factor, factor_bytes: int,
+                        stream=None):
+    _check(load().tsu_implicit_factor(C.byref(g), dtype_code(dtype), float(tau), float(sigma), C.byref(medium),
+                                      _ptr(factor), int(factor_bytes), _stream(stream)), "tsu_implicit_factor")
+
+
+def tsu_implicit_init(g: Grid, dtype, tau: float, sigma: float, medium: Medium, factor, u0, u1, state: State, ws,
+                      ws_bytes: int, stream=None):
+    _check(load().tsu_implicit_init(C.byref(g), dtype_code(dtype), float(tau), float(sigma), C.byref(medium),
+                                    _ptr(factor), _ptr(u0), _ptr(u1), C.byref(state), _ptr(ws), int(ws_bytes),
+                                    _stream(stream)), "tsu_implicit_init")
+
+
+def tsu_implicit_step_n(g: Grid, dtype, tau: float, sigma: float, medium: Medium, factor, state: State, nsteps: int,
+                        ws, ws_bytes: int, stream=None):
+    _check(load().tsu_implicit_step_n(C.byref(g), dtype_code(dtype), float(tau), float(sigma), C.byref(medium),
+                                      _ptr(factor), C.byref(state), int(nsteps), _ptr(ws), int(ws_bytes),
+                                      _stream(stream)), "tsu_implicit_step_n")
+
+
+class ImplicitSimulation:
+    """Buffers and calls of one problem stepped by the implicit comparator (marshalling only):
+    the depth, the line systems' factor, the workspace and the state (u, v)."""
+
+    def __init__(self, g, dtype, hx, hy, ext, tau, sigma, medium, factor, ws, bufs, state):
+        self.g, self.dtype, self.hx, self.hy, self.ext = g, dtype, hx, hy, ext
+        self.tau, self.sigma, self.medium = tau, sigma, medium
+        self.factor, self.ws, self.bufs, self.state = factor, ws, bufs, state
+
+    @classmethod
+    def create(cls, n: int, depth: dict, dtype="f64", tau=None, cfl: float = 0.4, sigma: float = 0.25, ny=None,
+               ld=None, stream=None, device="cuda"):
+        g = grid(n, ny, ld)
+        code = dtype_code(dtype)
+        hx = empty_field(g, code, device)
+        hy = empty_field(g, code, device)
+        ext_dev = torch.zeros(4, dtype=torch.float64, device=device)
+        ext = tsu_make_depth(g, depth, code, hx, hy, ext_dev, sync=True, stream=stream)
+        if tau is None:
+            tau = cfl * min(g.dx, g.dy) / float(np.sqrt(max(ext[1], ext[3])))
+        med = Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
+        fb, wb = tsu_implicit_sizes(g, code)
+        factor = torch.empty(fb, dtype=torch.uint8, device=device)
+        ws = torch.empty(wb, dtype=torch.uint8, device=device)
+        tsu_implicit_factor(g, code, tau, sigma, med, factor, fb, stream)
+        bufs = [empty_field(g, code, device) for _ in range(2)]
+        st = State()
+        for k, b in enumerate(bufs):
+            st.buf[k] = b.data_ptr()
+        st.nbuf = 2
+        st.form = TSU_FORM_INCREMENT
+        return cls(g, code, hx, hy, ext, float(tau), float(sigma), med, factor, ws, bufs, st)
+
+    def init(self, u0: torch.Tensor, u1: torch.Tensor | None = None, stream=None):
+        tsu_implicit_init(self.g, self.dtype, self.tau, self.sigma, self.medium, self.factor, u0, u1, self.state,
+                          self.ws, self.ws.numel(), stream)
+
+    def step(self, nsteps: int, stream=None):
+        tsu_implicit_step_n(self.g, self.dtype, self.tau, self.sigma, self.medium, self.factor, self.state, nsteps,
+                            self.ws, self.ws.numel(), stream)
+
+    @property
+    def u(self) -> torch.Tensor:
+        return self.bufs[self.state.cur]
+
+    @property
+    def v(self) -> torch.Tensor:
+        return self.bufs[self.state.aux]
+
+
 @dataclass
 class Simulation:
     """Buffers and calls of one forward problem (marshalling only)."""
