@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched, 16384^2 and paper Case 1 measurements")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch (from profiles/)")
-    ap.add_argument("--measure", choices=["adjoint", "batched", "large", "paper_case1"], default=None,
+    ap.add_argument("--measure", choices=["adjoint", "batched", "large", "paper_case1", "implicit"], default=None,
                     help="run only this side measurement and print its result (a profiling aid)")
-    ap.add_argument("--measure-n", type=int, default=2048, help="grid side of --measure adjoint")
+    ap.add_argument("--measure-n", type=int, default=0,
+                    help="grid side of --measure adjoint (0: 2048) or implicit (0: every Table 1 size)")
     ap.add_argument("--measure-steps", type=int, default=4000, help="leapfrog steps of --measure adjoint/batched")
     return ap.parse_args()
 
@@ -360,6 +361,7 @@ def run_gpu(args):
         extras["batched"] = measure_batched()
         extras["large"] = measure_large()
         extras["paper_case1"] = measure_paper_case1()
+        extras["implicit_table1"] = measure_implicit()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         r = oracle_sample(p.n, 64 if p.n >= 4096 else 256)
@@ -581,14 +583,56 @@ def measure_paper_case1(n=4097, steps=2000, warm=1):
             "energy_drift": float(np.max(np.abs(en - en[0])) / en[0])}
 
 
+# Sec. 4, Table 1: GPU time in seconds of the paper's implicit solver (cyclic reduction, Case 1, dt
+# = 0.05, T = 5, 100 steps) on an RTX 2080 Ti, per grid side.  Context only: other hardware.
+PAPER_TABLE1_GPU_S = {256: 0.88, 512: 2.07, 1024: 7.16, 2048: 20.30, 4096: 62.76}
+
+
+def measure_implicit(sizes=(256, 512, 1024, 2048, 4096)):
+    """The implicit comparator on the paper's Table 1 runs: the 2D Case 1 problem on n x n nodes,
+    dt = 0.05 in paper units (Courant number 1.3 .. 20), 100 steps, sigma = 1/4, FP64 and FP32.
+    Algorithmic bytes per node and step: the x pass reads u, hx, hy and the pivots and writes
+    the transposed result; the y pass reads it with the y pivots and coefficients, and reads and
+    writes v and u: 12 fields, 48 B in FP32, 96 B in FP64."""
+    import torch
+
+    from paper_2005_11931_gb300 import inputs, tsu
+
+    peak, _ = load_peaks()
+    out = {"workload": "paper Table 1 runs: Case 1 depth (step 100 -> 10, Friedrichs, eps 0.8), n x n nodes, "
+                       "dt = 0.05 (paper units), 100 steps, factorized implicit scheme, sigma = 1/4",
+           "bytes_per_node_step": {"f32": 48, "f64": 96}, "runs": []}
+    for dtype in ("f32", "f64"):
+        for n in sizes:
+            p = inputs.paper_table1(n)
+            sim = tsu.ImplicitSimulation.create(n, p.depth, dtype=dtype, tau=p.extra["tau"])
+            u0 = torch.from_numpy(p.initial(sim.g.ld)).to(tsu.DTYPES[sim.dtype]).cuda()
+
+            def run():
+                sim.init(u0)
+                sim.step(p.steps - 1)
+
+            run()
+            ms = _events_ms(run)
+            nodes = (n - 2) ** 2
+            gbs = nodes * p.steps * (48 if dtype == "f32" else 96) / (ms / 1e3) / 1e9
+            out["runs"].append({"dtype": dtype, "n": n, "ms": ms, "glups": nodes * p.steps / ms / 1e6,
+                                "gbs_algorithmic": gbs, "frac_of_measured_peak": gbs / peak,
+                                "paper_table1_gpu_s": PAPER_TABLE1_GPU_S.get(n)})
+            del sim
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.measure:
-        fn = {"adjoint": lambda: measure_adjoint(args.measure_n, args.measure_steps),
+        fn = {"adjoint": lambda: measure_adjoint(args.measure_n or 2048, args.measure_steps),
               "batched": lambda: measure_batched(args.measure_steps, rows=args.rows),
-              "large": measure_large, "paper_case1": measure_paper_case1}[args.measure]
+              "large": measure_large, "paper_case1": measure_paper_case1,
+              "implicit": lambda: measure_implicit((args.measure_n,) if args.measure_n else (256, 512, 1024, 2048, 4096))
+              }[args.measure]
         print(json.dumps(fn()))
         return 0
     return run_gpu(args)

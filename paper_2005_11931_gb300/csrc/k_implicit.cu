@@ -127,7 +127,15 @@ struct ImpArgs {
   int start;
 };
 
-// x pass: one warp per row j; R rows per CTA.
+// Fields of one segment of the x pass's forward substitution (one lane's four nodes).
+template <typename T>
+struct XSeg {
+  V4<T> uc, uu, ud, hx, hyu, hyd, m;
+  T ur;  // lane 31: u right of the segment
+};
+
+// x pass: one warp per row j; R rows per CTA.  Every loop loads the next segment's fields before
+// it works on the current one, so the loads of one segment overlap the scan of the previous.
 template <typename T, int R>
 __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
   __shared__ T tile[R][kImpSeg + 1];
@@ -137,65 +145,74 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
   const int nseg = (a.nx - 1 + kImpSeg - 1) / kImpSeg;
   const int64_t base = (int64_t)j * a.ld;
   T* line = a.scratch + (row_in ? base : 0);
+  auto load_fwd = [&](int s) {
+    XSeg<T> f{zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), T(0)};
+    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+    if (s < nseg && row_in && c0 < a.ld) {
+      f.uc = ld4(a.u + base + c0);
+      f.uu = ld4(a.u + base + a.ld + c0);
+      f.ud = ld4(a.u + base - a.ld + c0);
+      f.hx = ld4(a.hx + base + c0);
+      f.hyu = ld4(a.hy + base + c0);
+      f.hyd = ld4(a.hy + base - a.ld + c0);
+      f.m = ld4(a.mx + base + c0);
+      if (lane == 31 && c0 + 4 < a.ld) f.ur = a.u[base + c0 + 4];
+    }
+    return f;
+  };
   // forward: r = B u, then d_k = alpha_k d_{k-1} + beta_k
   T carry = T(0), cu = T(0), ch = T(0);  // d, u and hx at the node before the segment
+  XSeg<T> f = load_fwd(0);
   for (int s = 0; s < nseg; ++s) {
+    const XSeg<T> nf = load_fwd(s + 1);
     const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    const bool in = row_in && c0 < a.ld;
-    V4<T> uc = zero4<T>(), uu = zero4<T>(), ud = zero4<T>(), hxv = zero4<T>(), hyu = zero4<T>(),
-          hyd = zero4<T>(), m = zero4<T>();
-    T ur_own = T(0);
-    if (in) {
-      uc = ld4(a.u + base + c0);
-      uu = ld4(a.u + base + a.ld + c0);
-      ud = ld4(a.u + base - a.ld + c0);
-      hxv = ld4(a.hx + base + c0);
-      hyu = ld4(a.hy + base + c0);
-      hyd = ld4(a.hy + base - a.ld + c0);
-      m = ld4(a.mx + base + c0);
-      if (lane == 31 && c0 + 4 < a.ld) ur_own = a.u[base + c0 + 4];
-    }
-    T ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1), hl = __shfl_up_sync(0xffffffffu, hxv.a[3], 1);
-    T ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
+    T ul = __shfl_up_sync(0xffffffffu, f.uc.a[3], 1), hl = __shfl_up_sync(0xffffffffu, f.hx.a[3], 1);
+    T ur = __shfl_down_sync(0xffffffffu, f.uc.a[0], 1);
     if (lane == 0) {
       ul = cu;
       hl = ch;
     }
-    if (lane == 31) ur = ur_own;
+    if (lane == 31) ur = f.ur;
     V4<T> alpha, beta;
-    T fl = mul_(hl, sub_(uc.a[0], ul));  // x flux left of the lane's first node
+    T fl = mul_(hl, sub_(f.uc.a[0], ul));  // x flux left of the lane's first node
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const T right = e < 3 ? uc.a[e + 1] : ur;
-      const T fr = mul_(hxv.a[e], sub_(right, uc.a[e]));
+      const T right = e < 3 ? f.uc.a[e + 1] : ur;
+      const T fr = mul_(f.hx.a[e], sub_(right, f.uc.a[e]));
       const T fx = sub_(fr, fl);
-      const T fy = sub_(mul_(hyu.a[e], sub_(uu.a[e], uc.a[e])), mul_(hyd.a[e], sub_(uc.a[e], ud.a[e])));
+      const T fy = sub_(mul_(f.hyu.a[e], sub_(f.uu.a[e], f.uc.a[e])), mul_(f.hyd.a[e], sub_(f.uc.a[e], f.ud.a[e])));
       const T r = fma_(a.cx, fx, mul_(a.cy, fy));
-      const T hprev = e == 0 ? hl : hxv.a[e - 1];
-      const bool unk = m.a[e] != T(0);  // off the unknowns m = 0: the node holds 0
-      alpha.a[e] = unk ? mul_(mul_(a.sx, hprev), m.a[e]) : T(0);
-      beta.a[e] = unk ? mul_(m.a[e], r) : T(0);
+      const T hprev = e == 0 ? hl : f.hx.a[e - 1];
+      const bool unk = f.m.a[e] != T(0);  // off the unknowns m = 0: the node holds 0
+      alpha.a[e] = unk ? mul_(mul_(a.sx, hprev), f.m.a[e]) : T(0);
+      beta.a[e] = unk ? mul_(f.m.a[e], r) : T(0);
       fl = fr;
     }
     const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
-    if (in) st4(line + c0, d);
-    cu = __shfl_sync(0xffffffffu, uc.a[3], 31);
-    ch = __shfl_sync(0xffffffffu, hxv.a[3], 31);
+    if (row_in && c0 < a.ld) st4(line + c0, d);
+    cu = __shfl_sync(0xffffffffu, f.uc.a[3], 31);
+    ch = __shfl_sync(0xffffffffu, f.hx.a[3], 31);
+    f = nf;
   }
   // backward: z_k = gamma_k z_{k+1} + d_k, written transposed through the tile
-  carry = T(0);
-  for (int s = nseg - 1; s >= 0; --s) {
+  auto load_bwd = [&](int s, V4<T>& d, V4<T>& m, V4<T>& h) {
+    d = m = h = zero4<T>();
     const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    const bool in = row_in && c0 < a.ld;
-    V4<T> d = zero4<T>(), m = zero4<T>(), hxv = zero4<T>();
-    if (in) {
+    if (s >= 0 && row_in && c0 < a.ld) {
       d = ld4(line + c0);
       m = ld4(a.mx + base + c0);
-      hxv = ld4(a.hx + base + c0);
+      h = ld4(a.hx + base + c0);
     }
+  };
+  carry = T(0);
+  V4<T> d, m, h;
+  load_bwd(nseg - 1, d, m, h);
+  for (int s = nseg - 1; s >= 0; --s) {
+    V4<T> nd, nm, nh;
+    load_bwd(s - 1, nd, nm, nh);
     V4<T> gamma;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(a.sx, hxv.a[e]), m.a[e]) : T(0);
+    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(a.sx, h.a[e]), m.a[e]) : T(0);
     const V4<T> z = segment_solve<T, false>(gamma, d, carry, lane);
 #pragma unroll
     for (int e = 0; e < 4; ++e) tile[w][4 * lane + e] = z.a[e];
@@ -207,13 +224,18 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
       if (c < a.nx) a.zT[c * a.ldT + j0 + rr] = tile[rr][cc];
     }
     __syncthreads();
+    d = nd;
+    m = nm;
+    h = nh;
   }
 }
 
 // y pass: one warp per column i (a row of zT); R columns per CTA; w written back row-major and
-// folded into v and u.
+// folded into v and u.  Loads are issued a segment ahead as in the x pass, and the v and u each
+// thread updates after a segment's scan are read before the scan.
 template <typename T, int R>
 __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
+  constexpr int kPer = kImpSeg * R / (R * 32);  // tile entries each thread writes back: 4
   __shared__ T tile[R][kImpSeg + 1];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * R, i = i0 + wp;
@@ -221,16 +243,22 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
   const int nseg = (a.ny - 1 + kImpSeg - 1) / kImpSeg;
   const int64_t base = (int64_t)i * a.ldT;
   T* line = a.scratch + (col_in ? base : 0);
-  T carry = T(0), ck = T(0);  // d and s cy hy at the node before the segment
-  for (int s = 0; s < nseg; ++s) {
+  auto load3 = [&](int s, const T* first, V4<T>& x, V4<T>& m, V4<T>& k) {
+    x = m = k = zero4<T>();
     const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    const bool in = col_in && c0 < a.ldT;
-    V4<T> z = zero4<T>(), m = zero4<T>(), k = zero4<T>();
-    if (in) {
-      z = ld4(a.zT + base + c0);
+    if (s >= 0 && s < nseg && col_in && c0 < a.ldT) {
+      x = ld4(first + c0);
       m = ld4(a.myT + base + c0);
       k = ld4(a.kyT + base + c0);
     }
+  };
+  T carry = T(0), ck = T(0);  // d and s cy hy at the node before the segment
+  V4<T> z, m, k;
+  load3(0, a.zT + base, z, m, k);
+  for (int s = 0; s < nseg; ++s) {
+    V4<T> nz, nm, nk;
+    load3(s + 1, a.zT + base, nz, nm, nk);
+    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
     T kl = __shfl_up_sync(0xffffffffu, k.a[3], 1);
     if (lane == 0) kl = ck;
     V4<T> alpha, beta;
@@ -242,45 +270,59 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
       beta.a[e] = unk ? mul_(m.a[e], z.a[e]) : T(0);
     }
     const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
-    if (in) st4(line + c0, d);
+    if (col_in && c0 < a.ldT) st4(line + c0, d);
     ck = __shfl_sync(0xffffffffu, k.a[3], 31);
+    z = nz;
+    m = nm;
+    k = nk;
   }
   carry = T(0);
+  V4<T> d;
+  load3(nseg - 1, line, d, m, k);
   for (int s = nseg - 1; s >= 0; --s) {
-    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    const bool in = col_in && c0 < a.ldT;
-    V4<T> d = zero4<T>(), m = zero4<T>(), k = zero4<T>();
-    if (in) {
-      d = ld4(line + c0);
-      m = ld4(a.myT + base + c0);
-      k = ld4(a.kyT + base + c0);
+    // the nodes this thread updates after the scan (row jj, column ii of the tile), read now
+    T vq[kPer], uq[kPer], u1q[kPer];
+    int64_t oq[kPer];
+#pragma unroll
+    for (int p = 0; p < kPer; ++p) {
+      const int q = threadIdx.x + p * R * 32;
+      const int cc = q / R, rr = q - cc * R;
+      const int jj = s * kImpSeg + cc, ii = i0 + rr;
+      const bool node = jj >= 1 && jj <= a.ny - 2 && ii >= 1 && ii <= a.nx - 2;
+      oq[p] = node ? (int64_t)jj * a.ld + ii : -1;
+      vq[p] = uq[p] = u1q[p] = T(0);
+      if (node) {
+        uq[p] = a.uo[oq[p]];
+        if (a.start)
+          u1q[p] = a.u1 ? a.u1[oq[p]] : T(0);
+        else
+          vq[p] = a.v[oq[p]];
+      }
     }
+    V4<T> nd, nm, nk;
+    load3(s - 1, line, nd, nm, nk);
     V4<T> gamma;
 #pragma unroll
     for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(k.a[e], m.a[e]) : T(0);
-    const V4<T> w = segment_solve<T, false>(gamma, d, carry, lane);
+    const V4<T> wv = segment_solve<T, false>(gamma, d, carry, lane);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) tile[wp][4 * lane + e] = w.a[e];
+    for (int e = 0; e < 4; ++e) tile[wp][4 * lane + e] = wv.a[e];
     __syncthreads();
     // row j of the segment, columns i0 .. i0 + R - 1: v += w (or the start), u += v
-    for (int q = threadIdx.x; q < kImpSeg * R; q += R * 32) {
+#pragma unroll
+    for (int p = 0; p < kPer; ++p) {
+      if (oq[p] < 0) continue;
+      const int q = threadIdx.x + p * R * 32;
       const int cc = q / R, rr = q - cc * R;
-      const int jj = s * kImpSeg + cc, ii = i0 + rr;
-      if (jj >= 1 && jj <= a.ny - 2 && ii >= 1 && ii <= a.nx - 2) {
-        const int64_t o = (int64_t)jj * a.ld + ii;
-        const T wv = tile[rr][cc];
-        T vn;
-        if (a.start) {
-          const T u1 = a.u1 ? a.u1[o] : T(0);
-          vn = fma_(a.tau, u1, mul_(T(0.5), wv));
-        } else {
-          vn = a.v[o] + wv;
-        }
-        a.v[o] = vn;
-        a.uo[o] = a.uo[o] + vn;
-      }
+      const T wt = tile[rr][cc];
+      const T vn = a.start ? fma_(a.tau, u1q[p], mul_(T(0.5), wt)) : vq[p] + wt;
+      a.v[oq[p]] = vn;
+      a.uo[oq[p]] = uq[p] + vn;
     }
     __syncthreads();
+    d = nd;
+    m = nm;
+    k = nk;
   }
 }
 
