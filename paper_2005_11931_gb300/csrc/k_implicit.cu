@@ -127,15 +127,7 @@ struct ImpArgs {
   int start;
 };
 
-// Fields of one segment of the x pass's forward substitution (one lane's four nodes).
-template <typename T>
-struct XSeg {
-  V4<T> uc, uu, ud, hx, hyu, hyd, m;
-  T ur;  // lane 31: u right of the segment
-};
-
-// x pass: one warp per row j; R rows per CTA.  Every loop loads the next segment's fields before
-// it works on the current one, so the loads of one segment overlap the scan of the previous.
+// x pass: one warp per row j; R rows per CTA.
 template <typename T, int R>
 __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
   __shared__ T tile[R][kImpSeg + 1];
@@ -145,74 +137,65 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
   const int nseg = (a.nx - 1 + kImpSeg - 1) / kImpSeg;
   const int64_t base = (int64_t)j * a.ld;
   T* line = a.scratch + (row_in ? base : 0);
-  auto load_fwd = [&](int s) {
-    XSeg<T> f{zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), zero4<T>(), T(0)};
-    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    if (s < nseg && row_in && c0 < a.ld) {
-      f.uc = ld4(a.u + base + c0);
-      f.uu = ld4(a.u + base + a.ld + c0);
-      f.ud = ld4(a.u + base - a.ld + c0);
-      f.hx = ld4(a.hx + base + c0);
-      f.hyu = ld4(a.hy + base + c0);
-      f.hyd = ld4(a.hy + base - a.ld + c0);
-      f.m = ld4(a.mx + base + c0);
-      if (lane == 31 && c0 + 4 < a.ld) f.ur = a.u[base + c0 + 4];
-    }
-    return f;
-  };
   // forward: r = B u, then d_k = alpha_k d_{k-1} + beta_k
   T carry = T(0), cu = T(0), ch = T(0);  // d, u and hx at the node before the segment
-  XSeg<T> f = load_fwd(0);
   for (int s = 0; s < nseg; ++s) {
-    const XSeg<T> nf = load_fwd(s + 1);
     const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    T ul = __shfl_up_sync(0xffffffffu, f.uc.a[3], 1), hl = __shfl_up_sync(0xffffffffu, f.hx.a[3], 1);
-    T ur = __shfl_down_sync(0xffffffffu, f.uc.a[0], 1);
+    const bool in = row_in && c0 < a.ld;
+    V4<T> uc = zero4<T>(), uu = zero4<T>(), ud = zero4<T>(), hxv = zero4<T>(), hyu = zero4<T>(),
+          hyd = zero4<T>(), m = zero4<T>();
+    T ur_own = T(0);
+    if (in) {
+      uc = ld4(a.u + base + c0);
+      uu = ld4(a.u + base + a.ld + c0);
+      ud = ld4(a.u + base - a.ld + c0);
+      hxv = ld4(a.hx + base + c0);
+      hyu = ld4(a.hy + base + c0);
+      hyd = ld4(a.hy + base - a.ld + c0);
+      m = ld4(a.mx + base + c0);
+      if (lane == 31 && c0 + 4 < a.ld) ur_own = a.u[base + c0 + 4];
+    }
+    T ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1), hl = __shfl_up_sync(0xffffffffu, hxv.a[3], 1);
+    T ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
     if (lane == 0) {
       ul = cu;
       hl = ch;
     }
-    if (lane == 31) ur = f.ur;
+    if (lane == 31) ur = ur_own;
     V4<T> alpha, beta;
-    T fl = mul_(hl, sub_(f.uc.a[0], ul));  // x flux left of the lane's first node
+    T fl = mul_(hl, sub_(uc.a[0], ul));  // x flux left of the lane's first node
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const T right = e < 3 ? f.uc.a[e + 1] : ur;
-      const T fr = mul_(f.hx.a[e], sub_(right, f.uc.a[e]));
+      const T right = e < 3 ? uc.a[e + 1] : ur;
+      const T fr = mul_(hxv.a[e], sub_(right, uc.a[e]));
       const T fx = sub_(fr, fl);
-      const T fy = sub_(mul_(f.hyu.a[e], sub_(f.uu.a[e], f.uc.a[e])), mul_(f.hyd.a[e], sub_(f.uc.a[e], f.ud.a[e])));
+      const T fy = sub_(mul_(hyu.a[e], sub_(uu.a[e], uc.a[e])), mul_(hyd.a[e], sub_(uc.a[e], ud.a[e])));
       const T r = fma_(a.cx, fx, mul_(a.cy, fy));
-      const T hprev = e == 0 ? hl : f.hx.a[e - 1];
-      const bool unk = f.m.a[e] != T(0);  // off the unknowns m = 0: the node holds 0
-      alpha.a[e] = unk ? mul_(mul_(a.sx, hprev), f.m.a[e]) : T(0);
-      beta.a[e] = unk ? mul_(f.m.a[e], r) : T(0);
+      const T hprev = e == 0 ? hl : hxv.a[e - 1];
+      const bool unk = m.a[e] != T(0);  // off the unknowns m = 0: the node holds 0
+      alpha.a[e] = unk ? mul_(mul_(a.sx, hprev), m.a[e]) : T(0);
+      beta.a[e] = unk ? mul_(m.a[e], r) : T(0);
       fl = fr;
     }
     const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
-    if (row_in && c0 < a.ld) st4(line + c0, d);
-    cu = __shfl_sync(0xffffffffu, f.uc.a[3], 31);
-    ch = __shfl_sync(0xffffffffu, f.hx.a[3], 31);
-    f = nf;
+    if (in) st4(line + c0, d);
+    cu = __shfl_sync(0xffffffffu, uc.a[3], 31);
+    ch = __shfl_sync(0xffffffffu, hxv.a[3], 31);
   }
   // backward: z_k = gamma_k z_{k+1} + d_k, written transposed through the tile
-  auto load_bwd = [&](int s, V4<T>& d, V4<T>& m, V4<T>& h) {
-    d = m = h = zero4<T>();
+  carry = T(0);
+  for (int s = nseg - 1; s >= 0; --s) {
     const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    if (s >= 0 && row_in && c0 < a.ld) {
+    const bool in = row_in && c0 < a.ld;
+    V4<T> d = zero4<T>(), m = zero4<T>(), hxv = zero4<T>();
+    if (in) {
       d = ld4(line + c0);
       m = ld4(a.mx + base + c0);
-      h = ld4(a.hx + base + c0);
+      hxv = ld4(a.hx + base + c0);
     }
-  };
-  carry = T(0);
-  V4<T> d, m, h;
-  load_bwd(nseg - 1, d, m, h);
-  for (int s = nseg - 1; s >= 0; --s) {
-    V4<T> nd, nm, nh;
-    load_bwd(s - 1, nd, nm, nh);
     V4<T> gamma;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(a.sx, h.a[e]), m.a[e]) : T(0);
+    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(a.sx, hxv.a[e]), m.a[e]) : T(0);
     const V4<T> z = segment_solve<T, false>(gamma, d, carry, lane);
 #pragma unroll
     for (int e = 0; e < 4; ++e) tile[w][4 * lane + e] = z.a[e];
@@ -224,15 +207,13 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
       if (c < a.nx) a.zT[c * a.ldT + j0 + rr] = tile[rr][cc];
     }
     __syncthreads();
-    d = nd;
-    m = nm;
-    h = nh;
   }
 }
 
 // y pass: one warp per column i (a row of zT); R columns per CTA; w written back row-major and
-// folded into v and u.  Loads are issued a segment ahead as in the x pass, and the v and u each
-// thread updates after a segment's scan are read before the scan.
+// folded into v and u.  Each segment's fields are loaded one segment ahead, and the v and u each
+// thread updates after a segment's scan are read before the scan (4096^2 FP32: 136 against 239
+// us per pass).  The x pass does not load ahead: at 72 registers instead of 48 it ran slower.
 template <typename T, int R>
 __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
   constexpr int kPer = kImpSeg * R / (R * 32);  // tile entries each thread writes back: 4
@@ -404,9 +385,10 @@ cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const
   a.v = (T*)v;
   a.uo = (T*)u;
   a.u1 = (const T*)u1;
-  // 8 lines per CTA (a 32-byte run per transposed column); 16 (64-byte runs) once both passes
-  // have work for at least two CTAs of 16 lines per SM
-  const bool wide = g.nx >= 16 * 2 * 152 && g.ny >= 16 * 2 * 152;
+  // 8 lines per CTA (a 32-byte run per transposed column); 16 (64-byte runs) for FP32 grids of
+  // 2048^2 and up (Table 1 runs, FP32: 4096^2 23.2 against 27.2 ms, 2048^2 7.3 against 7.4 ms;
+  // FP64, bound by the FP64 pipe, gains nothing and lost at 1024^2)
+  const bool wide = sizeof(T) == 4 && g.nx >= 2048 && g.ny >= 2048;
   for (int64_t n = 0; n < (start ? 1 : nsteps); ++n) {
     a.start = start ? 1 : 0;
     const cudaError_t e = wide ? launch_pair<T, 16>(a, s) : launch_pair<T, 8>(a, s);
