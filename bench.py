@@ -177,6 +177,26 @@ def oracle_sample(n: int, steps_sample: int):
                        f"interior updates), {threads} OpenMP threads", seconds=dt)
 
 
+def oracle_implicit_sample(sizes=(256, 512, 1024)):
+    """The oracle's implicit comparator (FP64, Thomas elimination line by line) on the smaller
+    Table 1 runs, whole (100 steps each): the CPU time beside the GPU's."""
+    import oracle
+    from paper_2005_11931_gb300 import inputs
+
+    threads = oracle.set_threads(len(os.sched_getaffinity(0)))
+    runs = []
+    for n in sizes:
+        p = inputs.paper_table1(n)
+        g = oracle.grid(n, n)
+        t0 = time.perf_counter()
+        hx, hy, _ = oracle.make_depth(g, p.depth)
+        oracle.implicit_forward(g, p.extra["tau"], 0.25, hx, hy, p.initial(), None, p.steps)
+        dt = time.perf_counter() - t0
+        runs.append({"n": n, "ms": dt * 1e3, "glups": (n - 2) ** 2 * p.steps / dt / 1e9})
+    return {"kind": "oracle", "cores": threads, "unit": "ms for the 100-step run",
+            "sample": "FP64 oracle implicit comparator, whole Table 1 runs, depth included", "runs": runs}
+
+
 def workload_config(n: int, S: int, form: str, world: int) -> dict:
     """The config both arms report: the workload they measure (the reference arm times a bounded
     sample of it, described in its cpu_baseline)."""
@@ -367,6 +387,8 @@ def run_gpu(args):
     if not args.no_cpu_baseline and world == 1:
         r = oracle_sample(p.n, 64 if p.n >= 4096 else 256)
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        if "implicit_table1" in extras:
+            cpu["implicit_table1"] = oracle_implicit_sample()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
