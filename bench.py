@@ -155,13 +155,14 @@ class ClockSampler:
 # -----------------------------------------------------------------------------------------------
 # CPU oracle leg (the reference arm of this build and the cpu_baseline object)
 # -----------------------------------------------------------------------------------------------
-def oracle_sample(n: int, steps_sample: int):
-    """Time the FP64 oracle, as it stands, on the workload's full grid for a few steps."""
+def oracle_sample(n: int, steps_sample: int, threads: int = 0):
+    """Time the FP64 oracle, as it stands, on the workload's full grid for a few steps (on every
+    core of the process, or on `threads` threads)."""
     import oracle
     from paper_2005_11931_gb300 import inputs
 
     cores = len(os.sched_getaffinity(0))
-    threads = oracle.set_threads(cores)
+    threads = oracle.set_threads(threads or cores)
     p = inputs.point_fp32(n)
     g = oracle.grid(n, n)
     u0 = p.initial()
@@ -387,6 +388,8 @@ def run_gpu(args):
     if not args.no_cpu_baseline and world == 1:
         r = oracle_sample(p.n, 64 if p.n >= 4096 else 256)
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        r1 = oracle_sample(p.n, 16 if p.n >= 4096 else 64, threads=1)
+        cpu["single_thread"] = {k: r1[k] for k in ("value", "unit", "cores", "sample")}
         if "implicit_table1" in extras:
             cpu["implicit_table1"] = oracle_implicit_sample()
     line = {

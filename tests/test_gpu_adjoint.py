@@ -109,6 +109,27 @@ def test_fp32_adjoint_matches_oracle_across_tiles(form, every, S):
         assert np.max(np.abs(gg[k] - ref[k])) <= 1e-4 * np.max(np.abs(ref[k])), k
 
 
+def test_fp32_adjoint_full_gradients_at_256_and_500_steps():
+    """The adjoint workload's problem at a size the FP64 oracle adjoint takes whole (256^2, 500
+    steps, 32 receivers on y = 0.8, checkpoints every 20): every gradient field (dJ/dhx, dJ/dhy,
+    dJ/du0, dJ/du1) of the FP32 GPU adjoint against the oracle's FP64 one.  Measured relative L2
+    errors are a few 1e-6; the bar is 2e-5."""
+    case = inputs.adjoint_case(n=256, steps=500, nrec=32)
+    p = case["problem"]
+    n, S = p.n, p.steps
+    rng = np.random.default_rng(31)
+    u0 = p.initial()
+    u1 = np.zeros_like(u0)
+    dtr = 1e-2 * rng.standard_normal((S, len(case["receivers"])))
+    gg, tau = gpu_forward_adjoint(n, n, p.depth, u0, u1, S, case["receivers"], dtr, "f32", tsu.TSU_FORM_INCREMENT,
+                                  20)
+    og = oracle.grid(n, n)
+    hx, hy, ext = oracle.make_depth(og, p.depth)
+    ref = oracle.adjoint(og, tau, hx, hy, u0, u1, S, inputs.flat_index(case["receivers"], n), dtr)
+    for k in ("g_hx", "g_hy", "g_u0", "g_u1"):
+        assert relerr(gg[k], ref[k]) <= 2e-5, (k, relerr(gg[k], ref[k]))
+
+
 @pytest.mark.parametrize("nx,ny", [(3, 3), (5, 6), (17, 9), (130, 5), (6, 140)])
 def test_fp32_adjoint_tiny_and_thin_grids(nx, ny):
     """The four-step pass on grids smaller than a tile in one or both directions (one strip,
