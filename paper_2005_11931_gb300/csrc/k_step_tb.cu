@@ -135,18 +135,13 @@ __device__ void tb_energy_reduce(float (&es)[K], float (&ec)[K], const TbArgs& a
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int t = 0; t < K; ++t) {
+  // the last CTA sums the partials of level t in warp t, all levels at once (fixed order)
+  static_assert(K <= kTbThreads / 32, "one warp per level");
+  if (w < K) {
     double s = 0.0;
-    for (int64_t q = threadIdx.x; q < ncta; q += blockDim.x) s += __ldcg(&a.ews.partials[(int64_t)t * ncta + q]);
+    for (int64_t q = lane; q < ncta; q += 32) s += __ldcg(&a.ews.partials[(int64_t)w * ncta + q]);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    __syncthreads();
-    if (lane == 0) red[0][w] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (int q = 0; q < kTbThreads / 32; ++q) tot += red[0][q];
-      a.energy[t] = tot * a.escale;
-    }
+    if (lane == 0) a.energy[w] = s * a.escale;
   }
   if (threadIdx.x == 0) *a.ews.counter = 0u;
 }
