@@ -16,7 +16,9 @@
 // input).  Receiver values are added to mu (and so to lam) in registers, in
 // every tile whose extended region holds the receiver (halo copies included): the lanes hold the
 // tile's entries and a ballot per row and level finds the ones on it.  Arithmetic runs on paired
-// FP32 instructions with the rounding order of the scalar one-step adjoint pass.
+// FP32 instructions; B lam is evaluated in flux form (each face flux rounded once, shared by the
+// two nodes beside it), the one-step adjoint pass in fused multiply-add form: the two round
+// differently, within the FP32 adjoint's tolerance.
 #include <string.h>
 
 #include "stencil_common.cuh"
@@ -126,23 +128,24 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
   }
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
   // register windows, index 0 = newest row
-  P4 W[K][3];       // lam of level k = 0..K-1 (level 0 = lam^{n+1}) at rows r - k, r - k - 1, r - k - 2
+  P4 W[K][2];       // lam of level k = 0..K-1 (level 0 = lam^{n+1}) at rows r - k, r - k - 1
+  P4 GP[K];         // GP[k - 1]: level k's y flux of lam at the faces below its current row
   P4 MW[K][2];      // mu of level k at rows r - k, r - k - 1
   P4 UW[K][2];      // u^{n-f} at rows r - f, r - f - 1
   P4 HXW[K];        // hx at rows r - 1 .. r - K
-  P4 HYW[K + 1];    // hy at rows r - 1 .. r - K - 1
+  P4 HYW[K];        // hy at rows r - 1 .. r - K
   P4 cx_[K], cy_[K];  // gradient sums of levels 1..j at the row level j + 1 reaches next
   P4 g0 = kZeroP4;    // y-face (0, 1) terms of the levels that have passed row 1
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    W[k][0] = W[k][1] = W[k][2] = kZeroP4;
+    W[k][0] = W[k][1] = GP[k] = kZeroP4;
     MW[k][0] = MW[k][1] = kZeroP4;
     UW[k][0] = UW[k][1] = kZeroP4;
     HXW[k] = kZeroP4;
     cx_[k] = cy_[k] = kZeroP4;
   }
 #pragma unroll
-  for (int k = 0; k <= K; ++k) HYW[k] = kZeroP4;
+  for (int k = 0; k < K; ++k) HYW[k] = kZeroP4;
 
   const int q_lo = (tile_ok && a.rec_off) ? a.rec_off[tile] : 0, q_hi = (tile_ok && a.rec_off) ? a.rec_off[tile + 1] : 0;
   // the tile's first 32 receiver entries, one per lane (row -1: none), with their K values
@@ -196,26 +199,35 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
   // One reverse step at a row: b = B lam and mu_out = mu + b on interior nodes (0 elsewhere), and
   // the face-gradient terms -cx (lam_{i+1} - lam_i)(u_{i+1} - u_i), -cy (lam_{j+1} - lam_j)
   // (u_{j+1} - u_j) of that step with the state u (rows: uc, uu = uc + 1 for lam; us, usu for u).
-  auto level = [&](const P4& uc, const P4& uu, const P4& ud, const P4& hx, const P4& hyu, const P4& hyd,
-                   const P4& mu, const P4& us, const P4& usu, const bool row_in, P4& mout, P4& gx, P4& gy) {
+  // B lam in flux form, as the forward passes evaluate B u: each face's flux h (lam_right -
+  // lam_left) once, the x flux left of the lane's first column from the lane on the left, the y
+  // flux below the row carried in gp from the level's previous row; the lam differences are the
+  // gradient terms' too.
+  auto level = [&](const P4& uc, const P4& uu, const P4& hx, const P4& hyu, P4& gp, const P4& mu, const P4& us,
+                   const P4& usu, const bool row_in, P4& mout, P4& gx, P4& gy) {
     const float2 c01 = upk(uc.p[0]), c23 = upk(uc.p[1]);
-    const float2 h01 = upk(hx.p[0]), h23 = upk(hx.p[1]);
     const float2 s01 = upk(us.p[0]), s23 = upk(us.p[1]);
-    const float ul = __shfl_up_sync(0xffffffffu, c23.y, 1);
     const float ur = __shfl_down_sync(0xffffffffu, c01.x, 1);
-    const float hl = __shfl_up_sync(0xffffffffu, h23.y, 1);
     const float sr = __shfl_down_sync(0xffffffffu, s01.x, 1);
-    const f2x mid = pk(c01.y, c23.x), right1 = pk(c23.y, ur);
-    const f2x lpair[2] = {pk(ul, c01.x), mid}, rpair[2] = {mid, right1};
-    const f2x hlpair[2] = {pk(hl, h01.x), pk(h01.y, h23.x)};
-    const f2x srpair[2] = {pk(s01.y, s23.x), pk(s23.y, sr)};
+    // lam and u differences at the x faces right of the four columns
+    const f2x dl[2] = {pk(__fsub_rn(c01.y, c01.x), __fsub_rn(c23.x, c01.y)),
+                       pk(__fsub_rn(c23.y, c23.x), __fsub_rn(ur, c23.y))};
+    const f2x du[2] = {pk(__fsub_rn(s01.y, s01.x), __fsub_rn(s23.x, s01.y)),
+                       pk(__fsub_rn(s23.y, s23.x), __fsub_rn(sr, s23.y))};
+    const f2x F01 = mul2(hx.p[0], dl[0]), F23 = mul2(hx.p[1], dl[1]);
+    const float2 f01 = upk(F01), f23 = upk(F23);
+    const float fl = __shfl_up_sync(0xffffffffu, f23.y, 1);
+    const f2x fx[2] = {pk(__fsub_rn(f01.x, fl), __fsub_rn(f01.y, f01.x)),
+                       pk(__fsub_rn(f23.x, f01.y), __fsub_rn(f23.y, f23.x))};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const f2x b = stencil2(hlpair[q], hx.p[q], hyd.p[q], hyu.p[q], uc.p[q], lpair[q], rpair[q], uu.p[q], ud.p[q],
-                             cx2, cy2);
+      const f2x dy = sub2(uu.p[q], uc.p[q]);
+      const f2x g = mul2(hyu.p[q], dy);
+      const f2x b = fma2(cx2, fx[q], mul2(cy2, sub2(g, gp.p[q])));
+      gp.p[q] = g;
       mout.p[q] = row_in ? mul2(add2(mu.p[q], b), node2[q]) : 0ull;
-      gx.p[q] = mul2(gcx2[q], mul2(sub2(rpair[q], uc.p[q]), sub2(srpair[q], us.p[q])));
-      gy.p[q] = mul2(gcy2[q], mul2(sub2(uu.p[q], uc.p[q]), sub2(usu.p[q], us.p[q])));
+      gx.p[q] = mul2(gcx2[q], mul2(dl[q], du[q]));
+      gy.p[q] = mul2(gcy2[q], mul2(dy, sub2(usu.p[q], us.p[q])));
     }
   };
 
@@ -230,7 +242,6 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     cp_wait<kAwPre>();
     const unsigned s = (unsigned)it & (kAwRing - 1);
     // shift the input windows and take the new rows
-    W[0][2] = W[0][1];
     W[0][1] = W[0][0];
     W[0][0] = lds_p4(slot(s, F_L1));
     MW[0][1] = MW[0][0];
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     for (int k = K - 1; k >= 1; --k) HXW[k] = HXW[k - 1];
     HXW[0] = lds_p4(slot(s, F_HX));
 #pragma unroll
-    for (int k = K; k >= 1; --k) HYW[k] = HYW[k - 1];
+    for (int k = K - 1; k >= 1; --k) HYW[k] = HYW[k - 1];
     HYW[0] = lds_p4(slot(s, F_HY));
 
     P4 pend_x = kZeroP4, pend_y = kZeroP4;
@@ -252,8 +263,8 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     for (int k = 1; k <= K; ++k) {
       const int pk_row = r_in - k;
       P4 mk, gxk, gyk;
-      level(W[k - 1][1], W[k - 1][0], W[k - 1][2], HXW[k - 1], HYW[k - 1], HYW[k], MW[k - 1][1], UW[k - 1][1],
-            UW[k - 1][0], pk_row >= 1 && pk_row <= a.ny - 2, mk, gxk, gyk);
+      level(W[k - 1][1], W[k - 1][0], HXW[k - 1], HYW[k - 1], GP[k - 1], MW[k - 1][1], UW[k - 1][1], UW[k - 1][0],
+            pk_row >= 1 && pk_row <= a.ny - 2, mk, gxk, gyk);
       if (pk_row == 1) {  // y-face (0, 1): lam and u vanish on row 0, the term is -cy lam_1 u_1
 #pragma unroll
         for (int q = 0; q < 2; ++q) g0.p[q] = add2(g0.p[q], mul2(gcy2[q], mul2(W[k - 1][1].p[q], UW[k - 1][1].p[q])));
@@ -264,7 +275,6 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
       for (int q = 0; q < 2; ++q) lk.p[q] = add2(W[k - 1][1].p[q], mk.p[q]);
       const bool store_row = col_out && pk_row >= y0 && pk_row < y1;
       if (k < K) {
-        W[k][2] = W[k][1];
         W[k][1] = W[k][0];
         W[k][0] = lk;
         MW[k][1] = MW[k][0];
