@@ -98,8 +98,10 @@ struct ArithF32 {
   __device__ __forceinline__ float add(float a, float b) const { return __fadd_rn(a, b); }
 };
 
-// Adjoint passes (one-step and four-step, which agree with each other): B lambda with one fused
-// multiply-add per direction, fx = fma(hxl, ul - uc, hxr (ur - uc)), B = fma(cx, fx, cy fy).
+// The one-step adjoint pass: B lambda with one fused multiply-add per direction,
+// fx = fma(hxl, ul - uc, hxr (ur - uc)), B = fma(cx, fx, cy fy).  (The four-step adjoint pass
+// evaluates B lambda in flux form, like the forward passes; the two round differently, within
+// the FP32 adjoint's tolerance.)
 struct ArithF32Fma {
   float cx, cy;
   __device__ __forceinline__ float b(float hxr, float hxl, float hyu, float hyd, float uc, float ul, float ur,
@@ -165,14 +167,6 @@ __device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
   f2x d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
-}
-// B lambda for a pair of columns, in ArithF32Fma's order (the adjoint's): fx = fma(hxl, ul - uc,
-// hxr (ur - uc)), fy likewise, B = fma(cx, fx, cy fy)
-__device__ __forceinline__ f2x stencil2(f2x hxl, f2x hxr, f2x hyd, f2x hyu, f2x uc, f2x ul, f2x ur, f2x uu, f2x ud,
-                                        f2x cx, f2x cy) {
-  const f2x fx = fma2(hxl, sub2(ul, uc), mul2(hxr, sub2(ur, uc)));
-  const f2x fy = fma2(hyd, sub2(ud, uc), mul2(hyu, sub2(uu, uc)));
-  return fma2(cx, fx, mul2(cy, fy));
 }
 __device__ __forceinline__ P4 lds_p4(const float* s) {
   const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(s);
