@@ -404,20 +404,44 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   if constexpr (ENERGY) wtb_energy<K>(es, ec, a);
 }
 
+// Strip and chunk of a single-problem tile.  The tiles of the two outer strips (masked on every
+// row, the slowest) come first, so that a launch does not end on them (8192^2 979 against 938
+// GLUPS, 4096^2 831 against 771); the other strips follow chunk by chunk.  32-bit arithmetic:
+// the launchers refuse 2^31 tiles or more.
+__device__ __forceinline__ void wtb_tile_coords(const int64_t tile, const WtbArgs& a, uint32_t& strip,
+                                                uint32_t& chunk) {
+  const uint32_t t = (uint32_t)tile, ns = (uint32_t)a.nstrips, nchunks = (uint32_t)a.ntiles / ns;
+  if (ns < 3) {
+    strip = t % ns;
+    chunk = t / ns;
+  } else if (t < 2 * nchunks) {
+    strip = (t & 1) ? ns - 1 : 0;
+    chunk = t >> 1;
+  } else {
+    const uint32_t r = t - 2 * nchunks, inner = ns - 2;
+    chunk = r / inner;
+    strip = 1 + (r - chunk * inner);
+  }
+}
+
 template <int K, int FORM, bool ENERGY, bool REC>
 __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
+  uint32_t strip = 0, chunk = 0;
+  if (ok) wtb_tile_coords(tile, a, strip, chunk);
   // the unrolled row loop except with receivers (2048^2 forward with traces and checkpoints: 46.0
   // against 41.7 ms)
-  wtb_body<K, FORM, ENERGY, false, REC, !REC>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
+  wtb_body<K, FORM, ENERGY, false, REC, !REC>(a, ok, strip, chunk);
 }
 
 template <int K, int FORM>
 __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_seg(const WtbArgs a) {
   const int64_t tile = (int64_t)blockIdx.x * kWtbWarps + (threadIdx.x >> 5);
   const bool ok = tile < a.ntiles;
-  wtb_body<K, FORM, false, true, false, true>(a, ok, ok ? tile % a.nstrips : 0, ok ? tile / a.nstrips : 0);
+  uint32_t strip = 0, chunk = 0;
+  if (ok) wtb_tile_coords(tile, a, strip, chunk);
+  wtb_body<K, FORM, false, true, false, true>(a, ok, strip, chunk);
 }
 
 // Batched family: warp w of CTA b works on tile tiles[4 b + w] = (problem, strip, chunk) of
@@ -444,6 +468,7 @@ cudaError_t wtb_launch_kernel(const WtbArgs& a, unsigned grid, size_t smem, cuda
 
 template <int K, int FORM>
 cudaError_t wtb_launch(const WtbArgs& a, cudaStream_t s) {
+  if (a.ntiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // wtb_tile_coords is 32-bit
   const size_t smem = (size_t)WtbShape<K>::bytes * kWtbWarps * 32;
   const unsigned grid = (unsigned)((a.ntiles + kWtbWarps - 1) / kWtbWarps);
   const bool rec = a.traces && a.nrec > 0;
@@ -458,6 +483,7 @@ cudaError_t wtb_launch(const WtbArgs& a, cudaStream_t s) {
 
 template <int K, int FORM>
 cudaError_t wtb_launch_seg(const WtbArgs& a, cudaStream_t s) {
+  if (a.ntiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;  // wtb_tile_coords is 32-bit
   const size_t smem = (size_t)WtbShape<K>::bytes * kWtbWarps * 32;
   auto kern = k_leapfrog_wtb_seg<K, FORM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
