@@ -31,9 +31,9 @@ METRIC = "grid-point updates/s (GLUPS) and HBM roofline %; adjoint/forward time 
 # keyed by (kernel, form, n, steps per launch); only for kernels unchanged since the capture.
 TRAFFIC = {
     # profiles/k_leapfrog_wtb_increment_8192.md: one launch of the timed configuration (8192^2,
-    # 4 steps per pass, 117 rows per chunk, two rows per loop trip), dram__bytes_read.sum +
-    # dram__bytes_write.sum
-    ("k_leapfrog_wtb", "increment", 8192, 4): None,
+    # 4 steps per pass, 117 rows per chunk, two rows per loop trip, outer strips first),
+    # dram__bytes_read.sum + dram__bytes_write.sum
+    ("k_leapfrog_wtb", "increment", 8192, 4): 1.665618e9,
 }
 UNIT = "GLUPS"
 DEFAULT_KERNEL = 2  # warp-blocked pass, 4 steps per HBM pass
