@@ -15,6 +15,8 @@ check
   of the FP32 adjoint along 16 seeded random directions against central differences of the FP64
   forward (whose parity with the oracle the other tests establish).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -81,6 +83,108 @@ def test_crossing_lines_16384_block_matches_window_oracle_and_is_symmetric():
     # depth and data are symmetric under x <-> y
     blk = sim.u[c - 300:c + 300, c - 300:c + 300].double().cpu().numpy()
     assert relerr(blk, blk.T) <= 2e-6
+
+
+# ---- FP32 against FP64 after the workloads' full step counts -----------------------------------
+# The oracle cannot run 8192^2 x 5000 or 16384^2 x 20000 steps inside a test, so the reference is
+# the GPU FP64 path (one step per pass, standard form, FP64 inputs), whose agreement with the
+# oracle to 1e-12 the parity tests establish.  The bar is 1e-5 relative L2 of the final field.
+def _fp64_reference(p, S):
+    ref = tsu.Simulation.create(p.n, p.depth, dtype="f64", form=tsu.TSU_FORM_STANDARD, nbuf=2)
+    u0 = torch.from_numpy(p.initial(ref.g.ld, np.float64)).cuda()
+    ref.init(u0)
+    ref.step(S - 1, kernel=1)
+    torch.cuda.synchronize()
+    out = (ref.tau, ref.u.clone(), (ref.u - ref.u_prev).clone(), u0)
+    del ref
+    torch.cuda.empty_cache()
+    return out
+
+
+def _fp32_product(p, S, tau, u0):
+    """The timed configuration: FP32 increment form, automatic kernel (warp-blocked, 4 steps per
+    pass) and rows."""
+    sim = tsu.Simulation.create(p.n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT, tau=tau)
+    sim.init(u0.float())
+    sim.step(S - 1)
+    torch.cuda.synchronize()
+    return sim
+
+
+def _rel(a, b) -> float:
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def test_point_8192_fp32_after_5000_steps_matches_fp64():
+    """8192^2 point workload, all 5000 steps: measured 4.5e-6 relative L2."""
+    p = inputs.point_fp32()
+    S = p.steps
+    tau, u64, v64, u0 = _fp64_reference(p, S)
+    sim = _fp32_product(p, S, tau, u0)
+    e_u = _rel(sim.u.double(), u64)
+    assert e_u <= 1e-5, e_u
+    # the part of the error that is the FP32 arithmetic alone: the FP64 path started from the
+    # FP32-rounded hump (rounding u0 to FP32 perturbs v^1 = B u0 / 2 by its white-noise
+    # Laplacian, ~3e-3 of v here, which no scheme can undo)
+    del u64, v64
+    torch.cuda.empty_cache()
+    ref = tsu.Simulation.create(p.n, p.depth, dtype="f64", form=tsu.TSU_FORM_STANDARD, nbuf=2, tau=tau)
+    u0r = u0.float().double()
+    ref.init(u0r)
+    ref.step(S - 1, kernel=1)
+    torch.cuda.synchronize()
+    e_du = _rel(sim.u.double() - u0r, ref.u - u0r)
+    e_v = _rel(sim.v.double(), ref.u - ref.u_prev)
+    print(f"8192^2 x {S}: rel L2 u {e_u:.3e}, change u^S - u^0 {e_du:.3e}, v^S {e_v:.3e}")
+    assert e_du <= 1e-3, e_du
+    assert e_v <= 1e-2, e_v
+
+
+def test_crossing_lines_16384_fp32_after_20000_steps_matches_fp64():
+    """16384^2 crossing lines, all 20000 steps (the FP64 reference takes about 2.5 minutes):
+    measured 5.0e-6 relative L2."""
+    p = inputs.crossing_lines_fp32()
+    S = p.steps
+    tau, u64, v64, u0 = _fp64_reference(p, S)
+    sim = _fp32_product(p, S, tau, u0)
+    e_u = _rel(sim.u.double(), u64)
+    e_du = _rel(sim.u.double() - u0, u64 - u0)
+    print(f"16384^2 x {S}: rel L2 u {e_u:.3e}, change u^S - u^0 {e_du:.3e}")
+    assert e_u <= 1e-5, e_u
+    assert e_du <= 1e-5, e_du
+    del sim, u64, v64, u0
+    torch.cuda.empty_cache()
+
+
+def test_batched_family_members_after_2000_steps_match_the_oracle():
+    """The 64-problem eps-family run batched for its full 2000 steps (the timed configuration of
+    the batched measurement); the first member of every grid size, 512^2 .. 2048^2, against the
+    oracle run on the same problem for the same 2000 steps."""
+    probs = inputs.batched_family()
+    sims = []
+    for pr in probs:
+        sim = tsu.Simulation.create(pr.n, pr.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+        sim.init(torch.from_numpy(pr.initial(sim.g.ld, np.float32)).cuda())
+        sims.append(sim)
+    nsteps = [pr.steps - 1 for pr in probs]
+    wsb = tsu.tsu_batch_workspace(sims, nsteps)
+    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
+    tsu.tsu_batch_run(sims, nsteps, ws, wsb)
+    tsu.tsu_sync_status(ws, wsb)
+    first = {}
+    for k, pr in enumerate(probs):
+        first.setdefault(pr.n, k)
+    assert sorted(first) == [512, 768, 1024, 1536, 2048]
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    errs = {}
+    for n, k in sorted(first.items()):
+        pr, sim = probs[k], sims[k]
+        g = oracle.grid(n, n)
+        hx, hy, _ = oracle.make_depth(g, pr.depth)
+        ref = oracle.forward(g, sim.tau, hx, hy, pr.initial(), None, pr.steps, want_energy=False)
+        errs[n] = relerr(sim.u[:, :n].double().cpu().numpy(), ref["u"])
+    print("family members after 2000 steps, rel L2:", {n: f"{e:.2e}" for n, e in errs.items()})
+    assert max(errs.values()) <= 1e-5, errs
 
 
 def test_point_8192_full_run_conserves_energy():
