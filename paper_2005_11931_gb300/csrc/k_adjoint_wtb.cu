@@ -9,11 +9,12 @@
 // cone) by a chunk of rows it streams down; level k lags the input row by k rows.  Each thread
 // copies its own float4 of every input row through a private cp.async ring: lam^{n+1},
 // mu^{n+1}, hx and hy at the input row (the faces one row behind), u^{n-f} f rows behind, where
-// level f + 1 needs it, and the FP32 gradient accumulators K rows behind, where the last level
-// finishes a row; so nothing in the row loop waits on memory.  The face gradients of a row are
-// summed over the K steps in registers (carried from level to level) and added to the
-// accumulators once per pass.  Only the last level is stored (lam and mu: the next pass's
-// input).  Receiver values are added to mu (and so to lam) in registers, in
+// level f + 1 needs it; so nothing in the row loop waits on memory.  The ring keeps the previous
+// row of every field, so the levels read u, the input multipliers and the faces of the two
+// newest rows from it; only older rows live in registers (168 per thread: 3 CTAs per SM).  The
+// face gradients of a row are summed over the K steps in registers (carried from level to
+// level) and added to the FP32 accumulators once per pass, by a vector reduction in the L2.
+// Only the last level is stored (lam and mu: the next pass's input).  Receiver values are added to mu (and so to lam) in registers, in
 // every tile whose extended region holds the receiver (halo copies included): the lanes hold the
 // tile's entries and a ballot per row and level finds the ones on it.  Arithmetic runs on paired
 // FP32 instructions; B lam is evaluated in flux form (each face flux rounded once, shared by the
@@ -30,14 +31,14 @@ using namespace dev;
 constexpr int kAwWarps = 4;
 constexpr int kAwOut = 120;
 constexpr int kAwPre = 2;
-constexpr int kAwRing = 4;  // slots per field: in flight (2) + current, power of two
-// resident CTAs per SM (register-limited; checked against -Xptxas -v): K = 2 at <= 168
-// registers per thread, K = 4 at <= 255
+constexpr int kAwRing = 4;  // slots per field: the previous row, the current one, 2 in flight
+// resident CTAs per SM: the launch bound the kernel is compiled for (K = 2 at <= 168 registers per
+// thread, K = 4 at <= 168 as well; checked against -Xptxas -v), and what the rows rule sizes for
 template <int K>
-constexpr int aw_ctas_per_sm() { return K == 2 ? 3 : 2; }
-// ring fields: lam^{n+1}, mu^{n+1}, hx, hy, u^n .. u^{n-K+1}, gx, gy
+constexpr int aw_ctas_per_sm() { return 3; }
+// ring fields: lam^{n+1}, mu^{n+1}, hx, hy, u^n .. u^{n-K+1}
 template <int K>
-constexpr int aw_fields() { return K + 6; }
+constexpr int aw_fields() { return K + 4; }
 
 __device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
@@ -48,6 +49,15 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// acc[0..3] += v (one rounding each, as acc + v): the FP32 gradient accumulators of a row are
+// added to in the L2, without a read back into the SM.  Every node gets exactly one such add per
+// pass (only the tile that owns a row adds to it), so the sums do not depend on timing.
+__device__ __forceinline__ void red_add4(float* acc, const P4& v) {
+  const float2 a = upk(v.p[0]), b = upk(v.p[1]);
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(acc), "f"(a.x), "f"(a.y), "f"(b.x),
+               "f"(b.y)
+               : "memory");
 }
 
 template <int K>
@@ -72,9 +82,10 @@ struct AwArgs {
 };
 
 template <int K>
-__global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a) {
+__global__ void __launch_bounds__(kAwWarps * 32, aw_ctas_per_sm<K>()) k_adjoint_wtb(const AwArgs<K> a) {
   constexpr int NF = aw_fields<K>();
-  constexpr int F_L1 = 0, F_MU = 1, F_HX = 2, F_HY = 3, F_U = 4, F_GX = 4 + K, F_GY = 5 + K;
+  constexpr int F_L1 = 0, F_MU = 1, F_HX = 2, F_HY = 3, F_U = 4;
+  static_assert(K >= 2, "levels 1 and 2 read hx, hy from the ring, the others from registers");
   extern __shared__ __align__(16) unsigned char aw_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kAwWarps + warp;
@@ -93,28 +104,24 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     node_col[e] = (c0 + e >= 1) && (c0 + e <= a.nx - 2);
     face_x[e] = (c0 + e <= a.nx - 2);  // x-face (i, i+1) exists
   }
-  // per-thread ring: [kAwRing][NF] float4
+  // per-thread ring: [kAwRing][NF] float4; slot q & 3 holds what iteration q consumes, and the
+  // previous slot stays valid through an iteration (the copies issued at iteration q fill slot
+  // q + 2)
   float* ring = reinterpret_cast<float*>(aw_smem) + (size_t)threadIdx.x * 4;
   const int stride = kAwWarps * 32 * 4;
-  auto slot = [&](unsigned s, int f) { return ring + (size_t)(s * NF + f) * stride; };
+  auto slot = [&](unsigned s, int f) { return ring + (size_t)((s & (kAwRing - 1)) * NF + f) * stride; };
   auto issue = [&](int q) {  // the copies consumed at iteration q (input row r_first + q)
     const int r = r_first + q;
-    const unsigned s = (unsigned)q & (kAwRing - 1);
-    auto copy = [&](int f, const float* src, int row, bool extra) {
-      const bool ok = extra && col_in && row >= 0 && row < a.ny;
-      cp16(slot(s, f), src + (ok ? (int64_t)row * a.ld + c0 : 0), ok);
+    auto copy = [&](int f, const float* src, int row) {
+      const bool ok = col_in && row >= 0 && row < a.ny;
+      cp16(slot((unsigned)q, f), src + (ok ? (int64_t)row * a.ld + c0 : 0), ok);
     };
-    copy(F_L1, a.lam1, r, true);
-    copy(F_MU, a.mu1, r, true);
-    copy(F_HX, a.hx, r - 1, true);
-    copy(F_HY, a.hy, r - 1, true);
+    copy(F_L1, a.lam1, r);
+    copy(F_MU, a.mu1, r);
+    copy(F_HX, a.hx, r - 1);
+    copy(F_HY, a.hy, r - 1);
 #pragma unroll
-    for (int f = 0; f < K; ++f) copy(F_U + f, a.u[f], r - f, true);
-    // accumulators of row r - K, the row the last level finishes at iteration q; only rows this
-    // tile owns are read (no other tile writes them, and this tile writes each once)
-    const bool acc = col_out && r - K >= y0 && r - K < y1;
-    copy(F_GX, a.gx, r - K, acc);
-    copy(F_GY, a.gy, r - K, acc);
+    for (int f = 0; f < K; ++f) copy(F_U + f, a.u[f], r - f);
   };
   // per-thread column constants (the columns of a thread never change): node and face masks
   // folded into the coefficients of the gradient terms
@@ -127,25 +134,21 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     gcy2[q] = pk(node_col[e] ? -a.cy : 0.f, node_col[e + 1] ? -a.cy : 0.f);
   }
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy);
-  // register windows, index 0 = newest row
-  P4 W[K][2];       // lam of level k = 0..K-1 (level 0 = lam^{n+1}) at rows r - k, r - k - 1
+  // register windows, index 0 = newest row.  Level 0 (lam^{n+1}, mu^{n+1}), u and the faces of
+  // the two newest rows are read from the ring; what older rows the levels need is kept here.
+  P4 W[K][2];       // lam of level k = 1..K-1 at rows r - k, r - k - 1
   P4 GP[K];         // GP[k - 1]: level k's y flux of lam at the faces below its current row
-  P4 MW[K][2];      // mu of level k at rows r - k, r - k - 1
-  P4 UW[K][2];      // u^{n-f} at rows r - f, r - f - 1
-  P4 HXW[K];        // hx at rows r - 1 .. r - K
-  P4 HYW[K];        // hy at rows r - 1 .. r - K
+  P4 MW[K][2];      // mu of level k = 1..K-1 at rows r - k, r - k - 1
+  P4 HXO[K], HYO[K];  // hx, hy at rows r - 3 .. r - K (index k - 1 for level k >= 3)
   P4 cx_[K], cy_[K];  // gradient sums of levels 1..j at the row level j + 1 reaches next
   P4 g0 = kZeroP4;    // y-face (0, 1) terms of the levels that have passed row 1
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     W[k][0] = W[k][1] = GP[k] = kZeroP4;
     MW[k][0] = MW[k][1] = kZeroP4;
-    UW[k][0] = UW[k][1] = kZeroP4;
-    HXW[k] = kZeroP4;
+    HXO[k] = HYO[k] = kZeroP4;
     cx_[k] = cy_[k] = kZeroP4;
   }
-#pragma unroll
-  for (int k = 0; k < K; ++k) HYW[k] = kZeroP4;
 
   const int q_lo = (tile_ok && a.rec_off) ? a.rec_off[tile] : 0, q_hi = (tile_ok && a.rec_off) ? a.rec_off[tile + 1] : 0;
   // the tile's first 32 receiver entries, one per lane (row -1: none), with their K values
@@ -161,8 +164,7 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     for (int k = 0; k < K; ++k) pr_g[k] = a.g[k][rq.z];
   }
   // add g^{n-k} (k = kg) at the entries on row p to the lane's four multipliers (warp-uniform
-  // loop bounds)
-  // (kg is a constant once the level loop is unrolled)
+  // loop bounds; kg is a constant once the level loop is unrolled)
   auto inject = [&](int p, P4& l, const int kg) {
     for (int qb = q_lo; qb < q_hi; qb += 32) {
       int row = pr_row, col = pr_col;
@@ -231,48 +233,49 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
     }
   };
 
-  for (int q = 0; q < kAwPre; ++q) {
-    if (q < nit) issue(q);
-    cp_commit();
-  }
-  for (int it = 0; it < nit; ++it) {
+  // One iteration: input row r_in = r_first + it; level k = 1..nl computes row r_in - k.  Level k
+  // first matters at iteration 2k - 1 (its earlier rows lie above the cone of the tile's output
+  // rows; the iteration before its first needed row yields the y flux below that row), so the
+  // first 2K - 1 iterations run levels k <= (it + 1) / 2 only.
+  auto iterate = [&](const int it, const int nl) {
     const int r_in = r_first + it;
+    // hx, hy of row r - 3 leave the ring at this iteration's copies: keep them (and shift the
+    // older rows) first
+#pragma unroll
+    for (int k = K - 1; k >= 3; --k) {
+      HXO[k] = HXO[k - 1];
+      HYO[k] = HYO[k - 1];
+    }
+    HXO[2] = lds_p4(slot((unsigned)(it - 2), F_HX));
+    HYO[2] = lds_p4(slot((unsigned)(it - 2), F_HY));
     if (it + kAwPre < nit) issue(it + kAwPre);
     cp_commit();
     cp_wait<kAwPre>();
-    const unsigned s = (unsigned)it & (kAwRing - 1);
-    // shift the input windows and take the new rows
-    W[0][1] = W[0][0];
-    W[0][0] = lds_p4(slot(s, F_L1));
-    MW[0][1] = MW[0][0];
-    MW[0][0] = lds_p4(slot(s, F_MU));
-#pragma unroll
-    for (int f = 0; f < K; ++f) {
-      UW[f][1] = UW[f][0];
-      UW[f][0] = lds_p4(slot(s, F_U + f));
-    }
-#pragma unroll
-    for (int k = K - 1; k >= 1; --k) HXW[k] = HXW[k - 1];
-    HXW[0] = lds_p4(slot(s, F_HX));
-#pragma unroll
-    for (int k = K - 1; k >= 1; --k) HYW[k] = HYW[k - 1];
-    HYW[0] = lds_p4(slot(s, F_HY));
-
+    const unsigned s = (unsigned)it, sp = (unsigned)(it - 1);
     P4 pend_x = kZeroP4, pend_y = kZeroP4;
 #pragma unroll
     for (int k = 1; k <= K; ++k) {
+      if (k > nl) continue;  // a constant once the loops are unrolled
       const int pk_row = r_in - k;
+      // level k - 1 at rows r - k (centre) and r - k + 1; level 0 from the ring
+      const P4 lc = k == 1 ? lds_p4(slot(sp, F_L1)) : W[k - 1][1];
+      const P4 lu = k == 1 ? lds_p4(slot(s, F_L1)) : W[k - 1][0];
+      const P4 mc = k == 1 ? lds_p4(slot(sp, F_MU)) : MW[k - 1][1];
+      // u^{n-k+1} at rows r - k and r - k + 1 (copied at the previous and this iteration)
+      const P4 us = lds_p4(slot(sp, F_U + k - 1)), usu = lds_p4(slot(s, F_U + k - 1));
+      // hx, hy of row r - k: in the ring for k = 1, 2 (copied at iterations it, it - 1)
+      const P4 hxk = k <= 2 ? lds_p4(slot((unsigned)(it - k + 1), F_HX)) : HXO[k - 1];
+      const P4 hyk = k <= 2 ? lds_p4(slot((unsigned)(it - k + 1), F_HY)) : HYO[k - 1];
       P4 mk, gxk, gyk;
-      level(W[k - 1][1], W[k - 1][0], HXW[k - 1], HYW[k - 1], GP[k - 1], MW[k - 1][1], UW[k - 1][1], UW[k - 1][0],
-            pk_row >= 1 && pk_row <= a.ny - 2, mk, gxk, gyk);
+      level(lc, lu, hxk, hyk, GP[k - 1], mc, us, usu, pk_row >= 1 && pk_row <= a.ny - 2, mk, gxk, gyk);
       if (pk_row == 1) {  // y-face (0, 1): lam and u vanish on row 0, the term is -cy lam_1 u_1
 #pragma unroll
-        for (int q = 0; q < 2; ++q) g0.p[q] = add2(g0.p[q], mul2(gcy2[q], mul2(W[k - 1][1].p[q], UW[k - 1][1].p[q])));
+        for (int q = 0; q < 2; ++q) g0.p[q] = add2(g0.p[q], mul2(gcy2[q], mul2(lc.p[q], us.p[q])));
       }
       inject(pk_row, mk, k - 1);  // g^m into mu^m (receivers are interior nodes)
       P4 lk;  // lam^m = lam^{m+1} + mu^m (0 wherever mu^m and lam^{m+1} are)
 #pragma unroll
-      for (int q = 0; q < 2; ++q) lk.p[q] = add2(W[k - 1][1].p[q], mk.p[q]);
+      for (int q = 0; q < 2; ++q) lk.p[q] = add2(lc.p[q], mk.p[q]);
       const bool store_row = col_out && pk_row >= y0 && pk_row < y1;
       if (k < K) {
         W[k][1] = W[k][0];
@@ -302,24 +305,25 @@ __global__ void __launch_bounds__(kAwWarps * 32) k_adjoint_wtb(const AwArgs<K> a
         const int64_t o = (int64_t)pk_row * a.ld + c0;
         stg_p4(a.out_a + o, lk);
         stg_p4(a.out_b + o, mk);
-        P4 ax = lds_p4(slot(s, F_GX)), ay = lds_p4(slot(s, F_GY));
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          ax.p[q] = add2(ax.p[q], sx.p[q]);
-          ay.p[q] = add2(ay.p[q], sy.p[q]);
-        }
-        stg_p4(a.gx + o, ax);
-        stg_p4(a.gy + o, ay);
-        if (pk_row == 1) {  // y-face (0, 1) of all K steps
-          const ulonglong2 r0 = __ldcg(reinterpret_cast<const ulonglong2*>(a.gy + c0));  // once per tile column
-          P4 a0{{r0.x, r0.y}};
-#pragma unroll
-          for (int q = 0; q < 2; ++q) a0.p[q] = add2(a0.p[q], g0.p[q]);
-          stg_p4(a.gy + c0, a0);
-        }
+        red_add4(a.gx + o, sx);
+        red_add4(a.gy + o, sy);
+        if (pk_row == 1) red_add4(a.gy + c0, g0);  // y-face (0, 1) of all K steps
       }
     }
+  };
+
+  for (int q = 0; q < kAwPre; ++q) {
+    if (q < nit) issue(q);
+    cp_commit();
   }
+  int it = 0;
+  if (nit > 0) {  // every tile has nit >= 2K + 1 iterations
+#pragma unroll
+    for (int f = 0; f < 2 * K - 1; ++f) iterate(f, (f + 1) / 2);
+    it = 2 * K - 1;
+  }
+#pragma unroll 1
+  for (; it < nit; ++it) iterate(it, K);
   cp_wait<0>();
 }
 
