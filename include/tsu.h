@@ -89,12 +89,19 @@ typedef struct {
   const tsu_sing* sing; /* host array [nsing] */
 } tsu_depth;
 
-/* The medium as the steppers see it: device face arrays (element type = dtype) and the
- * face maxima returned by tsu_make_depth, used for the CFL check. */
+/* The medium as the steppers see it: device face arrays (element type = dtype) and the face
+ * extrema returned by tsu_make_depth (ext = {min hx, max hx, min hy, max hy}).  Every stepper
+ * checks them before it enqueues anything:
+ *   - positivity (Sec. 2, 0 < c0 <= h_j): each face family has 0 < min <= max, or is identically
+ *     zero (min = max = 0: the equation then decouples into 1D problems along the other
+ *     direction, the paper's 1D setting), and not both families are zero; otherwise TSU_ENONPOS;
+ *   - the leapfrog bound tau^2 (hx_max/dx^2 + hy_max/dy^2) <= 1; otherwise TSU_ECFL.
+ * The extrema are the caller's statement about the arrays; the kernels do not re-check them. */
 typedef struct {
   const void* hx;
   const void* hy;
   double hx_max, hy_max;
+  double hx_min, hy_min;
 } tsu_medium;
 
 /* Time-stepping state (device buffers of ny*ld elements, owned by the caller).
@@ -104,6 +111,11 @@ typedef struct {
  *   TSU_FORM_INCREMENT: a plain step writes v^{n+1} = v^n + B u^n in place and u^{n+1} = u^n + v^{n+1}
  *                       into a scratch buffer (nbuf >= 3).  Same scheme, rounded differently: it
  *                       keeps FP32 fields accurate when the per-step change is far below one ulp of u.
+ *   FP32 fields in TSU_FORM_STANDARD lose part of every update whose size is below one ulp of u,
+ *   and that error grows with the step count: over thousands of small steps they do NOT stay
+ *   within 1e-5 relative L2 of the FP64 solution (a 400-step run of a ragged grid is already at
+ *   ~3e-5).  Use TSU_FORM_INCREMENT for long FP32 runs; the standard form is exact in FP64 and for
+ *   data where each update is representable (d'Alembert at Courant number 1).
  *   The temporally blocked kernel writes both output levels into scratch buffers (nbuf = 4).
  * step = n.  cur, aux and step are updated on the host when work is enqueued.  tsu_init fills
  * every provided buffer (scratch buffers with zeros). */
@@ -187,24 +199,31 @@ int tsu_diff_norms(const tsu_grid* g, int dtype, const void* a, const void* b, d
  * (0 < cfl <= 1).  Host only.  Returns 0 on bad input. */
 double tsu_tau_for(const tsu_grid* g, double hx_max, double hy_max, double cfl);
 
+/* The time step of the workloads: tau = courant * min(dx, dy) / sqrt(max(hx_max, hy_max)), a
+ * Courant number relative to the fastest wave speed sqrt(h) over the sampled faces (the 2D runs
+ * of Sec. 3.3 take a fixed Courant number; the workloads here use 0.4).  Inside the leapfrog
+ * bound for courant <= 1/sqrt(2); the implicit comparator below also takes larger ones.  Host
+ * only.  Returns 0 on bad input (courant not positive and finite, no positive face maximum). */
+double tsu_tau_courant(const tsu_grid* g, const tsu_medium* m, double courant);
+
 /* Cauchy data to the first two time levels (eq. (2.1) initial conditions; Taylor start above).
  *   u0       device [ny][ld] displacement (boundary values ignored: taken as 0).
  *   u1       device [ny][ld] velocity, or NULL for u1 = 0.
  *   st       st->buf[0..nbuf-1] device buffers, st->nbuf and st->form are read.  On return
  *            st->step = 1 and cur/aux are set (standard: buf[0] = u^0, buf[1] = u^1;
  *            increment: buf[0] = u^1, buf[1] = v^1 = tau u1 + B u^0 / 2).
- * Errors: TSU_EINVAL, TSU_ECFL. */
+ * Errors: TSU_EINVAL, TSU_ENONPOS (the medium's extrema, see tsu_medium), TSU_ECFL. */
 int tsu_init(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, const void* u0,
              const void* u1, tsu_state* st, void* stream);
 
 /* Bytes of device workspace tsu_step_n and tsu_observe need (energy partial sums). */
 int tsu_step_workspace(const tsu_grid* g, int dtype, size_t* bytes);
 
-/* Advance the state by nsteps leapfrog steps (spec hot path; scheme above).
+/* Advance the state by nsteps leapfrog steps (the hot path; scheme above).
  *   opts  NULL or tsu_step_opts (outputs, tuning).  ws/ws_bytes: device workspace of
  *         tsu_step_workspace bytes (or NULL), zero-filled by the caller before its first use;
  *         needed for the energy and the temporally blocked kernel.
- * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
+ * Errors: TSU_EINVAL, TSU_ENONPOS, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
 int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, tsu_state* st,
                int64_t nsteps, const tsu_step_opts* opts, void* ws, size_t ws_bytes, void* stream);
 
@@ -231,13 +250,19 @@ int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps
  *             for FP32 fields FP32 partial sums over one segment are added into them)
  *   g_u0, g_u1  device [ny][ld] of dtype, overwritten with dJ/du0, dJ/du1
  * Every segment is recomputed from its checkpoint on a library-owned stream (one per device and
- * host thread, created by that thread's first call) concurrently with the reverse sweep of the
- * previous one; all of it is ordered before the call's last work on the caller's stream.
- * Errors: TSU_EINVAL, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
+ * host thread, created by that thread's first call and destroyed when the thread exits)
+ * concurrently with the reverse sweep of the previous one; all of it is ordered before the
+ * call's last work on the caller's stream.
+ * Errors: TSU_EINVAL, TSU_ENONPOS, TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
 int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_medium* m, int64_t nsteps,
                 int64_t ckpt_every, const void* ckpt, const void* u0, int32_t nrec, const int64_t* rec_idx,
                 const void* dtraces, double* g_hx, double* g_hy, void* g_u0, void* g_u1, void* ws, size_t ws_bytes,
                 void* stream);
+
+/* Diagnostic (the paper has no counterpart): the number of auxiliary streams the library holds
+ * right now.  tsu_adjoint creates one per device and calling host thread, with five events, on
+ * that thread's first call; they are destroyed when the thread exits. */
+int tsu_aux_streams(void);
 
 /* One problem of a batched family (all FP32, same form): grid, time step, medium, state (nbuf = 4,
  * initialised by tsu_init) and the number of steps to advance it. */
@@ -249,13 +274,20 @@ typedef struct {
   int64_t nsteps;
 } tsu_problem;
 
-/* Options of tsu_batch_run (NULL = defaults). */
+/* Options of tsu_batch_run (NULL = defaults).  How the tiles of the family are packed into each
+ * launch (order, rows) changes no result: every tile computes the same values wherever it runs. */
 typedef struct {
   int32_t tdepth; /* steps per batched pass (0 = the kernel's default: 4 for kernel 2, 8 for kernel 3) */
   int32_t rows;   /* rows per chunk (0 = 80, halved down to 16 while the tiles do not fill the GPU) */
   int32_t kernel; /* 0 or 2: warp-blocked (tdepth 2 or 4); 3: CTA-blocked (tdepth 4 or 8) */
   int32_t graph;  /* 1: capture every launch of the call into one CUDA graph and launch that (needs a
                      non-default stream); 0: launch on the stream directly */
+  int32_t order;  /* order of the tile table within problems of equal step counts:
+                     0 problem by problem (each problem's chunks in turn, strips within a chunk),
+                     1 every problem's full chunks first, the ragged last chunks at the end,
+                     2 the problems interleaved chunk by chunk (chunk 0 of every problem, then 1 ...) */
+  const int32_t* rows_per_problem; /* host [nprob] rows per chunk of each problem (>= 16; 0 = rows),
+                                      or NULL for rows throughout */
 } tsu_batch_opts;
 
 /* Bytes of device workspace tsu_batch_run needs for these problems (descriptors and tile table). */
@@ -267,7 +299,8 @@ int tsu_batch_workspace(int32_t nprob, const tsu_problem* probs, const tsu_batch
  * leftover steps (nsteps % tdepth) run one per pass.  Each problem ends in the same state, bit for
  * bit, as tsu_step_n would leave it.  The call uploads descriptors (it synchronises with the
  * host once) and updates every state's cur/aux/step; tsu_sync_status(ws) reports expired waits.
- * Errors: TSU_EINVAL (mixed forms, non-FP32 fields, nbuf != 4), TSU_ECFL, TSU_ENOMEM, TSU_ECUDA. */
+ * Errors: TSU_EINVAL (mixed forms, non-FP32 fields, nbuf != 4), TSU_ENONPOS, TSU_ECFL, TSU_ENOMEM,
+ * TSU_ECUDA. */
 int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, void* ws, size_t ws_bytes,
                   void* stream);
 
@@ -324,7 +357,7 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
  * tsu_implicit_step_n: nsteps steps in place on buf[cur] (u) and buf[aux] (v); step += nsteps.
  * Every call is asynchronous on `stream`; the workspace (16-byte aligned, >= the size above) is
  * scratch that must not be shared by calls in flight at the same time.
- * Errors: TSU_EINVAL (arguments, form, alignment), TSU_ECFL (sigma < 1/4 and
+ * Errors: TSU_EINVAL (arguments, form, alignment), TSU_ENONPOS (the medium's extrema), TSU_ECFL (sigma < 1/4 and
  * tau^2 (hx_max/dx^2 + hy_max/dy^2) (1 - 4 sigma) > 1), TSU_ENOMEM (factor or workspace too
  * small), TSU_ECUDA. */
 int tsu_implicit_sizes(const tsu_grid* g, int dtype, size_t* factor_bytes, size_t* ws_bytes);

@@ -9,8 +9,9 @@ this module compiles it with gcc on first use and wraps it with numpy arrays.
 Paper passages followed (arXiv:2005.11931):
 
 * Sec. 2, eq. (2.1): ``u_tt - sum_j d_j(h_j d_j u) = 0`` with vector depth.
-* Sec. 2.1: regularisation ``h_eps = h * psi_eps``, ``psi_eps = eps^-1 psi(x/eps)``
-  (``eps^-2`` for the 2D point mollifier; see the reading in the design notes).
+* Sec. 2.1: regularisation ``h_eps = h * psi_eps``, ``psi_eps = eps^-1 psi(x/eps)``.  That
+  normalisation has unit mass only on the line; the 2D point mollifier is scaled by ``eps^-2``
+  so that it keeps unit mass in the plane.
 * Sec. 3.1: the Friedrichs bump ``c exp(1/(x^2-1))`` with ``c ~ 2.2523``; delta and
   delta^2 singularities ``phi_eps`` and ``phi_eps^2``; the step depth h0.
 * Sec. 3.3: the 2D box with zero Dirichlet edges and the grid omega.

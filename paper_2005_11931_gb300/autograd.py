@@ -22,8 +22,7 @@ class TsunamiConfig:
     tau: float
     steps: int                 # S: the final state is u^S (the Taylor start is step 1)
     rec_idx: torch.Tensor      # int64 flat node indices j*ld + i (device)
-    hx_max: float              # face maxima for the CFL check (from tsu_make_depth)
-    hy_max: float
+    ext: tuple                 # face extrema [min hx, max hx, min hy, max hy] (from tsu_make_depth)
     form: int = tsu.TSU_FORM_INCREMENT
     ckpt_every: int = 64
 
@@ -34,7 +33,11 @@ class TsunamiFn(torch.autograd.Function):
         g, S = cfg.grid, int(cfg.steps)
         code = tsu.dtype_code(u0.dtype)
         dev = u0.device
-        med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), float(cfg.hx_max), float(cfg.hy_max))
+        for t, name in ((hx, "hx"), (hy, "hy"), (u0, "u0"), (u1, "u1")):
+            if t is not None and tuple(t.shape) != (g.ny, g.ld):
+                raise ValueError(f"{name} must have shape (ny, ld) = {(g.ny, g.ld)} (got {tuple(t.shape)})")
+        med = tsu.Medium(tsu._field(hx, g, code, "hx"), tsu._field(hy, g, code, "hy"), float(cfg.ext[1]),
+                         float(cfg.ext[3]), float(cfg.ext[0]), float(cfg.ext[2]))
         # four state buffers: FP32 runs then take the warp-blocked pass (receivers and checkpoints
         # recorded by it), FP64 runs one step per pass
         bufs = [torch.zeros_like(u0) for _ in range(4)]
@@ -65,7 +68,11 @@ class TsunamiFn(torch.autograd.Function):
         cfg = ctx.cfg
         g, S = cfg.grid, int(cfg.steps)
         code = tsu.dtype_code(u0.dtype)
-        med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), float(cfg.hx_max), float(cfg.hy_max))
+        nrec = int(cfg.rec_idx.numel())
+        if tuple(dtraces.shape) != (S, nrec):
+            raise ValueError(f"dtraces must have shape [S, nrec] = {(S, nrec)} (got {tuple(dtraces.shape)})")
+        med = tsu.Medium(tsu._field(hx, g, code, "hx"), tsu._field(hy, g, code, "hy"), float(cfg.ext[1]),
+                         float(cfg.ext[3]), float(cfg.ext[0]), float(cfg.ext[2]))
         dev = u0.device
         g_hx = torch.zeros(u0.shape, dtype=torch.float64, device=dev)
         g_hy = torch.zeros(u0.shape, dtype=torch.float64, device=dev)

@@ -1,6 +1,7 @@
 """Autotuner for the blocked passes: picks, by timing on the caller's own problems, the pass
 (warp-blocked or CTA-blocked), its temporal depth (steps per HBM pass), the rows per tile and, for
-the batched family, whether to launch through one CUDA graph.  Results are cached per problem
+the batched family, how the tiles are packed (tile-table order, rows scaled with each problem's
+size) and whether to launch through one CUDA graph.  Results are cached per problem
 signature (grid shapes, form, GPU name) in a JSON file.
 
 The timed runs advance scratch copies of the simulations (``Simulation.clone``), never the
@@ -25,14 +26,37 @@ class Choice:
     tdepth: int   # steps per pass (0: the kernel's default)
     rows: int     # rows per tile (0: the library's rule)
     graph: bool = False
+    order: int = 0        # batched tile-table order (tsu_batch_opts.order)
+    size_rows: bool = False  # batched: rows per chunk scaled with each problem's size (rows for the largest)
+
+    def rows_per_problem(self, sims):
+        """Per-problem rows of a size-scaled packing: ``rows`` for the largest grid, in proportion
+        to the row count below it (at least 16), so that every problem's chunks take about as
+        long; None for a uniform packing."""
+        if not self.size_rows or self.rows == 0:
+            return None
+        nmax = max(s.g.ny for s in sims)
+        return [max(16, int(round(self.rows * s.g.ny / nmax))) for s in sims]
+
+    def batch_opts(self, sims) -> dict:
+        """Keyword arguments of tsu.tsu_batch_run for this choice."""
+        return dict(tdepth=self.tdepth, rows=self.rows, kernel=self.kernel, graph=self.graph, order=self.order,
+                    rows_per_problem=self.rows_per_problem(sims))
 
 
 def batch_candidates() -> list[Choice]:
-    """Configurations tried for a batched family."""
+    """Configurations tried for a batched family: the pass and its depth, rows per chunk, the
+    packing of the tile table (order, size-scaled rows) and the graph launch."""
     out = []
     for rows in (0, 64, 96, 128, 192):
         for graph in (False, True):
             out.append(Choice(2, 4, rows, graph))
+    for order in (1, 2):
+        for rows in (0, 64, 96):
+            out.append(Choice(2, 4, rows, False, order))
+    for rows in (64, 96, 128):
+        for order in (0, 2):
+            out.append(Choice(2, 4, rows, False, order, True))
     out += [Choice(2, 2, 128, False), Choice(3, 8, 128, False), Choice(3, 4, 128, False)]
     return out
 
@@ -120,16 +144,16 @@ def tune_batch(sims, rounds: int = 4, cache: Cache | None = None, timer=wall_tim
     work = {}  # per candidate: step counts and workspace, made before any timing
 
     def run(c: Choice):
+        o = c.batch_opts(scratch)
         if c not in work:
             k = c.tdepth or (4 if c.kernel == 2 else 8)
             nsteps = [rounds * k] * len(scratch)
-            wsb = tsu.tsu_batch_workspace(scratch, nsteps, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel)
+            wsb = tsu.tsu_batch_workspace(scratch, nsteps, **{key: v for key, v in o.items() if key != "graph"})
             work[c] = (nsteps, torch.zeros(wsb, dtype=torch.uint8, device="cuda"), wsb)
         nsteps, ws, wsb = work[c]
         side.wait_stream(torch.cuda.current_stream())  # the workspace is zeroed on the current stream
         with torch.cuda.stream(side):
-            tsu.tsu_batch_run(scratch, nsteps, ws, wsb, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel, graph=c.graph,
-                              stream=side)
+            tsu.tsu_batch_run(scratch, nsteps, ws, wsb, stream=side, **o)
         side.synchronize()
 
     best, _ = pick(batch_candidates(), run, timer)

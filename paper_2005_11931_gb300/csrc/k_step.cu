@@ -217,14 +217,21 @@ typename ArithOf<T>::type make_arith(const StencilGeom& g) {
   return a;
 }
 
+constexpr int kStepThreads = 128;
+
+// launch geometry of the pass: CTAs of 128 threads x one vector each across, rows per CTA down
+template <typename T>
+dim3 step_grid(int64_t ld, int64_t ny, int& rows) {
+  const int64_t cols_per_cta = (int64_t)kStepThreads * Vec<T>::V;
+  if (rows <= 0) rows = auto_rows(ld, ny, cols_per_cta);
+  return dim3((unsigned)((ld + cols_per_cta - 1) / cols_per_cta), (unsigned)((ny - 2 + rows - 1) / rows));
+}
+
 template <typename T, int FORM>
 cudaError_t step_t(const StencilGeom& g, const void* hx, const void* hy, const void* u_prev, const void* u_cur,
                    void* v, void* u_next, const PassOut& o, bool store, int rows, cudaStream_t s) {
-  constexpr int V = Vec<T>::V;
-  const int threads = 128;
-  const int64_t cols_per_cta = (int64_t)threads * V;
-  if (rows <= 0) rows = auto_rows(g.ld, g.ny, cols_per_cta);
-  dim3 grid((unsigned)((g.ld + cols_per_cta - 1) / cols_per_cta), (unsigned)((g.ny - 2 + rows - 1) / rows));
+  const int threads = kStepThreads;
+  const dim3 grid = step_grid<T>(g.ld, g.ny, rows);
   const auto ar = make_arith<T>(g);
   const T* p_in = (const T*)(FORM == 0 ? u_prev : v);
   T* p_out = (T*)v;
@@ -252,6 +259,11 @@ cudaError_t step_t(const StencilGeom& g, const void* hx, const void* hy, const v
 }
 
 }  // namespace
+
+int64_t one_step_ctas(int64_t ld, int64_t ny, int dtype, int rows) {
+  const dim3 grid = dtype == TSU_F32 ? step_grid<float>(ld, ny, rows) : step_grid<double>(ld, ny, rows);
+  return (int64_t)grid.x * grid.y;
+}
 
 cudaError_t launch_step(const StencilGeom& g, int dtype, int form, const void* hx, const void* hy,
                         const void* u_prev, const void* u_cur, void* v, void* u_next, const PassOut& o, bool store,

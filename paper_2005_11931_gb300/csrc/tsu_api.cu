@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -29,52 +31,14 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-int check_grid(const tsu_grid* g) {
-  if (!g) return fail(TSU_EINVAL, "grid is NULL");
-  if (g->nx < 3 || g->ny < 3) return fail(TSU_EINVAL, "grid needs nx, ny >= 3 (got %d x %d)", g->nx, g->ny);
-  if (g->ld < g->nx || (g->ld % 4) != 0)
-    return fail(TSU_EINVAL, "ld must be >= nx and a multiple of 4 (ld=%lld nx=%d)", (long long)g->ld, g->nx);
-  if (!(g->dx > 0.0) || !(g->dy > 0.0)) return fail(TSU_EINVAL, "dx, dy must be positive");
-  if ((int64_t)g->ny * g->ld >= ((int64_t)1 << 40)) return fail(TSU_EINVAL, "grid too large");
-  return TSU_OK;
-}
-
-int check_dtype(int dtype) {
-  if (dtype != TSU_F32 && dtype != TSU_F64) return fail(TSU_EINVAL, "dtype must be TSU_F32 or TSU_F64");
-  return TSU_OK;
-}
-
-int check_field(const void* p, const char* name) {
-  if (!p) return fail(TSU_EINVAL, "%s is NULL", name);
-  if (!aligned16(p)) return fail(TSU_EINVAL, "%s is not 16-byte aligned", name);
-  return TSU_OK;
-}
-
+// the shared checks (tsu::check_*) with this file's thread-local message buffer
+int check_grid(const tsu_grid* g) { return tsu::check_grid(g, g_err, sizeof g_err); }
+int check_dtype(int dtype) { return tsu::check_dtype(dtype, g_err, sizeof g_err); }
+int check_field(const void* p, const char* name) { return tsu::check_field(p, name, g_err, sizeof g_err); }
 int check_cfl(const tsu_grid* g, double tau, const tsu_medium* m) {
-  if (!m) return fail(TSU_EINVAL, "medium is NULL");
-  if (!(tau > 0.0) || !isfinite(tau)) return fail(TSU_EINVAL, "tau must be positive and finite");
-  if (!(m->hx_max >= 0.0) || !(m->hy_max >= 0.0)) return fail(TSU_EINVAL, "medium maxima must be >= 0");
-  const double q = tau * tau * (m->hx_max / (g->dx * g->dx) + m->hy_max / (g->dy * g->dy));
-  if (q > 1.0)
-    return fail(TSU_ECFL, "tau^2 (hx_max/dx^2 + hy_max/dy^2) = %.6g > 1: leapfrog unstable", q);
-  return TSU_OK;
+  return tsu::check_medium(g, tau, m, g_err, sizeof g_err);
 }
-
-int check_state(const tsu_state* st, bool need_roles) {
-  if (!st) return fail(TSU_EINVAL, "state is NULL");
-  if (st->form != TSU_FORM_STANDARD && st->form != TSU_FORM_INCREMENT) return fail(TSU_EINVAL, "bad form");
-  const int need = st->form == TSU_FORM_STANDARD ? 2 : 3;
-  if (st->nbuf < need || st->nbuf > 4)
-    return fail(TSU_EINVAL, "state needs %d..4 buffers for this form (nbuf = %d)", need, st->nbuf);
-  for (int b = 0; b < st->nbuf; ++b) {
-    if (!st->buf[b] || ((uintptr_t)st->buf[b] & 15u)) return fail(TSU_EINVAL, "state buf[%d] NULL or misaligned", b);
-  }
-  if (need_roles) {
-    if (st->cur < 0 || st->cur >= st->nbuf || st->aux < 0 || st->aux >= st->nbuf || st->cur == st->aux)
-      return fail(TSU_EINVAL, "state cur/aux invalid (%d, %d)", st->cur, st->aux);
-  }
-  return TSU_OK;
-}
+int check_state(const tsu_state* st, bool need_roles) { return tsu::check_state(st, need_roles, g_err, sizeof g_err); }
 
 // first buffer index that is neither cur nor aux
 int scratch_index(const tsu_state* st, int skip) {
@@ -104,6 +68,94 @@ size_t elem_size(int dtype) { return dtype == TSU_F32 ? 4 : 8; }
   } while (0)
 }  // namespace
 
+namespace tsu {
+
+namespace {
+int errf(char* err, size_t n, int code, const char* fmt, ...) {
+  if (err && n) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, n, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+}  // namespace
+
+int check_grid(const tsu_grid* g, char* err, size_t n) {
+  if (!g) return errf(err, n, TSU_EINVAL, "grid is NULL");
+  if (g->nx < 3 || g->ny < 3) return errf(err, n, TSU_EINVAL, "grid needs nx, ny >= 3 (got %d x %d)", g->nx, g->ny);
+  if (g->ld < g->nx || (g->ld % 4) != 0)
+    return errf(err, n, TSU_EINVAL, "ld must be >= nx and a multiple of 4 (ld=%lld nx=%d)", (long long)g->ld, g->nx);
+  if (!(g->dx > 0.0) || !(g->dy > 0.0) || !isfinite(g->dx) || !isfinite(g->dy))
+    return errf(err, n, TSU_EINVAL, "dx, dy must be positive and finite");
+  if ((int64_t)g->ny * g->ld >= ((int64_t)1 << 40)) return errf(err, n, TSU_EINVAL, "grid too large");
+  return TSU_OK;
+}
+
+int check_dtype(int dtype, char* err, size_t n) {
+  if (dtype != TSU_F32 && dtype != TSU_F64) return errf(err, n, TSU_EINVAL, "dtype must be TSU_F32 or TSU_F64");
+  return TSU_OK;
+}
+
+int check_field(const void* p, const char* name, char* err, size_t n) {
+  if (!p) return errf(err, n, TSU_EINVAL, "%s is NULL", name);
+  if (((uintptr_t)p & 15u) != 0) return errf(err, n, TSU_EINVAL, "%s is not 16-byte aligned", name);
+  return TSU_OK;
+}
+
+// One face family's extrema: a positive depth (0 < min <= max, Sec. 2: 0 < c0 <= h_j), or a
+// family that is identically zero (min = max = 0: the equation decouples into 1D problems along
+// the other direction, the paper's 1D setting).
+static int check_family(double mn, double mx, const char* name, char* err, size_t n) {
+  if (!(mx >= 0.0) || !isfinite(mx) || !isfinite(mn))
+    return errf(err, n, TSU_EINVAL, "medium: %s extrema must be finite with max >= 0", name);
+  if (mx == 0.0 && mn == 0.0) return TSU_OK;
+  if (!(mn > 0.0) || mn > mx)
+    return errf(err, n, TSU_ENONPOS, "medium: %s face depth minimum %.6g is not in (0, max = %.6g]", name, mn, mx);
+  return TSU_OK;
+}
+
+// both families (and not both identically zero)
+static int check_positive(const tsu_medium* m, char* err, size_t n) {
+  int rc = check_family(m->hx_min, m->hx_max, "hx", err, n);
+  if (rc != TSU_OK) return rc;
+  rc = check_family(m->hy_min, m->hy_max, "hy", err, n);
+  if (rc != TSU_OK) return rc;
+  if (m->hx_max == 0.0 && m->hy_max == 0.0) return errf(err, n, TSU_ENONPOS, "medium: every face depth is 0");
+  return TSU_OK;
+}
+
+int check_medium(const tsu_grid* g, double tau, const tsu_medium* m, char* err, size_t n) {
+  if (!m) return errf(err, n, TSU_EINVAL, "medium is NULL");
+  if (!(tau > 0.0) || !isfinite(tau)) return errf(err, n, TSU_EINVAL, "tau must be positive and finite");
+  const int rc = check_positive(m, err, n);
+  if (rc != TSU_OK) return rc;
+  const double q = tau * tau * (m->hx_max / (g->dx * g->dx) + m->hy_max / (g->dy * g->dy));
+  if (!(q <= 1.0))
+    return errf(err, n, TSU_ECFL, "tau^2 (hx_max/dx^2 + hy_max/dy^2) = %.6g > 1: leapfrog unstable", q);
+  return TSU_OK;
+}
+
+int check_state(const tsu_state* st, bool need_roles, char* err, size_t n) {
+  if (!st) return errf(err, n, TSU_EINVAL, "state is NULL");
+  if (st->form != TSU_FORM_STANDARD && st->form != TSU_FORM_INCREMENT) return errf(err, n, TSU_EINVAL, "bad form");
+  const int need = st->form == TSU_FORM_STANDARD ? 2 : 3;
+  if (st->nbuf < need || st->nbuf > 4)
+    return errf(err, n, TSU_EINVAL, "state needs %d..4 buffers for this form (nbuf = %d)", need, st->nbuf);
+  for (int b = 0; b < st->nbuf; ++b) {
+    if (!st->buf[b] || ((uintptr_t)st->buf[b] & 15u))
+      return errf(err, n, TSU_EINVAL, "state buf[%d] NULL or misaligned", b);
+  }
+  if (need_roles) {
+    if (st->cur < 0 || st->cur >= st->nbuf || st->aux < 0 || st->aux >= st->nbuf || st->cur == st->aux)
+      return errf(err, n, TSU_EINVAL, "state cur/aux invalid (%d, %d)", st->cur, st->aux);
+  }
+  return TSU_OK;
+}
+
+}  // namespace tsu
+
 extern "C" {
 
 int tsu_version(void) { return 100; }
@@ -115,6 +167,13 @@ double tsu_tau_for(const tsu_grid* g, double hx_max, double hy_max, double cfl) 
   const double s = hx_max / (g->dx * g->dx) + hy_max / (g->dy * g->dy);
   if (!(s > 0)) return 0.0;
   return cfl / sqrt(s);
+}
+
+double tsu_tau_courant(const tsu_grid* g, const tsu_medium* m, double courant) {
+  if (!g || !m || !(g->dx > 0) || !(g->dy > 0) || !(courant > 0) || !isfinite(courant)) return 0.0;
+  const double hmax = m->hx_max > m->hy_max ? m->hx_max : m->hy_max;
+  if (!(hmax > 0) || !isfinite(hmax)) return 0.0;
+  return courant * (g->dx < g->dy ? g->dx : g->dy) / sqrt(hmax);
 }
 
 // validated depth descriptor -> device parameters
@@ -438,35 +497,62 @@ int tsu_adjoint_workspace(const tsu_grid* g, int dtype, int form, int64_t nsteps
 // One auxiliary (non-blocking) stream per device and host thread with its events, created on
 // first use, for overlapping the adjoint's segment recompute with its reverse sweep.  Per thread,
 // so that adjoints enqueued from several host threads never share the events that order them.
+// The thread owns them: they are destroyed when the thread exits (work still in flight on the
+// stream completes first; CUDA releases a busy stream once it is idle).
 namespace {
+std::atomic<int> g_aux_live{0};
+
 struct AuxStream {
-  cudaStream_t s;
-  cudaEvent_t start, computed[2], swept[2];
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t start = nullptr, computed[2] = {nullptr, nullptr}, swept[2] = {nullptr, nullptr};
+  AuxStream() = default;
+  AuxStream(const AuxStream&) = delete;
+  AuxStream& operator=(const AuxStream&) = delete;
+  ~AuxStream() {  // also releases a partial creation; errors at process teardown are ignored
+    int prev = -1;
+    const bool switch_dev = cudaGetDevice(&prev) == cudaSuccess && dev >= 0 && prev != dev;
+    if (switch_dev) cudaSetDevice(dev);
+    cudaEvent_t* evs[5] = {&start, &computed[0], &computed[1], &swept[0], &swept[1]};
+    for (cudaEvent_t* e : evs)
+      if (*e) cudaEventDestroy(*e);
+    if (s) {
+      cudaStreamDestroy(s);
+      g_aux_live.fetch_sub(1);
+    }
+    if (switch_dev) cudaSetDevice(prev);
+  }
 };
-thread_local AuxStream* g_aux[64] = {};
+
+struct AuxSet {
+  std::unique_ptr<AuxStream> dev[64];
+};
+thread_local AuxSet g_aux;
 
 AuxStream* aux_stream() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!g_aux[dev]) {
-    AuxStream* a = new AuxStream();
+  if (!g_aux.dev[dev]) {
+    std::unique_ptr<AuxStream> a(new AuxStream());
+    a->dev = dev;
     bool ok = cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) g_aux_live.fetch_add(1);
+    else a->s = nullptr;
     ok = ok && cudaEventCreateWithFlags(&a->start, cudaEventDisableTiming) == cudaSuccess;
     for (int b = 0; b < 2 && ok; ++b) {
       ok = cudaEventCreateWithFlags(&a->computed[b], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&a->swept[b], cudaEventDisableTiming) == cudaSuccess;
     }
-    if (!ok) {
-      delete a;
-      return nullptr;
-    }
-    g_aux[dev] = a;
+    if (!ok) return nullptr;  // the destructor releases what was created
+    g_aux.dev[dev] = std::move(a);
   }
-  return g_aux[dev];
+  return g_aux.dev[dev].get();
 }
 }  // namespace
 
 extern "C" {
+
+int tsu_aux_streams(void) { return g_aux_live.load(); }
 
 int64_t tsu_ckpt_slots(int64_t nsteps, int64_t ckpt_every) {
   if (nsteps < 2 || ckpt_every < 1) return 0;
@@ -670,6 +756,11 @@ int tsu_adjoint(const tsu_grid* g, int dtype, int form, double tau, const tsu_me
 // default 8); descriptor size and strip width follow the kernel
 static int batch_kernel(const tsu_batch_opts* opts) { return (opts && opts->kernel) ? opts->kernel : 2; }
 
+// rows per chunk of problem i under these options (rows: the call's uniform choice)
+static int batch_rows_of(const tsu_batch_opts* opts, int i, int rows) {
+  return (opts && opts->rows_per_problem && opts->rows_per_problem[i] > 0) ? opts->rows_per_problem[i] : rows;
+}
+
 static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts* opts, int* k_out,
                         int* rows_out, int64_t* ntiles_out, size_t* bytes_out) {
   if (nprob < 1 || !probs) return fail(TSU_EINVAL, "need at least one problem");
@@ -678,29 +769,27 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
   const int k = (opts && opts->tdepth) ? opts->tdepth : (kern == 2 ? 4 : 8);
   if (kern == 3 && !tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 3: tdepth must be 4 or 8");
   if (kern == 2 && !tsu::wtb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 2: tdepth must be 2 or 4");
+  if (opts && (opts->order < 0 || opts->order > 2)) return fail(TSU_EINVAL, "order must be 0, 1 or 2");
   const int W = kern == 2 ? tsu::wtb_strip_width() : tsu::tb_strip_width(k);
+  for (int i = 0; i < nprob; ++i) TRY(check_grid(&probs[i].grid));
   auto tiles_at = [&](int r) {
     int64_t t = 0;
-    for (int i = 0; i < nprob; ++i) t += ((probs[i].grid.ld + W - 1) / W) * ((probs[i].grid.ny - 2 + r - 1) / r);
+    for (int i = 0; i < nprob; ++i) {
+      const int ri = batch_rows_of(opts, i, r);
+      t += ((probs[i].grid.ld + W - 1) / W) * ((probs[i].grid.ny - 2 + ri - 1) / ri);
+    }
     return t;
   };
   // rows per chunk: 80 (64-problem family of 512^2..2048^2, FP32 GLUPS of the flux-form pass at
-  // 56/64/80/128 rows: 927/932/934/889; ordering the tile table longest tile first instead of
-  // problem by problem lost 2-3 % at every row count), fewer (down to 16) while the family's
-  // tiles would not fill one wave of the GPU (small problems)
+  // 56/64/80/128 rows: 927/932/934/889), fewer (down to 16) while the family's tiles would not
+  // fill one wave of the GPU (small problems)
   int rows = (opts && opts->rows) ? opts->rows : 80;
-  if (!(opts && opts->rows) && kern == 2) {
-    for (int i = 0; i < nprob; ++i) TRY(check_grid(&probs[i].grid));
+  if (!(opts && opts->rows) && kern == 2)
     while (rows > 16 && tiles_at(rows) < (int64_t)152 * 3 * 4) rows = rows > 32 ? rows / 2 : 16;
-  }
-  if (rows < 16) return fail(TSU_EINVAL, "rows must be >= 16");
+  for (int i = 0; i < nprob; ++i)
+    if (batch_rows_of(opts, i, rows) < 16) return fail(TSU_EINVAL, "problem %d: rows must be >= 16", i);
   const size_t ab = kern == 2 ? tsu::wtb_args_bytes() : tsu::tb_args_bytes();
-  int64_t ntiles = 0;
-  for (int i = 0; i < nprob; ++i) {
-    const tsu_grid& g = probs[i].grid;
-    TRY(check_grid(&g));
-    ntiles += ((g.ld + W - 1) / W) * ((g.ny - 2 + rows - 1) / rows);
-  }
+  const int64_t ntiles = tiles_at(rows);
   *k_out = k;
   *rows_out = rows;
   *ntiles_out = ntiles;
@@ -739,27 +828,54 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
   const int kern = batch_kernel(opts);
   const int W = kern == 2 ? tsu::wtb_strip_width() : tsu::tb_strip_width(k);
   const size_t ab = kern == 2 ? tsu::wtb_args_bytes() : tsu::tb_args_bytes();
-  // problems in decreasing order of blocked rounds: round r launches a prefix of the tile table
+  // problems in decreasing order of blocked rounds: round r launches a prefix of the tile table,
+  // the tiles of the problems that still have a round to go.  Problems with equal round counts
+  // form a group whose tiles are packed in the order the options ask for.
   std::vector<int> order(nprob);
   for (int i = 0; i < nprob; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return probs[a].nsteps / k > probs[b].nsteps / k; });
+  const int pack = opts ? opts->order : 0;
   std::vector<int32_t> tiles;  // int4 per tile
-  std::vector<int64_t> prefix;  // tiles of problems order[0..i]
+  std::vector<int64_t> prefix(nprob);  // tiles up to the end of the group of order[i]
   tiles.reserve((size_t)ntiles * 4);
-  for (int oi = 0; oi < nprob; ++oi) {
-    const int i = order[oi];
-    const tsu_grid& g = probs[i].grid;
-    const int strips = (int)((g.ld + W - 1) / W), chunks = (int)((g.ny - 2 + rows - 1) / rows);
-    for (int c = 0; c < chunks; ++c)
-      for (int st = 0; st < strips; ++st) {
-        tiles.push_back(i);
-        tiles.push_back(st);
-        tiles.push_back(c);
-        tiles.push_back(0);
-      }
-    prefix.push_back((int64_t)tiles.size() / 4);
+  auto put = [&](int i, int c, int st) {
+    tiles.push_back(i);
+    tiles.push_back(st);
+    tiles.push_back(c);
+    tiles.push_back(0);
+  };
+  auto strips_of = [&](int i) { return (int)((probs[i].grid.ld + W - 1) / W); };
+  auto chunks_of = [&](int i) {
+    const int ri = batch_rows_of(opts, i, rows);
+    return (int)((probs[i].grid.ny - 2 + ri - 1) / ri);
+  };
+  for (int g0 = 0; g0 < nprob;) {
+    int g1 = g0;
+    while (g1 < nprob && probs[order[g1]].nsteps / k == probs[order[g0]].nsteps / k) ++g1;
+    if (pack == 2) {  // chunk c of every problem of the group, then c + 1 ...
+      int cmax = 0;
+      for (int oi = g0; oi < g1; ++oi) cmax = std::max(cmax, chunks_of(order[oi]));
+      for (int c = 0; c < cmax; ++c)
+        for (int oi = g0; oi < g1; ++oi)
+          if (c < chunks_of(order[oi]))
+            for (int st = 0; st < strips_of(order[oi]); ++st) put(order[oi], c, st);
+    } else {
+      for (int pass = 0; pass < (pack == 1 ? 2 : 1); ++pass)
+        for (int oi = g0; oi < g1; ++oi) {
+          const int i = order[oi], nc = chunks_of(i), ri = batch_rows_of(opts, i, rows);
+          const bool ragged = (probs[i].grid.ny - 2) % ri != 0;
+          for (int c = 0; c < nc; ++c) {
+            // order 1: full chunks in the first pass, a ragged last chunk in the second
+            if (pack == 1 && (pass == 1) != (ragged && c == nc - 1)) continue;
+            for (int st = 0; st < strips_of(i); ++st) put(i, c, st);
+          }
+        }
+    }
+    for (int oi = g0; oi < g1; ++oi) prefix[oi] = (int64_t)tiles.size() / 4;
+    g0 = g1;
   }
+  if ((int64_t)tiles.size() / 4 != ntiles) return fail(TSU_EINVAL, "tile table size mismatch");
   // descriptor sets: launch 0, then the two role assignments that alternate from launch 1 on
   std::vector<unsigned char> host(3 * (size_t)nprob * ab, 0);
   std::vector<tsu_state> sim(nprob);
@@ -771,12 +887,13 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
       tsu_state& st = sim[i];
       const int f1 = scratch_index(&st, -1), f2 = scratch_index(&st, f1);
       void* dst = &host[((size_t)set * nprob + i) * ab];
+      const int ri = batch_rows_of(opts, i, rows);
       if (kern == 2)
         tsu::wtb_fill_args(dst, geom(&probs[i].grid, probs[i].tau), probs[i].medium.hx, probs[i].medium.hy,
-                           st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], rows);
+                           st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], ri);
       else
         tsu::tb_fill_args(dst, geom(&probs[i].grid, probs[i].tau), probs[i].medium.hx, probs[i].medium.hy,
-                          st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], status, rows);
+                          st.buf[st.cur], st.buf[st.aux], st.buf[f1], st.buf[f2], status, ri);
       st.cur = f1;
       st.aux = f2;
     }
@@ -931,7 +1048,7 @@ static int check_implicit(const tsu_grid* g, int dtype, double tau, double sigma
   TRY(check_field(m->hy, "hy"));
   if (!(tau > 0.0) || !isfinite(tau)) return fail(TSU_EINVAL, "tau must be positive and finite");
   if (!(sigma >= 0.0) || !isfinite(sigma)) return fail(TSU_EINVAL, "sigma must be >= 0 and finite");
-  if (!(m->hx_max >= 0.0) || !(m->hy_max >= 0.0)) return fail(TSU_EINVAL, "medium maxima must be >= 0");
+  TRY(tsu::check_positive(m, g_err, sizeof g_err));
   if (sigma < 0.25) {
     const double q = tau * tau * (m->hx_max / (g->dx * g->dx) + m->hy_max / (g->dy * g->dy));
     if (q * (1.0 - 4.0 * sigma) > 1.0)

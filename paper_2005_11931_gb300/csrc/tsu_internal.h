@@ -43,6 +43,16 @@ inline int auto_rows(int64_t ld, int64_t ny, int64_t cols_per_cta) {
 }
 
 size_t energy_ws_bytes(int64_t ny, int64_t ld);
+
+// Argument checks shared by the entry points (tsu_api.cu, tsu_noalloc.cu).  Each returns TSU_OK,
+// or a status code after writing a message into err[0 .. n).
+int check_grid(const tsu_grid* g, char* err, size_t n);
+int check_dtype(int dtype, char* err, size_t n);
+int check_field(const void* p, const char* name, char* err, size_t n);
+// tau finite and positive, the medium's extrema consistent (positive depth, or a face family that
+// is identically zero) and tau inside the leapfrog bound
+int check_medium(const tsu_grid* g, double tau, const tsu_medium* m, char* err, size_t n);
+int check_state(const tsu_state* st, bool need_roles, char* err, size_t n);
 EnergyWs energy_ws_carve(void* ws, size_t bytes, int64_t ny, int64_t ld);
 
 // Host-side mollifier normalisers, computed once by double-exponential quadrature.
@@ -77,6 +87,10 @@ struct PassOut {
 
 cudaError_t launch_init(const StencilGeom& g, int dtype, int form, const void* hx, const void* hy,
                         const void* u0, const void* u1, tsu_state* st, cudaStream_t s);
+
+// CTAs of one launch of the one-step pass (launch_step) for this grid, element type and rows per
+// CTA (rows <= 0: the automatic choice): one energy partial sum each.
+int64_t one_step_ctas(int64_t ld, int64_t ny, int dtype, int rows);
 
 // One leapfrog pass (standard or increment form) over the interior; store=false computes only
 // the side outputs (energy of the current pair, traces).

@@ -62,8 +62,6 @@ cudaError_t noalloc_scratch(void** out) {
   return cudaSuccess;
 }
 
-bool al16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; }
-
 }  // namespace
 
 extern "C" {
@@ -74,26 +72,20 @@ const char* tsu_noalloc_last_error(void) { return g_noalloc_err; }
 int tsu_step_n_noalloc(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, tsu_state* st,
                        int64_t nsteps, double* energy, void* stream) {
   g_noalloc_err[0] = 0;
-  if (!g || !m || !st) return na_fail(TSU_EINVAL, "grid, medium or state is NULL");
-  if (g->nx < 3 || g->ny < 3 || g->ld < g->nx || (g->ld % 4) != 0 || !(g->dx > 0) || !(g->dy > 0))
-    return na_fail(TSU_EINVAL, "bad grid (nx, ny >= 3, ld >= nx, ld % 4 == 0, dx, dy > 0)");
-  if (dtype != TSU_F32 && dtype != TSU_F64) return na_fail(TSU_EINVAL, "dtype must be TSU_F32 or TSU_F64");
+  char* err = g_noalloc_err;
+  const size_t n = sizeof g_noalloc_err;
+  // the same checks as tsu_step_n, in the same order, so that both refuse the same inputs
+  int rc = tsu::check_grid(g, err, n);
+  if (rc == TSU_OK) rc = tsu::check_dtype(dtype, err, n);
+  if (rc == TSU_OK) rc = tsu::check_medium(g, tau, m, err, n);
+  if (rc == TSU_OK) rc = tsu::check_field(m->hx, "hx", err, n);
+  if (rc == TSU_OK) rc = tsu::check_field(m->hy, "hy", err, n);
+  if (rc == TSU_OK) rc = tsu::check_state(st, true, err, n);
+  if (rc != TSU_OK) return rc;
   if (nsteps < 0) return na_fail(TSU_EINVAL, "nsteps must be >= 0");
-  if (!(tau > 0.0) || !(m->hx_max >= 0.0) || !(m->hy_max >= 0.0))
-    return na_fail(TSU_EINVAL, "tau must be positive and the medium maxima >= 0");
-  if (tau * tau * (m->hx_max / (g->dx * g->dx) + m->hy_max / (g->dy * g->dy)) > 1.0)
-    return na_fail(TSU_ECFL, "tau^2 (hx_max/dx^2 + hy_max/dy^2) > 1: leapfrog unstable");
-  if (!al16(m->hx) || !al16(m->hy)) return na_fail(TSU_EINVAL, "hx, hy NULL or not 16-byte aligned");
-  const int need = st->form == TSU_FORM_STANDARD ? 2 : (st->form == TSU_FORM_INCREMENT ? 3 : 99);
-  if (st->nbuf < need || st->nbuf > 4) return na_fail(TSU_EINVAL, "bad form or too few state buffers");
-  for (int b = 0; b < st->nbuf; ++b)
-    if (!al16(st->buf[b])) return na_fail(TSU_EINVAL, "state buffer NULL or not 16-byte aligned");
-  if (st->cur < 0 || st->cur >= st->nbuf || st->aux < 0 || st->aux >= st->nbuf || st->cur == st->aux)
-    return na_fail(TSU_EINVAL, "state cur/aux invalid");
+  if (energy && (((uintptr_t)energy) & 7u)) return na_fail(TSU_EINVAL, "energy must be a device double array");
   // one partial per CTA of the one-step pass; refuse grids the fixed array cannot hold
-  const int64_t cols = (int64_t)128 * (dtype == TSU_F32 ? 4 : 2);
-  const int64_t ctas = ((g->ld + cols - 1) / cols) * ((g->ny - 2 + kNoallocRows - 1) / kNoallocRows);
-  if (energy && ctas > kNoallocPartials)
+  if (energy && tsu::one_step_ctas(g->ld, g->ny, dtype, kNoallocRows) > kNoallocPartials)
     return na_fail(TSU_ENOMEM, "grid too large for the fixed scratch of tsu_step_n_noalloc "
                                "(more than 65536 energy partial sums); use tsu_step_n with a workspace");
   if (nsteps == 0) return TSU_OK;

@@ -58,7 +58,14 @@ class Depth(C.Structure):
 
 
 class Medium(C.Structure):
-    _fields_ = [("hx", C.c_void_p), ("hy", C.c_void_p), ("hx_max", C.c_double), ("hy_max", C.c_double)]
+    _fields_ = [("hx", C.c_void_p), ("hy", C.c_void_p), ("hx_max", C.c_double), ("hy_max", C.c_double),
+                ("hx_min", C.c_double), ("hy_min", C.c_double)]
+
+
+def medium(hx, hy, ext) -> Medium:
+    """The tsu_medium of face arrays hx, hy with the extrema ``ext`` = [min hx, max hx, min hy,
+    max hy] that tsu_make_depth returns."""
+    return Medium(_ptr(hx), _ptr(hy), float(ext[1]), float(ext[3]), float(ext[0]), float(ext[2]))
 
 
 class State(C.Structure):
@@ -78,7 +85,17 @@ class Problem(C.Structure):
 
 
 class BatchOpts(C.Structure):
-    _fields_ = [("tdepth", C.c_int32), ("rows", C.c_int32), ("kernel", C.c_int32), ("graph", C.c_int32)]
+    _fields_ = [("tdepth", C.c_int32), ("rows", C.c_int32), ("kernel", C.c_int32), ("graph", C.c_int32),
+                ("order", C.c_int32), ("rows_per_problem", C.POINTER(C.c_int32))]
+
+
+def _batch_opts(tdepth=0, rows=0, kernel=0, graph=False, order=0, rows_per_problem=None) -> BatchOpts:
+    o = BatchOpts(int(tdepth), int(rows), int(kernel), int(bool(graph)), int(order))
+    if rows_per_problem is not None:
+        arr = (C.c_int32 * len(rows_per_problem))(*[int(r) for r in rows_per_problem])
+        o.rows_per_problem = C.cast(arr, C.POINTER(C.c_int32))
+        o._keep = arr
+    return o
 
 
 _lib = None
@@ -98,6 +115,7 @@ def load():
         "tsu_last_error": ([], C.c_char_p),
         "tsu_make_depth": ([C.POINTER(Grid), C.POINTER(Depth), C.c_int, vp, vp, vp, C.POINTER(C.c_double), vp], C.c_int),
         "tsu_tau_for": ([C.POINTER(Grid), dbl, dbl, dbl], dbl),
+        "tsu_tau_courant": ([C.POINTER(Grid), C.POINTER(Medium), dbl], dbl),
         "tsu_depth_eps_derivative": ([C.POINTER(Grid), C.POINTER(Depth), C.c_int, vp, vp, vp], C.c_int),
         "tsu_reduce_workspace": ([], C.c_size_t),
         "tsu_depth_eps_gradient": ([C.POINTER(Grid), C.POINTER(Depth), vp, vp, vp, vp, C.c_size_t, vp], C.c_int),
@@ -108,6 +126,7 @@ def load():
                         C.POINTER(StepOpts), vp, C.c_size_t, vp], C.c_int),
         "tsu_sync_status": ([vp, C.c_size_t, vp], C.c_int),
         "tsu_ckpt_slots": ([i64, i64], i64),
+        "tsu_aux_streams": ([], C.c_int),
         "tsu_step_n_noalloc": ([C.POINTER(Grid), C.c_int, dbl, C.POINTER(Medium), C.POINTER(State), i64, vp, vp],
                                C.c_int),
         "tsu_noalloc_last_error": ([], C.c_char_p),
@@ -155,6 +174,42 @@ def _ptr(t) -> int | None:
     return int(t)
 
 
+# The C ABI takes raw device addresses and cannot see how large a buffer is, so every tensor that
+# crosses it is checked here first (device, element type, contiguity, size).  Plain integers are
+# passed through as device addresses: their extent is the caller's responsibility.
+def _checked(t, name: str, dtype, need: int):
+    if t is None or not isinstance(t, torch.Tensor):
+        return _ptr(t)
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype} (got {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < need:
+        raise ValueError(f"{name} holds {t.numel()} elements; {need} are needed")
+    return t.data_ptr()
+
+
+def _field(t, g: "Grid", code: int, name: str):
+    """A [ny][ld] device field of element type ``code``."""
+    return _checked(t, name, DTYPES[code], int(g.ny) * int(g.ld))
+
+
+def _vec(t, n: int, dtype, name: str):
+    """A device vector of at least ``n`` elements of ``dtype`` (None: any element type)."""
+    return _checked(t, name, dtype, int(n))
+
+
+def _bytes(t, n: int, name: str):
+    """A device byte buffer of at least ``n`` bytes (any element type)."""
+    if isinstance(t, torch.Tensor):
+        _checked(t, name, None, 0)
+        if t.numel() * t.element_size() < n:
+            raise ValueError(f"{name} holds {t.numel() * t.element_size()} bytes; {n} are needed")
+    return _ptr(t)
+
+
 def _stream(stream) -> int | None:
     if stream is None:
         return torch.cuda.current_stream().cuda_stream
@@ -190,9 +245,10 @@ def tsu_make_depth(g: Grid, depth: dict, dtype, hx: torch.Tensor, hy: torch.Tens
                    sync: bool = True, stream=None):
     """Face coefficients of the regularised depth; returns [min hx, max hx, min hy, max hy] when sync."""
     d = depth_struct(depth)
+    code = dtype_code(dtype)
     ext = (C.c_double * 4)() if sync else None
-    rc = load().tsu_make_depth(C.byref(g), C.byref(d), dtype_code(dtype), _ptr(hx), _ptr(hy), _ptr(ext_dev),
-                               ext, _stream(stream))
+    rc = load().tsu_make_depth(C.byref(g), C.byref(d), code, _field(hx, g, code, "hx"), _field(hy, g, code, "hy"),
+                               _vec(ext_dev, 4, torch.float64, "ext_dev"), ext, _stream(stream))
     _check(rc, "tsu_make_depth")
     return np.array(list(ext)) if sync else None
 
@@ -200,8 +256,9 @@ def tsu_make_depth(g: Grid, depth: dict, dtype, hx: torch.Tensor, hy: torch.Tens
 def tsu_depth_eps_derivative(g: Grid, depth: dict, dtype, dhx: torch.Tensor, dhy: torch.Tensor, stream=None):
     """d h_eps / d eps at the faces, same layout as tsu_make_depth's hx, hy."""
     d = depth_struct(depth)
-    _check(load().tsu_depth_eps_derivative(C.byref(g), C.byref(d), dtype_code(dtype), _ptr(dhx), _ptr(dhy),
-                                           _stream(stream)), "tsu_depth_eps_derivative")
+    code = dtype_code(dtype)
+    _check(load().tsu_depth_eps_derivative(C.byref(g), C.byref(d), code, _field(dhx, g, code, "dhx"),
+                                           _field(dhy, g, code, "dhy"), _stream(stream)), "tsu_depth_eps_derivative")
 
 
 def tsu_reduce_workspace() -> int:
@@ -212,15 +269,18 @@ def tsu_depth_eps_gradient(g: Grid, depth: dict, g_hx: torch.Tensor, g_hy: torch
                            ws: torch.Tensor, stream=None):
     """out[0] = dJ/deps = sum g_hx dhx/deps + g_hy dhy/deps (device double)."""
     d = depth_struct(depth)
-    _check(load().tsu_depth_eps_gradient(C.byref(g), C.byref(d), _ptr(g_hx), _ptr(g_hy), _ptr(out), _ptr(ws),
-                                         int(ws.numel() * ws.element_size()), _stream(stream)),
+    _check(load().tsu_depth_eps_gradient(C.byref(g), C.byref(d), _field(g_hx, g, TSU_F64, "g_hx"),
+                                         _field(g_hy, g, TSU_F64, "g_hy"), _vec(out, 1, torch.float64, "out"),
+                                         _bytes(ws, 0, "ws"), int(ws.numel() * ws.element_size()), _stream(stream)),
            "tsu_depth_eps_gradient")
 
 
 def tsu_diff_norms(g: Grid, dtype, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor, ws: torch.Tensor,
                    stream=None):
     """out[0] = sum (a - b)^2, out[1] = sum b^2 over nodes i < nx (device double[2])."""
-    _check(load().tsu_diff_norms(C.byref(g), dtype_code(dtype), _ptr(a), _ptr(b), _ptr(out), _ptr(ws),
+    code = dtype_code(dtype)
+    _check(load().tsu_diff_norms(C.byref(g), code, _field(a, g, code, "a"), _field(b, g, code, "b"),
+                                 _vec(out, 2, torch.float64, "out"), _bytes(ws, 0, "ws"),
                                  int(ws.numel() * ws.element_size()), _stream(stream)), "tsu_diff_norms")
 
 
@@ -228,9 +288,15 @@ def tsu_tau_for(g: Grid, hx_max: float, hy_max: float, cfl: float) -> float:
     return float(load().tsu_tau_for(C.byref(g), hx_max, hy_max, cfl))
 
 
+def tsu_tau_courant(g: Grid, medium: Medium, courant: float) -> float:
+    """tau = courant min(dx, dy) / sqrt(max face depth), the workloads' time step (0 on bad input)."""
+    return float(load().tsu_tau_courant(C.byref(g), C.byref(medium), float(courant)))
+
+
 def tsu_init(g: Grid, dtype, tau: float, medium: Medium, u0, u1, state: State, stream=None):
-    rc = load().tsu_init(C.byref(g), dtype_code(dtype), tau, C.byref(medium), _ptr(u0), _ptr(u1), C.byref(state),
-                         _stream(stream))
+    code = dtype_code(dtype)
+    rc = load().tsu_init(C.byref(g), code, tau, C.byref(medium), _field(u0, g, code, "u0"),
+                         _field(u1, g, code, "u1"), C.byref(state), _stream(stream))
     _check(rc, "tsu_init")
 
 
@@ -263,22 +329,40 @@ def _problems(sims, nsteps):
     return arr
 
 
-def tsu_batch_workspace(sims, nsteps, tdepth: int = 0, rows: int = 0, kernel: int = 0) -> int:
+def tsu_batch_workspace(sims, nsteps, tdepth: int = 0, rows: int = 0, kernel: int = 0, order: int = 0,
+                        rows_per_problem=None) -> int:
     arr = _problems(sims, nsteps)
-    o = BatchOpts(int(tdepth), int(rows), int(kernel))
+    o = _batch_opts(tdepth, rows, kernel, False, order, rows_per_problem)
     n = C.c_size_t(0)
     _check(load().tsu_batch_workspace(len(sims), arr, C.byref(o), C.byref(n)), "tsu_batch_workspace")
     return int(n.value)
 
 
 def tsu_batch_run(sims, nsteps, ws, ws_bytes: int, tdepth: int = 0, rows: int = 0, kernel: int = 0,
-                  graph: bool = False, stream=None):
+                  graph: bool = False, order: int = 0, rows_per_problem=None, stream=None):
     """Advance every Simulation in ``sims`` by its entry of ``nsteps`` in batched launches (captured
-    into one CUDA graph when ``graph``; that needs a non-default stream)."""
+    into one CUDA graph when ``graph``; that needs a non-default stream).  ``order`` and
+    ``rows_per_problem`` pack the tiles (tsu_batch_opts)."""
     arr = _problems(sims, nsteps)
-    o = BatchOpts(int(tdepth), int(rows), int(kernel), int(bool(graph)))
-    rc = load().tsu_batch_run(len(sims), arr, C.byref(o), _ptr(ws), int(ws_bytes), _stream(stream))
+    o = _batch_opts(tdepth, rows, kernel, graph, order, rows_per_problem)
+    rc = load().tsu_batch_run(len(sims), arr, C.byref(o), _bytes(ws, ws_bytes, "ws"), int(ws_bytes),
+                              _stream(stream))
     _check(rc, "tsu_batch_run")
+
+
+def batch_run(sims, nsteps, tune: bool = False, cache=None, stream=None, **opts):
+    """tsu_batch_run with a workspace of its own.  ``tune``: the configuration the autotuner picks
+    for these problems (timed once on scratch copies, then cached); otherwise ``opts`` (tdepth,
+    rows, kernel, graph, order, rows_per_problem) or the library's defaults.  Returns the options
+    used."""
+    if tune:
+        from . import autotune
+        opts = autotune.tune_batch(sims, cache=cache).batch_opts(sims)
+    dev = sims[0].hx.device
+    wsb = tsu_batch_workspace(sims, nsteps, **{k: v for k, v in opts.items() if k != "graph"})
+    ws = torch.zeros(wsb, dtype=torch.uint8, device=dev)
+    tsu_batch_run(sims, nsteps, ws, wsb, stream=stream, **opts)
+    return opts
 
 
 def tsu_step_n_noalloc(g: Grid, dtype, tau: float, medium: Medium, state: State, nsteps: int, energy=None,
@@ -286,9 +370,14 @@ def tsu_step_n_noalloc(g: Grid, dtype, tau: float, medium: Medium, state: State,
     """tsu_step_n (one step per pass, optional energy) without a caller workspace."""
     lib = load()
     rc = lib.tsu_step_n_noalloc(C.byref(g), dtype_code(dtype), tau, C.byref(medium), C.byref(state), int(nsteps),
-                                _ptr(energy), _stream(stream))
+                                _vec(energy, nsteps, torch.float64, "energy"), _stream(stream))
     if rc != TSU_OK:
         raise TsuError(rc, "tsu_step_n_noalloc", lib.tsu_noalloc_last_error().decode())
+
+
+def tsu_aux_streams() -> int:
+    """Auxiliary recompute streams the library holds (one per device and host thread that ran an adjoint)."""
+    return int(load().tsu_aux_streams())
 
 
 def tsu_ckpt_slots(nsteps: int, ckpt_every: int) -> int:
@@ -305,17 +394,27 @@ def tsu_adjoint_workspace(g: Grid, dtype, form: int, nsteps: int, ckpt_every: in
 def tsu_adjoint(g: Grid, dtype, form: int, tau: float, medium: Medium, nsteps: int, ckpt_every: int, ckpt, u0,
                 rec_idx, dtraces, g_hx, g_hy, g_u0, g_u1, ws, ws_bytes: int, stream=None):
     nrec = 0 if rec_idx is None else int(rec_idx.numel())
-    rc = load().tsu_adjoint(C.byref(g), dtype_code(dtype), int(form), tau, C.byref(medium), int(nsteps),
-                            int(ckpt_every), _ptr(ckpt), _ptr(u0), nrec, _ptr(rec_idx), _ptr(dtraces), _ptr(g_hx),
-                            _ptr(g_hy), _ptr(g_u0), _ptr(g_u1), _ptr(ws), int(ws_bytes), _stream(stream))
+    code = dtype_code(dtype)
+    fields = int(g.ny) * int(g.ld)
+    slots = tsu_ckpt_slots(nsteps, ckpt_every)
+    rc = load().tsu_adjoint(C.byref(g), code, int(form), tau, C.byref(medium), int(nsteps), int(ckpt_every),
+                            _vec(ckpt, 2 * slots * fields, DTYPES[code], "ckpt"), _field(u0, g, code, "u0"), nrec,
+                            _vec(rec_idx, nrec, torch.int64, "rec_idx"),
+                            _vec(dtraces, int(nsteps) * nrec, DTYPES[code], "dtraces"),
+                            _field(g_hx, g, TSU_F64, "g_hx"), _field(g_hy, g, TSU_F64, "g_hy"),
+                            _field(g_u0, g, code, "g_u0"), _field(g_u1, g, code, "g_u1"), _bytes(ws, ws_bytes, "ws"),
+                            int(ws_bytes), _stream(stream))
     _check(rc, "tsu_adjoint")
 
 
 def tsu_observe(g: Grid, dtype, tau: float, medium: Medium, state: State, energy_dev=None, rec_idx=None,
                 trace=None, ws=None, ws_bytes: int = 0, stream=None):
     nrec = 0 if rec_idx is None else int(rec_idx.numel())
-    rc = load().tsu_observe(C.byref(g), dtype_code(dtype), tau, C.byref(medium), C.byref(state), _ptr(energy_dev),
-                            nrec, _ptr(rec_idx), _ptr(trace), _ptr(ws), int(ws_bytes), _stream(stream))
+    code = dtype_code(dtype)
+    rc = load().tsu_observe(C.byref(g), code, tau, C.byref(medium), C.byref(state),
+                            _vec(energy_dev, 1, torch.float64, "energy"), nrec,
+                            _vec(rec_idx, nrec, torch.int64, "rec_idx"), _vec(trace, nrec, DTYPES[code], "trace"),
+                            _bytes(ws, ws_bytes, "ws"), int(ws_bytes), _stream(stream))
     _check(rc, "tsu_observe")
 
 
@@ -336,9 +435,11 @@ def tsu_implicit_factor(g: Grid, dtype, tau: float, sigma: float, medium: Medium
 
 def tsu_implicit_init(g: Grid, dtype, tau: float, sigma: float, medium: Medium, factor, u0, u1, state: State, ws,
                       ws_bytes: int, stream=None):
-    _check(load().tsu_implicit_init(C.byref(g), dtype_code(dtype), float(tau), float(sigma), C.byref(medium),
-                                    _ptr(factor), _ptr(u0), _ptr(u1), C.byref(state), _ptr(ws), int(ws_bytes),
-                                    _stream(stream)), "tsu_implicit_init")
+    code = dtype_code(dtype)
+    _check(load().tsu_implicit_init(C.byref(g), code, float(tau), float(sigma), C.byref(medium),
+                                    _ptr(factor), _field(u0, g, code, "u0"), _field(u1, g, code, "u1"),
+                                    C.byref(state), _bytes(ws, ws_bytes, "ws"), int(ws_bytes), _stream(stream)),
+           "tsu_implicit_init")
 
 
 def tsu_implicit_step_n(g: Grid, dtype, tau: float, sigma: float, medium: Medium, factor, state: State, nsteps: int,
@@ -366,9 +467,9 @@ class ImplicitSimulation:
         hy = empty_field(g, code, device)
         ext_dev = torch.zeros(4, dtype=torch.float64, device=device)
         ext = tsu_make_depth(g, depth, code, hx, hy, ext_dev, sync=True, stream=stream)
+        med = medium(hx, hy, ext)
         if tau is None:
-            tau = cfl * min(g.dx, g.dy) / float(np.sqrt(max(ext[1], ext[3])))
-        med = Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
+            tau = tsu_tau_courant(g, med, cfl)
         fb, wb = tsu_implicit_sizes(g, code)
         factor = torch.empty(fb, dtype=torch.uint8, device=device)
         ws = torch.empty(wb, dtype=torch.uint8, device=device)
@@ -424,10 +525,9 @@ class Simulation:
         hy = empty_field(g, code, device)
         ext_dev = torch.zeros(4, dtype=torch.float64, device=device)
         ext = tsu_make_depth(g, depth, code, hx, hy, ext_dev, sync=True, stream=stream)
-        if tau is None:
-            # the workloads' rule: tau = cfl * dx / sqrt(max h) over both face families
-            tau = cfl * min(g.dx, g.dy) / float(np.sqrt(max(ext[1], ext[3])))
-        med = Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
+        med = medium(hx, hy, ext)
+        if tau is None:  # the workloads' rule (tsu_tau_courant): cfl min(dx, dy) / sqrt(max face depth)
+            tau = tsu_tau_courant(g, med, cfl)
         nb = 4 if nbuf is None else nbuf
         bufs = [empty_field(g, code, device) for _ in range(nb)]
         st = State()
@@ -446,11 +546,15 @@ class Simulation:
              traces: torch.Tensor | None = None, ckpt: torch.Tensor | None = None, ckpt_every: int = 0,
              kernel: int = 0, rows: int = 0, tdepth: int = 0, debug: int = 0, stream=None):
         o = StepOpts()
-        o.energy = _ptr(energy)
-        o.nrec = 0 if rec_idx is None else int(rec_idx.numel())
-        o.rec_idx = _ptr(rec_idx)
-        o.traces = _ptr(traces)
-        o.ckpt = _ptr(ckpt)
+        nrec = 0 if rec_idx is None else int(rec_idx.numel())
+        fdt = DTYPES[self.dtype]
+        o.energy = _vec(energy, nsteps, torch.float64, "energy")
+        o.nrec = nrec
+        o.rec_idx = _vec(rec_idx, nrec, torch.int64, "rec_idx")
+        o.traces = _vec(traces, int(nsteps) * nrec, fdt, "traces")
+        if ckpt is not None and tuple(ckpt.shape[1:]) != (2, self.g.ny, self.g.ld):
+            raise ValueError(f"ckpt must be [slots][2][ny][ld] (got {tuple(ckpt.shape)})")
+        o.ckpt = _vec(ckpt, 0, fdt, "ckpt")
         o.ckpt_every = int(ckpt_every)
         o.ckpt_slots = 0 if ckpt is None else int(ckpt.shape[0])
         o.kernel, o.rows, o.tdepth, o.reserved = int(kernel), int(rows), int(tdepth), int(debug)

@@ -1,7 +1,12 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point include/tsu.h
 declares.  No GPU: no compute call is made here."""
 import ctypes as C
+import os
 import re
+import subprocess
+import sys
+
+import pytest
 
 from paper_2005_11931_gb300 import build, tsu
 
@@ -32,52 +37,30 @@ def test_binding_structs_match_header_layout():
                                                                  "include/tsu.h")).read()
     assert C.sizeof(tsu.Grid) == 32 and C.sizeof(tsu.Sing) == 32
     assert C.sizeof(tsu.State) == 4 * 8 + 4 * 4 + 8
-    for struct, cname in ((tsu.StepOpts, "tsu_step_opts"), (tsu.State, "tsu_state"), (tsu.Medium, "tsu_medium")):
+    for struct, cname in ((tsu.StepOpts, "tsu_step_opts"), (tsu.State, "tsu_state"), (tsu.Medium, "tsu_medium"),
+                          (tsu.BatchOpts, "tsu_batch_opts")):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + ";", hdr).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         fields = re.findall(r"(\w+)(?:\[\d+\])?\s*[;,]", body)
         assert [f[0] for f in struct._fields_] == fields, (cname, fields)
 
 
-def test_implicit_sizes_and_argument_checks_on_the_host():
-    """The implicit comparator's size query, and the argument checks that refuse a call before any
-    device work (no GPU: the pointers are never dereferenced, the stream is the null handle)."""
-    import pytest
+def _run_without_device(name: str):
+    """Run tests/host_checks.py:name in a child process that sees no CUDA device."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    code = f"import sys; sys.path.insert(0, {root!r}); from tests import host_checks; host_checks.{name}()"
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
 
-    g = tsu.grid(131, 77)  # ld 160, transposed rows of roundup(77, 32) = 96
-    fb, wb = tsu.tsu_implicit_sizes(g, tsu.TSU_F32)
-    ldT = 96
-    assert fb == 4 * (77 * 160 + 2 * 131 * ldT)
-    assert wb == 4 * (131 * ldT + max(77 * 160, 131 * ldT))
-    fb64, wb64 = tsu.tsu_implicit_sizes(g, tsu.TSU_F64)
-    assert (fb64, wb64) == (2 * fb, 2 * wb)
-    fake = 1 << 20  # 16-byte aligned, never touched
-    med = tsu.Medium(fake, fake, 2.0, 2.0)
-    with pytest.raises(tsu.TsuError) as e:  # weight below 0
-        tsu.tsu_implicit_factor(g, tsu.TSU_F32, 0.01, -0.1, med, fake, fb, stream=0)
-    assert e.value.code == tsu.TSU_EINVAL
-    with pytest.raises(tsu.TsuError) as e:  # weight below 1/4 beyond its Courant bound
-        tsu.tsu_implicit_factor(g, tsu.TSU_F32, 1.0, 0.0, med, fake, fb, stream=0)
-    assert e.value.code == tsu.TSU_ECFL
-    with pytest.raises(tsu.TsuError) as e:  # factor buffer too small
-        tsu.tsu_implicit_factor(g, tsu.TSU_F32, 1.0, 0.25, med, fake, fb - 4, stream=0)
-    assert e.value.code == tsu.TSU_ENOMEM
-    with pytest.raises(tsu.TsuError) as e:  # misaligned factor
-        tsu.tsu_implicit_factor(g, tsu.TSU_F32, 1.0, 0.25, med, fake + 4, fb, stream=0)
-    assert e.value.code == tsu.TSU_EINVAL
-    st = tsu.State()
-    st.buf[0], st.buf[1], st.nbuf, st.form = fake, fake + 4096, 2, tsu.TSU_FORM_STANDARD
-    with pytest.raises(tsu.TsuError) as e:  # the implicit scheme runs in the increment form
-        tsu.tsu_implicit_init(g, tsu.TSU_F32, 1.0, 0.25, med, fake, fake, None, st, fake, wb, stream=0)
-    assert e.value.code == tsu.TSU_EINVAL
-    st.form = tsu.TSU_FORM_INCREMENT
-    with pytest.raises(tsu.TsuError) as e:  # workspace too small
-        tsu.tsu_implicit_init(g, tsu.TSU_F32, 1.0, 0.25, med, fake, fake, None, st, fake, wb - 16, stream=0)
-    assert e.value.code == tsu.TSU_ENOMEM
-    st.cur, st.aux = 0, 0
-    with pytest.raises(tsu.TsuError) as e:  # roles must differ
-        tsu.tsu_implicit_step_n(g, tsu.TSU_F32, 1.0, 0.25, med, fake, st, 5, fake, wb, stream=0)
-    assert e.value.code == tsu.TSU_EINVAL
-    st.cur, st.aux = 0, 1
-    tsu.tsu_implicit_step_n(g, tsu.TSU_F32, 1.0, 0.25, med, fake, st, 0, fake, wb, stream=0)  # nothing to do
-    assert st.step == 0
+
+@pytest.mark.parametrize("name", ["noalloc_refuses_beyond_its_fixed_scratch",
+                                  "both_stepping_entry_points_refuse_the_same_inputs",
+                                  "init_refuses_a_nonpositive_medium",
+                                  "workload_time_step_rule",
+                                  "implicit_sizes_and_argument_checks"])
+def test_argument_checks_without_a_device(name):
+    """Refusals that happen before any device work, checked with addresses that point nowhere in a
+    process where no GPU is visible (a regression then fails with 'no device', never touches a
+    GPU)."""
+    _run_without_device(name)

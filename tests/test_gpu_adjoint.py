@@ -199,7 +199,7 @@ def test_tsunami_fn_autograd_matches_oracle_adjoint():
     hy = sim.hy.clone().requires_grad_(True)
     u0 = torch.from_numpy(u0n).cuda().requires_grad_(True)
     u1 = torch.zeros_like(u0).requires_grad_(True)
-    cfg = TsunamiConfig(g, sim.tau, S, torch.from_numpy(inputs.flat_index(rec, g.ld)).cuda(), sim.ext[1], sim.ext[3],
+    cfg = TsunamiConfig(g, sim.tau, S, torch.from_numpy(inputs.flat_index(rec, g.ld)).cuda(), tuple(sim.ext),
                         form=tsu.TSU_FORM_STANDARD, ckpt_every=16)
     tr = tsunami_traces(hx, hy, u0, u1, cfg)
     loss = 0.5 * ((tr - obs) ** 2).sum()
@@ -232,7 +232,7 @@ def test_tsunami_fn_autograd_fp32():
     hy = sim.hy.clone().requires_grad_(True)
     u0 = torch.from_numpy(u0n).float().cuda().requires_grad_(True)
     u1 = torch.zeros_like(u0).requires_grad_(True)
-    cfg = TsunamiConfig(g, sim.tau, S, torch.from_numpy(inputs.flat_index(rec, g.ld)).cuda(), sim.ext[1], sim.ext[3],
+    cfg = TsunamiConfig(g, sim.tau, S, torch.from_numpy(inputs.flat_index(rec, g.ld)).cuda(), tuple(sim.ext),
                         form=tsu.TSU_FORM_INCREMENT, ckpt_every=16)
     tr = tsunami_traces(hx, hy, u0, u1, cfg)
     loss = 0.5 * ((tr - obs) ** 2).sum()
@@ -283,3 +283,46 @@ def test_adjoints_from_two_host_threads():
     for k in range(2):
         for name in alone:
             assert np.array_equal(out[k][name], alone[name]), (k, name)
+
+
+def test_adjoint_streams_released_when_threads_exit():
+    """tsu_adjoint creates one auxiliary stream (and its events) per calling host thread; they are
+    destroyed when that thread exits, so adjoints run from many short-lived threads do not
+    accumulate streams."""
+    import threading
+    import time
+
+    nx, ny, S, every = 97, 80, 21, 8
+    rng = np.random.default_rng(41)
+    u0 = inputs.random_field(nx, ny, None, rng)
+    u1 = inputs.random_field(nx, ny, None, rng)
+    rec = receivers(nx, ny)
+    dtr = rng.standard_normal((S, len(rec)))
+    gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f32", tsu.TSU_FORM_INCREMENT, every)
+    base = tsu.tsu_aux_streams()
+    assert base >= 1  # this thread's stream
+    seen, errs = [], []
+
+    def work():
+        try:
+            torch.cuda.set_device(0)
+            gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f32", tsu.TSU_FORM_INCREMENT, every)
+            seen.append(tsu.tsu_aux_streams())
+        except Exception as ex:  # pragma: no cover - reported below
+            errs.append(ex)
+
+    def settled():
+        # Thread.join() returns once the thread's Python part is done; the OS thread runs its C++
+        # thread-local destructors (which release the stream) a moment later
+        deadline = time.monotonic() + 10.0
+        while tsu.tsu_aux_streams() != base and time.monotonic() < deadline:
+            time.sleep(0.005)
+        return tsu.tsu_aux_streams()
+
+    for _ in range(6):
+        t = threading.Thread(target=work)
+        t.start()
+        t.join()
+        assert settled() == base
+    assert not errs, errs
+    assert seen == [base + 1] * 6, (base, seen)  # the running thread's own, while it lives

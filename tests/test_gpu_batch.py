@@ -118,14 +118,12 @@ def test_autotuned_choices_keep_the_results(tmp_path):
         assert x.state.step == y.state.step and torch.equal(x.u, y.u)
     assert autotune.tune_batch(sims, cache=cache) == c  # cached
     steps = [p.steps - 1 for p in probs]
-    wsb = tsu.tsu_batch_workspace(sims, steps, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel)
-    ws = torch.zeros(wsb, dtype=torch.uint8, device="cuda")
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
-        tsu.tsu_batch_run(sims, steps, ws, wsb, tdepth=c.tdepth, rows=c.rows, kernel=c.kernel, graph=c.graph,
-                          stream=side)
+        used = tsu.batch_run(sims, steps, tune=True, cache=cache, stream=side)
     side.synchronize()
+    assert used == c.batch_opts(sims)
     for s, n in zip(ref, steps):
         s.step(n, kernel=1)
     torch.cuda.synchronize()
@@ -140,3 +138,26 @@ def test_autotuned_choices_keep_the_results(tmp_path):
     other.step(37, kernel=1)
     torch.cuda.synchronize()
     assert torch.equal(big.u, other.u)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("scaled", [False, True])
+def test_batch_packing_keeps_the_results(order, scaled):
+    """Every tile-table order, with uniform or size-scaled rows per chunk (uneven step counts, so
+    that the launches cover shrinking prefixes of the table): the same bits as each problem run
+    on its own, one step per pass."""
+    probs = family(steps=60, sizes=(129, 200, 257, 300, 521))
+    rng = np.random.default_rng(5)
+    steps = [int(s) for s in rng.integers(8, 60, size=len(probs))]
+    bat = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    rpp = [max(16, (7 * s.g.ny) // 40) for s in bat] if scaled else None
+    used = tsu.batch_run(bat, steps, rows=48, order=order, rows_per_problem=rpp)
+    assert used["order"] == order
+    seq = make_sims(probs, tsu.TSU_FORM_INCREMENT)
+    for sim, n in zip(seq, steps):
+        sim.step(n, kernel=1)
+    torch.cuda.synchronize()
+    for a, b, n in zip(seq, bat, steps):
+        assert b.state.step == 1 + n
+        assert torch.equal(a.u, b.u), n
+        assert torch.equal(a.v, b.v), n

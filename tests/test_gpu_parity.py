@@ -138,7 +138,7 @@ def test_dalembert_fp32_bit_exact(S, form):
     hy = tsu.empty_field(g, "f32")
     hx[:, : nx - 1] = 1.0
     tau = g.dx
-    med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), 1.0, 0.0)
+    med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), 1.0, 0.0, 1.0, 0.0)
     rng = np.random.default_rng(7)
     u0n = np.zeros((ny, nx))
     u0n[1:-1, 1:-1] = 2.0 * rng.integers(-500, 500, size=(ny - 2, nx - 2))
@@ -283,3 +283,33 @@ def test_argument_errors():
     before = sim.u.clone()
     tsu.tsu_step_n(sim.g, "f32", sim.tau, sim.medium, sim.state, 0)
     assert torch.equal(before, sim.u)
+
+
+def test_init_refuses_a_depth_that_is_not_positive():
+    """A depth that dips below zero (background 0.2 minus a line of amplitude 1 at eps = 0.05, so
+    min h ~ 0.2 - 11.3 < 0) breaks the positivity of Sec. 2: tsu_make_depth reports it when asked
+    for the extrema on the host, and tsu_init refuses a medium built from those extrema with
+    TSU_ENONPOS before it enqueues anything (the state buffers keep their contents)."""
+    n = 129
+    depth = dict(background=0.2, eps=0.05, mollifier=0, sings=[(0, 1, -1.0, 0.5, 0.5)])
+    g = tsu.grid(n)
+    hx, hy = tsu.empty_field(g, "f32"), tsu.empty_field(g, "f32")
+    ext_dev = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(tsu.TsuError) as ei:
+        tsu.tsu_make_depth(g, depth, "f32", hx, hy, ext_dev, sync=True)
+    assert ei.value.code == tsu.TSU_ENONPOS
+    tsu.tsu_make_depth(g, depth, "f32", hx, hy, ext_dev, sync=False)
+    ext = ext_dev.cpu().numpy()
+    assert ext[0] < 0 and ext[2] < 0  # h varies in x, so both face families sample the dip
+    med = tsu.medium(hx, hy, ext)
+    bufs = [torch.full((g.ny, g.ld), 7.0, device="cuda") for _ in range(3)]
+    st = tsu.State()
+    for k in range(3):
+        st.buf[k] = bufs[k].data_ptr()
+    st.nbuf, st.form = 3, tsu.TSU_FORM_INCREMENT
+    u0 = tsu.empty_field(g, "f32")
+    with pytest.raises(tsu.TsuError) as ei:
+        tsu.tsu_init(g, "f32", 1e-4, med, u0, None, st)
+    assert ei.value.code == tsu.TSU_ENONPOS
+    torch.cuda.synchronize()
+    assert all(bool((b == 7.0).all()) for b in bufs)

@@ -36,7 +36,8 @@ def courant_one(axis, n_along, n_across, S, K, form, rows=64, kernel=3):
     else:
         hy[: ny - 1, :nx] = 1.0
         tau = g.dy
-    med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), 1.0 if axis == "x" else 0.0, 1.0 if axis == "y" else 0.0)
+    one = 1.0 if axis == "x" else 0.0  # the other face family is identically zero (a 1D problem)
+    med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), one, 1.0 - one, one, 1.0 - one)
     rng = np.random.default_rng(17)
     u0n = np.zeros((ny, nx))
     u0n[1:-1, 1:-1] = 2.0 * rng.integers(-300, 300, size=(ny - 2, nx - 2))

@@ -2,7 +2,8 @@
 
 It must give what tsu_step_n gives with a caller workspace (same one-step pass, same energy), on
 two calls in a row (the fixed scratch array is shared between calls and keeps the last call's
-contents), and refuse grids its fixed scratch cannot hold.  This file is collected last.
+contents).  Its refusal of grids the fixed scratch cannot hold is checked without a device
+(tests/test_abi.py).  This file is collected last.
 """
 import numpy as np
 import pytest
@@ -34,21 +35,3 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(dtype, form):
         np.testing.assert_allclose(na.bufs[na.state.aux].double().cpu().numpy(),
                                    ref.bufs[ref.state.aux].double().cpu().numpy(), rtol=0, atol=1e-12)
         np.testing.assert_allclose(e_na[a:b].cpu().numpy(), e_ref[a:b].cpu().numpy(), rtol=1e-12, atol=0)
-
-
-def test_noalloc_refuses_grids_beyond_its_fixed_scratch():
-    # FP64 on 32800 x 32800 would need ceil(32800/256) * ceil(32798/32) = 129 * 1025 > 65536 partials;
-    # the call is refused before any device work, so small dummy buffers suffice
-    g = tsu.Grid(32800, 32800, 32800, 1 / 32799, 1 / 32799)
-    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
-    med = tsu.Medium(buf.data_ptr(), buf.data_ptr(), 1.0, 1.0)
-    st = tsu.State()
-    for k in range(2):
-        st.buf[k] = buf.data_ptr()
-    st.buf[1] = buf.data_ptr() + 64
-    st.nbuf, st.form, st.cur, st.aux = 2, tsu.TSU_FORM_STANDARD, 1, 0
-    e = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(tsu.TsuError) as ei:
-        tsu.tsu_step_n_noalloc(g, "f64", 1e-6, med, st, 1, energy=e)
-    assert ei.value.code == tsu.TSU_ENOMEM
-    assert "too large" in str(ei.value)
