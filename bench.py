@@ -36,6 +36,7 @@ TRAFFIC = {
     ("k_leapfrog_wtb", "increment", 8192, 4): 1.665618e9,
 }
 UNIT = "GLUPS"
+ORACLE_SAMPLE_STEPS = 32  # leapfrog steps of each timed oracle sample (depth evaluation included once)
 DEFAULT_KERNEL = 2  # warp-blocked pass, 4 steps per HBM pass
 
 
@@ -156,8 +157,10 @@ class ClockSampler:
 # CPU oracle leg (the reference arm of this build and the cpu_baseline object)
 # -----------------------------------------------------------------------------------------------
 def oracle_sample(n: int, steps_sample: int, threads: int = 0):
-    """Time the FP64 oracle, as it stands, on the workload's full grid for a few steps (on every
-    core of the process, or on `threads` threads)."""
+    """Time the FP64 oracle, as it stands, on the workload's full grid (on every core of the
+    process, or on `threads` threads): the depth evaluation once and `steps_sample` steps (start,
+    leapfrog steps with the energy of every step), extrapolated to the whole workload's
+    5000 steps, so that the depth weighs what it weighs in the GPU bench step."""
     import oracle
     from paper_2005_11931_gb300 import inputs
 
@@ -168,14 +171,17 @@ def oracle_sample(n: int, steps_sample: int, threads: int = 0):
     u0 = p.initial()
     t0 = time.perf_counter()
     hx, hy, ext = oracle.make_depth(g, p.depth)
+    t1 = time.perf_counter()
     tau = inputs.CFL * g.dx / max(ext[1], ext[3]) ** 0.5
     oracle.forward(g, tau, hx, hy, u0, None, steps_sample, want_energy=True)
-    dt = time.perf_counter() - t0
-    lups = (n - 2) ** 2 * steps_sample
-    return dict(value=lups / dt / 1e9, unit=UNIT, cores=threads, kind="oracle",
-                sample=f"FP64 oracle, {n}x{n} point workload, depth + Taylor start + {steps_sample - 1} "
-                       f"leapfrog steps with energy every step ({steps_sample} steps of {(n - 2) ** 2} "
-                       f"interior updates), {threads} OpenMP threads", seconds=dt)
+    t2 = time.perf_counter()
+    S = p.steps
+    est = (t1 - t0) + (t2 - t1) * S / steps_sample
+    return dict(value=(n - 2) ** 2 * S / est / 1e9, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"FP64 oracle, {n}x{n} point workload: depth ({t1 - t0:.2f} s) + Taylor start + "
+                       f"{steps_sample - 1} leapfrog steps with energy every step ({t2 - t1:.2f} s), "
+                       f"extrapolated to the workload's {S} steps; {threads} OpenMP threads",
+                seconds=t2 - t0)
 
 
 def oracle_implicit_sample(sizes=(256, 512, 1024)):
@@ -213,8 +219,9 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    # bounded sample: a few steps of the full grid per bench step
-    steps_sample = 16 if args.n >= 4096 else 64
+    # bounded sample: a few steps of the full grid per bench step (the same sample as the GPU
+    # line's cpu_baseline)
+    steps_sample = ORACLE_SAMPLE_STEPS
     for _ in range(args.warmup):
         oracle_sample(args.n, 2)
     vals, secs = [], 0.0
@@ -267,8 +274,8 @@ def run_gpu(args):
     ws = torch.zeros(ws_bytes, dtype=torch.uint8, device=dev)
     energy = torch.zeros(S, dtype=torch.float64, device=dev)
     ext = tsu.tsu_make_depth(g, p.depth, code, hx, hy, ext_dev, sync=True)
-    tau = inputs.CFL * g.dx / float(np.sqrt(max(ext[1], ext[3])))
-    med = tsu.Medium(hx.data_ptr(), hy.data_ptr(), float(ext[1]), float(ext[3]))
+    med = tsu.medium(hx, hy, ext)
+    tau = tsu.tsu_tau_courant(g, med, inputs.CFL)
     # kernel: --kernel, else the default below; the blocked kernels' steps and the leftover single
     # steps are separate calls so that each is timed on its own
     kernel = args.kernel or DEFAULT_KERNEL
@@ -379,16 +386,17 @@ def run_gpu(args):
         return 0
     extras = {}
     if not args.no_extras and world == 1:
-        extras["adjoint"] = measure_adjoint()
-        extras["batched"] = measure_batched()
-        extras["large"] = measure_large()
+        extras["implicit_table1"] = compact_implicit(measure_implicit())
         extras["paper_case1"] = measure_paper_case1()
-        extras["implicit_table1"] = measure_implicit()
+        extras["large"] = measure_large()
+        extras["single_sizes"] = [measure_single(n) for n in (2048, 4096)]
+        extras["batched"] = measure_batched()
+        extras["adjoint"] = measure_adjoint()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        r = oracle_sample(p.n, 64 if p.n >= 4096 else 256)
+        r = oracle_sample(p.n, ORACLE_SAMPLE_STEPS)
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        r1 = oracle_sample(p.n, 16 if p.n >= 4096 else 64, threads=1)
+        r1 = oracle_sample(p.n, 8, threads=1)
         cpu["single_thread"] = {k: r1[k] for k in ("value", "unit", "cores", "sample")}
         if "implicit_table1" in extras:
             cpu["implicit_table1"] = oracle_implicit_sample()
@@ -413,6 +421,17 @@ def run_gpu(args):
         "energy_drift": drift,
         **extras,
     }
+    if extras:
+        # the other parts of the metric in a few numbers, last in the line
+        a, b = extras["adjoint"], extras["batched"]
+        line["summary"] = {
+            "glups_8192_point": value, "roofline_frac": achieved / peak,
+            **{f"glups_{r['n']}_point": r["glups"] for r in extras["single_sizes"]},
+            "glups_16384_lines": extras["large"]["glups"], "glups_paper_case1_4097": extras["paper_case1"]["glups"],
+            "batched_glups": b["batched_glups"], "batched_tuned_glups": b.get("batched_tuned_glups"),
+            "batched_speedup_vs_sequential_auto": b["speedup_vs_sequential_auto"],
+            "batched_speedup_vs_sequential_one_step": b["speedup_vs_sequential_one_step"],
+            "adjoint_forward_ms": a["forward_ms"], "adjoint_ms": a["adjoint_ms"], "adjoint_ratio": a["ratio"]}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -433,6 +452,42 @@ def _events_ms(fn, reps=1):
     b.record(s)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def measure_single(n, steps=2000, warm=2):
+    """The point workload's problem on an n x n grid (one wave of tiles or less at 2048^2 and
+    4096^2): the bench step's calls (depth, start, steps with the energy of every step), timed
+    whole."""
+    import numpy as np
+    import torch
+
+    from paper_2005_11931_gb300 import inputs, tsu
+
+    p = inputs.point_fp32(n, steps)
+    sim = tsu.Simulation.create(n, p.depth, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+    u0 = torch.from_numpy(p.initial(sim.g.ld, np.float32)).cuda()
+    e = torch.zeros(steps, dtype=torch.float64, device="cuda")
+
+    def run():
+        sim.init(u0)
+        sim.step(steps - 1, energy=e[: steps - 1])
+        sim.observe(energy=e[steps - 1:])
+
+    for _ in range(warm):
+        run()
+    t = _events_ms(run, 3)
+    tsu.tsu_sync_status(sim.ws, sim.ws.numel())
+    return {"n": n, "steps": steps, "ms": t, "glups": (n - 2) ** 2 * steps / t / 1e6}
+
+
+def compact_implicit(r):
+    """Table 1 runs as {dtype: {n: ms}} plus the largest run's bandwidth fraction."""
+    out = {"workload": r["workload"], "ms": {}}
+    for x in r["runs"]:
+        out["ms"].setdefault(x["dtype"], {})[x["n"]] = round(x["ms"], 3)
+    big = [x for x in r["runs"] if x["dtype"] == "f32"][-1]
+    out["f32_largest_frac_of_measured_peak"] = big["frac_of_measured_peak"]
+    return out
 
 
 def measure_adjoint(n=2048, steps=4000, warm=1, reps=2):
@@ -541,6 +596,29 @@ def measure_batched(steps=2000, warm=1, rows=0):
     diff = max(float((sim.u - a).abs().max() / a.abs().max().clamp_min(1e-30)) for (_, sim, _), a in zip(sims, snap))
     t_s0 = _events_ms(lambda: sequential(0))
     tsu.tsu_sync_status(ws, wsb)
+    # the autotuner's packing of the same family (tuned here, with a cache of this run only), timed
+    # the same way on a side stream (a graph launch needs one)
+    import tempfile
+
+    from paper_2005_11931_gb300 import autotune
+
+    with tempfile.TemporaryDirectory() as td:
+        choice = autotune.tune_batch([s for _, s, _ in sims], cache=autotune.Cache(os.path.join(td, "tune.json")))
+    topts = choice.batch_opts([s for _, s, _ in sims])
+    twsb = tsu.tsu_batch_workspace([s for _, s, _ in sims], nsteps,
+                                   **{k: v for k, v in topts.items() if k != "graph"})
+    tws = torch.zeros(twsb, dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+
+    def tuned():
+        init_all()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            tsu.tsu_batch_run([s for _, s, _ in sims], nsteps, tws, twsb, stream=side, **topts)
+        torch.cuda.current_stream().wait_stream(side)
+
+    tuned()
+    t_t = _events_ms(tuned)
     lups = sum((pr.n - 2) ** 2 * pr.steps for pr in probs)
     # algorithmic bytes of the 4-step batched pass: u, v, hx, hy read and u, v written once per
     # 4 steps (1.5 fields per step) for every problem
@@ -550,6 +628,9 @@ def measure_batched(steps=2000, warm=1, rows=0):
                         f"N in {{512..2048}}, {steps} steps each, FP32 increment form",
             "lups": lups, "batched_ms": t_b, "sequential_one_step_ms": t_s1, "sequential_auto_ms": t_s0,
             "init_ms": t_init, "batched_glups": lups / t_b / 1e6, "batched_gbs_algorithmic": gbs,
+            "batched_tuned_ms": t_t, "batched_tuned_glups": lups / t_t / 1e6,
+            "tuned_choice": {k: v for k, v in topts.items() if k != "rows_per_problem"} | {
+                "size_rows": choice.size_rows},
             "batched_frac_of_measured_peak": gbs / peak, "speedup_vs_sequential_one_step": t_s1 / t_b,
             "speedup_vs_sequential_auto": t_s0 / t_b, "max_rel_diff_batched_vs_sequential": diff}
 
