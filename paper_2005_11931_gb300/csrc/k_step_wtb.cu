@@ -171,44 +171,66 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = gb[t] = kZeroP4;
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy), ncx2 = pk(-a.cx, -a.cx), ncy2 = pk(-a.cy, -a.cy);
   // receivers whose node this tile owns (output columns and rows), one per lane; more than 32
-  // in one tile are read back from memory at every record
+  // in one tile are read back from memory at every record.  The list is read four entries per
+  // lane at a time (independent loads); ownership of the tile's rows is decided by comparing the
+  // flat index with y0 ld and y1 ld, and only the few indices inside divide (32-bit).
   int rec_row = -1, rec_col = 0, rec_r = 0, rec_count = 0;
   if constexpr (REC) {
     const int64_t lo = xs + 4, hi = xs + 123;  // this strip's output columns
-    for (int base = 0; base < a.nrec; base += 32) {
-      const int q = base + lane;
-      int64_t j = -1, i = 0;
-      if (tile_ok && q < a.nrec) {
-        const int64_t idx = a.rec_idx[q];
-        if (idx >= 0 && idx < (int64_t)a.ny * a.ld) {
-          j = idx / a.ld;
-          i = idx - j * a.ld;
+    const int64_t row_lo = (int64_t)y0 * a.ld, row_hi = (int64_t)y1 * a.ld;
+    // (receivers on the boundary or outside the grid belong to no tile: k_trace_edges records
+    // them once per call)
+    const bool narrow = row_hi - row_lo < ((int64_t)1 << 32);  // offsets within the rows fit 32 bits
+    for (int base = 0; base < a.nrec; base += 128) {
+      int64_t idx[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int q = base + 32 * c + lane;
+        idx[c] = (tile_ok && q < a.nrec) ? __ldg(&a.rec_idx[q]) : -1;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int q = base + 32 * c + lane;
+        if (base + 32 * c >= a.nrec) break;  // warp-uniform
+        bool mine = false;
+        int j = 0, i = 0;
+        if (idx[c] >= row_lo && idx[c] < row_hi) {  // on one of the tile's rows (all interior)
+          const int64_t off = idx[c] - row_lo;
+          const int64_t dj = narrow ? (int64_t)((uint32_t)off / (uint32_t)a.ld) : off / a.ld;
+          j = y0 + (int)dj;
+          i = (int)(off - dj * a.ld);
+          mine = i >= lo && i <= hi && i >= 1 && i <= a.nx - 2;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, mine);
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const int rj = __shfl_sync(0xffffffffu, j, src), ri = __shfl_sync(0xffffffffu, i, src);
+          if (lane == rec_count) {
+            rec_row = rj;
+            rec_col = ri;
+            rec_r = base + 32 * c + src;
+          }
+          ++rec_count;
         }
       }
-      const bool interior = j >= 1 && j <= a.ny - 2 && i >= 1 && i <= a.nx - 2;
-      const bool mine = interior && j >= y0 && j < y1 && i >= lo && i <= hi;
-      // receivers on the boundary or outside the grid record 0 (the field's value there); the
-      // first tile writes those
-      if (tile_ok && strip == 0 && chunk == 0 && q < a.nrec && !interior)
-        for (int t = 0; t < K; ++t) a.traces[(int64_t)t * a.nrec + q] = 0.f;
-      unsigned m = __ballot_sync(0xffffffffu, mine);
-      while (m) {
-        const int src = __ffs(m) - 1;
-        m &= m - 1;
-        const int rj = __shfl_sync(0xffffffffu, (int)j, src), ri = __shfl_sync(0xffffffffu, (int)i, src);
-        if (lane == rec_count) {
-          rec_row = rj;
-          rec_col = ri;
-          rec_r = base + src;
-        }
-        ++rec_count;
-      }
+    }
+  }
+  // rows the tile's receivers lie on, from rec_rmin to rec_rmax: other rows skip the ballot
+  int rec_rmin = 0, rec_rmax = -1;
+  if constexpr (REC) {
+    if (rec_count > 32) {
+      rec_rmin = y0;
+      rec_rmax = y1 - 1;
+    } else if (rec_count > 0) {
+      rec_rmin = __reduce_min_sync(0xffffffffu, lane < rec_count ? rec_row : 0x7fffffff);
+      rec_rmax = __reduce_max_sync(0xffffffffu, lane < rec_count ? rec_row : -1);
     }
   }
   // trace of level t (u^{n+t}) at row r: the owning lane stores its element
   auto record = [&](int t, int r, const P4& v) {
     if constexpr (REC) {
-      if (rec_count == 0) return;
+      if (r < rec_rmin || r > rec_rmax) return;
       const float2 v01 = upk(v.p[0]), v23 = upk(v.p[1]);
       auto put = [&](int col, int rr) {
         const int64_t e = col - c0;
@@ -430,8 +452,6 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArg
   const bool ok = tile < a.ntiles;
   uint32_t strip = 0, chunk = 0;
   if (ok) wtb_tile_coords(tile, a, strip, chunk);
-  // the unrolled row loop except with receivers (2048^2 forward with traces and checkpoints: 46.0
-  // against 41.7 ms)
   wtb_body<K, FORM, ENERGY, false, REC, !REC>(a, ok, strip, chunk);
 }
 
@@ -455,6 +475,22 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_batched(cons
   const int4 t = ok ? tiles[tile] : make_int4(0, 0, 0, 0);
   const WtbArgs a = probs[t.x];
   wtb_body<K, FORM, false, false>(a, ok, t.y, t.z);
+}
+
+// traces[k nrec + r] = 0 for k < nsteps at every receiver r whose node is on the boundary or
+// outside the grid (Dirichlet: u = 0 there); the warp-blocked pass records only interior nodes.
+__global__ void k_trace_edges(const int32_t nx, const int32_t ny, const int64_t ld, const int64_t* rec_idx,
+                              const int32_t nrec, float* traces, const int64_t nsteps) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
+    const int64_t v = rec_idx[r];
+    bool interior = false;
+    if (v >= 0 && v < (int64_t)ny * ld) {
+      const int64_t j = v / ld, i = v - j * ld;
+      interior = j >= 1 && j <= ny - 2 && i >= 1 && i <= nx - 2;
+    }
+    if (!interior)
+      for (int64_t k = 0; k < nsteps; ++k) traces[k * nrec + r] = 0.f;
+  }
 }
 
 template <int K, int FORM, bool ENERGY, bool REC>
@@ -507,6 +543,14 @@ cudaError_t wtb_launch_batched(const WtbArgs* probs, const int4* tiles, int64_t 
 bool wtb_supported_depth(int k) { return k == 2 || k == 4; }
 
 int wtb_strip_width() { return kWtbOut; }
+
+cudaError_t launch_wtb_trace_edges(const StencilGeom& g, const int64_t* rec_idx, int32_t nrec, void* traces,
+                                   int64_t nsteps, cudaStream_t s) {
+  if (nrec <= 0 || nsteps <= 0) return cudaSuccess;
+  k_trace_edges<<<(unsigned)((nrec + 127) / 128), 128, 0, s>>>(g.nx, g.ny, g.ld, rec_idx, nrec, (float*)traces,
+                                                               nsteps);
+  return cudaGetLastError();
+}
 
 size_t wtb_args_bytes() {
   static_assert(sizeof(WtbArgs) % 16 == 0, "descriptor stride must be a multiple of 16 bytes");

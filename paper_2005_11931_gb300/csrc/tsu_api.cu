@@ -370,6 +370,10 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   const size_t field_bytes = (size_t)g->ny * g->ld * elem_size(dtype);
   cudaStream_t s = (cudaStream_t)stream;
   int64_t k = 0;
+  if (use_wtb && o.traces) {
+    cudaError_t e = tsu::launch_wtb_trace_edges(sg, o.rec_idx, o.nrec, o.traces, nsteps / wdepth * wdepth, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n receiver edges");
+  }
   if (use_wtb) {
     for (; k + wdepth <= nsteps; k += wdepth) {
       const int64_t n = st->step;  // state holds u^n: checkpoint (u^{n-1}, u^n) or (u^n, v^n)

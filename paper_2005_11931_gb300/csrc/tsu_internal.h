@@ -116,6 +116,10 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
                             cudaStream_t s, int32_t nrec = 0, const int64_t* rec_idx = nullptr,
                             void* traces = nullptr);
 int wtb_seg_rows(int64_t ny, int64_t ld);
+// traces of receivers on the boundary or outside the grid (0) for nsteps steps: the warp-blocked
+// pass records interior receivers only
+cudaError_t launch_wtb_trace_edges(const StencilGeom& g, const int64_t* rec_idx, int32_t nrec, void* traces,
+                                   int64_t nsteps, cudaStream_t s);
 // segment variant: u^{n+t} into seg + (t - 1) seg_stride for t = 1 .. k (elements), v^{n+k} into
 // v_out (increment form; unused in the standard form)
 cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
