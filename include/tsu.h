@@ -354,7 +354,11 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
  * tsu_implicit_init: u0 (device [ny][ld]; boundary nodes ignored) and u1 (device or NULL = 0) ->
  *   buf[0] = u^1, buf[1] = v^1 (st->form must be TSU_FORM_INCREMENT, nbuf >= 2; u0 may be
  *   buf[0]); sets cur = 0, aux = 1, step = 1.
- * tsu_implicit_step_n: nsteps steps in place on buf[cur] (u) and buf[aux] (v); step += nsteps.
+ * tsu_implicit_step_n: nsteps steps in place on buf[cur] (u) and buf[aux] (v); step += nsteps.  On a
+ *   stream that can be captured (not the legacy or per-thread default stream, not capturing) a call
+ *   of 4 steps or more runs its launches (two per step) as one CUDA graph; the executable graph is
+ *   kept per host thread and launched again while calls repeat the same arguments (same grid,
+ *   buffers, tau, sigma and nsteps).  The results are the same either way.
  * Every call is asynchronous on `stream`; the workspace (16-byte aligned, >= the size above) is
  * scratch that must not be shared by calls in flight at the same time.
  * Errors: TSU_EINVAL (arguments, form, alignment), TSU_ENONPOS (the medium's extrema), TSU_ECFL (sigma < 1/4 and

@@ -161,3 +161,42 @@ def test_implicit_argument_errors():
     # a very large step is fine at sigma = 1/4
     tsu.tsu_implicit_factor(g, "f64", 10.0, 0.25, sim.medium, sim.factor, fb)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_implicit_graph_launch_gives_the_same_bits(dtype):
+    """On a side stream a multi-step call runs as one CUDA graph (kept and launched again while
+    the calls repeat their arguments); it must give the bits of the launches made one by one on
+    the default stream: 2 + 3 x 10 steps, and the Table 1 run at 256^2 against the oracle."""
+    p = inputs.paper_table1(256)
+    sims, outs = [], []
+    for on_side in (False, True):
+        sim = tsu.ImplicitSimulation.create(p.n, p.depth, dtype=dtype, tau=p.extra["tau"])
+        u0 = torch.from_numpy(p.initial(sim.g.ld)).to(tsu.DTYPES[sim.dtype]).cuda()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        ctx = torch.cuda.stream(side) if on_side else torch.cuda.stream(torch.cuda.current_stream())
+        with ctx:
+            sim.init(u0)
+            sim.step(2)
+            for _ in range(3):  # the same call repeated: the kept graph is launched again
+                sim.step(10)
+        torch.cuda.synchronize()
+        assert sim.state.step == 33
+        outs.append((sim.u.clone(), sim.v.clone()))
+        sims.append(sim)
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    # the whole Table 1 run on the side stream against the oracle
+    sim = sims[1]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        u0 = torch.from_numpy(p.initial(sim.g.ld)).to(tsu.DTYPES[sim.dtype]).cuda()
+        sim.init(u0)
+        sim.step(p.steps - 1)
+    torch.cuda.synchronize()
+    og = oracle.grid(p.n, p.n)
+    hx, hy, _ = oracle.make_depth(og, p.depth)
+    ref, _ = oracle.implicit_forward(og, p.extra["tau"], 0.25, hx, hy, p.initial(), None, p.steps)
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    assert relerr(sim.u[:, : p.n].double().cpu().numpy(), ref) <= tol
