@@ -130,9 +130,10 @@ def pick(candidates, run, timer=wall_timer, repeats: int = 2) -> tuple[Choice, d
     return best, times
 
 
-def tune_batch(sims, rounds: int = 4, cache: Cache | None = None, timer=wall_timer, stream=None) -> Choice:
-    """Best configuration of tsu_batch_run for these simulations (FP32, nbuf 4), timing ``rounds``
-    blocked passes of scratch copies per candidate."""
+def tune_batch(sims, steps: int = 32, cache: Cache | None = None, timer=wall_timer, stream=None) -> Choice:
+    """Best configuration of tsu_batch_run for these simulations (FP32, nbuf 4), timing ``steps``
+    steps of scratch copies per candidate (the same for every candidate, whatever its depth:
+    a multiple of 8 keeps every depth's passes full)."""
     cache = cache if cache is not None else Cache()
     key = signature("batch", sims)
     hit = cache.get(key)
@@ -146,8 +147,7 @@ def tune_batch(sims, rounds: int = 4, cache: Cache | None = None, timer=wall_tim
     def run(c: Choice):
         o = c.batch_opts(scratch)
         if c not in work:
-            k = c.tdepth or (4 if c.kernel == 2 else 8)
-            nsteps = [rounds * k] * len(scratch)
+            nsteps = [steps] * len(scratch)
             wsb = tsu.tsu_batch_workspace(scratch, nsteps, **{key: v for key, v in o.items() if key != "graph"})
             work[c] = (nsteps, torch.zeros(wsb, dtype=torch.uint8, device="cuda"), wsb)
         nsteps, ws, wsb = work[c]

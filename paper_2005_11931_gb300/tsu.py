@@ -265,23 +265,31 @@ def tsu_reduce_workspace() -> int:
     return int(load().tsu_reduce_workspace())
 
 
+def _ws_bytes(ws, ws_bytes):
+    if ws_bytes is not None:
+        return int(ws_bytes)
+    return int(ws.numel() * ws.element_size()) if isinstance(ws, torch.Tensor) else 0
+
+
 def tsu_depth_eps_gradient(g: Grid, depth: dict, g_hx: torch.Tensor, g_hy: torch.Tensor, out: torch.Tensor,
-                           ws: torch.Tensor, stream=None):
+                           ws: torch.Tensor, stream=None, ws_bytes=None):
     """out[0] = dJ/deps = sum g_hx dhx/deps + g_hy dhy/deps (device double)."""
     d = depth_struct(depth)
+    wsb = _ws_bytes(ws, ws_bytes)
     _check(load().tsu_depth_eps_gradient(C.byref(g), C.byref(d), _field(g_hx, g, TSU_F64, "g_hx"),
                                          _field(g_hy, g, TSU_F64, "g_hy"), _vec(out, 1, torch.float64, "out"),
-                                         _bytes(ws, 0, "ws"), int(ws.numel() * ws.element_size()), _stream(stream)),
+                                         _bytes(ws, wsb, "ws"), wsb, _stream(stream)),
            "tsu_depth_eps_gradient")
 
 
 def tsu_diff_norms(g: Grid, dtype, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor, ws: torch.Tensor,
-                   stream=None):
+                   stream=None, ws_bytes=None):
     """out[0] = sum (a - b)^2, out[1] = sum b^2 over nodes i < nx (device double[2])."""
     code = dtype_code(dtype)
+    wsb = _ws_bytes(ws, ws_bytes)
     _check(load().tsu_diff_norms(C.byref(g), code, _field(a, g, code, "a"), _field(b, g, code, "b"),
-                                 _vec(out, 2, torch.float64, "out"), _bytes(ws, 0, "ws"),
-                                 int(ws.numel() * ws.element_size()), _stream(stream)), "tsu_diff_norms")
+                                 _vec(out, 2, torch.float64, "out"), _bytes(ws, wsb, "ws"), wsb, _stream(stream)),
+           "tsu_diff_norms")
 
 
 def tsu_tau_for(g: Grid, hx_max: float, hy_max: float, cfl: float) -> float:

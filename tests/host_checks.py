@@ -142,3 +142,17 @@ def implicit_sizes_and_argument_checks():
     st.cur, st.aux = 0, 1
     tsu.tsu_implicit_step_n(g, tsu.TSU_F32, 1.0, 0.25, med, FAKE, st, 0, FAKE, wb, stream=0)  # nothing to do
     assert st.step == 0
+
+
+def reductions_refuse_misaligned_fields():
+    """tsu_diff_norms and tsu_depth_eps_gradient refuse a field that is not 16-byte aligned, and a
+    workspace that is too small, before any device work."""
+    no_device_visible()
+    g = tsu.grid(100, 60)
+    wsb = tsu.tsu_reduce_workspace()
+    _expect(tsu.TSU_EINVAL, tsu.tsu_diff_norms, g, "f64", FAKE, FAKE + 8, FAKE, FAKE, stream=0, ws_bytes=wsb)
+    _expect(tsu.TSU_ENOMEM, tsu.tsu_diff_norms, g, "f64", FAKE, FAKE, FAKE, FAKE, stream=0, ws_bytes=wsb - 8)
+    depth = dict(background=1.0, eps=0.05, sings=[(0, 1, 1.0, 0.5, 0.5)])
+    _expect(tsu.TSU_EINVAL, tsu.tsu_depth_eps_gradient, g, depth, FAKE + 8, FAKE, FAKE, FAKE, stream=0,
+            ws_bytes=wsb)
+    assert wsb > 256

@@ -45,22 +45,23 @@ def test_binding_structs_match_header_layout():
         assert [f[0] for f in struct._fields_] == fields, (cname, fields)
 
 
-def _run_without_device(name: str):
-    """Run tests/host_checks.py:name in a child process that sees no CUDA device."""
+CHECKS = ["noalloc_refuses_beyond_its_fixed_scratch", "both_stepping_entry_points_refuse_the_same_inputs",
+          "init_refuses_a_nonpositive_medium", "workload_time_step_rule", "implicit_sizes_and_argument_checks",
+          "reductions_refuse_misaligned_fields"]
+
+
+def test_argument_checks_without_a_device():
+    """Refusals that happen before any device work, checked with addresses that point nowhere in a
+    child process where no GPU is visible (a regression then fails with 'no device' and never
+    touches a GPU).  Every function of tests/host_checks.py runs; each reports on its own."""
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
-    code = f"import sys; sys.path.insert(0, {root!r}); from tests import host_checks; host_checks.{name}()"
+    code = ("import sys, traceback; sys.path.insert(0, %r); from tests import host_checks\n"
+            "for name in %r:\n"
+            "    try:\n"
+            "        getattr(host_checks, name)(); print('PASS', name)\n"
+            "    except Exception:\n"
+            "        print('FAIL', name); traceback.print_exc()\n") % (root, CHECKS)
     r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 0, r.stdout + r.stderr
-
-
-@pytest.mark.parametrize("name", ["noalloc_refuses_beyond_its_fixed_scratch",
-                                  "both_stepping_entry_points_refuse_the_same_inputs",
-                                  "init_refuses_a_nonpositive_medium",
-                                  "workload_time_step_rule",
-                                  "implicit_sizes_and_argument_checks"])
-def test_argument_checks_without_a_device(name):
-    """Refusals that happen before any device work, checked with addresses that point nowhere in a
-    process where no GPU is visible (a regression then fails with 'no device', never touches a
-    GPU)."""
-    _run_without_device(name)
+    passed = [l.split()[1] for l in r.stdout.splitlines() if l.startswith("PASS ")]
+    assert r.returncode == 0 and passed == CHECKS, r.stdout + r.stderr

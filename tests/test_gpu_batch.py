@@ -111,7 +111,7 @@ def test_autotuned_choices_keep_the_results(tmp_path):
     probs = family(steps=50)
     sims = make_sims(probs, tsu.TSU_FORM_INCREMENT)
     ref = [s.clone() for s in sims]
-    c = autotune.tune_batch(sims, rounds=2, cache=cache)
+    c = autotune.tune_batch(sims, steps=16, cache=cache)
     assert isinstance(c, autotune.Choice)
     # tuning ran on scratch copies: the states did not move
     for x, y in zip(sims, ref):

@@ -150,6 +150,4 @@ def test_argument_errors_of_the_study_entry_points():
     with pytest.raises(tsu.TsuError) as e:
         tsu.tsu_depth_eps_derivative(g, dict(depth, eps=-1.0), "f64", f, f)
     assert e.value.code == tsu.TSU_EINVAL
-    with pytest.raises(tsu.TsuError) as e:
-        tsu.tsu_diff_norms(g, "f64", f, f.view(-1)[1:], out, ws)  # second field 8 bytes off alignment
-    assert e.value.code == tsu.TSU_EINVAL
+    # a misaligned field is refused too: checked without a device (tests/host_checks.py)
