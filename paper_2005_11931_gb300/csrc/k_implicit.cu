@@ -129,8 +129,11 @@ struct ImpArgs {
   int start;
 };
 
-// x pass: one warp per row j; R rows per CTA.
-template <typename T, int R>
+// x pass: one warp per row j; R rows per CTA.  NS > 0: lines of at most NS segments (small
+// grids) keep each segment's forward results, pivots and faces in registers (the loops unrolled,
+// so the next segment's loads are issued ahead of this one's scan) and the backward substitution
+// reads nothing back from memory; NS = 0: any length, forward results through the scratch line.
+template <typename T, int R, int NS>
 __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
   __shared__ T tile[R][kImpSeg + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -141,11 +144,12 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
   T* line = a.scratch + (row_in ? base : 0);
   // forward: r = B u, then d_k = alpha_k d_{k-1} + beta_k
   T carry = T(0), cu = T(0), ch = T(0);  // d, u and hx at the node before the segment
-  for (int s = 0; s < nseg; ++s) {
+  auto forward = [&](const int s, V4<T>& d, V4<T>& m, V4<T>& hxv) {
     const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
     const bool in = row_in && c0 < a.ld;
-    V4<T> uc = zero4<T>(), uu = zero4<T>(), ud = zero4<T>(), hxv = zero4<T>(), hyu = zero4<T>(),
-          hyd = zero4<T>(), m = zero4<T>();
+    V4<T> uc = zero4<T>(), uu = zero4<T>(), ud = zero4<T>(), hyu = zero4<T>(), hyd = zero4<T>();
+    m = zero4<T>();
+    hxv = zero4<T>();
     T ur_own = T(0);
     if (in) {
       uc = ld4(a.u + base + c0);
@@ -179,22 +183,12 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
       beta.a[e] = unk ? mul_(m.a[e], r) : T(0);
       fl = fr;
     }
-    const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
-    if (in) st4(line + c0, d);
+    d = segment_solve<T, true>(alpha, beta, carry, lane);
     cu = __shfl_sync(0xffffffffu, uc.a[3], 31);
     ch = __shfl_sync(0xffffffffu, hxv.a[3], 31);
-  }
+  };
   // backward: z_k = gamma_k z_{k+1} + d_k, written transposed through the tile
-  carry = T(0);
-  for (int s = nseg - 1; s >= 0; --s) {
-    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
-    const bool in = row_in && c0 < a.ld;
-    V4<T> d = zero4<T>(), m = zero4<T>(), hxv = zero4<T>();
-    if (in) {
-      d = ld4(line + c0);
-      m = ld4(a.mx + base + c0);
-      hxv = ld4(a.hx + base + c0);
-    }
+  auto backward = [&](const int s, const V4<T>& d, const V4<T>& m, const V4<T>& hxv) {
     V4<T> gamma;
 #pragma unroll
     for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(a.sx, hxv.a[e]), m.a[e]) : T(0);
@@ -209,6 +203,34 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
       if (c < a.nx) a.zT[c * a.ldT + j0 + rr] = tile[rr][cc];
     }
     __syncthreads();
+  };
+  if constexpr (NS > 0) {
+    V4<T> dk[NS], mk[NS], hk[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (s < nseg) forward(s, dk[s], mk[s], hk[s]);
+    carry = T(0);
+#pragma unroll
+    for (int s = NS - 1; s >= 0; --s)
+      if (s < nseg) backward(s, dk[s], mk[s], hk[s]);
+  } else {
+    for (int s = 0; s < nseg; ++s) {
+      V4<T> d, m, hxv;
+      forward(s, d, m, hxv);
+      const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+      if (row_in && c0 < a.ld) st4(line + c0, d);
+    }
+    carry = T(0);
+    for (int s = nseg - 1; s >= 0; --s) {
+      const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+      V4<T> d = zero4<T>(), m = zero4<T>(), hxv = zero4<T>();
+      if (row_in && c0 < a.ld) {
+        d = ld4(line + c0);
+        m = ld4(a.mx + base + c0);
+        hxv = ld4(a.hx + base + c0);
+      }
+      backward(s, d, m, hxv);
+    }
   }
 }
 
@@ -216,7 +238,9 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
 // folded into v and u.  Each segment's fields are loaded one segment ahead, and the v and u each
 // thread updates after a segment's scan are read before the scan (4096^2 FP32: 136 against 239
 // us per pass).  The x pass does not load ahead: at 72 registers instead of 48 it ran slower.
-template <typename T, int R>
+// NS > 0: columns of at most NS segments keep the forward results and coefficients in registers,
+// as in the x pass.
+template <typename T, int R, int NS>
 __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
   constexpr int kPer = kImpSeg * R / (R * 32);  // tile entries each thread writes back: 4
   __shared__ T tile[R][kImpSeg + 1];
@@ -236,12 +260,7 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
     }
   };
   T carry = T(0), ck = T(0);  // d and s cy hy at the node before the segment
-  V4<T> z, m, k;
-  load3(0, a.zT + base, z, m, k);
-  for (int s = 0; s < nseg; ++s) {
-    V4<T> nz, nm, nk;
-    load3(s + 1, a.zT + base, nz, nm, nk);
-    const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+  auto forward = [&](const V4<T>& z, const V4<T>& m, const V4<T>& k) {
     T kl = __shfl_up_sync(0xffffffffu, k.a[3], 1);
     if (lane == 0) kl = ck;
     V4<T> alpha, beta;
@@ -253,16 +272,10 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
       beta.a[e] = unk ? mul_(m.a[e], z.a[e]) : T(0);
     }
     const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
-    if (col_in && c0 < a.ldT) st4(line + c0, d);
     ck = __shfl_sync(0xffffffffu, k.a[3], 31);
-    z = nz;
-    m = nm;
-    k = nk;
-  }
-  carry = T(0);
-  V4<T> d;
-  load3(nseg - 1, line, d, m, k);
-  for (int s = nseg - 1; s >= 0; --s) {
+    return d;
+  };
+  auto backward = [&](const int s, const V4<T>& d, const V4<T>& m, const V4<T>& k) {
     // the nodes this thread updates after the scan (row jj, column ii of the tile), read now
     T vq[kPer], uq[kPer], u1q[kPer];
     int64_t oq[kPer];
@@ -282,8 +295,6 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
           vq[p] = a.v[oq[p]];
       }
     }
-    V4<T> nd, nm, nk;
-    load3(s - 1, line, nd, nm, nk);
     V4<T> gamma;
 #pragma unroll
     for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(k.a[e], m.a[e]) : T(0);
@@ -303,9 +314,44 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
       a.uo[oq[p]] = uq[p] + vn;
     }
     __syncthreads();
-    d = nd;
-    m = nm;
-    k = nk;
+  };
+  if constexpr (NS > 0) {
+    V4<T> dk[NS], mk[NS], kk[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (s < nseg) {
+        V4<T> z;
+        load3(s, a.zT + base, z, mk[s], kk[s]);
+        dk[s] = forward(z, mk[s], kk[s]);
+      }
+    carry = T(0);
+#pragma unroll
+    for (int s = NS - 1; s >= 0; --s)
+      if (s < nseg) backward(s, dk[s], mk[s], kk[s]);
+  } else {
+    V4<T> z, m, k;
+    load3(0, a.zT + base, z, m, k);
+    for (int s = 0; s < nseg; ++s) {
+      V4<T> nz, nm, nk;
+      load3(s + 1, a.zT + base, nz, nm, nk);
+      const int64_t c0 = (int64_t)s * kImpSeg + 4 * lane;
+      const V4<T> d = forward(z, m, k);
+      if (col_in && c0 < a.ldT) st4(line + c0, d);
+      z = nz;
+      m = nm;
+      k = nk;
+    }
+    carry = T(0);
+    V4<T> d;
+    load3(nseg - 1, line, d, m, k);
+    for (int s = nseg - 1; s >= 0; --s) {
+      V4<T> nd, nm, nk;
+      load3(s - 1, line, nd, nm, nk);
+      backward(s, d, m, k);
+      d = nd;
+      m = nm;
+      k = nk;
+    }
   }
 }
 
@@ -355,12 +401,12 @@ __global__ void k_imp_prepare(int32_t nx, int32_t ny, int64_t ld, const T* u0, T
   }
 }
 
-template <typename T, int R>
+template <typename T, int R, int NS>
 cudaError_t launch_pair(const ImpArgs<T>& a, cudaStream_t s) {
-  k_imp_x<T, R><<<(unsigned)((a.ny + R - 1) / R), R * 32, 0, s>>>(a);
+  k_imp_x<T, R, NS><<<(unsigned)((a.ny + R - 1) / R), R * 32, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_imp_y<T, R><<<(unsigned)((a.nx + R - 1) / R), R * 32, 0, s>>>(a);
+  k_imp_y<T, R, NS><<<(unsigned)((a.nx + R - 1) / R), R * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -390,10 +436,17 @@ bool imp_capturable(cudaStream_t s) {
   return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusNone;
 }
 
+// segments per line of the longer direction: up to 2 or 4 keep the lines in registers (256^2,
+// 512^2 and smaller), beyond that the generic passes
 template <typename T, int R>
 cudaError_t imp_steps(const ImpArgs<T>& a, int64_t nsteps, cudaStream_t s) {
+  const int nseg = (int)(((a.nx > a.ny ? a.nx : a.ny) - 1 + kImpSeg - 1) / kImpSeg);
   for (int64_t n = 0; n < nsteps; ++n) {
-    const cudaError_t e = launch_pair<T, R>(a, s);
+    cudaError_t e;
+    if constexpr (R == 8)
+      e = nseg <= 2 ? launch_pair<T, R, 2>(a, s) : nseg <= 4 ? launch_pair<T, R, 4>(a, s) : launch_pair<T, R, 0>(a, s);
+    else
+      e = launch_pair<T, R, 0>(a, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
