@@ -300,23 +300,41 @@ cudaError_t launch_init(const StencilGeom& g, int dtype, int form, const void* h
   return cudaGetLastError();
 }
 
-size_t energy_ws_bytes(int64_t ny, int64_t ld) {
-  // one partial per CTA of the register-streaming pass (at most ceil(ld/128) column groups x
-  // (ny - 2) row blocks), or per CTA and level of the temporally blocked pass (at least 16 rows
-  // per chunk, depth <= 8)
+// one partial per CTA of the register-streaming pass (at most ceil(ld/128) column groups x
+// (ny - 2) row blocks), or per CTA and level of the temporally blocked pass (at least 16 rows per
+// chunk, depth <= 8)
+static int64_t energy_slots(int64_t ny, int64_t ld) {
   const int64_t plain = ((ld + 127) / 128) * (ny > 2 ? ny - 2 : 1);
   const int64_t tb = tb_energy_slots(ny, ld, 8, 16);
-  return 256 + (size_t)(plain > tb ? plain : tb) * sizeof(double);
+  return plain > tb ? plain : tb;
+}
+
+// the warp-blocked pass's receiver table: tiles + 1 offsets (at least 16 rows per chunk) and
+// kWtbMaxReceivers entries
+static int64_t rec_table_tiles(int64_t ny, int64_t ld) { return wtb_tiles(ny, ld, 16); }
+static size_t rec_off_bytes(int64_t ny, int64_t ld) { return ((size_t)rec_table_tiles(ny, ld) + 1) * sizeof(int); }
+
+static size_t align16(size_t n) { return (n + 15) / 16 * 16; }
+
+size_t energy_ws_bytes(int64_t ny, int64_t ld) {
+  return 256 + align16((size_t)energy_slots(ny, ld) * sizeof(double)) +
+         align16(rec_off_bytes(ny, ld)) + (size_t)kWtbMaxReceivers * sizeof(int4);
 }
 
 EnergyWs energy_ws_carve(void* ws, size_t bytes, int64_t ny, int64_t ld) {
-  EnergyWs e;
+  EnergyWs e{};
   e.counter = (unsigned int*)ws;
   e.status = (int*)((char*)ws + 4);
   e.partials = (double*)((char*)ws + 256);
-  e.capacity = bytes > 256 ? (int64_t)((bytes - 256) / sizeof(double)) : 0;
-  (void)ny;
-  (void)ld;
+  e.capacity = energy_slots(ny, ld);
+  char* t = (char*)ws + 256 + align16((size_t)e.capacity * sizeof(double));
+  const size_t off = align16(rec_off_bytes(ny, ld));
+  if (bytes >= energy_ws_bytes(ny, ld)) {
+    e.rec_off = (int*)t;
+    e.rec_ent = (int4*)(t + off);
+    e.rec_tiles_cap = rec_table_tiles(ny, ld);
+    e.rec_ent_cap = kWtbMaxReceivers;
+  }
   return e;
 }
 

@@ -78,6 +78,8 @@ struct alignas(16) WtbArgs {
   const int64_t* rec_idx;  // receivers (flat node indices) or nullptr
   float* traces;           // traces[t * nrec + r] = u^{n+t}[rec_idx[r]], t = 0 .. K - 1
   int32_t nrec;
+  const int* rec_off;      // receiver table: tile t's entries rec_ent[rec_off[t] .. rec_off[t + 1])
+  const int4* rec_ent;     // (row, col, receiver, 0)
 };
 
 
@@ -124,7 +126,7 @@ __device__ void wtb_energy(float (&es)[K], float (&ec)[K], const WtbArgs& a) {
 
 template <int K, int FORM, bool ENERGY, bool ALL, bool REC = false, bool UNROLL2 = false>
 __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, const int64_t strip,
-                                         const int64_t chunk) {
+                                         const int64_t chunk, const int64_t tile_id = 0) {
   using Sh = WtbShape<K>;
   extern __shared__ __align__(16) unsigned char wtb_smem[];
   const int lane = threadIdx.x & 31;
@@ -170,49 +172,20 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 #pragma unroll
   for (int t = 0; t < K; ++t) vv[t][0] = vv[t][1] = gb[t] = kZeroP4;
   const f2x cx2 = pk(a.cx, a.cx), cy2 = pk(a.cy, a.cy), ncx2 = pk(-a.cx, -a.cx), ncy2 = pk(-a.cy, -a.cy);
-  // receivers whose node this tile owns (output columns and rows), one per lane; more than 32
-  // in one tile are read back from memory at every record.  The list is read four entries per
-  // lane at a time (independent loads); ownership of the tile's rows is decided by comparing the
-  // flat index with y0 ld and y1 ld, and only the few indices inside divide (32-bit).
-  int rec_row = -1, rec_col = 0, rec_r = 0, rec_count = 0;
+  // receivers whose node this tile owns (output columns and rows), from the call's receiver
+  // table (k_wtb_rec_table): one per lane; more than 32 in one tile are read back from the
+  // table at every record.  Receivers on the boundary or outside the grid belong to no tile:
+  // k_trace_edges records them once per call.
+  int rec_row = -1, rec_col = 0, rec_r = 0, rec_count = 0, rec_lo = 0;
   if constexpr (REC) {
-    const int64_t lo = xs + 4, hi = xs + 123;  // this strip's output columns
-    const int64_t row_lo = (int64_t)y0 * a.ld, row_hi = (int64_t)y1 * a.ld;
-    // (receivers on the boundary or outside the grid belong to no tile: k_trace_edges records
-    // them once per call)
-    const bool narrow = row_hi - row_lo < ((int64_t)1 << 32);  // offsets within the rows fit 32 bits
-    for (int base = 0; base < a.nrec; base += 128) {
-      int64_t idx[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int q = base + 32 * c + lane;
-        idx[c] = (tile_ok && q < a.nrec) ? __ldg(&a.rec_idx[q]) : -1;
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int q = base + 32 * c + lane;
-        if (base + 32 * c >= a.nrec) break;  // warp-uniform
-        bool mine = false;
-        int j = 0, i = 0;
-        if (idx[c] >= row_lo && idx[c] < row_hi) {  // on one of the tile's rows (all interior)
-          const int64_t off = idx[c] - row_lo;
-          const int64_t dj = narrow ? (int64_t)((uint32_t)off / (uint32_t)a.ld) : off / a.ld;
-          j = y0 + (int)dj;
-          i = (int)(off - dj * a.ld);
-          mine = i >= lo && i <= hi && i >= 1 && i <= a.nx - 2;
-        }
-        unsigned m = __ballot_sync(0xffffffffu, mine);
-        while (m) {
-          const int src = __ffs(m) - 1;
-          m &= m - 1;
-          const int rj = __shfl_sync(0xffffffffu, j, src), ri = __shfl_sync(0xffffffffu, i, src);
-          if (lane == rec_count) {
-            rec_row = rj;
-            rec_col = ri;
-            rec_r = base + 32 * c + src;
-          }
-          ++rec_count;
-        }
+    if (tile_ok) {
+      rec_lo = a.rec_off[tile_id];
+      rec_count = a.rec_off[tile_id + 1] - rec_lo;
+      if (lane < rec_count) {
+        const int4 e = a.rec_ent[rec_lo + lane];
+        rec_row = e.x;
+        rec_col = e.y;
+        rec_r = e.z;
       }
     }
   }
@@ -245,9 +218,9 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
           put(__shfl_sync(0xffffffffu, rec_col, src), __shfl_sync(0xffffffffu, rec_r, src));
         }
       } else {
-        for (int q = 0; q < a.nrec; ++q) {
-          const int64_t idx = a.rec_idx[q];
-          if (idx >= 0 && idx < (int64_t)a.ny * a.ld && idx / a.ld == r) put((int)(idx % a.ld), q);
+        for (int q = rec_lo; q < rec_lo + rec_count; ++q) {
+          const int4 e = a.rec_ent[q];
+          if (e.x == r) put(e.y, e.z);
         }
       }
     }
@@ -452,7 +425,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArg
   const bool ok = tile < a.ntiles;
   uint32_t strip = 0, chunk = 0;
   if (ok) wtb_tile_coords(tile, a, strip, chunk);
-  wtb_body<K, FORM, ENERGY, false, REC, !REC>(a, ok, strip, chunk);
+  wtb_body<K, FORM, ENERGY, false, REC, !REC>(a, ok, strip, chunk, tile);
 }
 
 template <int K, int FORM>
@@ -475,6 +448,79 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_batched(cons
   const int4 t = ok ? tiles[tile] : make_int4(0, 0, 0, 0);
   const WtbArgs a = probs[t.x];
   wtb_body<K, FORM, false, false>(a, ok, t.y, t.z);
+}
+
+// The tile index wtb_tile_coords maps to (strip, chunk).
+__device__ __forceinline__ int64_t wtb_tile_index(const int64_t strip, const int64_t chunk, const int64_t ns,
+                                                  const int64_t nchunks) {
+  if (ns < 3) return chunk * ns + strip;
+  if (strip == 0) return 2 * chunk;
+  if (strip == ns - 1) return 2 * chunk + 1;
+  return 2 * nchunks + chunk * (ns - 2) + (strip - 1);
+}
+
+// The receiver table of one call (one CTA): every interior receiver under the tile whose output
+// region (strip s: columns 120 s .. 120 s + 119; chunk c: rows 1 + c rows ..) holds its node.
+// Counts per tile, an inclusive scan (off[t] = the end of tile t), then each entry placed by an
+// atomic decrement (off[t] ends at the start of tile t; off[ntiles] = the total).  The order of a
+// tile's entries is not fixed, and nothing depends on it: each receiver has its own trace slot.
+__global__ void __launch_bounds__(1024) k_wtb_rec_table(const int32_t nx, const int32_t ny, const int64_t ld,
+                                                        const int rows, const int64_t nstrips, const int64_t ntiles,
+                                                        const int64_t* rec_idx, const int32_t nrec, int* off,
+                                                        int4* ent) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t nchunks = ntiles / nstrips;
+  auto tile_of = [&](const int r, int& j, int& i) -> int64_t {
+    const int64_t v = rec_idx[r];
+    if (v < 0 || v >= (int64_t)ny * ld) return -1;
+    const int64_t jj = v / ld, ii = v - jj * ld;
+    if (jj < 1 || jj > ny - 2 || ii < 1 || ii > nx - 2) return -1;
+    j = (int)jj;
+    i = (int)ii;
+    return wtb_tile_index(ii / kWtbOut, (jj - 1) / rows, nstrips, nchunks);
+  };
+  for (int64_t t = threadIdx.x; t <= ntiles; t += blockDim.x) off[t] = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+    int j, i;
+    const int64_t t = tile_of(r, j, i);
+    if (t >= 0) atomicAdd(&off[t], 1);
+  }
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    int v = t < ntiles ? off[t] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += n;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      int x = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += n;
+      }
+      wsum[lane] = x;
+    }
+    __syncthreads();
+    const int incl = v + (w > 0 ? wsum[w - 1] : 0) + carry;
+    if (t < ntiles) off[t] = incl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[ntiles] = carry;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+    int j = 0, i = 0;
+    const int64_t t = tile_of(r, j, i);
+    if (t >= 0) ent[atomicSub(&off[t], 1) - 1] = make_int4(j, i, r, 0);
+  }
 }
 
 // traces[k nrec + r] = 0 for k < nsteps at every receiver r whose node is on the boundary or
@@ -543,6 +589,17 @@ cudaError_t wtb_launch_batched(const WtbArgs* probs, const int4* tiles, int64_t 
 bool wtb_supported_depth(int k) { return k == 2 || k == 4; }
 
 int wtb_strip_width() { return kWtbOut; }
+
+cudaError_t launch_wtb_rec_table(const StencilGeom& g, int rows, const int64_t* rec_idx, int32_t nrec,
+                                 const EnergyWs& ews, cudaStream_t s) {
+  const int64_t nstrips = (g.ld + kWtbOut - 1) / kWtbOut;
+  const int64_t ntiles = nstrips * ((g.ny - 2 + rows - 1) / rows);
+  if (!ews.rec_off || ntiles > ews.rec_tiles_cap || nrec > ews.rec_ent_cap || ntiles >= ((int64_t)1 << 31))
+    return cudaErrorInvalidValue;
+  k_wtb_rec_table<<<1, 1024, 0, s>>>(g.nx, g.ny, g.ld, rows, nstrips, ntiles, rec_idx, nrec, ews.rec_off,
+                                     ews.rec_ent);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_wtb_trace_edges(const StencilGeom& g, const int64_t* rec_idx, int32_t nrec, void* traces,
                                    int64_t nsteps, cudaStream_t s) {
@@ -658,6 +715,9 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
   a.nrec = traces ? nrec : 0;
   a.rec_idx = rec_idx;
   a.traces = (float*)traces;
+  a.rec_off = ews.rec_off;
+  a.rec_ent = ews.rec_ent;
+  if (a.nrec > 0 && !a.rec_off) return cudaErrorInvalidValue;
   if (k == 2) return form == TSU_FORM_STANDARD ? wtb_launch<2, 0>(a, s) : wtb_launch<2, 1>(a, s);
   if (k == 4) return form == TSU_FORM_STANDARD ? wtb_launch<4, 0>(a, s) : wtb_launch<4, 1>(a, s);
   return cudaErrorInvalidValue;

@@ -303,8 +303,6 @@ int tsu_step_workspace(const tsu_grid* g, int dtype, size_t* bytes) {
   return TSU_OK;
 }
 
-// longest receiver list the warp-blocked pass records itself
-constexpr int32_t kWtbMaxReceivers = 2048;
 
 int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, tsu_state* st, int64_t nsteps,
                const tsu_step_opts* opts, void* ws, size_t ws_bytes, void* stream) {
@@ -349,7 +347,7 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   const bool ckpt_aligned = !o.ckpt || (o.ckpt_every % wdepth == 0 && ((st->step - 1) % wdepth + wdepth) % wdepth == 0);
   // receivers: every warp of the blocked pass scans the whole list once per launch, so long lists
   // go one step per pass (whose first CTA gathers them)
-  const bool wtb_possible = blocked_base && ckpt_aligned && (!o.traces || o.nrec <= kWtbMaxReceivers);
+  const bool wtb_possible = blocked_base && ckpt_aligned && (!o.traces || o.nrec <= tsu::kWtbMaxReceivers);
   const bool tb_possible = blocked_base && !o.traces && !o.ckpt;
   if (o.kernel == 2 && !wtb_possible)
     return fail(TSU_EINVAL, "kernel 2 needs FP32, nbuf = 4, a workspace and checkpoints on its launch boundaries");
@@ -371,8 +369,9 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   cudaStream_t s = (cudaStream_t)stream;
   int64_t k = 0;
   if (use_wtb && o.traces) {
-    cudaError_t e = tsu::launch_wtb_trace_edges(sg, o.rec_idx, o.nrec, o.traces, nsteps / wdepth * wdepth, s);
-    if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n receiver edges");
+    cudaError_t e = tsu::launch_wtb_rec_table(sg, wrows, o.rec_idx, o.nrec, ews, s);
+    if (e == cudaSuccess) e = tsu::launch_wtb_trace_edges(sg, o.rec_idx, o.nrec, o.traces, nsteps / wdepth * wdepth, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n receiver table");
   }
   if (use_wtb) {
     for (; k + wdepth <= nsteps; k += wdepth) {

@@ -26,12 +26,22 @@ struct StencilGeom {
 
 // Workspace of the steppers: a ticket counter and a device status word in the first 256 bytes,
 // then per-CTA FP64 energy partials.
+// The same workspace also holds, after the partials, the receiver table of the warp-blocked pass:
+// tile t's entries are rec_ent[rec_off[t] .. rec_off[t + 1]) (int4: row, col, receiver, 0), for
+// at most rec_tiles_cap tiles and rec_ent_cap receivers.
 struct EnergyWs {
   unsigned int* counter;
   int* status;
   double* partials;
   int64_t capacity;  // number of partial slots
+  int* rec_off;
+  int4* rec_ent;
+  int64_t rec_tiles_cap;
+  int32_t rec_ent_cap;
 };
+
+// receivers the warp-blocked pass records itself (longer lists go one step per pass)
+constexpr int32_t kWtbMaxReceivers = 2048;
 
 // Rows per CTA of the one-step passes when the caller does not choose: 32, halved (down to 4)
 // until the grid has at least 4 CTAs per SM (152 SMs), so that small grids still fill the GPU.
@@ -116,6 +126,10 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
                             cudaStream_t s, int32_t nrec = 0, const int64_t* rec_idx = nullptr,
                             void* traces = nullptr);
 int wtb_seg_rows(int64_t ny, int64_t ld);
+// the receiver table of the warp-blocked pass for this grid and rows per chunk (one CTA, into the
+// workspace): every interior receiver under the tile whose output region holds it
+cudaError_t launch_wtb_rec_table(const StencilGeom& g, int rows, const int64_t* rec_idx, int32_t nrec,
+                                 const EnergyWs& ews, cudaStream_t s);
 // traces of receivers on the boundary or outside the grid (0) for nsteps steps: the warp-blocked
 // pass records interior receivers only
 cudaError_t launch_wtb_trace_edges(const StencilGeom& g, const int64_t* rec_idx, int32_t nrec, void* traces,
