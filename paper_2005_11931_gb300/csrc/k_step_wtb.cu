@@ -236,8 +236,11 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   // Iterations whose levels all lie on interior output rows of a strip without boundary columns
   // take the fast path: no masking, no range checks (the edge path handles the rest).
   const bool interior_strip = (xs >= 1) && (xs + 127 <= (int64_t)a.nx - 2);
-  auto iterate = [&](auto edge_tag, const int it) {
+  // RECNOW: the iteration's rows (r_in - K .. r_in) reach the tile's receiver rows; iterations
+  // that do not run a copy of the row code without any receiver test
+  auto iterate = [&](auto edge_tag, auto rec_tag, const int it) {
     constexpr bool EDGE = decltype(edge_tag)::value;
+    constexpr bool RECNOW = REC && decltype(rec_tag)::value;
     const int r_in = r_first + it;
     const unsigned sa = (unsigned)it & (Sh::SA - 1);
     // ---- level 0: the input row
@@ -247,7 +250,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       w[t][1] = w[t][0];
     }
     w[0][0] = lds_p4(slotA(sa, 0));
-    if constexpr (REC) {
+    if constexpr (RECNOW) {
       if (r_in >= y0 && r_in < y1) record(0, r_in, w[0][0]);
     }
     if constexpr (FORM == 1) {
@@ -340,7 +343,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
         es[t - 1] = sum;
       }
       w[t][0] = un;
-      if constexpr (REC) {
+      if constexpr (RECNOW) {
         if (t < K && row_out) record(t, rt, un);
       }
       if constexpr (ALL) {
@@ -367,10 +370,18 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     if (it + kWtbPre < nit) issue(r_in + kWtbPre);
     cp_commit();
     cp_wait<kWtbPre>();  // this thread's copies of row r_in have landed
-    if (interior_strip && r_in - K >= y0 && r_in - 1 < y1)
-      iterate(std::integral_constant<bool, false>(), it);
-    else
-      iterate(std::integral_constant<bool, true>(), it);
+    const bool edge = !(interior_strip && r_in - K >= y0 && r_in - 1 < y1);
+    if (REC && r_in >= rec_rmin && r_in - K <= rec_rmax) {
+      if (edge)
+        iterate(std::integral_constant<bool, true>(), std::integral_constant<bool, true>(), it);
+      else
+        iterate(std::integral_constant<bool, false>(), std::integral_constant<bool, true>(), it);
+    } else {
+      if (edge)
+        iterate(std::integral_constant<bool, true>(), std::integral_constant<bool, false>(), it);
+      else
+        iterate(std::integral_constant<bool, false>(), std::integral_constant<bool, false>(), it);
+    }
   };
   int it = 0;
   if constexpr (UNROLL2) {
