@@ -216,7 +216,9 @@ double tsu_tau_courant(const tsu_grid* g, const tsu_medium* m, double courant);
 int tsu_init(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, const void* u0,
              const void* u1, tsu_state* st, void* stream);
 
-/* Bytes of device workspace tsu_step_n and tsu_observe need (energy partial sums). */
+/* Bytes of device workspace tsu_step_n and tsu_observe need: a status word, the energy partial
+ * sums and, for the warp-blocked pass, a table of each tile's receivers (rebuilt by every call
+ * that records traces). */
 int tsu_step_workspace(const tsu_grid* g, int dtype, size_t* bytes);
 
 /* Advance the state by nsteps leapfrog steps (the hot path; scheme above).

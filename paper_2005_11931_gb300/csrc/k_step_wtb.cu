@@ -75,8 +75,7 @@ struct alignas(16) WtbArgs {
   double escale;
   float* seg;       // segment variant: u^{n+t} at seg + (t - 1) seg_stride, t = 1 .. K - 1
   int64_t seg_stride;
-  const int64_t* rec_idx;  // receivers (flat node indices) or nullptr
-  float* traces;           // traces[t * nrec + r] = u^{n+t}[rec_idx[r]], t = 0 .. K - 1
+  float* traces;           // traces[t * nrec + r] = u^{n+t} at receiver r, t = 0 .. K - 1
   int32_t nrec;
   const int* rec_off;      // receiver table: tile t's entries rec_ent[rec_off[t] .. rec_off[t + 1])
   const int4* rec_ent;     // (row, col, receiver, 0)
@@ -724,7 +723,6 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
   a.seg = nullptr;
   a.seg_stride = 0;
   a.nrec = traces ? nrec : 0;
-  a.rec_idx = rec_idx;
   a.traces = (float*)traces;
   a.rec_off = ews.rec_off;
   a.rec_ent = ews.rec_ent;

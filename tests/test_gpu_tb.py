@@ -198,3 +198,15 @@ def test_long_receiver_lists_go_one_step_per_pass():
     a, tra, cka, _ = _trace_run(0, rec=rec, energy=False)
     b, trb, ckb, _ = _trace_run(1, rec=rec, energy=False)
     assert torch.equal(tra, trb) and torch.equal(cka, ckb) and torch.equal(a.u, b.u)
+
+
+def test_wtb_tile_with_more_than_32_receivers():
+    """A dense 15 x 15 block of receivers (225 in one tile, more than one per lane) and duplicates
+    of some of them: the warp-blocked pass reads them from its receiver table at every record;
+    traces, checkpoints and states equal the one-step passes' bit for bit."""
+    block = [[c, r] for c in range(40, 55) for r in range(60, 75)]
+    rec = np.array(block + block[:20] + [[500, 300], [0, 5]])
+    a, tra, cka, _ = _trace_run(2, rec=rec, energy=True)
+    b, trb, ckb, _ = _trace_run(1, rec=rec, energy=True)
+    assert not (tra == 7.0).any()
+    assert torch.equal(tra, trb) and torch.equal(cka, ckb) and torch.equal(a.u, b.u)
