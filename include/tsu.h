@@ -326,8 +326,8 @@ int tsu_step_n_noalloc(const tsu_grid* g, int dtype, double tau, const tsu_mediu
 const char* tsu_noalloc_last_error(void);
 
 /* Synchronise the stream, then read and clear the device status word in the workspace of
- * tsu_step_n: TSU_OK, or TSU_ETIMEOUT if a bounded device-side wait of a kernel expired (that
- * kernel stopped early; its outputs are invalid). */
+ * tsu_step_n or of the implicit calls: TSU_OK, or TSU_ETIMEOUT if a bounded device-side wait of a
+ * kernel expired (that kernel stopped early; its outputs are invalid). */
 int tsu_sync_status(void* ws, size_t ws_bytes, void* stream);
 
 /* Energy E^{n-1/2} of the current pair (u^{n-1}, u^n) into energy_dev[0] (device double, or NULL)
@@ -349,7 +349,8 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
  *
  * tsu_implicit_sizes: bytes of the factor buffer and of the workspace for this grid and dtype.
  *   Transposed fields have nx rows of ldT = roundup(ny, 32) elements; the factor holds
- *   [ny][ld] + 2 [nx][ldT] elements, the workspace [nx][ldT] + max(ny ld, nx ldT) elements.
+ *   [ny][ld] + 2 [nx][ldT] elements, the workspace a 256-byte header (its int at byte 4 is a
+ *   status word) and [nx][ldT] + max(ny ld, nx ldT) elements.
  * tsu_implicit_factor: the line systems' pivots for (tau, sigma, medium), computed once on the
  *   device into `factor` (caller-owned, 16-byte aligned, factor_bytes >= the size above).  Any
  *   change of tau, sigma or the depth needs a new factor.
@@ -360,9 +361,14 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
  *   stream that can be captured (not the legacy or per-thread default stream, not capturing) a call
  *   of 4 steps or more runs its launches (two per step) as one CUDA graph; the executable graph is
  *   kept per host thread and launched again while calls repeat the same arguments (same grid,
- *   buffers, tau, sigma and nsteps).  The results are the same either way.
- * Every call is asynchronous on `stream`; the workspace (16-byte aligned, >= the size above) is
- * scratch that must not be shared by calls in flight at the same time.
+ *   buffers, tau, sigma and nsteps).  FP32 grids of at most 129 x 129 nodes (256 x 256, ld and
+ *   ldT <= 256) run every step of the call in one launch of a cluster of 8 (16) CTAs that holds the
+ *   fields in shared memory; its hand-overs between CTAs are waited for with a bound (2 s), and
+ *   a wait that runs out ends the launch early with TSU_ETIMEOUT in the status word.  The results
+ *   are the same on every path.
+ * Every call is asynchronous on `stream`; the workspace (16-byte aligned, >= the size above,
+ * zero-filled by the caller before its first use) is scratch that must not be shared by calls in
+ * flight at the same time; tsu_sync_status(ws, ws_bytes, stream) reads and clears its status word.
  * Errors: TSU_EINVAL (arguments, form, alignment), TSU_ENONPOS (the medium's extrema), TSU_ECFL (sigma < 1/4 and
  * tau^2 (hx_max/dx^2 + hy_max/dy^2) (1 - 4 sigma) > 1), TSU_ENOMEM (factor or workspace too
  * small), TSU_ECUDA. */

@@ -22,8 +22,12 @@
 // a shared-memory tile of R rows x 128 columns, and the y pass reads rows of zT, then writes w
 // back to row-major order through the same kind of tile, fused with the update of v and u.
 // Forward results wait for the backward substitution in a global scratch line (mostly L2).
+#include <cooperative_groups.h>
 #include <string.h>
 
+#include <atomic>
+
+#include "mbarrier.cuh"
 #include "stencil_common.cuh"
 
 namespace tsu {
@@ -31,6 +35,8 @@ namespace {
 using namespace dev;
 
 constexpr int kImpSeg = 128;  // nodes per warp segment
+// the workspace starts with a header whose int at byte 4 is the status word (as for tsu_step_n)
+constexpr size_t kImpWsHeader = 256;
 
 template <typename T>
 struct V4 {
@@ -109,6 +115,114 @@ __device__ __forceinline__ V4<T> segment_solve(const V4<T>& c, const V4<T>& d, T
   return out;
 }
 
+// segment_solve over the NS segments of a whole line (segment 0 first when UP, NS - 1 first
+// otherwise), starting from 0.  The segments' warp scans do not depend on one another, so they
+// run interleaved; only the carries pass from segment to segment.  Every result rounds exactly as
+// in NS calls of segment_solve.
+template <typename T, bool UP, int NS>
+__device__ __forceinline__ void line_solve(const V4<T> (&c)[NS], const V4<T> (&d)[NS], V4<T> (&out)[NS],
+                                           const int lane) {
+  T A[NS], B[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A[s] = T(1);
+    B[s] = T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = UP ? q : 3 - q;
+      B[s] = fma_(c[s].a[e], B[s], d[s].a[e]);
+      A[s] = mul_(c[s].a[e], A[s]);
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const T A2 = UP ? __shfl_up_sync(0xffffffffu, A[s], off) : __shfl_down_sync(0xffffffffu, A[s], off);
+      const T B2 = UP ? __shfl_up_sync(0xffffffffu, B[s], off) : __shfl_down_sync(0xffffffffu, B[s], off);
+      if (UP ? lane >= off : lane + off < 32) {
+        B[s] = fma_(A[s], B2, B[s]);
+        A[s] = mul_(A[s], A2);
+      }
+    }
+  }
+  T A1[NS], B1[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A1[s] = UP ? __shfl_up_sync(0xffffffffu, A[s], 1) : __shfl_down_sync(0xffffffffu, A[s], 1);
+    B1[s] = UP ? __shfl_up_sync(0xffffffffu, B[s], 1) : __shfl_down_sync(0xffffffffu, B[s], 1);
+  }
+  const bool first = UP ? lane == 0 : lane == 31;
+  T carry = T(0);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int s = UP ? k : NS - 1 - k;
+    T x = first ? carry : fma_(A1[s], carry, B1[s]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = UP ? q : 3 - q;
+      x = fma_(c[s].a[e], x, d[s].a[e]);
+      out[s].a[e] = x;
+    }
+    if (k + 1 < NS) carry = __shfl_sync(0xffffffffu, x, UP ? 31 : 0);
+  }
+}
+
+// The coefficients of one segment's recurrences, shared by every kernel that solves the lines
+// (so that all of them round alike).  x pass, forward: r = B u in flux form over the lane's four
+// nodes (rows uc, uu = row + 1, ud = row - 1; faces hxv, hyu above and hyd below; pivots m), with
+// the neighbours across the lane's edges (ul, hl: node and face before it; ur: node after it);
+// alpha_k = s cx h_{k-1/2} m_k, beta_k = m_k r_k, both 0 off the unknowns (m = 0 there).
+template <typename T>
+__device__ __forceinline__ void imp_x_coeffs(const T cx, const T cy, const T sx, const V4<T>& uc, const V4<T>& uu,
+                                             const V4<T>& ud, const V4<T>& hxv, const V4<T>& hyu, const V4<T>& hyd,
+                                             const V4<T>& m, const T ul, const T hl, const T ur, V4<T>& alpha,
+                                             V4<T>& beta) {
+  T fl = mul_(hl, sub_(uc.a[0], ul));  // x flux left of the lane's first node
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const T right = e < 3 ? uc.a[e + 1] : ur;
+    const T fr = mul_(hxv.a[e], sub_(right, uc.a[e]));
+    const T fx = sub_(fr, fl);
+    const T fy = sub_(mul_(hyu.a[e], sub_(uu.a[e], uc.a[e])), mul_(hyd.a[e], sub_(uc.a[e], ud.a[e])));
+    const T r = fma_(cx, fx, mul_(cy, fy));
+    const T hprev = e == 0 ? hl : hxv.a[e - 1];
+    const bool unk = m.a[e] != T(0);
+    alpha.a[e] = unk ? mul_(mul_(sx, hprev), m.a[e]) : T(0);
+    beta.a[e] = unk ? mul_(m.a[e], r) : T(0);
+    fl = fr;
+  }
+}
+// x pass, backward: gamma_k = s cx h_{k+1/2} m_k
+template <typename T>
+__device__ __forceinline__ V4<T> imp_x_gamma(const T sx, const V4<T>& m, const V4<T>& hxv) {
+  V4<T> gamma;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(sx, hxv.a[e]), m.a[e]) : T(0);
+  return gamma;
+}
+// y pass, forward: z = the x pass's result along the column, k = s cy hy (kl: the face before the
+// lane's first node)
+template <typename T>
+__device__ __forceinline__ void imp_y_coeffs(const V4<T>& z, const V4<T>& m, const V4<T>& k, const T kl,
+                                             V4<T>& alpha, V4<T>& beta) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const T kprev = e == 0 ? kl : k.a[e - 1];
+    const bool unk = m.a[e] != T(0);
+    alpha.a[e] = unk ? mul_(kprev, m.a[e]) : T(0);
+    beta.a[e] = unk ? mul_(m.a[e], z.a[e]) : T(0);
+  }
+}
+// y pass, backward
+template <typename T>
+__device__ __forceinline__ V4<T> imp_y_gamma(const V4<T>& m, const V4<T>& k) {
+  V4<T> gamma;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(k.a[e], m.a[e]) : T(0);
+  return gamma;
+}
+
 template <typename T>
 struct ImpArgs {
   int32_t nx, ny;
@@ -126,6 +240,7 @@ struct ImpArgs {
   T* v;              // updated in place by the y pass
   T* uo;             // updated in place by the y pass
   const T* u1;       // start only: initial velocity or nullptr
+  int* status;       // status word of the workspace (TSU_ETIMEOUT when a bounded wait ran out)
   int start;
 };
 
@@ -169,30 +284,14 @@ __global__ void __launch_bounds__(R * 32) k_imp_x(const ImpArgs<T> a) {
     }
     if (lane == 31) ur = ur_own;
     V4<T> alpha, beta;
-    T fl = mul_(hl, sub_(uc.a[0], ul));  // x flux left of the lane's first node
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const T right = e < 3 ? uc.a[e + 1] : ur;
-      const T fr = mul_(hxv.a[e], sub_(right, uc.a[e]));
-      const T fx = sub_(fr, fl);
-      const T fy = sub_(mul_(hyu.a[e], sub_(uu.a[e], uc.a[e])), mul_(hyd.a[e], sub_(uc.a[e], ud.a[e])));
-      const T r = fma_(a.cx, fx, mul_(a.cy, fy));
-      const T hprev = e == 0 ? hl : hxv.a[e - 1];
-      const bool unk = m.a[e] != T(0);  // off the unknowns m = 0: the node holds 0
-      alpha.a[e] = unk ? mul_(mul_(a.sx, hprev), m.a[e]) : T(0);
-      beta.a[e] = unk ? mul_(m.a[e], r) : T(0);
-      fl = fr;
-    }
+    imp_x_coeffs(a.cx, a.cy, a.sx, uc, uu, ud, hxv, hyu, hyd, m, ul, hl, ur, alpha, beta);
     d = segment_solve<T, true>(alpha, beta, carry, lane);
     cu = __shfl_sync(0xffffffffu, uc.a[3], 31);
     ch = __shfl_sync(0xffffffffu, hxv.a[3], 31);
   };
   // backward: z_k = gamma_k z_{k+1} + d_k, written transposed through the tile
   auto backward = [&](const int s, const V4<T>& d, const V4<T>& m, const V4<T>& hxv) {
-    V4<T> gamma;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(mul_(a.sx, hxv.a[e]), m.a[e]) : T(0);
-    const V4<T> z = segment_solve<T, false>(gamma, d, carry, lane);
+    const V4<T> z = segment_solve<T, false>(imp_x_gamma(a.sx, m, hxv), d, carry, lane);
 #pragma unroll
     for (int e = 0; e < 4; ++e) tile[w][4 * lane + e] = z.a[e];
     __syncthreads();
@@ -264,13 +363,7 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
     T kl = __shfl_up_sync(0xffffffffu, k.a[3], 1);
     if (lane == 0) kl = ck;
     V4<T> alpha, beta;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const T kprev = e == 0 ? kl : k.a[e - 1];
-      const bool unk = m.a[e] != T(0);
-      alpha.a[e] = unk ? mul_(kprev, m.a[e]) : T(0);
-      beta.a[e] = unk ? mul_(m.a[e], z.a[e]) : T(0);
-    }
+    imp_y_coeffs(z, m, k, kl, alpha, beta);
     const V4<T> d = segment_solve<T, true>(alpha, beta, carry, lane);
     ck = __shfl_sync(0xffffffffu, k.a[3], 31);
     return d;
@@ -295,10 +388,7 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
           vq[p] = a.v[oq[p]];
       }
     }
-    V4<T> gamma;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) gamma.a[e] = m.a[e] != T(0) ? mul_(k.a[e], m.a[e]) : T(0);
-    const V4<T> wv = segment_solve<T, false>(gamma, d, carry, lane);
+    const V4<T> wv = segment_solve<T, false>(imp_y_gamma(m, k), d, carry, lane);
 #pragma unroll
     for (int e = 0; e < 4; ++e) tile[wp][4 * lane + e] = wv.a[e];
     __syncthreads();
@@ -353,6 +443,260 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
       k = nk;
     }
   }
+}
+
+// ---- every step of a small grid in one cluster (FP32, at most 256 x 256 nodes) -------------------
+// The fields of such a grid fit in the shared memory of one cluster of NC = 8 CTAs (lines of at
+// most 129 nodes, one segment) or NC = 16 (at most 256 nodes, two segments).  CTA c owns rows
+// 16 c .. 16 c + 15 (their u, v, hx and x pivots, the faces hy below them) and columns 16 c ..
+// 16 c + 15 (the y pivots and coefficients, and the x pass's result along them), read from memory
+// once, and keeps copies of the two rows next to its edge rows (u, v), updated as their owners
+// update them.  One step: the update v += w, u += v of the own and the copied rows from the
+// previous step's w; the x pass (warp w solves row 16 c + w and stores each result into the CTA
+// owning its column); the y pass (warp w solves column 16 c + w and stores each w into the CTA
+// owning its row and, for edge rows, into the neighbour holding the copy).
+//
+// Every hand-over is an asynchronous store into the receiver's shared memory that completes its
+// bytes on one of the receiver's two barriers (zb and wb received), so there is no cluster-wide
+// barrier and no fence in the loop: a CTA waits only for the bytes it needs, and knows how many
+// from the shape (every CTA's rows and columns lie in the solved segments; a line of NS segments
+// is solved whole, the nodes beyond the grid are zeros and add exact zeros).  The bytes of the
+// next step cannot arrive early: a CTA stores into zb of step n + 1 only after its own wb of
+// step n, which needs every CTA's y pass of step n, i.e. every zb of step n read.
+//
+// The arithmetic is that of k_imp_x / k_imp_y (imp_x_coeffs ... segment_solve), so the states equal
+// those of the two-kernel steps bit for bit; the launches, not memory, had bounded those on small
+// grids (Table 1 run at 256^2: 3.3 us per pass).
+constexpr int kCluLines = 16, kCluLen = 256;
+// The x pass's results for the CTA's 16 columns, zb[j][.] (every row j of the grid), and the y
+// pass's results for its 16 rows, wb[i][.] (every column i): a lane hands over the four values of
+// its four consecutive nodes, which fall in one owner's 16 lines, as one 16-byte store.  The
+// four 16-byte chunks of a line are swizzled by bits 3-4 of the other index (clu_pos), so that
+// a warp reading one line's values across 32 lanes (4 rows apart) meets at most 4-way bank
+// conflicts (rows 20 floats apart).
+constexpr int kCluGroup = 20;
+struct CluSmem {
+  float u[kCluLines][kCluLen], v[kCluLines][kCluLen], hx[kCluLines][kCluLen], mx[kCluLines][kCluLen];
+  float hy[kCluLines + 1][kCluLen];  // rows 16 c - 1 .. 16 c + 15
+  float myT[kCluLines][kCluLen], kyT[kCluLines][kCluLen];
+  float zb[kCluLen][kCluGroup], wb[kCluLen][kCluGroup];
+  // the rows next to the edge rows (0: row 16 c - 1, 1: row 16 c + 16) and their w
+  float uh[2][kCluLen], vh[2][kCluLen], wbh[2][kCluLen];
+  uint64_t full[2];  // zb, wb (with wbh) of the current step received
+};
+constexpr uint64_t kCluWaitNs = 2000000000ull;  // bound of every wait (a step takes microseconds)
+
+// offset of line q (0..15 within the owner) in entry n of zb / wb
+__device__ __forceinline__ int clu_pos(const int n, const int q) {
+  return ((((q >> 2) ^ (n >> 3)) & 3) << 2) | (q & 3);
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs<float> a, const int64_t nsteps) {
+  constexpr int NS = NC / 8;  // segments of kImpSeg nodes per line
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char clu_raw[];
+  CluSmem& sm = *reinterpret_cast<CluSmem*>(clu_raw);
+  const int rank = (int)cl.block_rank();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int j0 = rank * kCluLines, i0 = rank * kCluLines;
+  const int nth = blockDim.x;
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.full[0], 1);
+    mbar_init(&sm.full[1], 1);
+    fence_barrier_init();
+  }
+  // the CTA's part of the grid, zeros beyond the grid
+  for (int q = threadIdx.x; q < kCluLines * kCluLen; q += nth) {
+    const int r = q / kCluLen, c = q - r * kCluLen;
+    const int j = j0 + r, i = i0 + r;
+    const bool row = j < a.ny && c < a.ld;
+    const int64_t o = (int64_t)j * a.ld + c;
+    sm.u[r][c] = row ? a.u[o] : 0.f;
+    sm.v[r][c] = row ? a.v[o] : 0.f;
+    sm.hx[r][c] = row ? a.hx[o] : 0.f;
+    sm.mx[r][c] = row ? a.mx[o] : 0.f;
+    const bool col = i < a.nx && c < a.ldT;
+    const int64_t t = (int64_t)i * a.ldT + c;
+    sm.myT[r][c] = col ? a.myT[t] : 0.f;
+    sm.kyT[r][c] = col ? a.kyT[t] : 0.f;
+  }
+  for (int q = threadIdx.x; q < kCluLen * kCluGroup; q += nth) {
+    (&sm.zb[0][0])[q] = 0.f;
+    (&sm.wb[0][0])[q] = 0.f;
+  }
+  for (int q = threadIdx.x; q < (kCluLines + 1) * kCluLen; q += nth) {
+    const int r = q / kCluLen, c = q - r * kCluLen;
+    const int j = j0 - 1 + r;
+    sm.hy[r][c] = (j >= 0 && j < a.ny && c < a.ld) ? a.hy[(int64_t)j * a.ld + c] : 0.f;
+  }
+  for (int q = threadIdx.x; q < 2 * kCluLen; q += nth) {
+    const int h = q / kCluLen, c = q - h * kCluLen;
+    const int j = h == 0 ? j0 - 1 : j0 + kCluLines;
+    const bool row = j >= 0 && j < a.ny && c < a.ld;
+    sm.uh[h][c] = row ? a.u[(int64_t)j * a.ld + c] : 0.f;
+    sm.vh[h][c] = row ? a.v[(int64_t)j * a.ld + c] : 0.f;
+    sm.wbh[h][c] = 0.f;
+  }
+  cl.sync();  // every CTA's barriers initialised and buffers filled before the first store
+  // bytes received per step: the x pass of each of the NC * 16 rows hands over 16 columns (64 B),
+  // the y pass of each column 16 rows (64 B) and one w per copied row
+  const uint32_t zbytes = NC * kCluLines * 64;
+  const uint32_t wbytes = NC * kCluLines * 64 + ((rank > 0 ? 1 : 0) + (rank + 1 < NC ? 1 : 0)) * NC * kCluLines * 4;
+  const int j = j0 + wp, i = i0 + wp;
+  const bool row_in = j >= 1 && j <= a.ny - 2, col_in = i >= 1 && i <= a.nx - 2;
+  // v += w, u += v on the interior nodes of the own rows and of the two copied rows (the previous
+  // step's y pass left w in wb and wbh).  Thread t takes rows 4 g .. 4 g + 3 of column c (g, c
+  // from t and t + 512): their four w are one 16-byte chunk of wb, read whole (8 lanes a
+  // wavefront), and lanes along c read u, v without bank conflicts; then column t % 256 of copied
+  // row t / 256.
+  auto update = [&]() {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int q = threadIdx.x + k * kCluLines * 32;
+      const int g = q / kCluLen, c = q - g * kCluLen;
+      if (c < 1 || c > a.nx - 2) continue;
+      const V4<float> w = ld4(&sm.wb[c][clu_pos(c, 4 * g)]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 4 * g + e, jj = j0 + r;
+        if (jj >= 1 && jj <= a.ny - 2) {
+          const float vn = sm.v[r][c] + w.a[e];
+          sm.v[r][c] = vn;
+          sm.u[r][c] = sm.u[r][c] + vn;
+        }
+      }
+    }
+    const int h = threadIdx.x / kCluLen, c = threadIdx.x - h * kCluLen;
+    const int jj = h == 0 ? j0 - 1 : j0 + kCluLines;
+    if (jj >= 1 && jj <= a.ny - 2 && c >= 1 && c <= a.nx - 2) {
+      const float vn = sm.vh[h][c] + sm.wbh[h][c];
+      sm.vh[h][c] = vn;
+      sm.uh[h][c] = sm.uh[h][c] + vn;
+    }
+  };
+  bool dead = false;  // a wait ran out: stop and report TSU_ETIMEOUT
+  for (int64_t n = 0; n < nsteps; ++n) {
+    if (n > 0) {
+      if (!dead) dead = !mbar_wait_bounded<true>(&sm.full[1], (uint32_t)((n - 1) & 1), kCluWaitNs);
+      if (!dead) update();
+    }
+    if (threadIdx.x == 0 && !dead) {  // this step's phase of both barriers
+      mbar_expect_tx(&sm.full[0], zbytes);
+      mbar_expect_tx(&sm.full[1], wbytes);
+    }
+    if (__syncthreads_or(dead)) break;
+    // ---- x pass: row j
+    {
+      const float* ur_row = wp + 1 < kCluLines ? sm.u[wp + 1] : sm.uh[1];  // row j + 1
+      const float* ud_row = wp > 0 ? sm.u[wp - 1] : sm.uh[0];             // row j - 1
+      float cu = 0.f, ch = 0.f;
+      V4<float> mk[NS], hk[NS], alpha[NS], beta[NS];
+#pragma unroll
+      for (int sg = 0; sg < NS; ++sg) {
+        const int c0 = sg * kImpSeg + 4 * lane;
+        const bool in = row_in && c0 < a.ld;
+        V4<float> uc = zero4<float>(), uu = zero4<float>(), ud = zero4<float>(), hyu = zero4<float>(),
+                  hyd = zero4<float>();
+        mk[sg] = zero4<float>();
+        hk[sg] = zero4<float>();
+        float ur_own = 0.f;
+        if (in) {
+          uc = ld4(&sm.u[wp][c0]);
+          uu = ld4(ur_row + c0);
+          ud = ld4(ud_row + c0);
+          hk[sg] = ld4(&sm.hx[wp][c0]);
+          hyu = ld4(&sm.hy[wp + 1][c0]);
+          hyd = ld4(&sm.hy[wp][c0]);
+          mk[sg] = ld4(&sm.mx[wp][c0]);
+          if (lane == 31 && c0 + 4 < a.ld) ur_own = sm.u[wp][c0 + 4];
+        }
+        float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1), hl = __shfl_up_sync(0xffffffffu, hk[sg].a[3], 1);
+        float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
+        if (lane == 0) {
+          ul = cu;
+          hl = ch;
+        }
+        if (lane == 31) ur = ur_own;
+        imp_x_coeffs(a.cx, a.cy, a.sx, uc, uu, ud, hk[sg], hyu, hyd, mk[sg], ul, hl, ur, alpha[sg], beta[sg]);
+        cu = __shfl_sync(0xffffffffu, uc.a[3], 31);
+        ch = __shfl_sync(0xffffffffu, hk[sg].a[3], 31);
+      }
+      V4<float> dk[NS], gamma[NS], zk[NS];
+      line_solve<float, true, NS>(alpha, beta, dk, lane);
+#pragma unroll
+      for (int sg = 0; sg < NS; ++sg) gamma[sg] = imp_x_gamma(a.sx, mk[sg], hk[sg]);
+      line_solve<float, false, NS>(gamma, dk, zk, lane);
+#pragma unroll
+      for (int sg = 0; sg < NS; ++sg) {
+        const V4<float>& z = zk[sg];
+        // columns c0 .. c0 + 3 (0 beyond the grid) into their owner's zb row j
+        const int c0 = sg * kImpSeg + 4 * lane, o = c0 / kCluLines;
+        st_async(cluster_addr(&sm.zb[j][clu_pos(j, c0 % kCluLines)], o), z.a[0], z.a[1], z.a[2], z.a[3],
+                 cluster_addr(&sm.full[0], o));
+      }
+    }
+    if (!dead) dead = !mbar_wait_bounded<true>(&sm.full[0], (uint32_t)(n & 1), kCluWaitNs);
+    dead = __any_sync(0xffffffffu, dead);
+    // ---- y pass: column i
+    if (!dead) {
+      float ck = 0.f;
+      V4<float> mk[NS], kk[NS], alpha[NS], beta[NS];
+#pragma unroll
+      for (int sg = 0; sg < NS; ++sg) {
+        const int c0 = sg * kImpSeg + 4 * lane;
+        const bool in = col_in && c0 < a.ldT;
+        V4<float> z = zero4<float>();
+        mk[sg] = zero4<float>();
+        kk[sg] = zero4<float>();
+        if (in) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) z.a[e] = sm.zb[c0 + e][clu_pos(c0 + e, wp)];
+          mk[sg] = ld4(&sm.myT[wp][c0]);
+          kk[sg] = ld4(&sm.kyT[wp][c0]);
+        }
+        float kl = __shfl_up_sync(0xffffffffu, kk[sg].a[3], 1);
+        if (lane == 0) kl = ck;
+        imp_y_coeffs(z, mk[sg], kk[sg], kl, alpha[sg], beta[sg]);
+        ck = __shfl_sync(0xffffffffu, kk[sg].a[3], 31);
+      }
+      V4<float> dk[NS], gamma[NS], wk[NS];
+      line_solve<float, true, NS>(alpha, beta, dk, lane);
+#pragma unroll
+      for (int sg = 0; sg < NS; ++sg) gamma[sg] = imp_y_gamma(mk[sg], kk[sg]);
+      line_solve<float, false, NS>(gamma, dk, wk, lane);
+#pragma unroll
+      for (int sg = 0; sg < NS; ++sg) {
+        const V4<float>& wv = wk[sg];
+        // rows c0 .. c0 + 3 into their owner's wb entry i; the owner's first row is the copied
+        // row below of CTA o - 1, its last row the copied row above of CTA o + 1
+        const int c0 = sg * kImpSeg + 4 * lane;
+        const int o = c0 / kCluLines, q = c0 % kCluLines;
+        st_async(cluster_addr(&sm.wb[i][clu_pos(i, q)], o), wv.a[0], wv.a[1], wv.a[2], wv.a[3],
+                 cluster_addr(&sm.full[1], o));
+        if (q == 0 && o >= 1) st_async(cluster_addr(&sm.wbh[1][i], o - 1), wv.a[0], cluster_addr(&sm.full[1], o - 1));
+        if (q == kCluLines - 4 && o + 1 < NC)
+          st_async(cluster_addr(&sm.wbh[0][i], o + 1), wv.a[3], cluster_addr(&sm.full[1], o + 1));
+      }
+    }
+  }
+  dead = __syncthreads_or(dead);
+  if (!dead && nsteps > 0) {
+    dead = !mbar_wait_bounded<true>(&sm.full[1], (uint32_t)((nsteps - 1) & 1), kCluWaitNs);
+    if (!dead) update();
+  }
+  if (__syncthreads_or(dead) && threadIdx.x == 0) atomicExch(a.status, (int)TSU_ETIMEOUT);
+  for (int q = threadIdx.x; q < kCluLines * kCluLen; q += nth) {
+    const int r = q / kCluLen, c = q - r * kCluLen;
+    const int jj = j0 + r;
+    if (jj < a.ny && c < a.ld) {
+      const int64_t o = (int64_t)jj * a.ld + c;
+      a.uo[o] = sm.u[r][c];
+      a.v[o] = sm.v[r][c];
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still store into its shared memory
 }
 
 // Pivots of the x systems, one thread per row (once per medium and tau): for the unknowns
@@ -496,6 +840,59 @@ cudaError_t imp_steps_graph(const ImpArgs<T>& a, int64_t nsteps, cudaStream_t s)
   return cudaGraphLaunch(c.exec, s);
 }
 
+// Whether this device can place one cluster of k_imp_cluster<NC> (queried once per device and NC:
+// cluster size 16 is non-portable): 0 not asked yet, 1 yes, 2 no.
+std::atomic<int> g_clu_ok[2][64];
+
+// 0: the grid does not fit one cluster; else the cluster size
+int imp_cluster_ctas(const ImpArgs<float>& a) {
+  if (a.ld > kCluLen || a.ldT > kCluLen) return 0;
+  if (a.nx <= 8 * kCluLines + 1 && a.ny <= 8 * kCluLines + 1) return 8;  // node 128 is a boundary node
+  if (a.nx <= 16 * kCluLines && a.ny <= 16 * kCluLines) return 16;
+  return 0;
+}
+
+// Every step of the call in one cluster launch; *ran = false (and nothing launched) when the
+// device cannot place the cluster.
+template <int NC>
+cudaError_t imp_cluster_launch(const ImpArgs<float>& a, int64_t nsteps, cudaStream_t s, bool* ran) {
+  *ran = false;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC);
+  cfg.blockDim = dim3(kCluLines * 32);
+  cfg.dynamicSmemBytes = sizeof(CluSmem);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  std::atomic<int>& flag = g_clu_ok[NC == 16 ? 1 : 0][dev];
+  int ok = flag.load();
+  if (ok == 0) {
+    ok = 2;
+    if ((NC <= 8 ||
+         cudaFuncSetAttribute(k_imp_cluster<NC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) &&
+        cudaFuncSetAttribute(k_imp_cluster<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CluSmem)) ==
+            cudaSuccess) {
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, k_imp_cluster<NC>, &cfg) == cudaSuccess && clusters >= 1) ok = 1;
+    }
+    (void)cudaGetLastError();  // a refused query leaves no error behind
+    flag.store(ok);
+  }
+  if (ok != 1) return cudaSuccess;
+  e = cudaLaunchKernelEx(&cfg, k_imp_cluster<NC>, a, nsteps);
+  if (e == cudaSuccess) *ran = true;
+  return e;
+}
+
 template <typename T>
 cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const void* fac, void* u, void* v,
                     const void* u1, int64_t nsteps, bool start, void* ws, cudaStream_t s) {
@@ -515,7 +912,8 @@ cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const
   a.myT = a.mx + (int64_t)g.ny * g.ld;
   a.kyT = a.myT + (int64_t)g.nx * g.ldT;
   a.u = (const T*)u;
-  a.zT = (T*)ws;
+  a.status = (int*)((char*)ws + 4);
+  a.zT = (T*)((char*)ws + kImpWsHeader);
   a.scratch = a.zT + (int64_t)g.nx * g.ldT;
   a.v = (T*)v;
   a.uo = (T*)u;
@@ -526,6 +924,15 @@ cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const
   const bool wide = sizeof(T) == 4 && g.nx >= 2048 && g.ny >= 2048;
   a.start = start ? 1 : 0;
   const int64_t n = start ? 1 : nsteps;
+  if constexpr (sizeof(T) == 4) {  // small FP32 grids: every step in one cluster
+    const int nc = start ? 0 : imp_cluster_ctas(a);
+    if (nc > 0 && n >= 1) {
+      bool ran = false;
+      const cudaError_t e =
+          nc == 8 ? imp_cluster_launch<8>(a, n, s, &ran) : imp_cluster_launch<16>(a, n, s, &ran);
+      if (e != cudaSuccess || ran) return e;
+    }
+  }
   if (!start && n >= kImpGraphMinSteps && imp_capturable(s))
     return wide ? imp_steps_graph<T, 16>(a, n, s) : imp_steps_graph<T, 8>(a, n, s);
   return wide ? imp_steps<T, 16>(a, n, s) : imp_steps<T, 8>(a, n, s);
@@ -539,9 +946,9 @@ size_t implicit_factor_elems(const tsu_grid& g) {
   return (size_t)g.ny * g.ld + 2 * (size_t)g.nx * implicit_ldT(g.ny);
 }
 
-size_t implicit_ws_elems(const tsu_grid& g) {
+size_t implicit_ws_bytes(const tsu_grid& g, size_t elem) {
   const size_t t = (size_t)g.nx * implicit_ldT(g.ny), r = (size_t)g.ny * g.ld;
-  return t + (t > r ? t : r);
+  return kImpWsHeader + (t + (t > r ? t : r)) * elem;
 }
 
 cudaError_t launch_implicit_factor(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, void* fac,

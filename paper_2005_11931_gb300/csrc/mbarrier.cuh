@@ -1,0 +1,96 @@
+// Shared-memory barriers with transaction counts (mbarrier), the asynchronous copies and stores
+// that complete on them, and the bounded wait every kernel uses on them.
+//
+// A wait never spins without limit: mbar_wait_bounded gives up after a wall-clock limit (and an
+// iteration cap behind it) and returns false, and the caller records TSU_ETIMEOUT in its status
+// word and leaves.
+#pragma once
+#include <stdint.h>
+
+namespace tsu {
+namespace dev {
+
+constexpr long long kSpinCap = 1ll << 30;  // iteration cap behind the wall-clock limit
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// makes the initialised barriers visible to the cluster (other CTAs' asynchronous stores)
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// arrive once and expect `bytes` more of transactions in the current phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1D bulk copy global -> this CTA's shared memory, completing `bytes` on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// CLUSTER = true: acquire at cluster scope (the phase was completed by other CTAs' stores)
+template <bool CLUSTER = false>
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  if constexpr (CLUSTER) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: true when the phase of this parity completed, false after limit_ns of wall-clock
+// time (or kSpinCap polls)
+template <bool CLUSTER = false>
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait<CLUSTER>(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (long long it = 0; it < kSpinCap; ++it) {
+    if (mbar_try_wait<CLUSTER>(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+// Address of `p` (this CTA's shared memory) in the shared memory of CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+// Asynchronous stores into another CTA's shared memory (cluster addresses); each completes its
+// bytes on the barrier `bar` of the receiving CTA (also a cluster address).  No fence: the
+// receiver's wait on that barrier orders them.
+__device__ __forceinline__ void st_async(uint32_t addr, float x, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+               "r"(__float_as_uint(x)), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t addr, float x0, float x1, float x2, float x3, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+               "r"(__float_as_uint(x0)), "r"(__float_as_uint(x1)), "r"(__float_as_uint(x2)),
+               "r"(__float_as_uint(x3)), "r"(bar)
+               : "memory");
+}
+
+}  // namespace dev
+}  // namespace tsu

@@ -1078,7 +1078,7 @@ int tsu_implicit_sizes(const tsu_grid* g, int dtype, size_t* factor_bytes, size_
   TRY(check_dtype(dtype));
   if (!factor_bytes || !ws_bytes) return fail(TSU_EINVAL, "output pointer is NULL");
   *factor_bytes = tsu::implicit_factor_elems(*g) * elem_size(dtype);
-  *ws_bytes = tsu::implicit_ws_elems(*g) * elem_size(dtype);
+  *ws_bytes = tsu::implicit_ws_bytes(*g, elem_size(dtype));
   return TSU_OK;
 }
 
@@ -1104,7 +1104,7 @@ int tsu_implicit_init(const tsu_grid* g, int dtype, double tau, double sigma, co
   if (u1) TRY(check_field(u1, "u1"));
   TRY(check_implicit_state(st, false));
   TRY(check_field(ws, "workspace"));
-  const size_t need = tsu::implicit_ws_elems(*g) * elem_size(dtype);
+  const size_t need = tsu::implicit_ws_bytes(*g, elem_size(dtype));
   if (ws_bytes < need) return fail(TSU_ENOMEM, "workspace needs %zu B (got %zu)", need, ws_bytes);
   const tsu::ImplicitGeom ig = implicit_geom(g, tau, sigma);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1127,7 +1127,7 @@ int tsu_implicit_step_n(const tsu_grid* g, int dtype, double tau, double sigma, 
   if (nsteps < 0) return fail(TSU_EINVAL, "nsteps must be >= 0");
   if (nsteps == 0) return TSU_OK;
   TRY(check_field(ws, "workspace"));
-  const size_t need = tsu::implicit_ws_elems(*g) * elem_size(dtype);
+  const size_t need = tsu::implicit_ws_bytes(*g, elem_size(dtype));
   if (ws_bytes < need) return fail(TSU_ENOMEM, "workspace needs %zu B (got %zu)", need, ws_bytes);
   cudaError_t e = tsu::launch_implicit(implicit_geom(g, tau, sigma), dtype, m->hx, m->hy, factor, st->buf[st->cur],
                                        st->buf[st->aux], nullptr, nsteps, false, ws, (cudaStream_t)stream);

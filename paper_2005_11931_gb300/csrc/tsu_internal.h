@@ -204,7 +204,8 @@ struct ImplicitGeom {
 };
 int64_t implicit_ldT(int32_t ny);
 size_t implicit_factor_elems(const tsu_grid& g);
-size_t implicit_ws_elems(const tsu_grid& g);
+// workspace bytes: a 256-byte header (status word at byte 4), [nx][ldT] + max(ny ld, nx ldT) elements
+size_t implicit_ws_bytes(const tsu_grid& g, size_t elem);
 cudaError_t launch_implicit_factor(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, void* fac,
                                    cudaStream_t s);
 // u <- u0 on interior nodes and 0 elsewhere, v <- 0 (u0 may be u)

@@ -480,7 +480,7 @@ class ImplicitSimulation:
             tau = tsu_tau_courant(g, med, cfl)
         fb, wb = tsu_implicit_sizes(g, code)
         factor = torch.empty(fb, dtype=torch.uint8, device=device)
-        ws = torch.empty(wb, dtype=torch.uint8, device=device)
+        ws = torch.zeros(wb, dtype=torch.uint8, device=device)  # the status word starts at 0
         tsu_implicit_factor(g, code, tau, sigma, med, factor, fb, stream)
         bufs = [empty_field(g, code, device) for _ in range(2)]
         st = State()

@@ -119,9 +119,9 @@ def implicit_sizes_and_argument_checks():
     fb, wb = tsu.tsu_implicit_sizes(g, tsu.TSU_F32)
     ldT = 96
     assert fb == 4 * (77 * 160 + 2 * 131 * ldT)
-    assert wb == 4 * (131 * ldT + max(77 * 160, 131 * ldT))
+    assert wb == 256 + 4 * (131 * ldT + max(77 * 160, 131 * ldT))  # a header with the status word first
     fb64, wb64 = tsu.tsu_implicit_sizes(g, tsu.TSU_F64)
-    assert (fb64, wb64) == (2 * fb, 2 * wb)
+    assert (fb64, wb64) == (2 * fb, 256 + 2 * (wb - 256))
     med = tsu.Medium(FAKE, FAKE, 2.0, 2.0, 1.0, 1.0)
     _expect(tsu.TSU_EINVAL, tsu.tsu_implicit_factor, g, tsu.TSU_F32, 0.01, -0.1, med, FAKE, fb, stream=0)
     _expect(tsu.TSU_ECFL, tsu.tsu_implicit_factor, g, tsu.TSU_F32, 1.0, 0.0, med, FAKE, fb, stream=0)

@@ -200,3 +200,29 @@ def test_implicit_graph_launch_gives_the_same_bits(dtype):
     ref, _ = oracle.implicit_forward(og, p.extra["tau"], 0.25, hx, hy, p.initial(), None, p.steps)
     tol = 1e-12 if dtype == "f64" else 1e-5
     assert relerr(sim.u[:, : p.n].double().cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("nx,ny", [(250, 250), (200, 131), (97, 256), (130, 40), (129, 129), (64, 100), (7, 5)])
+def test_implicit_one_cluster_path_equals_the_two_kernel_steps(nx, ny):
+    """FP32 grids of at most 129 x 129 (256 x 256) nodes run every step of a call in one cluster
+    of 8 (16) CTAs, the fields in shared memory; a row pitch above 256 sends the same grid through
+    the two kernels per step.  The states must agree bit for bit, and with the oracle, and no
+    bounded wait of the cluster may have run out."""
+    depth = DEPTHS["paper_step"]
+    og = oracle.grid(nx, ny)
+    hx, hy, ext = oracle.make_depth(og, depth)
+    tau = 3.0 * min(og.dx, og.dy) / math.sqrt(max(ext[1], ext[3]))
+    u0n = inputs.gaussian_hump(nx, ny, None, 0.4, 0.45, 0.08)
+    out = []
+    for ld in (None, 320):
+        sim = tsu.ImplicitSimulation.create(nx, depth, dtype="f32", ny=ny, tau=tau, ld=ld)
+        u0 = tsu.empty_field(sim.g, "f32")
+        u0[:, :nx] = torch.from_numpy(u0n).float()
+        sim.init(u0)
+        sim.step(7)
+        sim.step(23)
+        tsu.tsu_sync_status(sim.ws, sim.ws.numel())
+        out.append((sim.u[:, :nx].clone(), sim.v[:, :nx].clone()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    ref, _ = oracle.implicit_forward(og, tau, 0.25, hx, hy, u0n, None, 31)
+    assert relerr(out[0][0].double().cpu().numpy(), ref) <= 1e-5
