@@ -448,10 +448,10 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
 // ---- every step of a small grid in one cluster (FP32, at most 256 x 256 nodes) -------------------
 // The fields of such a grid fit in the shared memory of one cluster of NC = 8 CTAs (lines of at
 // most 129 nodes, one segment) or NC = 16 (at most 256 nodes, two segments).  CTA c owns rows
-// 16 c .. 16 c + 15 (their u, v, hx and x pivots, the faces hy below them) and columns 16 c ..
-// 16 c + 15 (the y pivots and coefficients, and the x pass's result along them), read from memory
-// once, and keeps copies of the two rows next to its edge rows (u, v), updated as their owners
-// update them.  One step: the update v += w, u += v of the own and the copied rows from the
+// 16 c .. 16 c + 15 (their u and v in shared memory; faces and x pivots in the registers of the
+// warps solving them) and columns 16 c .. 16 c + 15 (y pivots and coefficients in registers, the
+// x pass's result along them in shared memory), read from memory once, and keeps copies of the
+// two rows next to its edge rows (u, v), updated as their owners update them.  One step: the update v += w, u += v of the own and the copied rows from the
 // previous step's w; the x pass (warp w solves row 16 c + w and stores each result into the CTA
 // owning its column); the y pass (warp w solves column 16 c + w and stores each w into the CTA
 // owning its row and, for edge rows, into the neighbour holding the copy).
@@ -476,9 +476,7 @@ constexpr int kCluLines = 16, kCluLen = 256;
 // conflicts (rows 20 floats apart).
 constexpr int kCluGroup = 20;
 struct CluSmem {
-  float u[kCluLines][kCluLen], v[kCluLines][kCluLen], hx[kCluLines][kCluLen], mx[kCluLines][kCluLen];
-  float hy[kCluLines + 1][kCluLen];  // rows 16 c - 1 .. 16 c + 15
-  float myT[kCluLines][kCluLen], kyT[kCluLines][kCluLen];
+  float u[kCluLines][kCluLen], v[kCluLines][kCluLen];
   float zb[kCluLen][kCluGroup], wb[kCluLen][kCluGroup];
   // the rows next to the edge rows (0: row 16 c - 1, 1: row 16 c + 16) and their w
   float uh[2][kCluLen], vh[2][kCluLen], wbh[2][kCluLen];
@@ -515,21 +513,10 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
     const int64_t o = (int64_t)j * a.ld + c;
     sm.u[r][c] = row ? a.u[o] : 0.f;
     sm.v[r][c] = row ? a.v[o] : 0.f;
-    sm.hx[r][c] = row ? a.hx[o] : 0.f;
-    sm.mx[r][c] = row ? a.mx[o] : 0.f;
-    const bool col = i < a.nx && c < a.ldT;
-    const int64_t t = (int64_t)i * a.ldT + c;
-    sm.myT[r][c] = col ? a.myT[t] : 0.f;
-    sm.kyT[r][c] = col ? a.kyT[t] : 0.f;
   }
   for (int q = threadIdx.x; q < kCluLen * kCluGroup; q += nth) {
     (&sm.zb[0][0])[q] = 0.f;
     (&sm.wb[0][0])[q] = 0.f;
-  }
-  for (int q = threadIdx.x; q < (kCluLines + 1) * kCluLen; q += nth) {
-    const int r = q / kCluLen, c = q - r * kCluLen;
-    const int j = j0 - 1 + r;
-    sm.hy[r][c] = (j >= 0 && j < a.ny && c < a.ld) ? a.hy[(int64_t)j * a.ld + c] : 0.f;
   }
   for (int q = threadIdx.x; q < 2 * kCluLen; q += nth) {
     const int h = q / kCluLen, c = q - h * kCluLen;
@@ -546,6 +533,39 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
   const uint32_t wbytes = NC * kCluLines * 64 + ((rank > 0 ? 1 : 0) + (rank + 1 < NC ? 1 : 0)) * NC * kCluLines * 4;
   const int j = j0 + wp, i = i0 + wp;
   const bool row_in = j >= 1 && j <= a.ny - 2, col_in = i >= 1 && i <= a.nx - 2;
+  // What does not change from step to step stays in registers: the lane's faces and pivots of
+  // row j (x pass; hxl: the face before the lane's first node) and of column i (y pass; kyl
+  // likewise), zeros off the solved lines and beyond the grid.
+  V4<float> hxk[NS], hyu[NS], hyd[NS], mxk[NS], myk[NS], kyk[NS];
+  float hxl[NS], kyl[NS];
+  {
+    float ch = 0.f, ck = 0.f;
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) {
+      const int c0 = sg * kImpSeg + 4 * lane;
+      hxk[sg] = hyu[sg] = hyd[sg] = mxk[sg] = myk[sg] = kyk[sg] = zero4<float>();
+      if (row_in && c0 < a.ld) {
+        const int64_t o = (int64_t)j * a.ld + c0;
+        hxk[sg] = ld4(a.hx + o);
+        hyu[sg] = ld4(a.hy + o);
+        hyd[sg] = ld4(a.hy + o - a.ld);
+        mxk[sg] = ld4(a.mx + o);
+      }
+      if (col_in && c0 < a.ldT) {
+        const int64_t t = (int64_t)i * a.ldT + c0;
+        myk[sg] = ld4(a.myT + t);
+        kyk[sg] = ld4(a.kyT + t);
+      }
+      hxl[sg] = __shfl_up_sync(0xffffffffu, hxk[sg].a[3], 1);
+      kyl[sg] = __shfl_up_sync(0xffffffffu, kyk[sg].a[3], 1);
+      if (lane == 0) {
+        hxl[sg] = ch;
+        kyl[sg] = ck;
+      }
+      ch = __shfl_sync(0xffffffffu, hxk[sg].a[3], 31);
+      ck = __shfl_sync(0xffffffffu, kyk[sg].a[3], 31);
+    }
+  }
   // v += w, u += v on the interior nodes of the own rows and of the two copied rows (the previous
   // step's y pass left w in wb and wbh).  Thread t takes rows 4 g .. 4 g + 3 of column c (g, c
   // from t and t + 512): their four w are one 16-byte chunk of wb, read whole (8 lanes a
@@ -591,42 +611,32 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
     {
       const float* ur_row = wp + 1 < kCluLines ? sm.u[wp + 1] : sm.uh[1];  // row j + 1
       const float* ud_row = wp > 0 ? sm.u[wp - 1] : sm.uh[0];             // row j - 1
-      float cu = 0.f, ch = 0.f;
-      V4<float> mk[NS], hk[NS], alpha[NS], beta[NS];
+      float cu = 0.f;
+      V4<float> alpha[NS], beta[NS];
 #pragma unroll
       for (int sg = 0; sg < NS; ++sg) {
         const int c0 = sg * kImpSeg + 4 * lane;
         const bool in = row_in && c0 < a.ld;
-        V4<float> uc = zero4<float>(), uu = zero4<float>(), ud = zero4<float>(), hyu = zero4<float>(),
-                  hyd = zero4<float>();
-        mk[sg] = zero4<float>();
-        hk[sg] = zero4<float>();
+        V4<float> uc = zero4<float>(), uu = zero4<float>(), ud = zero4<float>();
         float ur_own = 0.f;
         if (in) {
           uc = ld4(&sm.u[wp][c0]);
           uu = ld4(ur_row + c0);
           ud = ld4(ud_row + c0);
-          hk[sg] = ld4(&sm.hx[wp][c0]);
-          hyu = ld4(&sm.hy[wp + 1][c0]);
-          hyd = ld4(&sm.hy[wp][c0]);
-          mk[sg] = ld4(&sm.mx[wp][c0]);
           if (lane == 31 && c0 + 4 < a.ld) ur_own = sm.u[wp][c0 + 4];
         }
-        float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1), hl = __shfl_up_sync(0xffffffffu, hk[sg].a[3], 1);
+        float ul = __shfl_up_sync(0xffffffffu, uc.a[3], 1);
         float ur = __shfl_down_sync(0xffffffffu, uc.a[0], 1);
-        if (lane == 0) {
-          ul = cu;
-          hl = ch;
-        }
+        if (lane == 0) ul = cu;
         if (lane == 31) ur = ur_own;
-        imp_x_coeffs(a.cx, a.cy, a.sx, uc, uu, ud, hk[sg], hyu, hyd, mk[sg], ul, hl, ur, alpha[sg], beta[sg]);
+        imp_x_coeffs(a.cx, a.cy, a.sx, uc, uu, ud, hxk[sg], hyu[sg], hyd[sg], mxk[sg], ul, hxl[sg], ur, alpha[sg],
+                     beta[sg]);
         cu = __shfl_sync(0xffffffffu, uc.a[3], 31);
-        ch = __shfl_sync(0xffffffffu, hk[sg].a[3], 31);
       }
       V4<float> dk[NS], gamma[NS], zk[NS];
       line_solve<float, true, NS>(alpha, beta, dk, lane);
 #pragma unroll
-      for (int sg = 0; sg < NS; ++sg) gamma[sg] = imp_x_gamma(a.sx, mk[sg], hk[sg]);
+      for (int sg = 0; sg < NS; ++sg) gamma[sg] = imp_x_gamma(a.sx, mxk[sg], hxk[sg]);
       line_solve<float, false, NS>(gamma, dk, zk, lane);
 #pragma unroll
       for (int sg = 0; sg < NS; ++sg) {
@@ -641,30 +651,21 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
     dead = __any_sync(0xffffffffu, dead);
     // ---- y pass: column i
     if (!dead) {
-      float ck = 0.f;
-      V4<float> mk[NS], kk[NS], alpha[NS], beta[NS];
+      V4<float> alpha[NS], beta[NS];
 #pragma unroll
       for (int sg = 0; sg < NS; ++sg) {
         const int c0 = sg * kImpSeg + 4 * lane;
-        const bool in = col_in && c0 < a.ldT;
         V4<float> z = zero4<float>();
-        mk[sg] = zero4<float>();
-        kk[sg] = zero4<float>();
-        if (in) {
+        if (col_in && c0 < a.ldT) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) z.a[e] = sm.zb[c0 + e][clu_pos(c0 + e, wp)];
-          mk[sg] = ld4(&sm.myT[wp][c0]);
-          kk[sg] = ld4(&sm.kyT[wp][c0]);
         }
-        float kl = __shfl_up_sync(0xffffffffu, kk[sg].a[3], 1);
-        if (lane == 0) kl = ck;
-        imp_y_coeffs(z, mk[sg], kk[sg], kl, alpha[sg], beta[sg]);
-        ck = __shfl_sync(0xffffffffu, kk[sg].a[3], 31);
+        imp_y_coeffs(z, myk[sg], kyk[sg], kyl[sg], alpha[sg], beta[sg]);
       }
       V4<float> dk[NS], gamma[NS], wk[NS];
       line_solve<float, true, NS>(alpha, beta, dk, lane);
 #pragma unroll
-      for (int sg = 0; sg < NS; ++sg) gamma[sg] = imp_y_gamma(mk[sg], kk[sg]);
+      for (int sg = 0; sg < NS; ++sg) gamma[sg] = imp_y_gamma(myk[sg], kyk[sg]);
       line_solve<float, false, NS>(gamma, dk, wk, lane);
 #pragma unroll
       for (int sg = 0; sg < NS; ++sg) {
