@@ -476,10 +476,12 @@ constexpr int kCluLines = 16, kCluLen = 256;
 // conflicts (rows 20 floats apart).
 constexpr int kCluGroup = 20;
 struct CluSmem {
-  float u[kCluLines][kCluLen], v[kCluLines][kCluLen];
+  float u[kCluLines][kCluLen];
   float zb[kCluLen][kCluGroup], wb[kCluLen][kCluGroup];
-  // the rows next to the edge rows (0: row 16 c - 1, 1: row 16 c + 16) and their w
-  float uh[2][kCluLen], vh[2][kCluLen], wbh[2][kCluLen];
+  // the rows next to the edge rows (h = 0: row 16 c - 1, h = 1: row 16 c + 16); the w of each
+  // comes in the 16-byte chunk of four rows that holds it (as its last row for h = 0, its first
+  // for h = 1)
+  float uh[2][kCluLen], wbh[2][kCluLen][4];
   uint64_t full[2];  // zb, wb (with wbh) of the current step received
 };
 constexpr uint64_t kCluWaitNs = 2000000000ull;  // bound of every wait (a step takes microseconds)
@@ -512,7 +514,6 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
     const bool row = j < a.ny && c < a.ld;
     const int64_t o = (int64_t)j * a.ld + c;
     sm.u[r][c] = row ? a.u[o] : 0.f;
-    sm.v[r][c] = row ? a.v[o] : 0.f;
   }
   for (int q = threadIdx.x; q < kCluLen * kCluGroup; q += nth) {
     (&sm.zb[0][0])[q] = 0.f;
@@ -523,14 +524,13 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
     const int j = h == 0 ? j0 - 1 : j0 + kCluLines;
     const bool row = j >= 0 && j < a.ny && c < a.ld;
     sm.uh[h][c] = row ? a.u[(int64_t)j * a.ld + c] : 0.f;
-    sm.vh[h][c] = row ? a.v[(int64_t)j * a.ld + c] : 0.f;
-    sm.wbh[h][c] = 0.f;
+    sm.wbh[h][c][0] = sm.wbh[h][c][1] = sm.wbh[h][c][2] = sm.wbh[h][c][3] = 0.f;
   }
   cl.sync();  // every CTA's barriers initialised and buffers filled before the first store
   // bytes received per step: the x pass of each of the NC * 16 rows hands over 16 columns (64 B),
-  // the y pass of each column 16 rows (64 B) and one w per copied row
+  // the y pass of each column 16 rows (64 B) and, per copied row, the 16-byte chunk holding its w
   const uint32_t zbytes = NC * kCluLines * 64;
-  const uint32_t wbytes = NC * kCluLines * 64 + ((rank > 0 ? 1 : 0) + (rank + 1 < NC ? 1 : 0)) * NC * kCluLines * 4;
+  const uint32_t wbytes = NC * kCluLines * 64 + ((rank > 0 ? 1 : 0) + (rank + 1 < NC ? 1 : 0)) * NC * kCluLines * 16;
   const int j = j0 + wp, i = i0 + wp;
   const bool row_in = j >= 1 && j <= a.ny - 2, col_in = i >= 1 && i <= a.nx - 2;
   // What does not change from step to step stays in registers: the lane's faces and pivots of
@@ -568,9 +568,23 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
   }
   // v += w, u += v on the interior nodes of the own rows and of the two copied rows (the previous
   // step's y pass left w in wb and wbh).  Thread t takes rows 4 g .. 4 g + 3 of column c (g, c
-  // from t and t + 512): their four w are one 16-byte chunk of wb, read whole (8 lanes a
-  // wavefront), and lanes along c read u, v without bank conflicts; then column t % 256 of copied
-  // row t / 256.
+  // from t and t + 512), whose v it holds in registers: their four w are one 16-byte chunk of wb,
+  // read whole (8 lanes a wavefront), and lanes along c read u without bank conflicts; then column
+  // ch of copied row h (from t), whose v it holds too.
+  const int hh = threadIdx.x / kCluLen, ch = threadIdx.x - hh * kCluLen;
+  const int jh = hh == 0 ? j0 - 1 : j0 + kCluLines;
+  V4<float> vk[2];
+  float vhk = (jh >= 0 && jh < a.ny && ch < a.ld) ? a.v[(int64_t)jh * a.ld + ch] : 0.f;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int q = threadIdx.x + k * kCluLines * 32;
+    const int g = q / kCluLen, c = q - g * kCluLen;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int jj = j0 + 4 * g + e;
+      vk[k].a[e] = (jj < a.ny && c < a.ld) ? a.v[(int64_t)jj * a.ld + c] : 0.f;
+    }
+  }
   auto update = [&]() {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -582,18 +596,14 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
       for (int e = 0; e < 4; ++e) {
         const int r = 4 * g + e, jj = j0 + r;
         if (jj >= 1 && jj <= a.ny - 2) {
-          const float vn = sm.v[r][c] + w.a[e];
-          sm.v[r][c] = vn;
-          sm.u[r][c] = sm.u[r][c] + vn;
+          vk[k].a[e] = vk[k].a[e] + w.a[e];
+          sm.u[r][c] = sm.u[r][c] + vk[k].a[e];
         }
       }
     }
-    const int h = threadIdx.x / kCluLen, c = threadIdx.x - h * kCluLen;
-    const int jj = h == 0 ? j0 - 1 : j0 + kCluLines;
-    if (jj >= 1 && jj <= a.ny - 2 && c >= 1 && c <= a.nx - 2) {
-      const float vn = sm.vh[h][c] + sm.wbh[h][c];
-      sm.vh[h][c] = vn;
-      sm.uh[h][c] = sm.uh[h][c] + vn;
+    if (jh >= 1 && jh <= a.ny - 2 && ch >= 1 && ch <= a.nx - 2) {
+      vhk = vhk + sm.wbh[hh][ch][hh == 0 ? 3 : 0];
+      sm.uh[hh][ch] = sm.uh[hh][ch] + vhk;
     }
   };
   bool dead = false;  // a wait ran out: stop and report TSU_ETIMEOUT
@@ -676,9 +686,10 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
         const int o = c0 / kCluLines, q = c0 % kCluLines;
         st_async(cluster_addr(&sm.wb[i][clu_pos(i, q)], o), wv.a[0], wv.a[1], wv.a[2], wv.a[3],
                  cluster_addr(&sm.full[1], o));
-        if (q == 0 && o >= 1) st_async(cluster_addr(&sm.wbh[1][i], o - 1), wv.a[0], cluster_addr(&sm.full[1], o - 1));
-        if (q == kCluLines - 4 && o + 1 < NC)
-          st_async(cluster_addr(&sm.wbh[0][i], o + 1), wv.a[3], cluster_addr(&sm.full[1], o + 1));
+        const int oh = q == 0 ? o - 1 : q == kCluLines - 4 ? o + 1 : -1;
+        if (oh >= 0 && oh < NC)
+          st_async(cluster_addr(&sm.wbh[q == 0 ? 1 : 0][i][0], oh), wv.a[0], wv.a[1], wv.a[2], wv.a[3],
+                   cluster_addr(&sm.full[1], oh));
       }
     }
   }
@@ -691,10 +702,16 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
   for (int q = threadIdx.x; q < kCluLines * kCluLen; q += nth) {
     const int r = q / kCluLen, c = q - r * kCluLen;
     const int jj = j0 + r;
-    if (jj < a.ny && c < a.ld) {
-      const int64_t o = (int64_t)jj * a.ld + c;
-      a.uo[o] = sm.u[r][c];
-      a.v[o] = sm.v[r][c];
+    if (jj < a.ny && c < a.ld) a.uo[(int64_t)jj * a.ld + c] = sm.u[r][c];
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int q = threadIdx.x + k * kCluLines * 32;
+    const int g = q / kCluLen, c = q - g * kCluLen;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int jj = j0 + 4 * g + e;
+      if (jj < a.ny && c < a.ld) a.v[(int64_t)jj * a.ld + c] = vk[k].a[e];
     }
   }
   cl.sync();  // no CTA leaves while another may still store into its shared memory
