@@ -362,8 +362,8 @@ int tsu_observe(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, c
  *   of 4 steps or more runs its launches (two per step) as one CUDA graph; the executable graph is
  *   kept per host thread and launched again while calls repeat the same arguments (same grid,
  *   buffers, tau, sigma and nsteps).  FP32 grids of at most 129 x 129 nodes (256 x 256, ld and
- *   ldT <= 256) run every step of the call in one launch of a cluster of 8 (16) CTAs that holds the
- *   fields in shared memory; its hand-overs between CTAs are waited for with a bound (2 s), and
+ *   ldT <= 256) run every step of the call, and the start of tsu_implicit_init, in one launch of a
+ *   cluster of 8 (16) CTAs that holds the fields in shared memory; its hand-overs between CTAs are waited for with a bound (2 s), and
  *   a wait that runs out ends the launch early with TSU_ETIMEOUT in the status word.  The results
  *   are the same on every path.
  * Every call is asynchronous on `stream`; the workspace (16-byte aligned, >= the size above,

@@ -507,13 +507,17 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
     mbar_init(&sm.full[1], 1);
     fence_barrier_init();
   }
-  // the CTA's part of the grid, zeros beyond the grid
+  // the CTA's part of the grid, zeros beyond the grid; a start call (a.start) reads u^0 = u0 on
+  // the interior nodes and 0 on the boundary, with v^0 = 0
+  const bool first = a.start != 0;
+  auto u_at = [&](const int jj, const int c) -> float {
+    const bool take = jj >= 0 && jj < a.ny && c < a.ld &&
+                      (!first || (jj >= 1 && jj <= a.ny - 2 && c >= 1 && c <= a.nx - 2));
+    return take ? a.u[(int64_t)jj * a.ld + c] : 0.f;
+  };
   for (int q = threadIdx.x; q < kCluLines * kCluLen; q += nth) {
     const int r = q / kCluLen, c = q - r * kCluLen;
-    const int j = j0 + r, i = i0 + r;
-    const bool row = j < a.ny && c < a.ld;
-    const int64_t o = (int64_t)j * a.ld + c;
-    sm.u[r][c] = row ? a.u[o] : 0.f;
+    sm.u[r][c] = u_at(j0 + r, c);
   }
   for (int q = threadIdx.x; q < kCluLen * kCluGroup; q += nth) {
     (&sm.zb[0][0])[q] = 0.f;
@@ -522,8 +526,7 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
   for (int q = threadIdx.x; q < 2 * kCluLen; q += nth) {
     const int h = q / kCluLen, c = q - h * kCluLen;
     const int j = h == 0 ? j0 - 1 : j0 + kCluLines;
-    const bool row = j >= 0 && j < a.ny && c < a.ld;
-    sm.uh[h][c] = row ? a.u[(int64_t)j * a.ld + c] : 0.f;
+    sm.uh[h][c] = u_at(j, c);
     sm.wbh[h][c][0] = sm.wbh[h][c][1] = sm.wbh[h][c][2] = sm.wbh[h][c][3] = 0.f;
   }
   cl.sync();  // every CTA's barriers initialised and buffers filled before the first store
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
   const int hh = threadIdx.x / kCluLen, ch = threadIdx.x - hh * kCluLen;
   const int jh = hh == 0 ? j0 - 1 : j0 + kCluLines;
   V4<float> vk[2];
-  float vhk = (jh >= 0 && jh < a.ny && ch < a.ld) ? a.v[(int64_t)jh * a.ld + ch] : 0.f;
+  float vhk = (!first && jh >= 0 && jh < a.ny && ch < a.ld) ? a.v[(int64_t)jh * a.ld + ch] : 0.f;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int q = threadIdx.x + k * kCluLines * 32;
@@ -582,10 +585,12 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int jj = j0 + 4 * g + e;
-      vk[k].a[e] = (jj < a.ny && c < a.ld) ? a.v[(int64_t)jj * a.ld + c] : 0.f;
+      vk[k].a[e] = (!first && jj < a.ny && c < a.ld) ? a.v[(int64_t)jj * a.ld + c] : 0.f;
     }
   }
-  auto update = [&]() {
+  // START: the start rule v = tau u1 + w / 2 instead of v += w (own rows only: a start call is
+  // one step, the copied rows are not read again)
+  auto update = [&](const bool START) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int q = threadIdx.x + k * kCluLines * 32;
@@ -596,7 +601,12 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
       for (int e = 0; e < 4; ++e) {
         const int r = 4 * g + e, jj = j0 + r;
         if (jj >= 1 && jj <= a.ny - 2) {
-          vk[k].a[e] = vk[k].a[e] + w.a[e];
+          if (START) {
+            const float u1 = a.u1 ? a.u1[(int64_t)jj * a.ld + c] : 0.f;
+            vk[k].a[e] = fma_(a.tau, u1, mul_(0.5f, w.a[e]));
+          } else {
+            vk[k].a[e] = vk[k].a[e] + w.a[e];
+          }
           sm.u[r][c] = sm.u[r][c] + vk[k].a[e];
         }
       }
@@ -610,7 +620,7 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
   for (int64_t n = 0; n < nsteps; ++n) {
     if (n > 0) {
       if (!dead) dead = !mbar_wait_bounded<true>(&sm.full[1], (uint32_t)((n - 1) & 1), kCluWaitNs);
-      if (!dead) update();
+      if (!dead) update(false);
     }
     if (threadIdx.x == 0 && !dead) {  // this step's phase of both barriers
       mbar_expect_tx(&sm.full[0], zbytes);
@@ -696,7 +706,7 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
   dead = __syncthreads_or(dead);
   if (!dead && nsteps > 0) {
     dead = !mbar_wait_bounded<true>(&sm.full[1], (uint32_t)((nsteps - 1) & 1), kCluWaitNs);
-    if (!dead) update();
+    if (!dead) update(first);
   }
   if (__syncthreads_or(dead) && threadIdx.x == 0) atomicExch(a.status, (int)TSU_ETIMEOUT);
   for (int q = threadIdx.x; q < kCluLines * kCluLen; q += nth) {
@@ -911,9 +921,10 @@ cudaError_t imp_cluster_launch(const ImpArgs<float>& a, int64_t nsteps, cudaStre
   return e;
 }
 
+// start: u0 (may be u) and u1 -> the state after the start step; otherwise nsteps steps of (u, v)
 template <typename T>
-cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const void* fac, void* u, void* v,
-                    const void* u1, int64_t nsteps, bool start, void* ws, cudaStream_t s) {
+cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const void* fac, const void* u0, void* u,
+                    void* v, const void* u1, int64_t nsteps, bool start, void* ws, cudaStream_t s) {
   ImpArgs<T> a;
   memset(&a, 0, sizeof a);  // the graph cache compares the bytes
   a.nx = g.nx;
@@ -943,13 +954,20 @@ cudaError_t imp_run(const ImplicitGeom& g, const void* hx, const void* hy, const
   a.start = start ? 1 : 0;
   const int64_t n = start ? 1 : nsteps;
   if constexpr (sizeof(T) == 4) {  // small FP32 grids: every step in one cluster
-    const int nc = start ? 0 : imp_cluster_ctas(a);
+    const int nc = imp_cluster_ctas(a);
     if (nc > 0 && n >= 1) {
+      ImpArgs<T> c = a;
+      if (start) c.u = (const T*)u0;  // the cluster reads u0 itself: no prepare pass
       bool ran = false;
       const cudaError_t e =
-          nc == 8 ? imp_cluster_launch<8>(a, n, s, &ran) : imp_cluster_launch<16>(a, n, s, &ran);
+          nc == 8 ? imp_cluster_launch<8>(c, n, s, &ran) : imp_cluster_launch<16>(c, n, s, &ran);
       if (e != cudaSuccess || ran) return e;
     }
+  }
+  if (start) {  // u <- u0 on interior nodes, v <- 0, then the start step
+    k_imp_prepare<T><<<152 * 8, 256, 0, s>>>(g.nx, g.ny, g.ld, (const T*)u0, (T*)u, (T*)v);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   if (!start && n >= kImpGraphMinSteps && imp_capturable(s))
     return wide ? imp_steps_graph<T, 16>(a, n, s) : imp_steps_graph<T, 8>(a, n, s);
@@ -993,20 +1011,11 @@ cudaError_t launch_implicit_factor(const ImplicitGeom& g, int dtype, const void*
   return cudaGetLastError();
 }
 
-cudaError_t launch_implicit_prepare(const ImplicitGeom& g, int dtype, const void* u0, void* u, void* v,
-                                    cudaStream_t s) {
-  if (dtype == TSU_F32)
-    k_imp_prepare<float><<<152 * 8, 256, 0, s>>>(g.nx, g.ny, g.ld, (const float*)u0, (float*)u, (float*)v);
-  else
-    k_imp_prepare<double><<<152 * 8, 256, 0, s>>>(g.nx, g.ny, g.ld, (const double*)u0, (double*)u, (double*)v);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_implicit(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, const void* fac,
-                            void* u, void* v, const void* u1, int64_t nsteps, bool start, void* ws,
+                            const void* u0, void* u, void* v, const void* u1, int64_t nsteps, bool start, void* ws,
                             cudaStream_t s) {
-  return dtype == TSU_F32 ? imp_run<float>(g, hx, hy, fac, u, v, u1, nsteps, start, ws, s)
-                          : imp_run<double>(g, hx, hy, fac, u, v, u1, nsteps, start, ws, s);
+  return dtype == TSU_F32 ? imp_run<float>(g, hx, hy, fac, u0, u, v, u1, nsteps, start, ws, s)
+                          : imp_run<double>(g, hx, hy, fac, u0, u, v, u1, nsteps, start, ws, s);
 }
 
 }  // namespace tsu

@@ -1108,9 +1108,8 @@ int tsu_implicit_init(const tsu_grid* g, int dtype, double tau, double sigma, co
   if (ws_bytes < need) return fail(TSU_ENOMEM, "workspace needs %zu B (got %zu)", need, ws_bytes);
   const tsu::ImplicitGeom ig = implicit_geom(g, tau, sigma);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = tsu::launch_implicit_prepare(ig, dtype, u0, st->buf[0], st->buf[1], s);
-  if (e == cudaSuccess)
-    e = tsu::launch_implicit(ig, dtype, m->hx, m->hy, factor, st->buf[0], st->buf[1], u1, 1, true, ws, s);
+  const cudaError_t e =
+      tsu::launch_implicit(ig, dtype, m->hx, m->hy, factor, u0, st->buf[0], st->buf[1], u1, 1, true, ws, s);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_implicit_init launch");
   st->cur = 0;
   st->aux = 1;
@@ -1129,8 +1128,9 @@ int tsu_implicit_step_n(const tsu_grid* g, int dtype, double tau, double sigma, 
   TRY(check_field(ws, "workspace"));
   const size_t need = tsu::implicit_ws_bytes(*g, elem_size(dtype));
   if (ws_bytes < need) return fail(TSU_ENOMEM, "workspace needs %zu B (got %zu)", need, ws_bytes);
-  cudaError_t e = tsu::launch_implicit(implicit_geom(g, tau, sigma), dtype, m->hx, m->hy, factor, st->buf[st->cur],
-                                       st->buf[st->aux], nullptr, nsteps, false, ws, (cudaStream_t)stream);
+  cudaError_t e = tsu::launch_implicit(implicit_geom(g, tau, sigma), dtype, m->hx, m->hy, factor, nullptr,
+                                       st->buf[st->cur], st->buf[st->aux], nullptr, nsteps, false, ws,
+                                       (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "tsu_implicit_step_n launch");
   st->step += nsteps;
   return TSU_OK;

@@ -208,12 +208,10 @@ size_t implicit_factor_elems(const tsu_grid& g);
 size_t implicit_ws_bytes(const tsu_grid& g, size_t elem);
 cudaError_t launch_implicit_factor(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, void* fac,
                                    cudaStream_t s);
-// u <- u0 on interior nodes and 0 elsewhere, v <- 0 (u0 may be u)
-cudaError_t launch_implicit_prepare(const ImplicitGeom& g, int dtype, const void* u0, void* u, void* v,
-                                    cudaStream_t s);
-// start (start = true: v = tau u1 + w^0 / 2, u += v) or nsteps steps (v += w^n, u += v), in place
+// start = true: u^0 = u0 on interior nodes (0 elsewhere; u0 may be u), v = tau u1 + w^0 / 2,
+// u = u^0 + v; else nsteps steps (v += w^n, u += v) in place
 cudaError_t launch_implicit(const ImplicitGeom& g, int dtype, const void* hx, const void* hy, const void* fac,
-                            void* u, void* v, const void* u1, int64_t nsteps, bool start, void* ws,
+                            const void* u0, void* u, void* v, const void* u1, int64_t nsteps, bool start, void* ws,
                             cudaStream_t s);
 
 }  // namespace tsu

@@ -207,22 +207,31 @@ def test_implicit_one_cluster_path_equals_the_two_kernel_steps(nx, ny):
     """FP32 grids of at most 129 x 129 (256 x 256) nodes run every step of a call in one cluster
     of 8 (16) CTAs, the fields in shared memory; a row pitch above 256 sends the same grid through
     the two kernels per step.  The states must agree bit for bit, and with the oracle, and no
-    bounded wait of the cluster may have run out."""
+    bounded wait of the cluster may have run out.  The start call takes the same path (u0 with
+    nonzero boundary values, which it must ignore, and an initial velocity u1)."""
     depth = DEPTHS["paper_step"]
     og = oracle.grid(nx, ny)
     hx, hy, ext = oracle.make_depth(og, depth)
     tau = 3.0 * min(og.dx, og.dy) / math.sqrt(max(ext[1], ext[3]))
+    rng = np.random.default_rng(nx * 1000 + ny)
     u0n = inputs.gaussian_hump(nx, ny, None, 0.4, 0.45, 0.08)
+    u0b = u0n + 0.1 * inputs.random_field(nx, ny, None, rng, zero_boundary=False)
+    u0n = u0b.copy()
+    u0n[0, :] = u0n[-1, :] = 0.0
+    u0n[:, 0] = u0n[:, -1] = 0.0
+    u1n = 0.2 * inputs.random_field(nx, ny, None, rng)
     out = []
     for ld in (None, 320):
         sim = tsu.ImplicitSimulation.create(nx, depth, dtype="f32", ny=ny, tau=tau, ld=ld)
         u0 = tsu.empty_field(sim.g, "f32")
-        u0[:, :nx] = torch.from_numpy(u0n).float()
-        sim.init(u0)
+        u0[:, :nx] = torch.from_numpy(u0b).float()
+        u1 = torch.zeros_like(u0)
+        u1[:, :nx] = torch.from_numpy(u1n).float()
+        sim.init(u0, u1)
         sim.step(7)
         sim.step(23)
         tsu.tsu_sync_status(sim.ws, sim.ws.numel())
         out.append((sim.u[:, :nx].clone(), sim.v[:, :nx].clone()))
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
-    ref, _ = oracle.implicit_forward(og, tau, 0.25, hx, hy, u0n, None, 31)
+    ref, _ = oracle.implicit_forward(og, tau, 0.25, hx, hy, u0n, u1n, 31)
     assert relerr(out[0][0].double().cpu().numpy(), ref) <= 1e-5
