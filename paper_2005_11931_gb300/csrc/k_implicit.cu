@@ -515,9 +515,18 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
                       (!first || (jj >= 1 && jj <= a.ny - 2 && c >= 1 && c <= a.nx - 2));
     return take ? a.u[(int64_t)jj * a.ld + c] : 0.f;
   };
-  for (int q = threadIdx.x; q < kCluLines * kCluLen; q += nth) {
-    const int r = q / kCluLen, c = q - r * kCluLen;
-    sm.u[r][c] = u_at(j0 + r, c);
+  {  // all loads in flight at once: the prologue's round trips to memory are what a short call waits for
+    float uv[kCluLen / 32];
+#pragma unroll
+    for (int k = 0; k < kCluLen / 32; ++k) {
+      const int q = threadIdx.x + k * kCluLines * 32;
+      uv[k] = u_at(j0 + q / kCluLen, q % kCluLen);
+    }
+#pragma unroll
+    for (int k = 0; k < kCluLen / 32; ++k) {
+      const int q = threadIdx.x + k * kCluLines * 32;
+      sm.u[q / kCluLen][q % kCluLen] = uv[k];
+    }
   }
   for (int q = threadIdx.x; q < kCluLen * kCluGroup; q += nth) {
     (&sm.zb[0][0])[q] = 0.f;
@@ -529,7 +538,6 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
     sm.uh[h][c] = u_at(j, c);
     sm.wbh[h][c][0] = sm.wbh[h][c][1] = sm.wbh[h][c][2] = sm.wbh[h][c][3] = 0.f;
   }
-  cl.sync();  // every CTA's barriers initialised and buffers filled before the first store
   // bytes received per step: the x pass of each of the NC * 16 rows hands over 16 columns (64 B),
   // the y pass of each column 16 rows (64 B) and, per copied row, the 16-byte chunk holding its w
   const uint32_t zbytes = NC * kCluLines * 64;
@@ -588,6 +596,7 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
       vk[k].a[e] = (!first && jj < a.ny && c < a.ld) ? a.v[(int64_t)jj * a.ld + c] : 0.f;
     }
   }
+  cl.sync();  // every CTA's barriers initialised and buffers filled before the first store
   // START: the start rule v = tau u1 + w / 2 instead of v += w (own rows only: a start call is
   // one step, the copied rows are not read again)
   auto update = [&](const bool START) {
