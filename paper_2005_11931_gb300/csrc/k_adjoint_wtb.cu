@@ -45,6 +45,19 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
   const int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(n) : "memory");
 }
+// the same with an L2 eviction priority (a policy from createpolicy)
+__device__ __forceinline__ void cp16_hint(void* smem, const void* gmem, bool valid, uint64_t pol) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(d), "l"(gmem), "r"(n),
+               "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -110,11 +123,18 @@ __global__ void __launch_bounds__(kAwWarps * 32, aw_ctas_per_sm<K>()) k_adjoint_
   float* ring = reinterpret_cast<float*>(aw_smem) + (size_t)threadIdx.x * 4;
   const int stride = kAwWarps * 32 * 4;
   auto slot = [&](unsigned s, int f) { return ring + (size_t)((s & (kAwRing - 1)) * NF + f) * stride; };
+  // The first 2K input rows of a tile are the last rows the tile above reads, at its end: they
+  // are copied with a priority to stay in the L2 until then.
+  const uint64_t keep = l2_evict_last();
   auto issue = [&](int q) {  // the copies consumed at iteration q (input row r_first + q)
     const int r = r_first + q;
     auto copy = [&](int f, const float* src, int row) {
       const bool ok = col_in && row >= 0 && row < a.ny;
-      cp16(slot((unsigned)q, f), src + (ok ? (int64_t)row * a.ld + c0 : 0), ok);
+      const float* g = src + (ok ? (int64_t)row * a.ld + c0 : 0);
+      if (q < 2 * K)
+        cp16_hint(slot((unsigned)q, f), g, ok, keep);
+      else
+        cp16(slot((unsigned)q, f), g, ok);
     };
     copy(F_L1, a.lam1, r);
     copy(F_MU, a.mu1, r);

@@ -51,6 +51,19 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
   const int n = valid ? 16 : 0;  // 0: fill with zeros, read nothing
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(n) : "memory");
 }
+// the same with an L2 eviction priority (a policy from createpolicy)
+__device__ __forceinline__ void cp16_hint(void* smem, const void* gmem, bool valid, uint64_t pol) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(d), "l"(gmem), "r"(n),
+               "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -146,14 +159,25 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
 #pragma unroll
   for (int e = 0; e < 4; ++e) node_col[e] = (c0 + e >= 1) && (c0 + e <= a.nx - 2);
 
+  // ALL (the segment recompute, whose fields exceed the L2 on the grids it runs on): the first 2K
+  // input rows of a tile are the last rows the tile above reads, at its end; they are copied with
+  // a priority to stay in the L2 until then
+  [[maybe_unused]] const uint64_t keep = ALL ? l2_evict_last() : 0ull;
   auto issue = [&](int r) {  // copies of input row r into the rings (zeros outside the grid)
     const bool ok = col_in && r >= 0 && r < a.ny;
     const int64_t go = ok ? (int64_t)r * a.ld + c0 : 0;
     const unsigned sa = (unsigned)(r - r_first) & (Sh::SA - 1), sb = (unsigned)(r - r_first) & (Sh::SB - 1);
-    cp16(slotA(sa, 0), a.u + go, ok);
-    cp16(slotA(sa, 1), a.p + go, ok);
-    cp16(slotB(sb, 0), a.hx + go, ok);
-    cp16(slotB(sb, 1), a.hy + go, ok);
+    if (ALL && r - r_first < 2 * K) {
+      cp16_hint(slotA(sa, 0), a.u + go, ok, keep);
+      cp16_hint(slotA(sa, 1), a.p + go, ok, keep);
+      cp16_hint(slotB(sb, 0), a.hx + go, ok, keep);
+      cp16_hint(slotB(sb, 1), a.hy + go, ok, keep);
+    } else {
+      cp16(slotA(sa, 0), a.u + go, ok);
+      cp16(slotA(sa, 1), a.p + go, ok);
+      cp16(slotB(sb, 0), a.hx + go, ok);
+      cp16(slotB(sb, 1), a.hy + go, ok);
+    }
   };
   auto ringB = [&](int r, int f) -> P4 {  // hx (f = 0) or hy (f = 1) of row r, zeros outside
     if (r < r_first) return kZeroP4;
