@@ -1,9 +1,10 @@
-// Shared-memory barriers with transaction counts (mbarrier), the asynchronous copies and stores
-// that complete on them, and the bounded wait every kernel uses on them.
+// Asynchronous copies into shared memory: per-thread 16-byte copies in commit groups (each thread
+// waits for its own), and shared-memory barriers with transaction counts (mbarrier) with the bulk
+// copies and remote stores that complete on them, and the bounded wait every kernel uses on them.
 //
-// A wait never spins without limit: mbar_wait_bounded gives up after a wall-clock limit (and an
-// iteration cap behind it) and returns false, and the caller records TSU_ETIMEOUT in its status
-// word and leaves.
+// A wait on an mbarrier never spins without limit: mbar_wait_bounded gives up after a wall-clock
+// limit (and an iteration cap behind it) and returns false, and the caller records TSU_ETIMEOUT
+// in its status word and leaves.
 #pragma once
 #include <stdint.h>
 
@@ -13,6 +14,31 @@ namespace dev {
 constexpr long long kSpinCap = 1ll << 30;  // iteration cap behind the wall-clock limit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// 16 bytes global -> shared by this thread; valid = false fills zeros and reads nothing
+__device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(n) : "memory");
+}
+// the same with an L2 eviction priority (a policy from l2_evict_last)
+__device__ __forceinline__ void cp16_hint(void* smem, const void* gmem, bool valid, uint64_t pol) {
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(n), "l"(pol)
+               : "memory");
+}
+// a policy under which lines stay in the L2 longer than others
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's commit groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

@@ -22,6 +22,7 @@
 // differently, within the FP32 adjoint's tolerance.
 #include <string.h>
 
+#include "async_copy.cuh"
 #include "stencil_common.cuh"
 
 namespace tsu {
@@ -40,29 +41,6 @@ constexpr int aw_ctas_per_sm() { return 3; }
 template <int K>
 constexpr int aw_fields() { return K + 4; }
 
-__device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(n) : "memory");
-}
-// the same with an L2 eviction priority (a policy from createpolicy)
-__device__ __forceinline__ void cp16_hint(void* smem, const void* gmem, bool valid, uint64_t pol) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(d), "l"(gmem), "r"(n),
-               "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 // acc[0..3] += v (one rounding each, as acc + v): the FP32 gradient accumulators of a row are
 // added to in the L2, without a read back into the SM.  Every node gets exactly one such add per
 // pass (only the tile that owns a row adds to it), so the sums do not depend on timing.

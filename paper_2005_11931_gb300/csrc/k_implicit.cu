@@ -27,7 +27,7 @@
 
 #include <atomic>
 
-#include "mbarrier.cuh"
+#include "async_copy.cuh"
 #include "stencil_common.cuh"
 
 namespace tsu {

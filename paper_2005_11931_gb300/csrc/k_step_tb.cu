@@ -21,7 +21,7 @@
 // drains its own copies (bounded) and returns.
 #include <string.h>
 
-#include "mbarrier.cuh"
+#include "async_copy.cuh"
 #include "stencil_common.cuh"
 #include "tsu_internal.h"
 

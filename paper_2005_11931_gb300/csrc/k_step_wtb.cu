@@ -22,6 +22,7 @@
 
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "stencil_common.cuh"
 
 namespace tsu {
@@ -45,30 +46,6 @@ struct WtbShape {
   // bytes per thread
   static constexpr int bytes = (SA * 2 + SB * 2) * 16;
 };
-
-__device__ __forceinline__ void cp16(void* smem, const void* gmem, bool valid) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;  // 0: fill with zeros, read nothing
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(n) : "memory");
-}
-// the same with an L2 eviction priority (a policy from createpolicy)
-__device__ __forceinline__ void cp16_hint(void* smem, const void* gmem, bool valid, uint64_t pol) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(d), "l"(gmem), "r"(n),
-               "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // 16-byte aligned: arrays of descriptors have the same stride on the host and the device.
 struct alignas(16) WtbArgs {
