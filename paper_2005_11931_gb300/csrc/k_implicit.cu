@@ -450,11 +450,12 @@ __global__ void __launch_bounds__(R * 32) k_imp_y(const ImpArgs<T> a) {
 // most 129 nodes, one segment) or NC = 16 (at most 256 nodes, two segments).  CTA c owns rows
 // 16 c .. 16 c + 15 (their u and v in shared memory; faces and x pivots in the registers of the
 // warps solving them) and columns 16 c .. 16 c + 15 (y pivots and coefficients in registers, the
-// x pass's result along them in shared memory), read from memory once, and keeps copies of the
-// two rows next to its edge rows (u, v), updated as their owners update them.  One step: the update v += w, u += v of the own and the copied rows from the
-// previous step's w; the x pass (warp w solves row 16 c + w and stores each result into the CTA
-// owning its column); the y pass (warp w solves column 16 c + w and stores each w into the CTA
-// owning its row and, for edge rows, into the neighbour holding the copy).
+// x pass's result along them in shared memory), read from memory once.  It also keeps copies of
+// the two rows next to its edge rows (u in shared memory, v in registers), updated as their
+// owners update them.  One step: the update v += w, u += v of the own and the copied rows from
+// the previous step's w; the x pass (warp w solves row 16 c + w and stores each result into the
+// CTA owning its column); the y pass (warp w solves column 16 c + w and stores each w into the
+// CTA owning its row and, for edge rows, into the neighbour holding the copy).
 //
 // Every hand-over is an asynchronous store into the receiver's shared memory that completes its
 // bytes on one of the receiver's two barriers (zb and wb received), so there is no cluster-wide
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(kCluLines * 32, 1) k_imp_cluster(const ImpArgs
                       (!first || (jj >= 1 && jj <= a.ny - 2 && c >= 1 && c <= a.nx - 2));
     return take ? a.u[(int64_t)jj * a.ld + c] : 0.f;
   };
-  {  // all loads in flight at once: the prologue's round trips to memory are what a short call waits for
+  {  // the loads first, then the stores: one round trip to memory
     float uv[kCluLen / 32];
 #pragma unroll
     for (int k = 0; k < kCluLen / 32; ++k) {
