@@ -27,8 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "grid-point updates/s (GLUPS) and HBM roofline %; adjoint/forward time ratio"
-# DRAM bytes (read + write) per launch of the dominant kernel from ncu captures (profiles/),
-# keyed by (kernel, form, n, steps per launch); only for kernels unchanged since the capture.
+# DRAM bytes (read + write) per pass of the dominant kernel from ncu captures (profiles/),
+# keyed by (kernel, form, n, steps per pass); only for kernels unchanged since the capture.
 TRAFFIC = {
     # profiles/k_leapfrog_wtb_increment_8192.md: one launch of the timed configuration (8192^2,
     # 4 steps per pass, 117 rows per chunk, two rows per loop trip, outer strips first),
@@ -37,7 +37,7 @@ TRAFFIC = {
 }
 UNIT = "GLUPS"
 ORACLE_SAMPLE_STEPS = 32  # leapfrog steps of each timed oracle sample (depth evaluation included once)
-DEFAULT_KERNEL = 2  # warp-blocked pass, 4 steps per HBM pass
+DEFAULT_KERNEL = 4  # warp-blocked pass, 4 steps per HBM pass, every pass of a call in one persistent launch
 
 
 def parse():
@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--form", default="increment", choices=["increment", "standard"])
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0,
-                    help="0 = 2; 1 one step per pass, 2 warp-blocked (tdepth 2/4), 3 CTA-blocked (tdepth 4/8)")
+                    help="0 = 4; 1 one step per pass, 2 warp-blocked (tdepth 2/4), 3 CTA-blocked (tdepth 4/8), "
+                         "4 warp-blocked passes in one persistent launch")
     ap.add_argument("--tdepth", type=int, default=0, help="steps per blocked pass (0: 4 for kernel 2, 8 for 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -279,8 +280,8 @@ def run_gpu(args):
     # kernel: --kernel, else the default below; the blocked kernels' steps and the leftover single
     # steps are separate calls so that each is timed on its own
     kernel = args.kernel or DEFAULT_KERNEL
-    blocked = kernel in (2, 3)
-    K = (args.tdepth or (4 if kernel == 2 else 8)) if blocked else 1
+    blocked = kernel in (2, 3, 4)
+    K = (args.tdepth or (8 if kernel == 3 else 4)) if blocked else 1
     n_main = ((S - 1) // K) * K if blocked else S - 1
     n_left = (S - 1) - n_main
     opts = tsu.StepOpts()
@@ -310,9 +311,10 @@ def run_gpu(args):
         o_e = energy[S - 1:]
         tsu.tsu_observe(g, code, tau, med, st, o_e, None, None, ws, ws_bytes, stream)
 
-    main_launches = n_main // K if blocked else n_main
-    # depth (reset, eval, decode), init, main passes, leftover passes, observe
-    launches_per_step = 3 + 1 + main_launches + n_left + 1
+    main_launches = n_main // K if blocked else n_main  # passes (kernel 4: all in one launch)
+    # depth (reset, eval, decode), init, main passes (kernel 4: its counters' reset and one
+    # launch), leftover passes, observe
+    launches_per_step = 3 + 1 + (2 if kernel == 4 else main_launches) + n_left + 1
 
     for _ in range(args.warmup):
         one_step(u0)
@@ -340,12 +342,15 @@ def run_gpu(args):
     # K steps.
     if blocked:
         bpn = 24
-        kname = "k_leapfrog_wtb" if kernel == 2 else "k_leapfrog_tb"
+        kname = {2: "k_leapfrog_wtb", 3: "k_leapfrog_tb", 4: "k_leapfrog_wtb_flow"}[kernel]
     else:
         bpn = 24 if form == tsu.TSU_FORM_INCREMENT else 20
         kname = "k_leapfrog"
-    launch_ms = sum(kernel_ms) / (len(kernel_ms) * main_launches)
-    achieved = bpn * (p.n - 2) ** 2 / (launch_ms / 1e3) / 1e9
+    # per pass (K steps); kernel 4 runs every pass of the call in one launch (its counters' reset,
+    # a few microseconds, included)
+    pass_ms = sum(kernel_ms) / (len(kernel_ms) * main_launches)
+    passes_per_launch = main_launches if kernel == 4 else 1
+    achieved = bpn * (p.n - 2) ** 2 / (pass_ms / 1e3) / 1e9
     traffic = args.traffic
     if traffic is None and args.rows == 0:  # the captured launches used the automatic rows per chunk
         traffic = TRAFFIC.get((kname, args.form, p.n, K if blocked else 1))
@@ -407,12 +412,13 @@ def run_gpu(args):
         "config": workload_config(p.n, S, args.form, world),
         "kernel": f"{'%d steps per blocked pass' % K if blocked else 'one step per pass'}, tau = {tau:.6g}",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind, "bytes_per_launch_per_node": bpn,
-                     "steps_per_launch": K if blocked else 1, "kernel": kname, "launch_ms": launch_ms,
-                     "launches_per_step": main_launches,
-                     # DRAM bytes the ncu capture counted per launch over the live launch time, and the
+                     "traffic": traffic, "peak_kind": peak_kind, "bytes_per_pass_per_node": bpn,
+                     "steps_per_pass": K if blocked else 1, "kernel": kname, "pass_ms": pass_ms,
+                     "passes_per_launch": passes_per_launch, "launch_ms": pass_ms * passes_per_launch,
+                     "launches_per_step": main_launches // passes_per_launch,
+                     # DRAM bytes the ncu capture counted per pass over the live pass time, and the
                      # algorithmic rate against the 8 TB/s nominal figure (context)
-                     "dram_frac": (traffic / (launch_ms / 1e3) / 1e9 / peak) if traffic else None,
+                     "dram_frac": (traffic / (pass_ms / 1e3) / 1e9 / peak) if traffic else None,
                      "frac_of_nominal_8tbs": achieved / 8000.0},
         "cpu_baseline": cpu,
         "e2e": e2e,

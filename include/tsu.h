@@ -146,10 +146,16 @@ typedef struct {
                        2 or 4 steps per pass, default 4), 3 CTA-blocked (tdepth = 4 or 8, default 8);
                        2 and 3 need FP32, nbuf = 4 and a workspace; 2 records up to 2048
                        receivers and takes checkpoints when ckpt_every is a multiple of tdepth and
-                       the call starts at step 1 + j tdepth; 3 takes neither; auto picks kernel 2
-                       (tdepth 4) whenever it can.  All kernels round every operation the same way, so the FP32
-                       states do not depend on the choice */
-  int32_t rows;     /* rows per CTA (kernels 1, 3) or per warp tile (kernel 2); 0 = auto */
+                       the call starts at step 1 + j tdepth; 3 takes neither; 4 runs kernel 2's
+                       passes (tdepth 4, increment form, no traces or checkpoints) all in one
+                       persistent cooperative launch, a tile's next pass starting once the tiles
+                       around it finished the current one (its waits are bounded: TSU_ETIMEOUT
+                       through tsu_sync_status); auto picks kernel 4 where it can run and its tiles
+                       number between half and 2.5 times the device's resident warps (FP32 grids
+                       of about 2K to 8K per side), else kernel 2 (tdepth 4) whenever it can.  All
+                       kernels round every operation the same way, so the FP32 states do not
+                       depend on the choice */
+  int32_t rows;     /* rows per CTA (kernels 1, 3) or per warp tile (kernels 2, 4); 0 = auto */
   int32_t tdepth;   /* steps per pass of kernels 2 and 3 (0 = default); leftover steps run one per pass */
   int32_t reserved; /* 0.  Bit 0 is a test hook of the failure detection: kernel 3 then never
                        issues one row copy, its bounded wait (20 ms) expires and tsu_sync_status

@@ -316,9 +316,14 @@ static size_t rec_off_bytes(int64_t ny, int64_t ld) { return ((size_t)rec_table_
 
 static size_t align16(size_t n) { return (n + 15) / 16 * 16; }
 
+static int64_t flow_tiles(int64_t ny, int64_t ld) {
+  const int64_t t = rec_table_tiles(ny, ld);
+  return t < kFlowMaxTiles ? t : kFlowMaxTiles;
+}
+
 size_t energy_ws_bytes(int64_t ny, int64_t ld) {
   return 256 + align16((size_t)energy_slots(ny, ld) * sizeof(double)) +
-         align16(rec_off_bytes(ny, ld)) + (size_t)kWtbMaxReceivers * sizeof(int4);
+         align16(rec_off_bytes(ny, ld)) + (size_t)kWtbMaxReceivers * sizeof(int4) + flow_bytes(flow_tiles(ny, ld));
 }
 
 EnergyWs energy_ws_carve(void* ws, size_t bytes, int64_t ny, int64_t ld) {
@@ -334,6 +339,8 @@ EnergyWs energy_ws_carve(void* ws, size_t bytes, int64_t ny, int64_t ld) {
     e.rec_ent = (int4*)(t + off);
     e.rec_tiles_cap = rec_table_tiles(ny, ld);
     e.rec_ent_cap = kWtbMaxReceivers;
+    e.flow = t + off + (size_t)kWtbMaxReceivers * sizeof(int4);
+    e.flow_tiles_cap = flow_tiles(ny, ld);
   }
   return e;
 }

@@ -20,6 +20,8 @@
 // 4 + (16 + 4)/K B per node and step instead of 24 B for one step per pass.
 #include <string.h>
 
+#include <atomic>
+
 #include <type_traits>
 
 #include "async_copy.cuh"
@@ -113,9 +115,14 @@ __device__ void wtb_energy(float (&es)[K], float (&ec)[K], const WtbArgs& a) {
   if (threadIdx.x == 0) *a.ews.counter = 0u;
 }
 
-template <int K, int FORM, bool ENERGY, bool ALL, bool REC = false, bool UNROLL2 = false>
+// One tile's K steps: input state (in_u, in_p), output state (o_a, o_b).  FLOW: the tile's
+// per-level energy sums go to fpart[t * fstride + tile_id] (warp-reduced as wtb_energy does)
+// instead of into the CTA's partial.
+template <int K, int FORM, bool ENERGY, bool ALL, bool REC = false, bool UNROLL2 = false, bool FLOW = false>
 __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, const int64_t strip,
-                                         const int64_t chunk, const int64_t tile_id = 0) {
+                                         const int64_t chunk, const int64_t tile_id, const float* in_u,
+                                         const float* in_p, float* o_a, float* o_b, double* fpart = nullptr,
+                                         const int64_t fstride = 0) {
   using Sh = WtbShape<K>;
   extern __shared__ __align__(16) unsigned char wtb_smem[];
   const int lane = threadIdx.x & 31;
@@ -145,13 +152,13 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     const int64_t go = ok ? (int64_t)r * a.ld + c0 : 0;
     const unsigned sa = (unsigned)(r - r_first) & (Sh::SA - 1), sb = (unsigned)(r - r_first) & (Sh::SB - 1);
     if (ALL && r - r_first < 2 * K) {
-      cp16_hint(slotA(sa, 0), a.u + go, ok, keep);
-      cp16_hint(slotA(sa, 1), a.p + go, ok, keep);
+      cp16_hint(slotA(sa, 0), in_u + go, ok, keep);
+      cp16_hint(slotA(sa, 1), in_p + go, ok, keep);
       cp16_hint(slotB(sb, 0), a.hx + go, ok, keep);
       cp16_hint(slotB(sb, 1), a.hy + go, ok, keep);
     } else {
-      cp16(slotA(sa, 0), a.u + go, ok);
-      cp16(slotA(sa, 1), a.p + go, ok);
+      cp16(slotA(sa, 0), in_u + go, ok);
+      cp16(slotA(sa, 1), in_p + go, ok);
       cp16(slotB(sb, 0), a.hx + go, ok);
       cp16(slotB(sb, 1), a.hy + go, ok);
     }
@@ -357,11 +364,11 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       }
       if (t == K && row_out && col_out) {
         const int64_t o = (int64_t)rt * a.ld + c0;
-        stg_p4(a.out_a + o, un);
+        stg_p4(o_a + o, un);
         if constexpr (FORM == 1)
-          stg_p4(a.out_b + o, vn);
+          stg_p4(o_b + o, vn);
         else if constexpr (!ALL)
-          stg_p4(a.out_b + o, w[K - 1][1]);  // level K-1 at the same row (the segment has it already)
+          stg_p4(o_b + o, w[K - 1][1]);  // level K-1 at the same row (the segment has it already)
       }
     }
   };
@@ -407,7 +414,18 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     }
   }
   cp_wait<0>();
-  if constexpr (ENERGY) wtb_energy<K>(es, ec, a);
+  if constexpr (ENERGY) {
+    if constexpr (FLOW) {
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        double v = (double)es[t] - (double)ec[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) fpart[(int64_t)t * fstride + tile_id] = v;
+      }
+    } else {
+      wtb_energy<K>(es, ec, a);
+    }
+  }
 }
 
 // Strip and chunk of a single-problem tile.  The tiles of the two outer strips (masked on every
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb(const WtbArg
   const bool ok = tile < a.ntiles;
   uint32_t strip = 0, chunk = 0;
   if (ok) wtb_tile_coords(tile, a, strip, chunk);
-  wtb_body<K, FORM, ENERGY, false, REC, !REC>(a, ok, strip, chunk, tile);
+  wtb_body<K, FORM, ENERGY, false, REC, !REC>(a, ok, strip, chunk, tile, a.u, a.p, a.out_a, a.out_b);
 }
 
 template <int K, int FORM>
@@ -445,7 +463,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_seg(const Wt
   const bool ok = tile < a.ntiles;
   uint32_t strip = 0, chunk = 0;
   if (ok) wtb_tile_coords(tile, a, strip, chunk);
-  wtb_body<K, FORM, false, true, false, true>(a, ok, strip, chunk);
+  wtb_body<K, FORM, false, true, false, true>(a, ok, strip, chunk, 0, a.u, a.p, a.out_a, a.out_b);
 }
 
 // Batched family: warp w of CTA b works on tile tiles[4 b + w] = (problem, strip, chunk) of
@@ -458,7 +476,7 @@ __global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_batched(cons
   const bool ok = tile < ntiles;
   const int4 t = ok ? tiles[tile] : make_int4(0, 0, 0, 0);
   const WtbArgs a = probs[t.x];
-  wtb_body<K, FORM, false, false>(a, ok, t.y, t.z);
+  wtb_body<K, FORM, false, false>(a, ok, t.y, t.z, 0, a.u, a.p, a.out_a, a.out_b);
 }
 
 // The tile index wtb_tile_coords maps to (strip, chunk).
@@ -548,6 +566,131 @@ __global__ void k_trace_edges(const int32_t nx, const int32_t ny, const int64_t 
     if (!interior)
       for (int64_t k = 0; k < nsteps; ++k) traces[k * nrec + r] = 0.f;
   }
+}
+
+// ---- all K-step passes of a call in one persistent launch --------------------------------------
+// Each warp takes tasks (pass, tile) in increasing order from a counter, and starts one once the
+// 3 x 3 tiles around it have finished the pass before.  Those tiles are the ones whose outputs
+// it reads as its halo, and the ones that read the buffer it is about to overwrite.  So a tile's
+// next pass begins while far-away tiles still finish the current one, instead of every SM
+// waiting for the slowest tile at the end of each launch.  Passes alternate between two
+// (u, v) pairs.  Every wait is bounded (TSU_ETIMEOUT in the status word).  No task waits for a
+// later one, and the launch is cooperative (every CTA resident), so every wait ends.  A
+// tile's energy sums go to a slot of kFlowSlots per-pass partials.  The task that finishes a
+// pass last sums them in the order wtb_energy uses, so the energies, like the states, equal those
+// of the launch-per-pass path bit for bit.
+struct WtbFlow {
+  float* u[2];  // pass p reads (u, v)[p & 1] and writes (u, v)[(p + 1) & 1]
+  float* v[2];
+  double* energy;  // K doubles per pass, or nullptr
+  unsigned int* next;
+  int* count;    // [kFlowSlots] tiles that finished the pass held by the slot
+  int* reduced;  // [kFlowSlots] the last pass whose partials the slot gave up
+  int* done;     // [ntiles] passes finished
+  double* part;  // [kFlowSlots][K][nt4]
+  int* status;
+  int64_t npass, nt4;
+  uint64_t limit_ns;
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// bounded wait for *p >= target
+__device__ bool wait_ge(const int* p, const int target, const uint64_t limit_ns) {
+  if (ld_acquire(p) >= target) return true;
+  const uint64_t t0 = global_ns();
+  for (long long it = 0; it < kSpinCap; ++it) {
+    __nanosleep(100);
+    if (ld_acquire(p) >= target) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(kWtbWarps * 32, 4) k_leapfrog_wtb_flow(const WtbArgs a, const WtbFlow f) {
+  constexpr int K = 4;
+  const int lane = threadIdx.x & 31;
+  // 32-bit task numbers (the launcher keeps npass * ntiles below 2^31); what the body does not
+  // need is recomputed from the task number after it
+  for (;;) {
+    unsigned int task = 0;
+    if (lane == 0) task = atomicAdd(f.next, 1u);
+    task = __shfl_sync(0xffffffffu, task, 0);
+    if (task >= (unsigned int)f.npass * (unsigned int)a.ntiles) break;
+    const unsigned int nt = (unsigned int)a.ntiles;
+    const unsigned int pass = task / nt, tile = task - pass * nt;
+    uint32_t strip = 0, chunk = 0;
+    wtb_tile_coords(tile, a, strip, chunk);
+    const unsigned int slot = pass % kFlowSlots;
+    bool ok = true;
+    if (lane < 9 && pass > 0) {
+      const int ns = (int)a.nstrips, nch = (int)(nt / (unsigned int)ns);
+      const int sx = (int)strip + lane % 3 - 1, cy = (int)chunk + lane / 3 - 1;
+      if (sx >= 0 && sx < ns && cy >= 0 && cy < nch)
+        ok = wait_ge(f.done + wtb_tile_index(sx, cy, ns, nch), (int)pass, f.limit_ns);
+    }
+    if (ENERGY && lane == 9 && pass >= kFlowSlots)
+      ok = wait_ge(f.reduced + slot, (int)(pass - kFlowSlots), f.limit_ns);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicExch(f.status, (int)TSU_ETIMEOUT);
+      break;
+    }
+    {
+      const int q = (int)(pass & 1);
+      wtb_body<K, 1, ENERGY, false, false, true, true>(a, true, strip, chunk, tile, f.u[q], f.v[q], f.u[q ^ 1],
+                                                       f.v[q ^ 1], f.part + (int64_t)slot * K * f.nt4, f.nt4);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      st_release(f.done + tile, (int)(pass + 1));
+    }
+    if constexpr (ENERGY) {
+      int last = 0;
+      if (lane == 0) last = atomicAdd(f.count + slot, 1) == (int)(nt - 1) ? 1 : 0;
+      if (__shfl_sync(0xffffffffu, last, 0)) {
+        __threadfence();
+        // CTA c of the launch-per-pass path held tiles 4c .. 4c + 3: its partial, then the sum
+        // over CTAs lane by lane and a shuffle tree, as wtb_energy
+        const int64_t ncta = f.nt4 / kWtbWarps;
+        for (int t = 0; t < K; ++t) {
+          const double* pt = f.part + ((int64_t)slot * K + t) * f.nt4;
+          double sum = 0.0;
+          for (int64_t c = lane; c < ncta; c += 32) {
+            double cs = 0.0;
+            for (int w = 0; w < kWtbWarps; ++w) cs += __ldcg(pt + c * kWtbWarps + w);
+            sum += cs;
+          }
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+          if (lane == 0) f.energy[(int64_t)pass * K + t] = sum * a.escale;
+        }
+        if (lane == 0) {
+          f.count[slot] = 0;
+          __threadfence();
+          st_release(f.reduced + slot, (int)pass);
+        }
+      }
+    }
+  }
+}
+
+// counters and partials of the persistent pass (one launch before it)
+__global__ void k_wtb_flow_init(const WtbFlow f, const int64_t ntiles) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, n = (int64_t)gridDim.x * blockDim.x;
+  if (i == 0) *f.next = 0u;
+  if (i < kFlowSlots) {
+    f.count[i] = 0;
+    f.reduced[i] = -1;
+  }
+  for (int64_t k = i; k < ntiles; k += n) f.done[k] = 0;
+  for (int64_t k = i; k < (int64_t)kFlowSlots * 4 * f.nt4; k += n) f.part[k] = 0.0;
 }
 
 template <int K, int FORM, bool ENERGY, bool REC>
@@ -731,6 +874,104 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
   if (k == 2) return form == TSU_FORM_STANDARD ? wtb_launch<2, 0>(a, s) : wtb_launch<2, 1>(a, s);
   if (k == 4) return form == TSU_FORM_STANDARD ? wtb_launch<4, 0>(a, s) : wtb_launch<4, 1>(a, s);
   return cudaErrorInvalidValue;
+}
+
+namespace {
+// resident CTAs of the persistent pass on this device (0: no cooperative launch), once per device
+std::atomic<int> g_flow_ctas[64];
+int flow_resident_ctas(cudaStream_t) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  int v = g_flow_ctas[dev].load();
+  if (v != 0) return v > 0 ? v : 0;
+  int coop = 0, nsm = 0, per_sm = 0;
+  const size_t smem = (size_t)WtbShape<4>::bytes * kWtbWarps * 32;
+  bool ok = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  for (int e = 0; ok && e < 2; ++e) {
+    void (*kern)(const WtbArgs, const WtbFlow) = e ? k_leapfrog_wtb_flow<true> : k_leapfrog_wtb_flow<false>;
+    int q = 0;
+    ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, kern, kWtbWarps * 32, smem) == cudaSuccess && q >= 1;
+    per_sm = e ? (q < per_sm ? q : per_sm) : q;
+  }
+  (void)cudaGetLastError();  // a refused query leaves no error behind
+  v = ok ? per_sm * nsm : -1;
+  g_flow_ctas[dev].store(v);
+  return v > 0 ? v : 0;
+}
+}  // namespace
+
+// Rows per tile of the persistent pass: tiles about 1.2 x the resident warps, so that every warp
+// has a tile of each pass and finishing tiles are followed at once by the next pass's (2048^2:
+// 610 GLUPS at 16 rows, 544 at 24, 495 at 32; 4096^2: 940 at 48 rows, 889 at 32, 857 at 64),
+// at least 16 rows and no more than the launch-per-pass rule gives (8192^2: 993 at its 117 rows,
+// 992 at 96, 987 at 160).
+int wtb_flow_rows(int64_t ny, int64_t ld) {
+  const int ctas = flow_resident_ctas(nullptr);
+  const int r0 = wtb_seg_rows(ny, ld);
+  if (ctas <= 0) return r0;
+  const int64_t strips = (ld + kWtbOut - 1) / kWtbOut;
+  const int64_t warps = (int64_t)ctas * kWtbWarps;
+  int64_t rows = ((ny - 2) * strips * 5 + warps * 6 - 1) / (warps * 6);
+  if (rows > r0) rows = r0;
+  return (int)(rows < 16 ? 16 : rows);
+}
+
+// Whether the automatic choice takes the persistent pass: when its tiles number between half and
+// 2.5 times the resident warps.  Measured, FP32 GLUPS over 400 steps with the energy, launch per
+// pass against persistent: 1024^2 201 / 196, 2048^2 484 / 591, 3072^2 697 / 821, 4096^2 820 /
+// 921, 6144^2 921 / 962, 8192^2 969 / 976, 16384^2 1043 / 974 (14000 tiles).
+bool wtb_flow_preferred(int64_t ny, int64_t ld) {
+  const int ctas = flow_resident_ctas(nullptr);
+  if (ctas <= 0) return false;
+  const int64_t warps = (int64_t)ctas * kWtbWarps;
+  const int64_t tiles = wtb_tiles(ny, ld, wtb_flow_rows(ny, ld));
+  return tiles * 2 >= warps && tiles * 2 <= warps * 5;
+}
+
+cudaError_t launch_step_wtb_flow(const StencilGeom& g, const void* hx, const void* hy, void* const u[2], void* const v[2],
+                                 double* energy, const EnergyWs& ews, int rows, int64_t npass, cudaStream_t s,
+                                 bool* ran) {
+  *ran = false;
+  WtbArgs a{};
+  wtb_fill_args(&a, g, hx, hy, u[0], v[0], u[1], v[1], rows);
+  a.ews = ews;
+  a.escale = g.dxdy / (2.0 * g.tau * g.tau);
+  if (!ews.flow || !ews.status || a.ntiles > ews.flow_tiles_cap || npass <= 0 ||
+      npass * a.ntiles >= ((int64_t)1 << 31))
+    return cudaSuccess;
+  const int ctas = flow_resident_ctas(s);
+  if (ctas <= 0) return cudaSuccess;
+  const size_t smem = (size_t)WtbShape<4>::bytes * kWtbWarps * 32;
+  void (*kern)(const WtbArgs, const WtbFlow) = energy ? k_leapfrog_wtb_flow<true> : k_leapfrog_wtb_flow<false>;
+  // every CTA resident at once (a cooperative launch refuses more), no more warps than tasks
+  int64_t grid = ctas;
+  const int64_t need = (npass * a.ntiles + kWtbWarps - 1) / kWtbWarps;
+  if (grid > need) grid = need;
+  WtbFlow f{};
+  char* base = (char*)ews.flow;
+  f.nt4 = (a.ntiles + 3) / 4 * 4;
+  f.next = (unsigned int*)base;
+  f.count = (int*)(base + 8);
+  f.reduced = (int*)(base + 8 + 4 * kFlowSlots);
+  f.done = (int*)(base + 128);
+  f.part = (double*)(base + 128 + ((size_t)f.nt4 * sizeof(int) + 15) / 16 * 16);
+  for (int q = 0; q < 2; ++q) {
+    f.u[q] = (float*)u[q];
+    f.v[q] = (float*)v[q];
+  }
+  f.energy = energy;
+  f.status = ews.status;
+  f.npass = npass;
+  f.limit_ns = 2000000000ull;
+  k_wtb_flow_init<<<64, 256, 0, s>>>(f, a.ntiles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a, (void*)&f};
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(kWtbWarps * 32), args, smem, s);
+  if (e == cudaSuccess) *ran = true;
+  return e;
 }
 
 cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,

@@ -321,7 +321,7 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   if (o.traces && (o.nrec == 0 || !o.rec_idx)) return fail(TSU_EINVAL, "traces need nrec > 0 and rec_idx");
   if (o.ckpt && (o.ckpt_every < 1 || o.ckpt_slots < 1 || !aligned16(o.ckpt)))
     return fail(TSU_EINVAL, "checkpoints need ckpt_every >= 1, ckpt_slots >= 1 and an aligned store");
-  if (o.kernel < 0 || o.kernel > 3) return fail(TSU_EINVAL, "kernel must be 0..3");
+  if (o.kernel < 0 || o.kernel > 4) return fail(TSU_EINVAL, "kernel must be 0..4");
   if (o.rows < 0) return fail(TSU_EINVAL, "rows must be >= 0");
   if (o.tdepth != 0 && o.kernel == 3 && !tsu::tb_supported_depth(o.tdepth))
     return fail(TSU_EINVAL, "kernel 3: tdepth must be 0, 4 or 8");
@@ -351,6 +351,11 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   const bool tb_possible = blocked_base && !o.traces && !o.ckpt;
   if (o.kernel == 2 && !wtb_possible)
     return fail(TSU_EINVAL, "kernel 2 needs FP32, nbuf = 4, a workspace and checkpoints on its launch boundaries");
+  const bool flow_possible = blocked_base && st->form == TSU_FORM_INCREMENT && !o.traces && !o.ckpt &&
+                             (o.tdepth == 0 || o.tdepth == 4);
+  if (o.kernel == 4 && !flow_possible)
+    return fail(TSU_EINVAL, "kernel 4 needs FP32 in the increment form, nbuf = 4, a workspace, depth 4 and no "
+                            "traces or checkpoints");
   if (o.kernel == 3 && !tb_possible)
     return fail(TSU_EINVAL, "kernel 3 needs FP32, nbuf = 4, a workspace and no traces/checkpoints");
   // kernel 2: warp-blocked pass, tdepth steps per launch (default 4); also the automatic choice
@@ -358,7 +363,7 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
   // to 16384^2).  All passes give the same bits, so the choice never changes a result.
   int wrows = o.rows ? (o.rows < 16 ? 16 : o.rows) : tsu::wtb_auto_rows(g->ny, g->ld, wdepth);
   const bool use_wtb = wtb_possible && nsteps >= wdepth && tsu::wtb_supported_depth(wdepth) &&
-                       (o.kernel == 2 || o.kernel == 0);
+                       (o.kernel == 2 || o.kernel == 0 || o.kernel == 4);
   // kernel 3: CTA-blocked pass, on request only
   const int tdepth = o.tdepth ? o.tdepth : 8;
   int tb_rows = o.rows ? o.rows : 128;
@@ -372,6 +377,27 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
     cudaError_t e = tsu::launch_wtb_rec_table(sg, wrows, o.rec_idx, o.nrec, ews, s);
     if (e == cudaSuccess) e = tsu::launch_wtb_trace_edges(sg, o.rec_idx, o.nrec, o.traces, nsteps / wdepth * wdepth, s);
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n receiver table");
+  }
+  if (use_wtb && flow_possible && (o.kernel == 4 || (o.kernel == 0 && tsu::wtb_flow_preferred(g->ny, g->ld)))) {
+    // kernel 4, and the automatic choice for grids of 2K to 8K per side: every pass of the call
+    // in one persistent launch (the same states; 2048^2 591 against 484 GLUPS, 4096^2 921 against
+    // 820, 8192^2 976 against 969)
+    const int64_t npass = nsteps / wdepth;
+    const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
+    void* const uu[2] = {st->buf[st->cur], st->buf[f1]};
+    void* const vv[2] = {st->buf[st->aux], st->buf[f2]};
+    const int frows = o.rows ? wrows : tsu::wtb_flow_rows(g->ny, g->ld);
+    bool ran = false;
+    cudaError_t e = tsu::launch_step_wtb_flow(sg, m->hx, m->hy, uu, vv, o.energy, ews, frows, npass, s, &ran);
+    if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n persistent warp-blocked launch");
+    if (ran) {
+      k = npass * wdepth;
+      if (npass & 1) {
+        st->cur = f1;
+        st->aux = f2;
+      }
+      st->step += k;
+    }
   }
   if (use_wtb) {
     for (; k + wdepth <= nsteps; k += wdepth) {

@@ -38,7 +38,20 @@ struct EnergyWs {
   int4* rec_ent;
   int64_t rec_tiles_cap;
   int32_t rec_ent_cap;
+  void* flow;              // the persistent warp-blocked pass's counters and energy partials, or nullptr
+  int64_t flow_tiles_cap;  // tiles it holds room for
 };
+
+// The persistent warp-blocked pass (k_leapfrog_wtb_flow): energy partials of kFlowSlots passes
+// in flight at once, for grids of at most kFlowMaxTiles tiles.  Its region of the workspace: a
+// 128-byte header (task counter, per-slot tile counts and last reduced pass), a done counter per
+// tile, then [kFlowSlots][4][tiles rounded up to 4] doubles.
+constexpr int kFlowSlots = 8;
+constexpr int64_t kFlowMaxTiles = 32768;
+inline size_t flow_bytes(int64_t tiles) {
+  const size_t t4 = (size_t)(tiles + 3) / 4 * 4;
+  return 128 + (t4 * sizeof(int) + 15) / 16 * 16 + (size_t)kFlowSlots * 4 * t4 * sizeof(double);
+}
 
 // receivers the warp-blocked pass records itself (longer lists go one step per pass)
 constexpr int32_t kWtbMaxReceivers = 2048;
@@ -136,6 +149,17 @@ cudaError_t launch_wtb_trace_edges(const StencilGeom& g, const int64_t* rec_idx,
                                    int64_t nsteps, cudaStream_t s);
 // segment variant: u^{n+t} into seg + (t - 1) seg_stride for t = 1 .. k (elements), v^{n+k} into
 // v_out (increment form; unused in the standard form)
+// rows per tile of the persistent pass (k_leapfrog_wtb_flow) on this device
+int wtb_flow_rows(int64_t ny, int64_t ld);
+// whether the automatic kernel choice takes the persistent pass for this grid
+bool wtb_flow_preferred(int64_t ny, int64_t ld);
+// All nsteps / 4 passes of the warp-blocked pass (increment form, K = 4) in one persistent
+// cooperative launch: pass p reads (u, v)[p & 1] and writes (u, v)[(p + 1) & 1]; energy (K doubles
+// per pass) or nullptr.  *ran = false and nothing enqueued when the device, the workspace or the
+// grid do not allow it.
+cudaError_t launch_step_wtb_flow(const StencilGeom& g, const void* hx, const void* hy, void* const u[2], void* const v[2],
+                                 double* energy, const EnergyWs& ews, int rows, int64_t npass, cudaStream_t s,
+                                 bool* ran);
 cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
                                 const void* p, void* seg, int64_t seg_stride, void* v_out, int rows, cudaStream_t s);
 // batched warp-blocked pass: descriptors of wtb_args_bytes() each, int4 tiles (problem, strip, chunk)
