@@ -148,7 +148,7 @@ typedef struct {
                        receivers and takes checkpoints when ckpt_every is a multiple of tdepth and
                        the call starts at step 1 + j tdepth; 3 takes neither; 4 runs kernel 2's
                        passes (tdepth 4, increment form, no traces or checkpoints) all in one
-                       persistent cooperative launch, a tile's next pass starting once the tiles
+                       persistent launch, a tile's next pass starting once the tiles
                        around it finished the current one (its waits are bounded: TSU_ETIMEOUT
                        through tsu_sync_status); auto picks kernel 4 where it can run and its tiles
                        number between half and 2.5 times the device's resident warps (FP32 grids

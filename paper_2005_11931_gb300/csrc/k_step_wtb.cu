@@ -574,8 +574,8 @@ __global__ void k_trace_edges(const int32_t nx, const int32_t ny, const int64_t 
 // it reads as its halo, and the ones that read the buffer it is about to overwrite.  So a tile's
 // next pass begins while far-away tiles still finish the current one, instead of every SM
 // waiting for the slowest tile at the end of each launch.  Passes alternate between two
-// (u, v) pairs.  Every wait is bounded (TSU_ETIMEOUT in the status word).  No task waits for a
-// later one, and the launch is cooperative (every CTA resident), so every wait ends.  A
+// (u, v) pairs.  Every wait is bounded (TSU_ETIMEOUT in the status word).  A task waits only for
+// tasks handed out before it, which running warps hold, so every wait ends.  A
 // tile's energy sums go to a slot of kFlowSlots per-pass partials.  The task that finishes a
 // pass last sums them in the order wtb_energy uses, so the energies, like the states, equal those
 // of the launch-per-pass path bit for bit.
@@ -877,28 +877,57 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
 }
 
 namespace {
-// resident CTAs of the persistent pass on this device (0: no cooperative launch), once per device
+using FlowKernel = void (*)(const WtbArgs, const WtbFlow);
+// resident CTAs of the persistent passes on this device (0: not available), once per device
 std::atomic<int> g_flow_ctas[64];
-int flow_resident_ctas(cudaStream_t) {
+int flow_resident_ctas() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   int v = g_flow_ctas[dev].load();
   if (v != 0) return v > 0 ? v : 0;
-  int coop = 0, nsm = 0, per_sm = 0;
+  int nsm = 0, per_sm = 0;
   const size_t smem = (size_t)WtbShape<4>::bytes * kWtbWarps * 32;
-  bool ok = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  bool ok = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  const FlowKernel kerns[2] = {k_leapfrog_wtb_flow<false>, k_leapfrog_wtb_flow<true>};
   for (int e = 0; ok && e < 2; ++e) {
-    void (*kern)(const WtbArgs, const WtbFlow) = e ? k_leapfrog_wtb_flow<true> : k_leapfrog_wtb_flow<false>;
     int q = 0;
-    ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
-         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, kern, kWtbWarps * 32, smem) == cudaSuccess && q >= 1;
+    ok = cudaFuncSetAttribute(kerns[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, kerns[e], kWtbWarps * 32, smem) == cudaSuccess && q >= 1;
     per_sm = e ? (q < per_sm ? q : per_sm) : q;
   }
   (void)cudaGetLastError();  // a refused query leaves no error behind
   v = ok ? per_sm * nsm : -1;
   g_flow_ctas[dev].store(v);
   return v > 0 ? v : 0;
+}
+
+// The persistent launch: one CTA per resident slot (more would only wait), its counters reset
+// first.  A plain launch suffices: warps take tasks in order, so every task a warp waits for is
+// held by a warp already running, resident or not.
+cudaError_t flow_launch(const WtbArgs& a, WtbFlow& f, void* region, int64_t npass, FlowKernel kern, cudaStream_t s,
+                        bool* ran) {
+  const int ctas = flow_resident_ctas();
+  if (ctas <= 0 || npass <= 0 || npass * a.ntiles >= ((int64_t)1 << 31)) return cudaSuccess;
+  const size_t smem = (size_t)WtbShape<4>::bytes * kWtbWarps * 32;
+  int64_t grid = ctas;
+  const int64_t need = (npass * a.ntiles + kWtbWarps - 1) / kWtbWarps;
+  if (grid > need) grid = need;
+  char* base = (char*)region;
+  f.nt4 = (a.ntiles + 3) / 4 * 4;
+  f.next = (unsigned int*)base;
+  f.count = (int*)(base + 8);
+  f.reduced = (int*)(base + 8 + 4 * kFlowSlots);
+  f.done = (int*)(base + 128);
+  f.part = (double*)(base + 128 + ((size_t)f.nt4 * sizeof(int) + 15) / 16 * 16);
+  f.npass = npass;
+  f.limit_ns = 2000000000ull;
+  k_wtb_flow_init<<<64, 256, 0, s>>>(f, a.ntiles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kWtbWarps * 32, smem, s>>>(a, f);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) *ran = true;
+  return e;
 }
 }  // namespace
 
@@ -908,7 +937,7 @@ int flow_resident_ctas(cudaStream_t) {
 // at least 16 rows and no more than the launch-per-pass rule gives (8192^2: 993 at its 117 rows,
 // 992 at 96, 987 at 160).
 int wtb_flow_rows(int64_t ny, int64_t ld) {
-  const int ctas = flow_resident_ctas(nullptr);
+  const int ctas = flow_resident_ctas();
   const int r0 = wtb_seg_rows(ny, ld);
   if (ctas <= 0) return r0;
   const int64_t strips = (ld + kWtbOut - 1) / kWtbOut;
@@ -923,7 +952,7 @@ int wtb_flow_rows(int64_t ny, int64_t ld) {
 // pass against persistent: 1024^2 201 / 196, 2048^2 484 / 591, 3072^2 697 / 821, 4096^2 820 /
 // 921, 6144^2 921 / 962, 8192^2 969 / 976, 16384^2 1043 / 974 (14000 tiles).
 bool wtb_flow_preferred(int64_t ny, int64_t ld) {
-  const int ctas = flow_resident_ctas(nullptr);
+  const int ctas = flow_resident_ctas();
   if (ctas <= 0) return false;
   const int64_t warps = (int64_t)ctas * kWtbWarps;
   const int64_t tiles = wtb_tiles(ny, ld, wtb_flow_rows(ny, ld));
@@ -938,40 +967,16 @@ cudaError_t launch_step_wtb_flow(const StencilGeom& g, const void* hx, const voi
   wtb_fill_args(&a, g, hx, hy, u[0], v[0], u[1], v[1], rows);
   a.ews = ews;
   a.escale = g.dxdy / (2.0 * g.tau * g.tau);
-  if (!ews.flow || !ews.status || a.ntiles > ews.flow_tiles_cap || npass <= 0 ||
-      npass * a.ntiles >= ((int64_t)1 << 31))
-    return cudaSuccess;
-  const int ctas = flow_resident_ctas(s);
-  if (ctas <= 0) return cudaSuccess;
-  const size_t smem = (size_t)WtbShape<4>::bytes * kWtbWarps * 32;
-  void (*kern)(const WtbArgs, const WtbFlow) = energy ? k_leapfrog_wtb_flow<true> : k_leapfrog_wtb_flow<false>;
-  // every CTA resident at once (a cooperative launch refuses more), no more warps than tasks
-  int64_t grid = ctas;
-  const int64_t need = (npass * a.ntiles + kWtbWarps - 1) / kWtbWarps;
-  if (grid > need) grid = need;
+  if (!ews.flow || !ews.status || a.ntiles > ews.flow_tiles_cap) return cudaSuccess;
   WtbFlow f{};
-  char* base = (char*)ews.flow;
-  f.nt4 = (a.ntiles + 3) / 4 * 4;
-  f.next = (unsigned int*)base;
-  f.count = (int*)(base + 8);
-  f.reduced = (int*)(base + 8 + 4 * kFlowSlots);
-  f.done = (int*)(base + 128);
-  f.part = (double*)(base + 128 + ((size_t)f.nt4 * sizeof(int) + 15) / 16 * 16);
   for (int q = 0; q < 2; ++q) {
     f.u[q] = (float*)u[q];
     f.v[q] = (float*)v[q];
   }
   f.energy = energy;
   f.status = ews.status;
-  f.npass = npass;
-  f.limit_ns = 2000000000ull;
-  k_wtb_flow_init<<<64, 256, 0, s>>>(f, a.ntiles);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&a, (void*)&f};
-  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(kWtbWarps * 32), args, smem, s);
-  if (e == cudaSuccess) *ran = true;
-  return e;
+  return flow_launch(a, f, ews.flow, npass,
+                     energy ? k_leapfrog_wtb_flow<true> : k_leapfrog_wtb_flow<false>, s, ran);
 }
 
 cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,

@@ -154,9 +154,9 @@ int wtb_flow_rows(int64_t ny, int64_t ld);
 // whether the automatic kernel choice takes the persistent pass for this grid
 bool wtb_flow_preferred(int64_t ny, int64_t ld);
 // All nsteps / 4 passes of the warp-blocked pass (increment form, K = 4) in one persistent
-// cooperative launch: pass p reads (u, v)[p & 1] and writes (u, v)[(p + 1) & 1]; energy (K doubles
-// per pass) or nullptr.  *ran = false and nothing enqueued when the device, the workspace or the
-// grid do not allow it.
+// launch: pass p reads (u, v)[p & 1] and writes (u, v)[(p + 1) & 1]; energy (K doubles per pass)
+// or nullptr.  *ran = false and nothing enqueued when the device, the workspace or the grid do
+// not allow it.
 cudaError_t launch_step_wtb_flow(const StencilGeom& g, const void* hx, const void* hy, void* const u[2], void* const v[2],
                                  double* energy, const EnergyWs& ews, int rows, int64_t npass, cudaStream_t s,
                                  bool* ran);

@@ -7,8 +7,7 @@ tile the states and the energies must agree with kernel 2 bit for bit: with and 
 energy, for odd and even pass counts and with leftover steps, on grids from a few tiles to more
 tiles than one wave.  With its own rows rule (rows = 0) the tiles differ from kernel 2's, so each
 thread's FP32 energy sum covers other nodes and the energies agree to FP32 rounding; the states
-still agree bit for bit.  It is also the
-automatic choice, and must equal the one-step pass.
+still agree bit for bit.  It is also the automatic choice, and must equal the one-step pass.
 """
 import numpy as np
 import pytest
