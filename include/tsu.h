@@ -157,8 +157,9 @@ typedef struct {
                        depend on the choice */
   int32_t rows;     /* rows per CTA (kernels 1, 3) or per warp tile (kernels 2, 4); 0 = auto */
   int32_t tdepth;   /* steps per pass of kernels 2 and 3 (0 = default); leftover steps run one per pass */
-  int32_t reserved; /* 0.  Bit 0 is a test hook of the failure detection: kernel 3 then never
-                       issues one row copy, its bounded wait (20 ms) expires and tsu_sync_status
+  int32_t reserved; /* 0.  Bits 0 and 1 are test hooks of the failure detection: with bit 0
+                       kernel 3 never issues one row copy, with bit 1 kernel 4 never reports
+                       tile 0 done; their bounded waits (20 ms) expire and tsu_sync_status
                        reports TSU_ETIMEOUT; outputs of that call are invalid. */
 } tsu_step_opts;
 

@@ -388,7 +388,8 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
     void* const vv[2] = {st->buf[st->aux], st->buf[f2]};
     const int frows = o.rows ? wrows : tsu::wtb_flow_rows(g->ny, g->ld);
     bool ran = false;
-    cudaError_t e = tsu::launch_step_wtb_flow(sg, m->hx, m->hy, uu, vv, o.energy, ews, frows, npass, s, &ran);
+    cudaError_t e =
+        tsu::launch_step_wtb_flow(sg, m->hx, m->hy, uu, vv, o.energy, ews, frows, npass, o.reserved, s, &ran);
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n persistent warp-blocked launch");
     if (ran) {
       k = npass * wdepth;

@@ -155,10 +155,10 @@ int wtb_flow_rows(int64_t ny, int64_t ld);
 bool wtb_flow_preferred(int64_t ny, int64_t ld);
 // All nsteps / 4 passes of the warp-blocked pass (increment form, K = 4) in one persistent
 // launch: pass p reads (u, v)[p & 1] and writes (u, v)[(p + 1) & 1]; energy (K doubles per pass)
-// or nullptr.  *ran = false and nothing enqueued when the device, the workspace or the grid do
-// not allow it.
+// or nullptr; debug bit 1: the failure-detection test hook (tsu_step_opts.reserved).  *ran =
+// false and nothing enqueued when the device, the workspace or the grid do not allow it.
 cudaError_t launch_step_wtb_flow(const StencilGeom& g, const void* hx, const void* hy, void* const u[2], void* const v[2],
-                                 double* energy, const EnergyWs& ews, int rows, int64_t npass, cudaStream_t s,
+                                 double* energy, const EnergyWs& ews, int rows, int64_t npass, int debug, cudaStream_t s,
                                  bool* ran);
 cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
                                 const void* p, void* seg, int64_t seg_stride, void* v_out, int rows, cudaStream_t s);

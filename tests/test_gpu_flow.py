@@ -72,3 +72,24 @@ def test_persistent_pass_refuses_what_it_cannot_do():
     with pytest.raises(tsu.TsuError) as ex:
         sim.step(8, kernel=4)
     assert ex.value.code == tsu.TSU_EINVAL
+
+
+@pytest.mark.parametrize("energy", [True, False])
+def test_persistent_pass_bounded_wait_reports_timeout_and_context_survives(energy):
+    """Failure detection without a fault: the test hook keeps tile 0 from ever reporting a pass
+    done, so the tasks around it wait until their bounded wait (20 ms) expires.  The status word
+    then says TSU_ETIMEOUT, every warp leaves, and the next call on the same context works and
+    equals the launch-per-pass path."""
+    n, steps = 600, 40
+    sim = tsu.Simulation.create(n, DEPTH, dtype="f32", form=tsu.TSU_FORM_INCREMENT)
+    u0 = torch.from_numpy(inputs.gaussian_hump(n, n, sim.g.ld, 0.3, 0.5, 0.05)).float().cuda()
+    sim.init(u0)
+    e = torch.zeros(steps, dtype=torch.float64, device="cuda") if energy else None
+    sim.step(steps, energy=e, kernel=4, rows=16, debug=2)
+    with pytest.raises(tsu.TsuError) as ei:
+        tsu.tsu_sync_status(sim.ws, sim.ws.numel())
+    assert ei.value.code == tsu.TSU_ETIMEOUT
+    # the status was cleared and the context is usable
+    ua, va, _, _ = run(n, n, steps, 4, energy, 16)
+    ub, vb, _, _ = run(n, n, steps, 2, energy, 16)
+    assert torch.equal(ua, ub) and torch.equal(va, vb)
