@@ -22,7 +22,7 @@ from . import tsu
 
 @dataclass(frozen=True)
 class Choice:
-    kernel: int   # 1 one step per pass, 2 warp-blocked, 3 CTA-blocked
+    kernel: int   # 1 one step per pass, 2 warp-blocked, 3 CTA-blocked, 4 warp-blocked in one persistent launch
     tdepth: int   # steps per pass (0: the kernel's default)
     rows: int     # rows per tile (0: the library's rule)
     graph: bool = False
@@ -62,10 +62,13 @@ def batch_candidates() -> list[Choice]:
 
 
 def step_candidates() -> list[Choice]:
-    """Configurations tried for one problem (FP32, four state buffers, no per-step traces)."""
+    """Configurations tried for one problem (FP32, four state buffers, no per-step traces); the
+    persistent pass (kernel 4) only runs in the increment form, and is skipped otherwise."""
     out = [Choice(1, 0, 0)]
     for rows in (0, 32, 64, 96, 160):
         out.append(Choice(2, 4, rows))
+    for rows in (0, 16, 32, 48, 96):
+        out.append(Choice(4, 0, rows))
     out += [Choice(2, 2, 0), Choice(3, 8, 128), Choice(3, 4, 128)]
     return out
 

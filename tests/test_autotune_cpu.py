@@ -57,4 +57,6 @@ def test_candidates_are_valid_configurations():
     for c in autotune.batch_candidates():
         assert c.kernel in (2, 3) and (c.tdepth in (2, 4) if c.kernel == 2 else c.tdepth in (4, 8))
     for c in autotune.step_candidates():
-        assert c.kernel in (1, 2, 3)
+        assert c.kernel in (1, 2, 3, 4)
+        if c.kernel == 4:  # the persistent pass has one depth (4 steps per pass)
+            assert c.tdepth in (0, 4)
