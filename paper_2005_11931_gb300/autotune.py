@@ -1,5 +1,6 @@
 """Autotuner for the blocked passes: picks, by timing on the caller's own problems, the pass
-(warp-blocked or CTA-blocked), its temporal depth (steps per HBM pass), the rows per tile and, for
+(warp-blocked, launched per pass or all passes in one persistent launch, or CTA-blocked), its
+temporal depth (steps per HBM pass), the rows per tile and, for
 the batched family, how the tiles are packed (tile-table order, rows scaled with each problem's
 size) and whether to launch through one CUDA graph.  Results are cached per problem
 signature (grid shapes, form, GPU name) in a JSON file.
