@@ -3,7 +3,18 @@
 //
 // Every warp works alone on a tile: a strip of 128 columns (one float4 per lane) of which the
 // middle 120 are output (a 4-column halo on each side covers the K-step dependency cone), and a
-// chunk of L output rows it streams down.  Each thread stages its own float4 of every input row
+// chunk of L output rows it streams down.  Strip s reads columns 120 s - x .. 120 s - x + 127 and
+// outputs the middle 120, with x = 8 or 4 per launch.  At x = 8 its reads start on a 32-byte
+// sector (rows of a multiple of 8 floats): a row of a field touches 16 sectors, the one at each
+// side shared with the neighbouring strip, and its writes start 16 bytes into one.  At x = 4 the
+// writes are sector-aligned and a read touches 17 sectors, two of them half used.  Measured on
+// GB300 (FP32 GLUPS, x = 8 against x = 4): the persistent pass 1049 against 969 at 8192^2 (DRAM
+// reads per pass 1.199 against 1.251 GB), 988 against 919-932 at 4096^2; the batched family 974
+// against 929; the receiver-recording pass (2048^2 adjoint workload) 33.9 against 35.1 ms.  The
+// launch-per-pass pass without receivers, its tiles running in lockstep, moves the same DRAM
+// bytes either way, but at x = 8 it makes 47 % more L2 read-sector requests and runs slower:
+// 850 against 963 at 8192^2, 766 against 824 at 4096^2, 989 against 1076 at 16384^2; it keeps
+// x = 4.  Each thread stages its own float4 of every input row
 // (u^n, u^{n-1} or v^n, hx, hy) through a private ring in shared memory with 16-byte cp.async
 // copies, P rows ahead, and reads back only what it copied itself (cp.async.wait_group), so no
 // thread waits for another.  Time level t lags the input by t rows; for each level the thread
@@ -33,6 +44,14 @@ using namespace dev;
 
 constexpr int kWtbWarps = 4;       // warps (independent tiles) per CTA
 constexpr int kWtbOut = 120;       // output columns per strip
+constexpr int kWtbXAligned = 8;    // strip offset x with sector-aligned reads
+constexpr int kWtbXLockstep = 4;   // strip offset x with sector-aligned writes
+// strips over the columns 0 .. ld - 1 (strip s outputs 120 s + 4 - x .. 120 s + 123 - x), and the
+// strip whose output columns hold column i
+__host__ __device__ __forceinline__ int64_t wtb_nstrips(int64_t ld, int x) {
+  return (ld + x - 4 + kWtbOut - 1) / kWtbOut;
+}
+__host__ __device__ __forceinline__ int64_t wtb_strip_of(int64_t i, int x) { return (i + x - 4) / kWtbOut; }
 constexpr int kWtbPre = 2;         // rows in flight ahead of the one being consumed
 // Tiles are sized for one wave of three CTAs per SM (the kernels are bounded to 128 registers so
 // that four fit: 8192^2 801 against 792 GLUPS unbounded at 130 registers, 16384^2 952 against
@@ -61,6 +80,7 @@ struct alignas(16) WtbArgs {
   float* out_a;     // u^{n+K}
   float* out_b;     // u^{n+K-1} (standard) or v^{n+K} (increment)
   int rows;         // output rows per chunk
+  int xoff;         // strip s reads the columns 120 s - xoff .. 120 s - xoff + 127 (4 or 8)
   int64_t nstrips, ntiles;
   double* energy;   // K doubles or nullptr
   EnergyWs ews;
@@ -132,7 +152,8 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   auto slotA = [&](unsigned s, int f) { return ringA + (size_t)(s * 2 + f) * stride; };
   auto slotB = [&](unsigned s, int f) { return ringA + (size_t)(Sh::SA * 2 + s * 2 + f) * stride; };
 
-  const int64_t xs = strip * kWtbOut - 4;
+  // first column read (lane 0, halo); the persistent pass always takes the aligned layout
+  const int64_t xs = strip * kWtbOut - (FLOW ? kWtbXAligned : a.xoff);
   const int64_t c0 = xs + 4 * lane;  // first of this lane's four columns
   const int y0 = 1 + (int)chunk * a.rows;
   const int y1 = tile_ok ? min(y0 + a.rows, a.ny - 1) : y0;
@@ -508,7 +529,7 @@ __global__ void __launch_bounds__(1024) k_wtb_rec_table(const int32_t nx, const 
     if (jj < 1 || jj > ny - 2 || ii < 1 || ii > nx - 2) return -1;
     j = (int)jj;
     i = (int)ii;
-    return wtb_tile_index(ii / kWtbOut, (jj - 1) / rows, nstrips, nchunks);
+    return wtb_tile_index(wtb_strip_of(ii, kWtbXAligned), (jj - 1) / rows, nstrips, nchunks);
   };
   for (int64_t t = threadIdx.x; t <= ntiles; t += blockDim.x) off[t] = 0;
   __syncthreads();
@@ -743,11 +764,11 @@ cudaError_t wtb_launch_batched(const WtbArgs* probs, const int4* tiles, int64_t 
 
 bool wtb_supported_depth(int k) { return k == 2 || k == 4; }
 
-int wtb_strip_width() { return kWtbOut; }
+int64_t wtb_strips(int64_t ld) { return wtb_nstrips(ld, kWtbXAligned); }
 
 cudaError_t launch_wtb_rec_table(const StencilGeom& g, int rows, const int64_t* rec_idx, int32_t nrec,
                                  const EnergyWs& ews, cudaStream_t s) {
-  const int64_t nstrips = (g.ld + kWtbOut - 1) / kWtbOut;
+  const int64_t nstrips = wtb_nstrips(g.ld, kWtbXAligned);  // the layout of the receiver-recording pass
   const int64_t ntiles = nstrips * ((g.ny - 2 + rows - 1) / rows);
   if (!ews.rec_off || ntiles > ews.rec_tiles_cap || nrec > ews.rec_ent_cap || ntiles >= ((int64_t)1 << 31))
     return cudaErrorInvalidValue;
@@ -784,7 +805,8 @@ void wtb_fill_args(void* dst, const StencilGeom& g, const void* hx, const void* 
   a.out_a = (float*)out_a;
   a.out_b = (float*)out_b;
   a.rows = rows;
-  a.nstrips = (g.ld + kWtbOut - 1) / kWtbOut;
+  a.xoff = kWtbXAligned;
+  a.nstrips = wtb_nstrips(g.ld, a.xoff);
   a.ntiles = a.nstrips * ((g.ny - 2 + rows - 1) / rows);
   a.energy = nullptr;
   memcpy(dst, &a, sizeof a);
@@ -803,7 +825,7 @@ cudaError_t launch_step_wtb_batched(int form, int k, const void* probs_dev, size
 }
 
 int64_t wtb_tiles(int64_t ny, int64_t ld, int rows) {
-  return ((ld + 4 + kWtbOut - 1) / kWtbOut) * ((ny - 2 + rows - 1) / rows);
+  return wtb_nstrips(ld, kWtbXAligned) * ((ny - 2 + rows - 1) / rows);  // the larger count of the two layouts
 }
 
 // Rows per chunk.  When one wave of 152 SMs x 3 CTAs x 4 warps holds every tile at no more than
@@ -812,7 +834,7 @@ int64_t wtb_tiles(int64_t ny, int64_t ld, int rows) {
 // register bound lets four reside), for the smallest m whose chunks have at most 160 rows, so
 // that the last wave is full.
 int wtb_seg_rows(int64_t ny, int64_t ld) {
-  const int64_t strips = (ld + 4 + kWtbOut - 1) / kWtbOut;
+  const int64_t strips = wtb_nstrips(ld, kWtbXAligned);
   const int64_t inner = ny - 2;
   const int64_t one_wave = (int64_t)152 * kWtbCtasPerSm * kWtbWarps / strips;
   if (one_wave >= 1) {
@@ -859,8 +881,9 @@ cudaError_t launch_step_wtb(const StencilGeom& g, int form, int k, const void* h
   a.out_a = (float*)out_a;
   a.out_b = (float*)out_b;
   a.rows = rows;
-  // strips cover columns [0, ld): the last output column of strip s is 120 s + 119
-  a.nstrips = (g.ld + kWtbOut - 1) / kWtbOut;
+  // strips cover columns [0, ld); receivers: the layout the receiver table is built for
+  a.xoff = (traces && nrec > 0) ? kWtbXAligned : kWtbXLockstep;
+  a.nstrips = wtb_nstrips(g.ld, a.xoff);
   a.ntiles = a.nstrips * ((g.ny - 2 + rows - 1) / rows);
   a.energy = energy;
   a.ews = ews;
@@ -941,7 +964,7 @@ int wtb_flow_rows(int64_t ny, int64_t ld) {
   const int ctas = flow_resident_ctas();
   const int r0 = wtb_seg_rows(ny, ld);
   if (ctas <= 0) return r0;
-  const int64_t strips = (ld + kWtbOut - 1) / kWtbOut;
+  const int64_t strips = wtb_nstrips(ld, kWtbXAligned);
   const int64_t warps = (int64_t)ctas * kWtbWarps;
   int64_t rows = ((ny - 2) * strips * 5 + warps * 6 - 1) / (warps * 6);
   if (rows > r0) rows = r0;

@@ -800,13 +800,15 @@ static int batch_layout(int32_t nprob, const tsu_problem* probs, const tsu_batch
   if (kern == 3 && !tsu::tb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 3: tdepth must be 4 or 8");
   if (kern == 2 && !tsu::wtb_supported_depth(k)) return fail(TSU_EINVAL, "kernel 2: tdepth must be 2 or 4");
   if (opts && (opts->order < 0 || opts->order > 2)) return fail(TSU_EINVAL, "order must be 0, 1 or 2");
-  const int W = kern == 2 ? tsu::wtb_strip_width() : tsu::tb_strip_width(k);
   for (int i = 0; i < nprob; ++i) TRY(check_grid(&probs[i].grid));
+  auto strips = [&](int64_t ld) {
+    return kern == 2 ? tsu::wtb_strips(ld) : (ld + tsu::tb_strip_width(k) - 1) / tsu::tb_strip_width(k);
+  };
   auto tiles_at = [&](int r) {
     int64_t t = 0;
     for (int i = 0; i < nprob; ++i) {
       const int ri = batch_rows_of(opts, i, r);
-      t += ((probs[i].grid.ld + W - 1) / W) * ((probs[i].grid.ny - 2 + ri - 1) / ri);
+      t += strips(probs[i].grid.ld) * ((probs[i].grid.ny - 2 + ri - 1) / ri);
     }
     return t;
   };
@@ -856,7 +858,6 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
     if (p.nsteps < 0) return fail(TSU_EINVAL, "problem %d: nsteps < 0", i);
   }
   const int kern = batch_kernel(opts);
-  const int W = kern == 2 ? tsu::wtb_strip_width() : tsu::tb_strip_width(k);
   const size_t ab = kern == 2 ? tsu::wtb_args_bytes() : tsu::tb_args_bytes();
   // problems in decreasing order of blocked rounds: round r launches a prefix of the tile table,
   // the tiles of the problems that still have a round to go.  Problems with equal round counts
@@ -875,7 +876,10 @@ int tsu_batch_run(int32_t nprob, const tsu_problem* probs, const tsu_batch_opts*
     tiles.push_back(c);
     tiles.push_back(0);
   };
-  auto strips_of = [&](int i) { return (int)((probs[i].grid.ld + W - 1) / W); };
+  auto strips_of = [&](int i) {
+    const int64_t ld = probs[i].grid.ld;
+    return (int)(kern == 2 ? tsu::wtb_strips(ld) : (ld + tsu::tb_strip_width(k) - 1) / tsu::tb_strip_width(k));
+  };
   auto chunks_of = [&](int i) {
     const int ri = batch_rows_of(opts, i, rows);
     return (int)((probs[i].grid.ny - 2 + ri - 1) / ri);

@@ -162,8 +162,9 @@ cudaError_t launch_step_wtb_flow(const StencilGeom& g, const void* hx, const voi
                                  bool* ran);
 cudaError_t launch_step_wtb_seg(const StencilGeom& g, int form, int k, const void* hx, const void* hy, const void* u,
                                 const void* p, void* seg, int64_t seg_stride, void* v_out, int rows, cudaStream_t s);
-// batched warp-blocked pass: descriptors of wtb_args_bytes() each, int4 tiles (problem, strip, chunk)
-int wtb_strip_width();
+// batched warp-blocked pass: descriptors of wtb_args_bytes() each, int4 tiles (problem, strip, chunk);
+// wtb_strips(ld) strips per row of tiles
+int64_t wtb_strips(int64_t ld);
 size_t wtb_args_bytes();
 void wtb_fill_args(void* dst, const StencilGeom& g, const void* hx, const void* hy, const void* u, const void* p,
                    void* out_a, void* out_b, int rows);

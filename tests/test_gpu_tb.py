@@ -154,12 +154,14 @@ def _trace_run(kernel, n=1001, ny=777, S=61, every=8, rec=None, energy=True, for
 @pytest.mark.parametrize("form", [tsu.TSU_FORM_INCREMENT, tsu.TSU_FORM_STANDARD])
 @pytest.mark.parametrize("energy", [True, False])
 def test_wtb_records_traces_and_checkpoints_like_one_step_passes(form, energy):
-    """Receivers on and next to strip edges (columns 119/120/121, 239/240), chunk edges, the
+    """Receivers on and next to strip edges (columns 3/4, 115/116, 235/236; and 119/120/121,
+    239/240), chunk edges, the
     corners, duplicates and boundary nodes; checkpoints every 8 steps.  The warp-blocked pass
     records them itself and copies checkpoints between launches: traces, checkpoints and states
     equal the one-step passes' bit for bit."""
     rng = np.random.default_rng(12)
-    rec = [[c, r] for c in (1, 2, 119, 120, 121, 239, 240, 998) for r in (1, 2, 96, 97, 160, 161, 500, 775)]
+    rec = [[c, r] for c in (1, 2, 3, 4, 115, 116, 119, 120, 121, 235, 236, 239, 240, 998)
+           for r in (1, 2, 96, 97, 160, 161, 500, 775)]
     rec += [[120, 97], [0, 300], [500, 0], [999, 776]] + [[int(x), int(y)] for x, y in zip(
         rng.integers(1, 999, 60), rng.integers(1, 775, 60))]
     rec = np.array(rec)
