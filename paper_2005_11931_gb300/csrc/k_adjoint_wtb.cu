@@ -6,7 +6,8 @@
 //   dJ/dhx_ij  += -cx (lam^{m+1}_{i+1} - lam^{m+1}_i)(u^m_{i+1} - u^m_i)   (hy likewise)
 // (level 0 = (lam^{n+1}, mu^{n+1}) is the input).  Every warp owns a tile: 128
 // columns (one float4 per lane; the middle 120 are output, a 4-column halo covers the K-step
-// cone) by a chunk of rows it streams down; level k lags the input row by k rows.  Each thread
+// cone; strip s reads the columns 120 s - 8 .. 120 s + 119, so each row read starts on a 32-byte
+// sector) by a chunk of rows it streams down; level k lags the input row by k rows.  Each thread
 // copies its own float4 of every input row through a private cp.async ring: lam^{n+1},
 // mu^{n+1}, hx and hy at the input row (the faces one row behind), u^{n-f} f rows behind, where
 // level f + 1 needs it; so nothing in the row loop waits on memory.  The ring keeps the previous
@@ -31,6 +32,8 @@ using namespace dev;
 
 constexpr int kAwWarps = 4;
 constexpr int kAwOut = 120;
+// strips over the columns 0 .. ld - 1: strip s outputs 120 s - 4 .. 120 s + 115
+__host__ __device__ __forceinline__ int64_t aw_nstrips(int64_t ld) { return (ld + 4 + kAwOut - 1) / kAwOut; }
 constexpr int kAwPre = 2;
 constexpr int kAwRing = 4;  // slots per field: the previous row, the current one, 2 in flight
 // resident CTAs per SM: the launch bound the kernel is compiled for (K = 2 at <= 168 registers per
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(kAwWarps * 32, aw_ctas_per_sm<K>()) k_adjoint_
   const int64_t tile = (int64_t)blockIdx.x * kAwWarps + warp;
   const bool tile_ok = tile < a.ntiles;
   const int64_t strip = tile_ok ? tile % a.nstrips : 0, chunk = tile_ok ? tile / a.nstrips : 0;
-  const int64_t xs = strip * kAwOut - 4;
+  const int64_t xs = strip * kAwOut - 8;  // first column read (lane 0, halo)
   const int64_t c0 = xs + 4 * lane;
   const int y0 = 1 + (int)chunk * a.rows;
   const int y1 = tile_ok ? min(y0 + a.rows, a.ny - 1) : y0;
@@ -325,8 +328,8 @@ __global__ void __launch_bounds__(kAwWarps * 32, aw_ctas_per_sm<K>()) k_adjoint_
   cp_wait<0>();
 }
 
-// Receivers of the K-step pass: for every tile whose extended region (columns 120 s - 4 ..
-// 120 s + 123, rows y0 - (K - 1) .. y1 + (K - 2), where the levels before the last need the
+// Receivers of the K-step pass: for every tile whose extended region (columns 120 s - 8 ..
+// 120 s + 119, rows y0 - (K - 1) .. y1 + (K - 2), where the levels before the last need the
 // values) holds a receiver's interior node, one entry (row, col, r, 0), tiles in order,
 // receivers in order within a tile (at most 4 per receiver).  One thread; nrec is small.
 __global__ void k_rec_tiles(const int32_t nx, const int32_t ny, const int64_t ld, const int64_t* idx,
@@ -341,9 +344,9 @@ __global__ void k_rec_tiles(const int32_t nx, const int32_t ny, const int64_t ld
       if (q < 0 || q >= (int64_t)ny * ld) continue;
       const int64_t j = q / ld, i = q - j * ld;
       if (!(i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2)) continue;
-      const int64_t s_lo = (i + 4) / kAwOut - 1, c_lo = (j - 1) / rows - 1;
+      const int64_t s_lo = (i + 8) / kAwOut - 1, c_lo = (j - 1) / rows - 1;
       for (int64_t sc = s_lo; sc <= s_lo + 2; ++sc) {
-        if (sc < 0 || sc >= nstrips || i < sc * kAwOut - 4 || i >= sc * kAwOut + 124) continue;
+        if (sc < 0 || sc >= nstrips || i < sc * kAwOut - 8 || i >= sc * kAwOut + 120) continue;
         for (int64_t ch = c_lo; ch <= c_lo + 2; ++ch) {
           if (ch < 0 || ch >= nchunks) continue;
           const int64_t y0 = 1 + ch * rows, y1 = (y0 + rows < ny - 1) ? y0 + rows : ny - 1;
@@ -376,7 +379,7 @@ cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void
 // of 4 warps), between 16 (halo rows cost (rows + 2K) / rows) and 64.  Tiles of a second, partly
 // filled wave would leave most SMs idle while it runs.
 int adjoint_wtb_rows(int k, int64_t ny, int64_t ld) {
-  const int64_t strips = (ld + kAwOut - 1) / kAwOut;
+  const int64_t strips = aw_nstrips(ld);
   const int64_t wave_tiles = (int64_t)152 * (k == 2 ? aw_ctas_per_sm<2>() : aw_ctas_per_sm<4>()) * kAwWarps;
   const int64_t chunks = wave_tiles / strips;
   if (chunks < 1) return 64;
@@ -385,12 +388,12 @@ int adjoint_wtb_rows(int k, int64_t ny, int64_t ld) {
 }
 
 int64_t adjoint_wtb_tiles(int64_t ny, int64_t ld, int rows) {
-  return ((ld + kAwOut - 1) / kAwOut) * ((ny - 2 + rows - 1) / rows);
+  return aw_nstrips(ld) * ((ny - 2 + rows - 1) / rows);
 }
 
 cudaError_t launch_rec_tiles(const StencilGeom& g, int k, const int64_t* idx, int32_t nrec, int rows, int* off,
                              int4* ent, cudaStream_t s) {
-  const int64_t nstrips = (g.ld + kAwOut - 1) / kAwOut;
+  const int64_t nstrips = aw_nstrips(g.ld);
   k_rec_tiles<<<1, 32, 0, s>>>(g.nx, g.ny, g.ld, idx, nrec, rows, k - 1, k - 2, nstrips,
                                adjoint_wtb_tiles(g.ny, g.ld, rows), off, ent);
   return cudaGetLastError();
@@ -420,7 +423,7 @@ cudaError_t aw_launch(const StencilGeom& g, int rows, const void* hx, const void
   a.gx = (float*)gx;
   a.gy = (float*)gy;
   a.rows = rows;
-  a.nstrips = (g.ld + kAwOut - 1) / kAwOut;
+  a.nstrips = aw_nstrips(g.ld);
   a.ntiles = adjoint_wtb_tiles(g.ny, g.ld, rows);
   a.rec_off = rec_off;
   a.rec = rec;

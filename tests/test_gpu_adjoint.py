@@ -94,7 +94,7 @@ def test_fp32_adjoint_matches_oracle_across_tiles(form, every, S):
     rng = np.random.default_rng(23)
     u0 = inputs.random_field(nx, ny, None, rng)
     u1 = inputs.random_field(nx, ny, None, rng)
-    cols = [1, 3, 4, 116, 119, 120, 123, 124, 236, 239, 240, 243, 299]
+    cols = [1, 3, 4, 111, 112, 115, 116, 119, 120, 123, 124, 231, 232, 235, 236, 239, 240, 243, 299]
     rows = [1, 2, 3, 13, 14, 15, 16, 17, 18, 19, 20, 32, 33, 144, 145, 147, 148]
     rec = np.array([[cols[k % len(cols)], rows[k % len(rows)]] for k in range(3 * len(cols))]
                    + [[120, 17], [0, 40], [150, 149]])
@@ -320,7 +320,22 @@ def test_adjoint_streams_released_when_threads_exit():
     rec = receivers(nx, ny)
     dtr = rng.standard_normal((S, len(rec)))
     gpu_forward_adjoint(nx, ny, DEPTH, u0, u1, S, rec, dtr, "f32", tsu.TSU_FORM_INCREMENT, every)
-    base = tsu.tsu_aux_streams()
+
+    def stable():
+        # threads of earlier tests may still be running their thread-local destructors: take the
+        # count once it has not changed for half a second
+        deadline = time.monotonic() + 10.0
+        last, since = tsu.tsu_aux_streams(), time.monotonic()
+        while time.monotonic() < deadline:
+            time.sleep(0.01)
+            v = tsu.tsu_aux_streams()
+            if v != last:
+                last, since = v, time.monotonic()
+            elif time.monotonic() - since > 0.5:
+                break
+        return last
+
+    base = stable()
     assert base >= 1  # this thread's stream
     seen, errs = [], []
 
