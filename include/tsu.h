@@ -151,8 +151,8 @@ typedef struct {
                        persistent launch, a tile's next pass starting once the tiles
                        around it finished the current one (its waits are bounded: TSU_ETIMEOUT
                        through tsu_sync_status); auto picks kernel 4 where it can run and its tiles
-                       number between half and 2.5 times the device's resident warps (FP32 grids
-                       of about 2K to 8K per side), else kernel 2 (tdepth 4) whenever it can.  All
+                       number between half and 6 times the device's resident warps (FP32 grids
+                       of about 2K to 12K per side), else kernel 2 (tdepth 4) whenever it can.  All
                        kernels round every operation the same way, so the FP32 states do not
                        depend on the choice */
   int32_t rows;     /* rows per CTA (kernels 1, 3) or per warp tile (kernels 2, 4); 0 = auto */

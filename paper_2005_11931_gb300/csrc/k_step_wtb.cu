@@ -958,11 +958,12 @@ cudaError_t flow_launch(const WtbArgs& a, WtbFlow& f, void* region, int64_t npas
 // Rows per tile of the persistent pass: tiles about 1.2 x the resident warps, so that every warp
 // has a tile of each pass and finishing tiles are followed at once by the next pass's (2048^2:
 // 610 GLUPS at 16 rows, 544 at 24, 495 at 32; 4096^2: 940 at 48 rows, 889 at 32, 857 at 64),
-// at least 16 rows and no more than the launch-per-pass rule gives (8192^2: 993 at its 117 rows,
-// 992 at 96, 987 at 160).
+// at least 16 rows and no more than the launch-per-pass rule gives, nor 96 (with sector-aligned
+// reads, 8192^2: 1040 at 96 rows, 1044 at 80, 1030 at the launch-per-pass rule's 117, 1004 at
+// 140; 12288^2: 1042 at 96, 1002 at the rule's).
 int wtb_flow_rows(int64_t ny, int64_t ld) {
   const int ctas = flow_resident_ctas();
-  const int r0 = wtb_seg_rows(ny, ld);
+  const int r0 = wtb_seg_rows(ny, ld) < 96 ? wtb_seg_rows(ny, ld) : 96;
   if (ctas <= 0) return r0;
   const int64_t strips = wtb_nstrips(ld, kWtbXAligned);
   const int64_t warps = (int64_t)ctas * kWtbWarps;
@@ -972,15 +973,17 @@ int wtb_flow_rows(int64_t ny, int64_t ld) {
 }
 
 // Whether the automatic choice takes the persistent pass: when its tiles number between half and
-// 2.5 times the resident warps.  Measured, FP32 GLUPS over 400 steps with the energy, launch per
-// pass against persistent: 1024^2 201 / 196, 2048^2 484 / 591, 3072^2 697 / 821, 4096^2 820 /
-// 921, 6144^2 921 / 962, 8192^2 969 / 976, 16384^2 1043 / 974 (14000 tiles).
+// 6 times the resident warps.  Measured, FP32 GLUPS with the energy, launch per pass against
+// persistent, with the persistent pass's rows rule and sector-aligned reads: 6144^2 914 / 1037,
+// 8192^2 963 / 1030-1052, 12288^2 1013 / 1042 (13184 tiles of 96 rows, 5.4 times the warps),
+// 16384^2 997 / 996 (23427 tiles); earlier, with unaligned reads, 1024^2 201 / 196, 2048^2 484 /
+// 591, 3072^2 697 / 821, 4096^2 820 / 921.
 bool wtb_flow_preferred(int64_t ny, int64_t ld) {
   const int ctas = flow_resident_ctas();
   if (ctas <= 0) return false;
   const int64_t warps = (int64_t)ctas * kWtbWarps;
   const int64_t tiles = wtb_tiles(ny, ld, wtb_flow_rows(ny, ld));
-  return tiles * 2 >= warps && tiles * 2 <= warps * 5;
+  return tiles * 2 >= warps && tiles <= warps * 6;
 }
 
 cudaError_t launch_step_wtb_flow(const StencilGeom& g, const void* hx, const void* hy, void* const u[2], void* const v[2],

@@ -379,9 +379,9 @@ int tsu_step_n(const tsu_grid* g, int dtype, double tau, const tsu_medium* m, ts
     if (e != cudaSuccess) return cuda_fail(e, "tsu_step_n receiver table");
   }
   if (use_wtb && flow_possible && (o.kernel == 4 || (o.kernel == 0 && tsu::wtb_flow_preferred(g->ny, g->ld)))) {
-    // kernel 4, and the automatic choice for grids of 2K to 8K per side: every pass of the call
-    // in one persistent launch (the same states; 2048^2 591 against 484 GLUPS, 4096^2 921 against
-    // 820, 8192^2 976 against 969)
+    // kernel 4, and the automatic choice for grids of 2K to 12K per side: every pass of the call
+    // in one persistent launch (the same states; 2048^2 611 against 481 GLUPS, 4096^2 988 against
+    // 826, 8192^2 1030-1052 against 963)
     const int64_t npass = nsteps / wdepth;
     const int f1 = scratch_index(st, -1), f2 = scratch_index(st, f1);
     void* const uu[2] = {st->buf[st->cur], st->buf[f1]};
