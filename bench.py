@@ -34,10 +34,10 @@ TRAFFIC = {
     # 4 steps per pass, 117 rows per chunk, two rows per loop trip, outer strips first),
     # dram__bytes_read.sum + dram__bytes_write.sum
     ("k_leapfrog_wtb", "increment", 8192, 4): 1.665618e9,
-    # profiles/k_leapfrog_wtb_flow_8192_2048.md: the persistent pass (sector-aligned reads) at the
-    # bench's launch shape, one launch of 10 passes (41 steps),
+    # profiles/k_leapfrog_wtb_flow_8192_2048.md: the persistent pass (sector-aligned reads, 96 rows
+    # per tile) at the bench's launch shape, one launch of 10 passes (41 steps),
     # dram__bytes_read.sum + dram__bytes_write.sum / 10
-    ("k_leapfrog_wtb_flow", "increment", 8192, 4): 1.7418607e9,
+    ("k_leapfrog_wtb_flow", "increment", 8192, 4): 1.7419624e9,
 }
 UNIT = "GLUPS"
 ORACLE_SAMPLE_STEPS = 32  # leapfrog steps of each timed oracle sample (depth evaluation included once)
