@@ -266,8 +266,16 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
   const bool interior_strip = (xs >= 1) && (xs + 127 <= (int64_t)a.nx - 2);
   // RECNOW: the iteration's rows (r_in - K .. r_in) reach the tile's receiver rows; iterations
   // that do not run a copy of the row code without any receiver test
-  auto iterate = [&](auto edge_tag, auto rec_tag, const int it) {
-    constexpr bool EDGE = decltype(edge_tag)::value;
+  // MODE 0: every level's row is an output row of an interior strip; 1 (RMASK, the segment pass
+  // only): rows of an interior strip inside the grid, some of them outside the tile's output
+  // rows (the tile's first 2K and last K - 1 iterations), whose results are only kept from
+  // stores and the energy; 2 (EDGE): everything else, masked node by node.  In the other passes
+  // a third copy of the row code (twice over with two rows per loop trip) cost more than it
+  // saved: the persistent pass ran 449 against 611 GLUPS at 2048^2, 890 against 988 at 4096^2;
+  // the segment pass gains (the 2048^2 adjoint 68.6 against 70.4 ms).
+  auto iterate = [&](auto mode_tag, auto rec_tag, const int it) {
+    constexpr bool EDGE = decltype(mode_tag)::value == 2;
+    constexpr bool RMASK = decltype(mode_tag)::value == 1;
     constexpr bool RECNOW = REC && decltype(rec_tag)::value;
     const int r_in = r_first + it;
     const unsigned sa = (unsigned)it & (Sh::SA - 1);
@@ -314,7 +322,7 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
       const float2 F01 = upk(fr01), F23 = upk(fr23);
       const float fl = __shfl_up_sync(0xffffffffu, F23.y, 1);
       const bool row_in = !EDGE || (rt >= 1 && rt <= a.ny - 2);
-      const bool row_out = !EDGE || (rt >= y0 && rt < y1);
+      const bool row_out = !(EDGE || RMASK) || (rt >= y0 && rt < y1);
       P4 bv, un, fx, gy;
       fx.p[0] = pk(__fsub_rn(F01.x, fl), __fsub_rn(F01.y, F01.x));
       fx.p[1] = pk(__fsub_rn(F23.x, F01.y), __fsub_rn(F23.y, F23.x));
@@ -361,7 +369,11 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
             erow += (n0 && o ? ef.x : 0.f) + (n1 && o ? ef.y : 0.f);
           }
         } else if constexpr (ENERGY) {
-          erow += ef.x + ef.y;  // lanes that are not output are masked once at the end
+          // lanes that are not output are masked once at the end
+          if constexpr (RMASK)
+            erow += row_out ? ef.x + ef.y : 0.f;
+          else
+            erow += ef.x + ef.y;
         }
       }
       if constexpr (ENERGY) {
@@ -398,17 +410,30 @@ __device__ __forceinline__ void wtb_body(const WtbArgs& a, const bool tile_ok, c
     if (it + kWtbPre < nit) issue(r_in + kWtbPre);
     cp_commit();
     cp_wait<kWtbPre>();  // this thread's copies of row r_in have landed
+    // rows r_in - K .. r_in - 1 of the levels: all output rows, or all inside the grid.  Levels
+    // whose rows lie above the tile's first input row (the first K iterations) read ring slots of
+    // the tile before; those rows are outside the dependency cone of the output rows and feed
+    // nothing that is kept.
     const bool edge = !(interior_strip && r_in - K >= y0 && r_in - 1 < y1);
+    using M0 = std::integral_constant<int, 0>;
+    using M1 = std::integral_constant<int, 1>;
+    using M2 = std::integral_constant<int, 2>;
     if (REC && r_in >= rec_rmin && r_in - K <= rec_rmax) {
       if (edge)
-        iterate(std::integral_constant<bool, true>(), std::integral_constant<bool, true>(), it);
+        iterate(M2(), std::integral_constant<bool, true>(), it);
       else
-        iterate(std::integral_constant<bool, false>(), std::integral_constant<bool, true>(), it);
+        iterate(M0(), std::integral_constant<bool, true>(), it);
     } else {
+      if constexpr (ALL && !REC) {
+        if (edge && interior_strip && r_in - K >= 1 && r_in - 1 <= a.ny - 2) {
+          iterate(M1(), std::integral_constant<bool, false>(), it);
+          return;
+        }
+      }
       if (edge)
-        iterate(std::integral_constant<bool, true>(), std::integral_constant<bool, false>(), it);
+        iterate(M2(), std::integral_constant<bool, false>(), it);
       else
-        iterate(std::integral_constant<bool, false>(), std::integral_constant<bool, false>(), it);
+        iterate(M0(), std::integral_constant<bool, false>(), it);
     }
   };
   int it = 0;
