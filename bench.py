@@ -159,7 +159,7 @@ class ClockSampler:
 
 
 # -----------------------------------------------------------------------------------------------
-# CPU oracle leg (the reference arm of this build and the cpu_baseline object)
+# CPU oracle leg (the `--impl reference` arm and the cpu_baseline object)
 # -----------------------------------------------------------------------------------------------
 def oracle_sample(n: int, steps_sample: int, threads: int = 0):
     """Time the FP64 oracle, as it stands, on the workload's full grid (on every core of the
