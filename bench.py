@@ -161,11 +161,12 @@ class ClockSampler:
 # -----------------------------------------------------------------------------------------------
 # CPU oracle leg (the `--impl reference` arm and the cpu_baseline object)
 # -----------------------------------------------------------------------------------------------
-def oracle_sample(n: int, steps_sample: int, threads: int = 0):
+def oracle_sample(n: int, steps_sample: int, threads: int = 0, total_steps: int = 0):
     """Time the FP64 oracle, as it stands, on the workload's full grid (on every core of the
     process, or on `threads` threads): the depth evaluation once and `steps_sample` steps (start,
     leapfrog steps with the energy of every step), extrapolated to the whole workload's
-    5000 steps, so that the depth weighs what it weighs in the GPU bench step."""
+    `total_steps` steps (default: the workload's 5000), so that the depth weighs what it weighs in
+    the GPU bench step."""
     import oracle
     from paper_2005_11931_gb300 import inputs
 
@@ -180,7 +181,7 @@ def oracle_sample(n: int, steps_sample: int, threads: int = 0):
     tau = inputs.CFL * g.dx / max(ext[1], ext[3]) ** 0.5
     oracle.forward(g, tau, hx, hy, u0, None, steps_sample, want_energy=True)
     t2 = time.perf_counter()
-    S = p.steps
+    S = total_steps or p.steps
     est = (t1 - t0) + (t2 - t1) * S / steps_sample
     return dict(value=(n - 2) ** 2 * S / est / 1e9, unit=UNIT, cores=threads, kind="oracle",
                 sample=f"FP64 oracle, {n}x{n} point workload: depth ({t1 - t0:.2f} s) + Taylor start + "
@@ -228,10 +229,10 @@ def run_reference(args):
     # line's cpu_baseline)
     steps_sample = ORACLE_SAMPLE_STEPS
     for _ in range(args.warmup):
-        oracle_sample(args.n, 2)
+        oracle_sample(args.n, 2, total_steps=args.nsteps)
     vals, secs = [], 0.0
     for _ in range(args.steps):
-        r = oracle_sample(args.n, steps_sample)
+        r = oracle_sample(args.n, steps_sample, total_steps=args.nsteps)
         vals.append(r["value"])
         secs += r["seconds"]
     v = statistics.mean(vals)
@@ -403,9 +404,9 @@ def run_gpu(args):
         extras["adjoint"] = measure_adjoint()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        r = oracle_sample(p.n, ORACLE_SAMPLE_STEPS)
+        r = oracle_sample(p.n, ORACLE_SAMPLE_STEPS, total_steps=args.nsteps)
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        r1 = oracle_sample(p.n, 8, threads=1)
+        r1 = oracle_sample(p.n, 8, threads=1, total_steps=args.nsteps)
         cpu["single_thread"] = {k: r1[k] for k in ("value", "unit", "cores", "sample")}
         if "implicit_table1" in extras:
             cpu["implicit_table1"] = oracle_implicit_sample()
